@@ -1,0 +1,295 @@
+"""FP64 CPU oracle for the p-norm (x,max) semiring product (arXiv 1511.05690).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the GPU library (``paper_1511_05690_gb300``)
+and never imports it.
+
+The arithmetic lives in ``oracle.c`` (plain loops, FP64, OpenMP over output
+rows); this module only loads it and marshals numpy arrays.  Functions and the
+passages they follow:
+
+* ``maxprod`` / ``maxprod_f32`` -- Alg. 2 (naive (x,max) product).
+* ``minplus`` / ``minplus_f32`` -- Alg. 1 (naive (+,min) product).
+* ``ringprod`` -- Alg. 3 (naive (x,+) product).
+* ``row_scales`` / ``col_scales`` -- the scaled H' of Sec. 2.1 (power-of-two
+  reading, see ``oracle.c``).
+* ``psums`` -- Alg. 5 first loop: S^(p) = (A'^p)(B'^p) for every p in P.
+* ``estimate`` -- Alg. 5 second loop with the plain
+  estimateMaxFromNormPowerSequence (largest stable p).
+* ``pnorm`` -- the two together.
+* ``entries`` -- exact max and p-sums at selected entries only.
+* ``floyd_warshall`` -- exact APSP (the comparison of Sec. 3.1).
+* ``apsp_pnorm`` -- Sec. 2.2: exp(-W), repeated p-norm squaring, -log.
+* ``pnorm_grad`` -- gradient of the p-norm product at fixed p per entry.
+* ``default_tau`` -- the stability threshold reading (Sec. 2.1, tau).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# compute-mode numbers used by default_tau (same meaning as the library's
+# pn_compute enum, written out here independently).
+F32_EXACT, TF32, BF16, F16, E4M3 = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so with gcc (OpenMP if available)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-ffp-contract=off", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_SO)
+            i64, dbl, vp, ci = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+            for name in ("orc_maxprod_f64", "orc_maxprod_f32", "orc_minplus_f64",
+                         "orc_minplus_f32", "orc_ringprod_f64"):
+                getattr(lib, name).argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64]
+                getattr(lib, name).restype = None
+            lib.orc_row_scales.argtypes = [i64, i64, vp, i64, ci, vp]
+            lib.orc_col_scales.argtypes = [i64, i64, vp, i64, ci, vp]
+            lib.orc_psums.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
+            lib.orc_estimate.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, vp, vp, vp]
+            lib.orc_pnorm.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci,
+                                      vp, vp, vp, vp, vp, vp]
+            lib.orc_pnorm.restype = ci
+            lib.orc_entries.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp,
+                                        i64, vp, vp, vp, vp]
+            lib.orc_floyd_warshall.argtypes = [i64, vp, i64]
+            lib.orc_apsp_pnorm.argtypes = [i64, vp, i64, ci, ci, vp, dbl, ci, ci, vp, i64, vp]
+            lib.orc_apsp_pnorm.restype = ci
+            lib.orc_pnorm_grad.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_row_logloss.argtypes = [i64, i64, vp, vp, vp]
+            lib.orc_row_logloss.restype = dbl
+            lib.orc_col_logloss.argtypes = [i64, i64, vp, vp, vp]
+            lib.orc_col_logloss.restype = dbl
+            lib.orc_default_tau.argtypes = [i64, ci]
+            lib.orc_default_tau.restype = dbl
+            lib.orc_num_threads.restype = ci
+            lib.orc_set_num_threads.argtypes = [ci]
+            _lib = lib
+    return _lib
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _f32(x):
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _plog(p_log2):
+    return np.ascontiguousarray(p_log2, dtype=np.int32)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    _load().orc_set_num_threads(int(n))
+
+
+def default_tau(K: int, compute: int) -> float:
+    return float(_load().orc_default_tau(int(K), int(compute)))
+
+
+def _prod(fn, A, B, conv, out_dtype):
+    A, B = conv(A), conv(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.empty((M, N), dtype=out_dtype)
+    fn(M, N, K, _p(A), K, _p(B), N, _p(C), N)
+    return C
+
+
+def maxprod(A, B):
+    """Alg. 2 in FP64: C_ij = max_k a_ik b_kj."""
+    return _prod(_load().orc_maxprod_f64, A, B, _f64, np.float64)
+
+
+def maxprod_f32(A, B):
+    """Alg. 2 with FP32 products (bit-exact reference for the GPU exact kernel)."""
+    return _prod(_load().orc_maxprod_f32, A, B, _f32, np.float32)
+
+
+def minplus(A, B):
+    """Alg. 1 in FP64: C_ij = min_k a_ik + b_kj."""
+    return _prod(_load().orc_minplus_f64, A, B, _f64, np.float64)
+
+
+def minplus_f32(A, B):
+    return _prod(_load().orc_minplus_f32, A, B, _f32, np.float32)
+
+
+def ringprod(A, B):
+    """Alg. 3 in FP64: C_ij = sum_k a_ik b_kj (plain triple loop)."""
+    return _prod(_load().orc_ringprod_f64, A, B, _f64, np.float64)
+
+
+def row_scales(A, mode: int = 2):
+    A = _f64(A)
+    M, K = A.shape
+    r = np.empty(M, dtype=np.float64)
+    _load().orc_row_scales(M, K, _p(A), K, int(mode), _p(r))
+    return r
+
+
+def col_scales(B, mode: int = 2):
+    B = _f64(B)
+    K, N = B.shape
+    c = np.empty(N, dtype=np.float64)
+    _load().orc_col_scales(K, N, _p(B), N, int(mode), _p(c))
+    return c
+
+
+def psums(A, B, p_log2, r=None, c=None, scaling: int = 2):
+    """S[q] = sum_k (a_ik/r_i * b_kj/c_j)^(2^p_log2[q]); shape (n_p, M, N)."""
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    _, N = B.shape
+    r = row_scales(A, scaling) if r is None else _f64(r)
+    c = col_scales(B, scaling) if c is None else _f64(c)
+    pl = _plog(p_log2)
+    S = np.empty((len(pl), M, N), dtype=np.float64)
+    _load().orc_psums(M, N, K, _p(A), K, _p(B), N, _p(r), _p(c), len(pl), _p(pl), _p(S))
+    return S
+
+
+def estimate(S, p_log2, r, c, tau: float):
+    """Largest stable p per entry; returns (Chat, p_sel, S_sel)."""
+    S = _f64(S)
+    n_p, M, N = S.shape
+    pl = _plog(p_log2)
+    assert len(pl) == n_p
+    r, c = _f64(r), _f64(c)
+    Chat = np.empty((M, N), dtype=np.float64)
+    psel = np.empty((M, N), dtype=np.uint8)
+    Ssel = np.empty((M, N), dtype=np.float64)
+    _load().orc_estimate(M, N, n_p, _p(pl), _p(S), _p(r), _p(c), float(tau), _p(Chat),
+                         _p(psel), _p(Ssel))
+    return Chat, psel, Ssel
+
+
+def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False):
+    """Full p-norm estimate of the (x,max) product (Alg. 5 with H = Alg. 3).
+
+    Returns a dict with Chat, p_sel, S_sel, r, c and (if want_S) S_all.
+    """
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    pl = _plog(p_log2)
+    Chat = np.empty((M, N), dtype=np.float64)
+    psel = np.empty((M, N), dtype=np.uint8)
+    Ssel = np.empty((M, N), dtype=np.float64)
+    r = np.empty(M, dtype=np.float64)
+    c = np.empty(N, dtype=np.float64)
+    S = np.empty((len(pl), M, N), dtype=np.float64) if want_S else None
+    rc = _load().orc_pnorm(M, N, K, _p(A), K, _p(B), N, len(pl), _p(pl), float(tau),
+                           int(scaling), _p(Chat), _p(psel), _p(Ssel),
+                           _p(S) if S is not None else None, _p(r), _p(c))
+    if rc:
+        raise MemoryError("oracle pnorm allocation failed")
+    out = dict(C=Chat, p_sel=psel, S_sel=Ssel, r=r, c=c)
+    if want_S:
+        out["S"] = S
+    return out
+
+
+def entries(A, B, ii, jj, p_log2, r, c):
+    """Exact max and all p-sums at the entries (ii[e], jj[e])."""
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    _, N = B.shape
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    pl = _plog(p_log2)
+    r, c = _f64(r), _f64(c)
+    ex = np.empty(len(ii), dtype=np.float64)
+    S = np.empty((len(ii), len(pl)), dtype=np.float64)
+    _load().orc_entries(M, N, K, _p(A), K, _p(B), N, _p(r), _p(c), len(pl), _p(pl), len(ii),
+                        _p(ii), _p(jj), _p(ex), _p(S))
+    return ex, S
+
+
+def floyd_warshall(W):
+    """Exact APSP distances; W uses +inf for missing edges."""
+    D = np.array(W, dtype=np.float64, copy=True, order="C")
+    n = D.shape[0]
+    _load().orc_floyd_warshall(n, _p(D), n)
+    return D
+
+
+def apsp_pnorm(W, p_log2, tau: float, n_squarings: int = 0, scaling: int = 2,
+               diag_policy: int = 1):
+    W = _f64(W)
+    n = W.shape[0]
+    D = np.empty((n, n), dtype=np.float64)
+    psel = np.empty((n, n), dtype=np.uint8)
+    pl = _plog(p_log2)
+    rc = _load().orc_apsp_pnorm(n, _p(W), n, int(n_squarings), len(pl), _p(pl), float(tau),
+                                int(scaling), int(diag_policy), _p(D), n, _p(psel))
+    if rc:
+        raise MemoryError("oracle apsp allocation failed")
+    return D, psel
+
+
+def pnorm_grad(A, B, plog, G, scaling: int = 2):
+    """dL/dA, dL/dB for L with dL/dC = G, p per entry = 2^plog (flag bits masked)."""
+    A, B, G = _f64(A), _f64(B), _f64(G)
+    M, K = A.shape
+    _, N = B.shape
+    r = row_scales(A, scaling)
+    c = col_scales(B, scaling)
+    pl = np.ascontiguousarray(np.asarray(plog) & 0x7F, dtype=np.uint8)
+    dA = np.empty((M, K), dtype=np.float64)
+    dB = np.empty((K, N), dtype=np.float64)
+    _load().orc_pnorm_grad(M, N, K, _p(A), _p(B), _p(r), _p(c), _p(pl), _p(G), _p(dA), _p(dB))
+    return dA, dB
+
+
+def row_logloss(arow, B, plog_row):
+    arow, B = _f64(arow), _f64(B)
+    K, N = B.shape
+    pl = np.ascontiguousarray(np.asarray(plog_row) & 0x7F, dtype=np.uint8)
+    return float(_load().orc_row_logloss(N, K, _p(arow), _p(B), _p(pl)))
+
+
+def col_logloss(A, bcol, plog_col):
+    A, bcol = _f64(A), _f64(bcol)
+    M, K = A.shape
+    pl = np.ascontiguousarray(np.asarray(plog_col) & 0x7F, dtype=np.uint8)
+    return float(_load().orc_col_logloss(M, K, _p(A), _p(bcol), _p(pl)))

@@ -1,0 +1,469 @@
+/*
+ * Oracle for the p-norm estimate of the (x,max) semiring matrix product.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously-correct
+ * CPU implementation (FP64 unless stated) of what the GPU library computes.
+ * It shares no code, header, table or helper with the CUDA path.  Only the
+ * tests, the smoke check and the CPU-baseline leg of the benchmark may load it.
+ *
+ * Paper: O. Serang, "Fast Computation on Semirings Isomorphic to (x, max) on
+ * R+" (arXiv 1511.05690).  Each function names the passage it follows.
+ *
+ * Readings of the paper that this file adopts (where the paper is silent or
+ * garbled) are:
+ *   - scaling (Sec. 2.1, definition of H'): operands are divided by a power of
+ *     two per row of A and per column of B, r_i = 2^ceil(log2 max_k a_ik),
+ *     c_j = 2^ceil(log2 max_k b_kj); the scale is undone after the 1/p root.
+ *     A zero row/column gets scale 1.  mode 1 = one global scale per operand
+ *     (the paper's literal H'), mode 0 = no scaling.
+ *   - estimator (Sec. 2.1, estimateMaxFromNormPowerSequence; Alg. 5): the
+ *     plain form, (S^(p*))^(1/p*) at the largest p in P with S^(p) >= tau.
+ *     If no p passes, p* is the smallest p in P and the result carries an
+ *     "unstable" flag (0x80 in p_sel).
+ *   - APSP (Sec. 2.2, Eq. for A^n): the diagonal is reset to 1 (distance 0)
+ *     after each squaring when diag_policy == 1.
+ *
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC oracle.c
+ * (-ffp-contract=off keeps every product and sum separately rounded.)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Alg. 2 (F'_APSP): naive matrix multiplication on the semiring (x, max). */
+/* C[i][j] = max_k A[i][k] * B[k][j].  FP64.  Empty max (K == 0) = 0, the  */
+/* zero of the semiring on R+.                                             */
+void orc_maxprod_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, double* C, int64_t ldc) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double r = 0.0;
+      for (int64_t k = 0; k < K; ++k) {
+        double t = A[i * lda + k] * B[k * ldb + j];
+        if (t > r) r = t;
+      }
+      C[i * ldc + j] = r;
+    }
+  }
+}
+
+/* Same as above with FP32 inputs: every product is rounded to float (one */
+/* correctly rounded multiply), the max is exact.  This is the bit-exact   */
+/* reference for the GPU's exact CUDA-core kernel.                         */
+void orc_maxprod_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, float* C, int64_t ldc) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      float r = 0.0f;
+      for (int64_t k = 0; k < K; ++k) {
+        volatile float t = A[i * lda + k] * B[k * ldb + j];
+        if (t > r) r = t;
+      }
+      C[i * ldc + j] = r;
+    }
+  }
+}
+
+/* Alg. 1 (F_APSP): naive matrix multiplication on the semiring (+, min).  */
+/* Empty min (K == 0) = +inf.                                              */
+void orc_minplus_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, double* C, int64_t ldc) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double r = INFINITY;
+      for (int64_t k = 0; k < K; ++k) {
+        double t = A[i * lda + k] + B[k * ldb + j];
+        if (t < r) r = t;
+      }
+      C[i * ldc + j] = r;
+    }
+  }
+}
+
+void orc_minplus_f32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                     const float* B, int64_t ldb, float* C, int64_t ldc) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      float r = INFINITY;
+      for (int64_t k = 0; k < K; ++k) {
+        volatile float t = A[i * lda + k] + B[k * ldb + j];
+        if (t < r) r = t;
+      }
+      C[i * ldc + j] = r;
+    }
+  }
+}
+
+/* Alg. 3 (G_APSP): naive matrix multiplication on the ring (x, +).  FP64. */
+void orc_ringprod_f64(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                      const double* B, int64_t ldb, double* C, int64_t ldc) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double s = 0.0;
+      for (int64_t k = 0; k < K; ++k) s += A[i * lda + k] * B[k * ldb + j];
+      C[i * ldc + j] = s;
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Default stability threshold tau (Sec. 2.1: tau depends on the numeric    */
+/* stability of H; the paper gives 1e-12 only for FFT convolution).  For a  */
+/* GEMM of nonnegative terms the only loss is operand underflow.  With the  */
+/* powered operands stored as q = x^p * 2^s in a format whose smallest      */
+/* normal is mu and which keeps m mantissa bits, operands below mu may be   */
+/* flushed, dropping at most K * mu * 2^-s from S.  Requiring that loss to  */
+/* stay below 2^-m * S gives tau = K * mu * 2^(m - s).                      */
+/*   compute 0 (FP32 via 3xTF32 split): mu 2^-126, m 21, s 0               */
+/*   compute 1 (TF32):                  mu 2^-126, m 10, s 0               */
+/*   compute 2 (BF16):                  mu 2^-126, m 7,  s 0               */
+/*   compute 3 (FP16):                  mu 2^-14,  m 10, s 15              */
+/*   compute 4 (FP8 E4M3):              mu 2^-6,   m 3,  s 8               */
+double orc_default_tau(int64_t K, int compute) {
+  int e_mu, m, s;
+  switch (compute) {
+    case 0: e_mu = -126; m = 21; s = 0; break;
+    case 1: e_mu = -126; m = 10; s = 0; break;
+    case 2: e_mu = -126; m = 7; s = 0; break;
+    case 3: e_mu = -14; m = 10; s = 15; break;
+    case 4: e_mu = -6; m = 3; s = 8; break;
+    default: return -1.0;
+  }
+  return (double)(K > 0 ? K : 1) * ldexp(1.0, e_mu + m - s);
+}
+
+/* Scaling (Sec. 2.1, H'): the smallest power of two >= m, for m > 0.      */
+/* m = f * 2^e with f in [0.5, 1): if f == 0.5, m = 2^(e-1) exactly.        */
+static double pow2_ceil(double m) {
+  if (!(m > 0.0)) return 1.0;
+  int e = 0;
+  double f = frexp(m, &e);
+  return ldexp(1.0, f == 0.5 ? e - 1 : e);
+}
+
+/* Row scales of A (M x K): mode 2 per row, mode 1 one global, mode 0 none. */
+void orc_row_scales(int64_t M, int64_t K, const double* A, int64_t lda, int mode, double* r) {
+  if (mode == 0) {
+    for (int64_t i = 0; i < M; ++i) r[i] = 1.0;
+    return;
+  }
+  double gmax = 0.0;
+  for (int64_t i = 0; i < M; ++i) {
+    double m = 0.0;
+    for (int64_t k = 0; k < K; ++k)
+      if (A[i * lda + k] > m) m = A[i * lda + k];
+    r[i] = pow2_ceil(m);
+    if (m > gmax) gmax = m;
+  }
+  if (mode == 1) {
+    double g = pow2_ceil(gmax);
+    for (int64_t i = 0; i < M; ++i) r[i] = g;
+  }
+}
+
+/* Column scales of B (K x N). */
+void orc_col_scales(int64_t K, int64_t N, const double* B, int64_t ldb, int mode, double* c) {
+  if (mode == 0) {
+    for (int64_t j = 0; j < N; ++j) c[j] = 1.0;
+    return;
+  }
+  double gmax = 0.0;
+  for (int64_t j = 0; j < N; ++j) {
+    double m = 0.0;
+    for (int64_t k = 0; k < K; ++k)
+      if (B[k * ldb + j] > m) m = B[k * ldb + j];
+    c[j] = pow2_ceil(m);
+    if (m > gmax) gmax = m;
+  }
+  if (mode == 1) {
+    double g = pow2_ceil(gmax);
+    for (int64_t j = 0; j < N; ++j) c[j] = g;
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Alg. 5 (E_APSP), first loop: for each p in P, the ring product of the   */
+/* scaled, powered operands (Alg. 3 on A'^p and B'^p), FP64, term by term: */
+/*   S[q][i][j] = sum_k pow(a_ik / r_i * b_kj / c_j, p_q),  p_q = 2^p_log2[q]. */
+/* pow() per term is used on purpose (no squaring chain).                   */
+void orc_psums(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+               int64_t ldb, const double* r, const double* c, int n_p, const int* p_log2,
+               double* S) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      for (int q = 0; q < n_p; ++q) {
+        double p = ldexp(1.0, p_log2[q]);
+        double s = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+          double u = (A[i * lda + k] / r[i]) * (B[k * ldb + j] / c[j]);
+          s += pow(u, p);
+        }
+        S[((int64_t)q * M + i) * N + j] = s;
+      }
+    }
+  }
+}
+
+/* Alg. 5, second loop, with the plain estimateMaxFromNormPowerSequence:    */
+/* p* = largest p in P with S^(p) >= tau (the stable set is a prefix of P   */
+/* because S^(p) is non-increasing in p once every term is <= 1).           */
+/* Chat = r_i * c_j * (S^(p*))^(1/p*).  p_sel = log2(p*) | 0x80 if unstable. */
+void orc_estimate(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
+                  const double* r, const double* c, double tau, double* Chat, uint8_t* psel,
+                  double* Ssel) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      int q_sel = -1;
+      for (int q = n_p - 1; q >= 0; --q) {
+        if (S[((int64_t)q * M + i) * N + j] >= tau) {
+          q_sel = q;
+          break;
+        }
+      }
+      int unstable = 0;
+      if (q_sel < 0) {
+        q_sel = 0;
+        unstable = 1;
+      }
+      double s = S[((int64_t)q_sel * M + i) * N + j];
+      double p = ldexp(1.0, p_log2[q_sel]);
+      double root = s > 0.0 ? pow(s, 1.0 / p) : 0.0;
+      if (Chat) Chat[i * N + j] = r[i] * c[j] * root;
+      if (psel) psel[i * N + j] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
+      if (Ssel) Ssel[i * N + j] = s;
+    }
+  }
+}
+
+/* Scales + p-sums + estimate.  S (n_p*M*N doubles) may be NULL, in which   */
+/* case a temporary is used.                                                 */
+int orc_pnorm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+              int64_t ldb, int n_p, const int* p_log2, double tau, int scaling, double* Chat,
+              uint8_t* psel, double* Ssel, double* S_all, double* r_out, double* c_out) {
+  double* r = (double*)malloc(sizeof(double) * (M > 0 ? M : 1));
+  double* c = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
+  double* S = S_all ? S_all : (double*)malloc(sizeof(double) * (size_t)n_p * (M * N > 0 ? M * N : 1));
+  if (!r || !c || !S) return -1;
+  orc_row_scales(M, K, A, lda, scaling, r);
+  orc_col_scales(K, N, B, ldb, scaling, c);
+  orc_psums(M, N, K, A, lda, B, ldb, r, c, n_p, p_log2, S);
+  orc_estimate(M, N, n_p, p_log2, S, r, c, tau, Chat, psel, Ssel);
+  if (r_out) memcpy(r_out, r, sizeof(double) * M);
+  if (c_out) memcpy(c_out, c, sizeof(double) * N);
+  free(r);
+  free(c);
+  if (!S_all) free(S);
+  return 0;
+}
+
+/* Selected entries only: for n_e pairs (ii[e], jj[e]) of the product A*B, */
+/* the exact max (Alg. 2) and every p-sum (Alg. 5 first loop), given the   */
+/* scales r (length M) and c (length N).  Cost O(n_e * K * n_p).            */
+void orc_entries(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, const double* r, const double* c, int n_p, const int* p_log2,
+                 int64_t n_e, const int64_t* ii, const int64_t* jj, double* exact, double* S) {
+  (void)M;
+  (void)N;
+  int64_t e;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (e = 0; e < n_e; ++e) {
+    int64_t i = ii[e], j = jj[e];
+    double mx = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+      double t = A[i * lda + k] * B[k * ldb + j];
+      if (t > mx) mx = t;
+    }
+    if (exact) exact[e] = mx;
+    if (S) {
+      for (int q = 0; q < n_p; ++q) {
+        double p = ldexp(1.0, p_log2[q]);
+        double s = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+          double u = (A[i * lda + k] / r[i]) * (B[k * ldb + j] / c[j]);
+          s += pow(u, p);
+        }
+        S[e * n_p + q] = s;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Floyd-Warshall (Sec. 3.1 comparison): exact APSP in O(n^3), in place.    */
+/* D holds the weights on entry (+inf = no edge) and distances on return.  */
+void orc_floyd_warshall(int64_t n, double* D, int64_t ldd) {
+  for (int64_t k = 0; k < n; ++k) {
+    const double* Dk = D + k * ldd;
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < n; ++i) {
+      double dik = D[i * ldd + k];
+      if (dik == INFINITY) continue;
+      double* Di = D + i * ldd;
+      for (int64_t j = 0; j < n; ++j) {
+        double t = dik + Dk[j];
+        if (t < Di[j]) Di[j] = t;
+      }
+    }
+  }
+}
+
+/* p-norm APSP (Sec. 2.2): X = exp(-W) (+inf -> 0), X_ii = 1 if diag_policy,*/
+/* then n_sq times X <- E(X, X) (the p-norm product above) with the same    */
+/* diagonal reset, and D = -log X.  n_sq <= 0 means ceil(log2 n).           */
+int orc_apsp_pnorm(int64_t n, const double* W, int64_t ldw, int n_sq, int n_p, const int* p_log2,
+                   double tau, int scaling, int diag_policy, double* D, int64_t ldd,
+                   uint8_t* psel_last) {
+  if (n <= 0) return 0;
+  if (n_sq <= 0) {
+    n_sq = 0;
+    while (((int64_t)1 << n_sq) < n) ++n_sq;
+  }
+  double* X = (double*)malloc(sizeof(double) * n * n);
+  double* Y = (double*)malloc(sizeof(double) * n * n);
+  if (!X || !Y) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double w = W[i * ldw + j];
+      X[i * n + j] = (w == INFINITY) ? 0.0 : exp(-w);
+    }
+  if (diag_policy == 1)
+    for (int64_t i = 0; i < n; ++i) X[i * n + i] = 1.0;
+  for (int t = 0; t < n_sq; ++t) {
+    int rc = orc_pnorm(n, n, n, X, n, X, n, n_p, p_log2, tau, scaling, Y,
+                       (t == n_sq - 1) ? psel_last : NULL, NULL, NULL, NULL, NULL);
+    if (rc) return rc;
+    if (diag_policy == 1)
+      for (int64_t i = 0; i < n; ++i) Y[i * n + i] = 1.0;
+    double* tmp = X;
+    X = Y;
+    Y = tmp;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double x = X[i * n + j];
+      D[i * ldd + j] = (x > 0.0) ? -log(x) : INFINITY;
+    }
+  free(X);
+  free(Y);
+  return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Gradient of the p-norm product with the selected p held fixed per entry */
+/* (the derivative of (sum_k (a_ik b_kj)^p)^(1/p), the estimator of Alg. 5  */
+/* at p = p_ij; the Discussion notes the p-norm rings are differentiable).  */
+/*   dC_ij/da_ik = C_ij^(1-p) a_ik^(p-1) b_kj^p                            */
+/*   dA_ik = sum_j G_ij dC_ij/da_ik,  dB_kj = sum_i G_ij dC_ij/db_kj.       */
+/* Written in the scaled variables to stay in range:                       */
+/*   C_ij^(1-p) a_ik^(p-1) b_kj^p = (C_ij/S_ij) (a'_ik^(p-1)/r_i) b'_kj^p,  */
+/* with S_ij the scaled p-sum at p_ij.  Entries with S_ij == 0 contribute 0.*/
+/* plog[i*N+j] holds log2(p_ij) (flag bits already masked off).             */
+void orc_pnorm_grad(int64_t M, int64_t N, int64_t K, const double* A, const double* B,
+                    const double* r, const double* c, const uint8_t* plog, const double* G,
+                    double* dA, double* dB) {
+  double* Wt = (double*)malloc(sizeof(double) * (M * N > 0 ? M * N : 1));
+  /* W_ij = G_ij * C_ij / S_ij computed from the definition. */
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      double p = ldexp(1.0, plog[i * N + j]);
+      double s = 0.0;
+      for (int64_t k = 0; k < K; ++k) s += pow((A[i * K + k] / r[i]) * (B[k * N + j] / c[j]), p);
+      double C = s > 0.0 ? r[i] * c[j] * pow(s, 1.0 / p) : 0.0;
+      Wt[i * N + j] = s > 0.0 ? G[i * N + j] * C / s : 0.0;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t k = 0; k < K; ++k) {
+      double acc = 0.0;
+      double ap = A[i * K + k] / r[i];
+      for (int64_t j = 0; j < N; ++j) {
+        double p = ldexp(1.0, plog[i * N + j]);
+        double bp = B[k * N + j] / c[j];
+        acc += Wt[i * N + j] * pow(ap, p - 1.0) / r[i] * pow(bp, p);
+      }
+      dA[i * K + k] = acc;
+    }
+  }
+  int64_t k;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (k = 0; k < K; ++k) {
+    for (int64_t j = 0; j < N; ++j) {
+      double acc = 0.0;
+      double bp = B[k * N + j] / c[j];
+      for (int64_t ii2 = 0; ii2 < M; ++ii2) {
+        double p = ldexp(1.0, plog[ii2 * N + j]);
+        double ap = A[ii2 * K + k] / r[ii2];
+        acc += Wt[ii2 * N + j] * pow(ap, p) * pow(bp, p - 1.0) / c[j];
+      }
+      dB[k * N + j] = acc;
+    }
+  }
+  free(Wt);
+}
+
+/* Loss L = sum_j log C_ij over one row i of the product, at fixed p per    */
+/* entry; used by finite differences (a_ik only changes row i of C).       */
+double orc_row_logloss(int64_t N, int64_t K, const double* arow, const double* B,
+                       const uint8_t* plog_row) {
+  double L = 0.0;
+  for (int64_t j = 0; j < N; ++j) {
+    double p = ldexp(1.0, plog_row[j]);
+    double s = 0.0;
+    for (int64_t k = 0; k < K; ++k) s += pow(arow[k] * B[k * N + j], p);
+    L += log(pow(s, 1.0 / p));
+  }
+  return L;
+}
+
+/* Loss over one column j of the product (b_kj only changes column j). */
+double orc_col_logloss(int64_t M, int64_t K, const double* A, const double* bcol,
+                       const uint8_t* plog_col) {
+  double L = 0.0;
+  for (int64_t i = 0; i < M; ++i) {
+    double p = ldexp(1.0, plog_col[i]);
+    double s = 0.0;
+    for (int64_t k = 0; k < K; ++k) s += pow(A[i * K + k] * bcol[k], p);
+    L += log(pow(s, 1.0 / p));
+  }
+  return L;
+}

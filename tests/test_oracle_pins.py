@@ -1,0 +1,357 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: a hand-worked
+example, a closed form, a library routine (numpy, scipy), an invariant the
+paper states, or a second independent algorithm.  Shapes are non-square so a
+transposed operand or swapped index fails.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            rows.setdefault(key, []).append([Fraction(v) for v in vals])
+    return rows
+
+
+# ---------------------------------------------------------------- golden ---
+def test_hand_worked_3x3(orc):
+    """Hand-derived exact values (tests/golden/tiny_3x3.txt)."""
+    g = _read_golden("tiny_3x3.txt")
+    A = np.array(g["A"], dtype=np.float64)
+    B = np.array(g["B"], dtype=np.float64)
+    np.testing.assert_array_equal(orc.maxprod(A, B), np.array(g["C"], dtype=np.float64))
+    np.testing.assert_array_equal(orc.row_scales(A), np.array(g["r"][0], dtype=np.float64))
+    np.testing.assert_array_equal(orc.col_scales(B), np.array(g["c"][0], dtype=np.float64))
+    S = orc.psums(A, B, [0, 1])
+    np.testing.assert_array_equal(S[0], np.array(g["S1"], dtype=np.float64))
+    np.testing.assert_array_equal(S[1], np.array(g["S2"], dtype=np.float64))
+    out = orc.pnorm(A, B, [0, 1], tau=0.2)
+    np.testing.assert_array_equal(out["p_sel"], np.array(g["psel"], dtype=np.uint8))
+    r = np.array(g["r"][0], dtype=np.float64)
+    c = np.array(g["c"][0], dtype=np.float64)
+    S1 = np.array(g["S1"], dtype=np.float64)
+    S2 = np.array(g["S2"], dtype=np.float64)
+    psel = np.array(g["psel"])
+    expect = np.where(psel == 1, np.sqrt(S2), S1) * r[:, None] * c[None, :]
+    np.testing.assert_allclose(out["C"], expect, rtol=1e-15)
+
+
+# ------------------------------------------------------ exact products ---
+def test_maxprod_rank_one_closed_form(orc):
+    """A = u v^T, B = x y^T  =>  C_ij = u_i y_j max_k v_k x_k."""
+    g = workloads.rng(7)
+    u, v = g.random(9) + 0.1, g.random(13)
+    x, y = g.random(13), g.random(6) + 0.1
+    C = orc.maxprod(np.outer(u, v), np.outer(x, y))
+    np.testing.assert_allclose(C, np.outer(u, y) * np.max(v * x), rtol=1e-15)
+
+
+def test_maxprod_permutation(orc):
+    """A permutation matrix P gives C = P B (rows of B reordered)."""
+    g = workloads.rng(8)
+    perm = g.permutation(11)
+    P = np.eye(11)[perm]
+    B = g.random((11, 5))
+    np.testing.assert_array_equal(orc.maxprod(P, B), B[perm])
+
+
+def test_maxprod_limit_of_ring_products(orc):
+    """max_k u_k = lim_p (sum_k u_k^p)^(1/p) (Sec. 1), evaluated by scipy's
+    logsumexp at p = 2^20; the gap is at most log(K)/p."""
+    from scipy.special import logsumexp
+    A, B = workloads.uniform_pair(7, 5, 19, seed=3, dtype=np.float64)
+    p = 2.0 ** 20
+    L = (np.log(A)[:, :, None] + np.log(B)[None, :, :]) * p
+    approx = np.exp(logsumexp(L, axis=1) / p)
+    C = orc.maxprod(A, B)
+    assert np.all(C <= approx * (1 + 1e-12))
+    assert np.all(approx <= C * np.exp(math.log(19) / p) * (1 + 1e-12))
+
+
+def test_maxprod_f32_is_rounded_f64(orc):
+    """Rounding is monotone, so max_k fl32(a b) = fl32(max_k a b) exactly."""
+    A, B = workloads.uniform_pair(17, 23, 31, seed=4)
+    C32 = orc.maxprod_f32(A, B)
+    C64 = orc.maxprod(A.astype(np.float64), B.astype(np.float64))
+    np.testing.assert_array_equal(C32, C64.astype(np.float32))
+
+
+def test_exp_isomorphism_between_minplus_and_maxprod(orc):
+    """x = exp(-w) maps (+,min) to (x,max) (Sec. 2.2)."""
+    g = workloads.rng(9)
+    X, Y = g.random((6, 10)) * 3, g.random((10, 8)) * 3
+    np.testing.assert_allclose(orc.maxprod(np.exp(-X), np.exp(-Y)),
+                               np.exp(-orc.minplus(X, Y)), rtol=1e-14)
+
+
+def test_minplus_f32_exact_against_f64(orc):
+    g = workloads.rng(10)
+    X = g.random((9, 12)).astype(np.float32)
+    Y = g.random((12, 7)).astype(np.float32)
+    ref = (X.astype(np.float64)[:, :, None] + Y.astype(np.float64)[None]).astype(np.float32)
+    np.testing.assert_array_equal(orc.minplus_f32(X, Y), ref.min(axis=1))
+
+
+def test_ringprod_matches_numpy(orc):
+    """Alg. 3 is the ordinary product; compare with numpy's GEMM."""
+    A, B = workloads.uniform_pair(13, 7, 29, seed=5, dtype=np.float64)
+    np.testing.assert_allclose(orc.ringprod(A, B), A @ B, rtol=1e-13)
+
+
+def test_empty_reductions(orc):
+    A = np.zeros((3, 0))
+    B = np.zeros((0, 4))
+    assert np.all(orc.maxprod(A, B) == 0.0)
+    assert np.all(np.isinf(orc.minplus(A, B)))
+
+
+# --------------------------------------------------------------- scales ---
+def test_scales_are_powers_of_two_bracketing_the_max(orc):
+    A, B = workloads.uniform_pair(40, 30, 50, seed=6, dtype=np.float64)
+    A *= np.exp(workloads.rng(1).normal(0, 20, size=(40, 1)))
+    A[3] = 0.0
+    A[5, :] = 0.25  # exact power of two: scale must be 0.25, not 0.5
+    r = orc.row_scales(A)
+    assert r[3] == 1.0 and r[5] == 0.25
+    m, e = np.frexp(r)
+    assert np.all(m == 0.5)
+    mx = A.max(axis=1)
+    nz = mx > 0
+    assert np.all(mx[nz] / r[nz] <= 1.0) and np.all(mx[nz] / r[nz] > 0.5)
+    c = orc.col_scales(B)
+    assert np.all(B.max(axis=0) / c <= 1.0) and np.all(B.max(axis=0) / c > 0.5)
+    g = orc.row_scales(A, mode=1)
+    assert np.all(g == g[0]) and A.max() / g[0] <= 1.0 and A.max() / g[0] > 0.5
+    assert np.all(orc.row_scales(A, mode=0) == 1.0)
+
+
+# ---------------------------------------------------------------- p-sums ---
+def test_p1_equals_ordinary_product(orc):
+    """p = 1 gives the ring product (Alg. 3): r_i c_j S^(1)_ij = (A B)_ij."""
+    A, B = workloads.wide_range_pair(21, 9, 33, seed=11, dtype=np.float64)
+    A *= 3.0
+    B *= 0.01
+    r, c = orc.row_scales(A), orc.col_scales(B)
+    S = orc.psums(A, B, [0])
+    np.testing.assert_allclose(S[0] * r[:, None] * c[None, :], A @ B, rtol=1e-13)
+
+
+def test_psums_monotone_in_p(orc):
+    """Scaled terms are <= 1, so S^(p) is non-increasing in p (Sec. 1)."""
+    A, B = workloads.uniform_pair(12, 14, 40, seed=12, dtype=np.float64)
+    S = orc.psums(A, B, list(range(8)))
+    assert np.all(np.diff(S, axis=0) <= 1e-15)
+
+
+def test_psums_expectation_uniform(orc):
+    """For i.i.d. U(0,1] entries with unit scales, E[S^(p)] = K/(p+1)^2."""
+    M = N = 64
+    K = 512
+    A, B = workloads.uniform_pair(M, N, K, seed=13, dtype=np.float64)
+    assert np.all(orc.row_scales(A) == 1.0) and np.all(orc.col_scales(B) == 1.0)
+    pl = [0, 1, 2, 3, 4]
+    S = orc.psums(A, B, pl)
+    for q, lp in enumerate(pl):
+        p = 2 ** lp
+        expect = K / (p + 1) ** 2
+        tol = {1: 0.02, 2: 0.03, 4: 0.05, 8: 0.08, 16: 0.12}[p]
+        assert abs(S[q].mean() / expect - 1) < tol, (p, S[q].mean(), expect)
+
+
+# ------------------------------------------------------------- estimator ---
+def test_estimator_selection_rule(orc):
+    """p* = largest p in P with S^(p) >= tau (Alg. 5); none -> smallest p, flagged."""
+    pl = [0, 1, 2, 3]
+    S = np.array([[[5.0, 2.0, 1e-3, 0.0]],
+                  [[4.0, 1.0, 1e-8, 0.0]],
+                  [[3.0, 1e-9, 1e-20, 0.0]],
+                  [[2.0, 1e-30, 1e-40, 0.0]]])  # shape (n_p=4, M=1, N=4)
+    r = np.array([2.0])
+    c = np.array([1.0, 0.5, 4.0, 1.0])
+    Chat, psel, Ssel = orc.estimate(S, pl, r, c, tau=1e-6)
+    assert list(psel[0]) == [3, 1, 0, 0x80 | 0]
+    np.testing.assert_allclose(Chat[0, 0], 2 * 1 * 2.0 ** (1 / 8), rtol=1e-15)
+    np.testing.assert_allclose(Chat[0, 1], 2 * 0.5 * 1.0 ** 0.5, rtol=1e-15)
+    np.testing.assert_allclose(Chat[0, 2], 2 * 4.0 * 1e-3, rtol=1e-15)
+    assert Chat[0, 3] == 0.0
+    assert list(Ssel[0]) == [2.0, 1.0, 1e-3, 0.0]
+
+
+def test_all_ones_upper_envelope_is_tight(orc):
+    """A = B = ones(K): S^(p) = K, Chat = K^(1/p*), C = 1 (Sec. 1 bound n^(1/p))."""
+    K = 37
+    A = np.ones((5, K))
+    B = np.ones((K, 6))
+    out = orc.pnorm(A, B, [0, 1, 2, 3, 4], tau=1e-30, want_S=True)
+    assert np.all(out["S"] == K)
+    assert np.all(out["p_sel"] == 4)
+    np.testing.assert_allclose(out["C"], K ** (1 / 16), rtol=1e-15)
+
+
+def test_single_term_is_exact(orc):
+    """A with one nonzero per row: every p-norm equals the max (u has one term)."""
+    g = workloads.rng(14)
+    K = 20
+    A = np.zeros((8, K))
+    A[np.arange(8), g.integers(0, K, 8)] = g.random(8) + 0.01
+    B = g.random((K, 9)) + 0.01
+    out = orc.pnorm(A, B, [0, 2, 5], tau=1e-300)
+    np.testing.assert_allclose(out["C"], orc.maxprod(A, B), rtol=1e-14)
+
+
+def test_envelope_and_convergence(orc):
+    """C <= Chat <= K^(1/p*) C (Sec. 1), and the gap shrinks as p grows."""
+    A, B = workloads.uniform_pair(16, 12, 64, seed=15, dtype=np.float64)
+    C = orc.maxprod(A, B)
+    prev = None
+    for lp in range(0, 8):
+        out = orc.pnorm(A, B, [lp], tau=1e-300)
+        Chat = out["C"]
+        assert np.all(Chat >= C * (1 - 1e-13))
+        assert np.all(Chat <= C * 64 ** (1 / 2 ** lp) * (1 + 1e-13))
+        if prev is not None:
+            assert np.all(Chat <= prev * (1 + 1e-13))
+        prev = Chat
+
+
+def test_convergence_to_max_at_huge_p(orc):
+    """With a unit maximal term per entry, p = 2^20 reproduces the max to ~log(K)/p."""
+    K = 30
+    g = workloads.rng(16)
+    A = g.random((6, K)) * 0.9
+    B = g.random((K, 7)) * 0.9
+    A[:, 0] = 1.0
+    B[0, :] = 1.0
+    out = orc.pnorm(A, B, [20], tau=1e-300)
+    np.testing.assert_allclose(out["C"], orc.maxprod(A, B), rtol=4e-6)
+
+
+def test_default_tau_reading(orc):
+    """tau = K * mu * 2^(m - s) per powered-operand format (reading of Sec. 2.1)."""
+    assert orc.default_tau(16384, orc.BF16) == 16384 * 2.0 ** -119
+    assert orc.default_tau(16384, orc.F32_EXACT) == 16384 * 2.0 ** -105
+    assert orc.default_tau(100, orc.TF32) == 100 * 2.0 ** -116
+    assert orc.default_tau(16384, orc.F16) == 16384 * 2.0 ** -19
+    assert orc.default_tau(16384, orc.E4M3) == 8.0
+
+
+# ------------------------------------------------------------------ APSP ---
+def test_complete_graph_one_squaring_closed_form(orc):
+    """Equal weights w on every edge, x = e^-w, X_ii = 1: for i != j,
+    S^(p)_ij = 2 e^(-p w) + (n-2) e^(-2 p w) (k = i or j, or any other k)."""
+    n, w = 9, 0.3
+    X = np.full((n, n), math.exp(-w))
+    np.fill_diagonal(X, 1.0)
+    S = orc.psums(X, X, [0, 3, 6])
+    for q, p in enumerate([1, 8, 64]):
+        expect = 2 * math.exp(-p * w) + (n - 2) * math.exp(-2 * p * w)
+        off = S[q][~np.eye(n, dtype=bool)]
+        np.testing.assert_allclose(off, expect, rtol=1e-14)
+
+
+def test_floyd_warshall_matches_scipy(orc):
+    from scipy.sparse.csgraph import shortest_path
+    W = workloads.apsp_weights(60, density=0.15, seed=17).astype(np.float64)
+    D = orc.floyd_warshall(W)
+    G = np.where(np.isinf(W), 0.0, W)
+    np.fill_diagonal(G, 0.0)
+    # scipy treats 0 as "no edge" in dense input; weights here are > 0 a.s.
+    ref = shortest_path(G, method="D", directed=True)
+    np.testing.assert_allclose(D, ref, rtol=1e-12)
+
+
+def test_floyd_warshall_matches_repeated_minplus(orc):
+    """APSP by repeated (+,min) squaring, ceil(log2 n) times (Sec. 1)."""
+    n = 33
+    W = workloads.apsp_weights(n, density=0.2, seed=18).astype(np.float64)
+    D = W.copy()
+    for _ in range(math.ceil(math.log2(n))):
+        D = orc.minplus(D, D)
+    np.testing.assert_allclose(orc.floyd_warshall(W), D, rtol=1e-14)
+
+
+def test_apsp_pnorm_underestimates_distance(orc):
+    """Chat >= C at every squaring, so the p-norm distance is <= the exact one."""
+    n = 64
+    W = workloads.apsp_weights(n, density=0.1, seed=19).astype(np.float64)
+    D = orc.floyd_warshall(W)
+    pl = list(range(7))
+    Dh, psel = orc.apsp_pnorm(W, pl, tau=orc.default_tau(n, orc.F32_EXACT))
+    finite = np.isfinite(D)
+    assert np.all(np.isfinite(Dh) == finite)
+    assert np.all(Dh[finite] <= D[finite] + 1e-12)
+    assert np.all(np.diag(Dh) == 0.0)
+
+
+def test_apsp_pnorm_one_squaring_envelope(orc):
+    """One squaring: exact 2-hop distance d1 = minplus(W, W) (diagonal 0) and
+    d1 - ln(n)/p* <= dhat <= d1, from C <= Chat <= n^(1/p*) C in x = exp(-w)."""
+    n = 48
+    W = workloads.apsp_weights(n, density=0.2, seed=22).astype(np.float64)
+    d1 = orc.minplus(W, W)
+    pl = list(range(7))
+    Dh, psel = orc.apsp_pnorm(W, pl, tau=orc.default_tau(n, orc.F32_EXACT), n_squarings=1)
+    finite = np.isfinite(d1)
+    assert np.all(np.isfinite(Dh) == finite)
+    p = 2.0 ** (psel & 0x7F)
+    off = finite & ~np.eye(n, dtype=bool)
+    assert np.all(Dh[off] <= d1[off] + 1e-12)
+    assert np.all(Dh[off] >= d1[off] - np.log(n) / p[off] - 1e-12)
+
+
+# -------------------------------------------------------------- gradient ---
+def test_gradient_central_differences(orc):
+    """Oracle gradient of L = sum log C against central differences (step 1e-3 rel)."""
+    M, N, K = 6, 5, 9
+    A, B = workloads.uniform_pair(M, N, K, seed=20, dtype=np.float64)
+    pl = [4]  # p fixed at 16
+    out = orc.pnorm(A, B, pl, tau=1e-300)
+    plog = out["p_sel"] & 0x7F
+    G = 1.0 / out["C"]
+    dA, dB = orc.pnorm_grad(A, B, plog, G)
+    for (i, k) in [(0, 0), (2, 5), (5, 8), (3, 1)]:
+        h = 1e-3 * A[i, k]
+        ap, am = A[i].copy(), A[i].copy()
+        ap[k] += h
+        am[k] -= h
+        fd = (orc.row_logloss(ap, B, plog[i]) - orc.row_logloss(am, B, plog[i])) / (2 * h)
+        assert abs(fd - dA[i, k]) <= 1e-4 * abs(dA[i, k]) + 1e-9, (i, k, fd, dA[i, k])
+    for (k, j) in [(0, 0), (4, 2), (8, 4)]:
+        h = 1e-3 * B[k, j]
+        bp, bm = B[:, j].copy(), B[:, j].copy()
+        bp[k] += h
+        bm[k] -= h
+        fd = (orc.col_logloss(A, bp, plog[:, j]) - orc.col_logloss(A, bm, plog[:, j])) / (2 * h)
+        assert abs(fd - dB[k, j]) <= 1e-4 * abs(dB[k, j]) + 1e-9, (k, j, fd, dB[k, j])
+
+
+def test_gradient_euler_homogeneity(orc):
+    """C_ij is homogeneous of degree 1 in row i of A and in column j of B, so
+    sum_k a_ik dC_ij/da_ik = C_ij = sum_k b_kj dC_ij/db_kj (one-hot G)."""
+    M, N, K = 4, 3, 11
+    A, B = workloads.wide_range_pair(M, N, K, seed=21, dtype=np.float64)
+    out = orc.pnorm(A, B, [0, 2, 4], tau=1e-300)
+    plog = out["p_sel"] & 0x7F
+    for (i, j) in [(0, 0), (3, 2), (1, 1)]:
+        G = np.zeros((M, N))
+        G[i, j] = 1.0
+        dA, dB = orc.pnorm_grad(A, B, plog, G)
+        np.testing.assert_allclose(np.dot(A[i], dA[i]), out["C"][i, j], rtol=1e-12)
+        np.testing.assert_allclose(np.dot(B[:, j], dB[:, j]), out["C"][i, j], rtol=1e-12)
+        assert np.all(dA[np.arange(M) != i] == 0.0)
