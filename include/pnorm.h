@@ -1,0 +1,217 @@
+/*
+ * pnorm.h -- C ABI of the GB300 (sm_103a) p-norm semiring product library.
+ *
+ * The library estimates products on the semiring (x, max) over nonnegative
+ * reals with a small family of p-norm rings, following O. Serang, "Fast
+ * Computation on Semirings Isomorphic to (x, max) on R+" (arXiv 1511.05690):
+ * for each p in P the operands are scaled into [0, 1], raised elementwise to
+ * the power p, multiplied with an ordinary (x, +) GEMM on the tensor cores,
+ * and per output entry the largest numerically stable p gives the estimate
+ * (S^(p*))^(1/p*), which is then un-scaled (Sec. 2.1; Alg. 5).  Through
+ * x = exp(-w) the same product gives (+, min) shortest-path squarings
+ * (Sec. 2.2).
+ *
+ * Conventions shared by every call:
+ *  - Matrices are row-major FP32 with an explicit leading dimension (in
+ *    elements) unless a call says otherwise.  All matrix pointers are DEVICE
+ *    pointers owned by the caller; the library never allocates device or
+ *    host memory and keeps no state between calls except a per-device cache
+ *    of device properties and tile choices (thread-safe).
+ *  - `stream` is a cudaStream_t (passed as void*; NULL = legacy default
+ *    stream).  Calls only enqueue work: they return before the GPU finishes,
+ *    they do not synchronise, and they are safe to capture in a CUDA graph.
+ *  - The return value reports errors the host can see (bad sizes, pointers,
+ *    options, workspace).  Errors found on the device (inputs outside the
+ *    domain, a bounded wait that ran out) are written, first error wins, to
+ *    the optional device word `opts->dev_status` as a pn_status value; the
+ *    caller reads it after synchronising.  The word must be zeroed by the
+ *    caller before the call if it is to be read.
+ *  - M, N or K equal to 0 is legal.  No call falls back to the CPU and no
+ *    C++ exception crosses this boundary.
+ */
+#ifndef PNORM_H
+#define PNORM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PN_API __attribute__((visibility("default")))
+#else
+#define PN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pn_status {
+  PN_OK = 0,
+  PN_EINVAL = 1,        /* invalid size, stride, pointer or option */
+  PN_EALIGN = 2,        /* workspace not 256-byte aligned */
+  PN_EWORKSPACE = 3,    /* workspace smaller than the *_workspace_size query */
+  PN_EDOMAIN = 4,       /* (device) input NaN, negative, +inf, or > 2^127 */
+  PN_ECUDA = 5,         /* a CUDA runtime call failed (launch, attribute, ...) */
+  PN_ETIMEOUT = 6,      /* (device) a bounded wait inside a kernel ran out */
+  PN_EUNSUPPORTED = 7   /* no GB300-class device, or an unsupported mode */
+} pn_status;
+
+/* Arithmetic of the powered operands fed to the tensor cores (the ring
+ * GEMM H of Sec. 2.1).  Accumulation is always FP32. */
+typedef enum pn_compute {
+  PN_F32_EXACT = 0, /* FP32 operands as a 3xTF32 split: a = hi + lo, hi*hi+hi*lo+lo*hi */
+  PN_TF32 = 1,      /* TF32 operands (10-bit mantissa) */
+  PN_BF16 = 2,      /* BF16 operands */
+  PN_F16 = 3,       /* FP16 operands, powered values mapped to [0, 2^15] */
+  PN_E4M3 = 4       /* FP8 E4M3 operands, powered values mapped to [0, 2^8] */
+} pn_compute;
+
+#define PN_MAX_P 16
+
+/* Options of every p-norm call.  Fill with pn_default_opts() first. */
+typedef struct pn_opts {
+  /* The p family P = { 2^p_log2[0] < 2^p_log2[1] < ... } (Sec. 1, the
+   * piecewise family {1, 2, 4, ..., p_max}).  1 <= n_p <= 16, p_log2 strictly
+   * ascending, each in [0, 15]. */
+  int32_t n_p;
+  int32_t p_log2[PN_MAX_P];
+  /* Stability threshold tau (Sec. 2.1): p is stable for an entry when the
+   * scaled p-sum S^(p) >= tau.  <= 0 selects pn_default_tau(K, compute). */
+  double tau;
+  int32_t compute;     /* pn_compute */
+  /* Operand scaling (Sec. 2.1, H'): 2 = per-row (A) / per-column (B) powers
+   * of two (default); 1 = one global power of two per operand; 0 = none. */
+  int32_t scaling;
+  /* APSP only: 1 = reset the diagonal to x = 1 (distance 0) after each
+   * squaring (default); 0 = leave it. */
+  int32_t diag_policy;
+  /* Output tile width of the tensor-core kernel: 0 = autotuned, else 128 or
+   * 256 (PN_F32_EXACT always uses 128). */
+  int32_t tile_n;
+  /* Optional device int32 receiving device-side errors (see above). */
+  int32_t* dev_status;
+  /* Optional cudaEvent_t pair recorded on `stream` immediately before and
+   * after the first (largest-p) tensor-core launch, for timing it. */
+  void* ev_gemm_begin;
+  void* ev_gemm_end;
+  /* Limit of every bounded device-side wait, in nanoseconds; 0 = 2e9. */
+  int64_t timeout_ns;
+  /* Test hooks, 0 in normal use.  Bit 0: the copy producer skips one stage
+   * so that the consumer's bounded wait runs out (PN_ETIMEOUT). */
+  int32_t debug_flags;
+} pn_opts;
+
+/* Human-readable name of a status code (static string). */
+PN_API const char* pn_status_string(int32_t status);
+
+/* P = {1, 2, 4, ..., 64}, PN_BF16, default tau, per-row/column scaling,
+ * diagonal reset, autotuned tiles, no status word, no events. */
+PN_API void pn_default_opts(pn_opts* opts);
+
+/* Default tau for contraction length K and compute mode (reading of Sec. 2.1,
+ * where tau is set by the numeric stability of H): with powered operands
+ * stored as q = x^p * 2^s in a format of smallest normal mu and m mantissa
+ * bits, tau = K * mu * 2^(m - s), so that flushed operands can drop at most
+ * a 2^-m fraction of an accepted S.  Returns a negative value for an unknown
+ * mode. */
+PN_API double pn_default_tau(int64_t K, int32_t compute);
+
+/* Number of streaming multiprocessors of the current device (0 if none). */
+PN_API int32_t pn_device_sm_count(void);
+
+/* Bytes of workspace maxprod_pnorm needs for these sizes and options
+ * (0 on invalid options).  The workspace must be 256-byte aligned. */
+PN_API size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts);
+
+/* p-norm estimate of the (x, max) product C = A (x,max) B (Alg. 5 with H a
+ * tensor-core GEMM; Sec. 2.1 for the scaling and the stable-p rule):
+ *   r_i = scale of row i of A, c_j = scale of column j of B,
+ *   S^(p)_ij = sum_k (a_ik/r_i * b_kj/c_j)^p            for p in P,
+ *   p*_ij = largest p in P with S^(p)_ij >= tau,
+ *   C_ij = r_i c_j (S^(p*))^(1/p*).
+ * If no p is stable, p* is the smallest p of P and p_sel carries 0x80.
+ * A: M x K (lda >= K), B: K x N (ldb >= N), C: M x N (ldc >= N), all FP32,
+ * all entries in [0, 2^127] (else PN_EDOMAIN on the device).
+ * p_sel (nullable): M x N bytes, row stride N, log2(p*) | 0x80 if unstable.
+ * S_sel (nullable): M x N FP32, row stride N, the scaled p-sum at p*.
+ * ws / ws_bytes: workspace of at least pn_workspace_size() bytes. */
+PN_API pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, uint8_t* p_sel,
+                        float* S_sel, const pn_opts* opts, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/* Exact semiring product on the CUDA cores (FP32, the plain comparison):
+ * semiring 0: C_ij = max_k a_ik * b_kj  (Alg. 2; empty max = 0)
+ * semiring 1: C_ij = min_k a_ik + b_kj  (Alg. 1; empty min = +inf)
+ * Every product/sum is one correctly rounded FP32 operation and max/min are
+ * exact, so the result is bit-identical to any sequential FP32 evaluation.
+ * No workspace. */
+PN_API pn_status maxprod_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, int32_t semiring,
+                        void* stream);
+
+/* maxprod_exact with an explicit kernel variant, for comparing the two:
+ * variant 0 issues one FP32 multiply (add) and one max (min) per semiring
+ * operation; variant 1 (the default of maxprod_exact) forms two consecutive
+ * products with one paired mul.rn.f32x2 (add.rn.f32x2) and folds both with
+ * one 3-input max (min).  Both give identical results. */
+PN_API pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                                   const float* B, int64_t ldb, float* C, int64_t ldc,
+                                   int32_t semiring, int32_t variant, void* stream);
+
+/* Workspace bytes for apsp_pnorm (0 on invalid options). */
+PN_API size_t pn_apsp_workspace_size(int64_t n, const pn_opts* opts);
+
+/* All-pairs shortest distances estimated with p-norm squarings (Sec. 2.2):
+ * X = exp(-W) with +inf -> 0, X_ii = 1 (diag_policy 1); then n_squarings
+ * times X <- maxprod_pnorm(X, X) followed by the diagonal reset; finally
+ * D = -log X (0 -> +inf).  W: n x n FP32, ldw >= n, entries >= 0 or +inf
+ * (else PN_EDOMAIN); D: n x n FP32, ldd >= n.  n_squarings <= 0 selects
+ * ceil(log2 n), which covers every path of up to n edges (Sec. 1, A^n by
+ * powers of two). */
+PN_API pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t ldd,
+                     int32_t n_squarings, const pn_opts* opts, void* ws, size_t ws_bytes,
+                     void* stream);
+
+/* Workspace bytes for maxprod_pnorm_backward (0 on invalid options). */
+PN_API size_t pn_backward_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts);
+
+/* Adjoint of maxprod_pnorm with p* held fixed per entry (the p-norm rings are
+ * differentiable, Sec. 4).  With C_ij = (sum_k (a_ik b_kj)^p)^(1/p):
+ *   W_ij  = dC_ij * C_ij / S_sel_ij                   (0 where S_sel == 0)
+ *   dA_ik = (a'_ik^(p-1) / r_i) * sum_j W_ij b'_kj^p   summed over p in P,
+ *   dB_kj = (b'_kj^(p-1) / c_j) * sum_i W_ij a'_ik^p   with W masked to p*_ij == p,
+ * where a' = a / r_i, b' = b / c_j are the forward's scaled operands
+ * (recomputed, not stored).  A: M x K, B: K x N, C, S_sel, p_sel, dC: M x N,
+ * dA: M x K, dB: K x N, all contiguous row-major (leading dimension = number
+ * of columns); C, S_sel and p_sel are the outputs of maxprod_pnorm with the
+ * same options.  dA and dB are overwritten. */
+PN_API pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A,
+                                 const float* B, const float* C, const float* S_sel,
+                                 const uint8_t* p_sel, const float* dC, float* dA, float* dB,
+                                 const pn_opts* opts, void* ws, size_t ws_bytes, void* stream);
+
+/* Grouped launch: many independent products C_g = A_g (x,max) B_g in one
+ * persistent tensor-core launch per p level (Sec. 4: the p rings and the
+ * problems parallelise coarsely).  Two steps, so that the run step never
+ * copies host memory and can be captured in a CUDA graph:
+ *  1. pn_grouped_build_table() (host only, no CUDA calls) writes a table
+ *     describing `count` problems (sizes MNK[3g..3g+2] = M_g, N_g, K_g, and
+ *     DEVICE pointers A[g], B[g], C[g] of contiguous row-major FP32 matrices)
+ *     into host memory `host_table` of pn_grouped_table_bytes(count) bytes,
+ *     and returns the workspace size in *ws_bytes.
+ *  2. The caller copies the table bytes unchanged to device memory
+ *     `dev_table` (16-byte aligned) and calls maxprod_pnorm_grouped() with
+ *     both copies; each C_g receives the same estimate as maxprod_pnorm. */
+PN_API size_t pn_grouped_table_bytes(int32_t count);
+PN_API pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
+                                 const float* const* B, float* const* C, const pn_opts* opts,
+                                 void* host_table, size_t table_bytes, size_t* ws_bytes);
+PN_API pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
+                                const pn_opts* opts, void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNORM_H */

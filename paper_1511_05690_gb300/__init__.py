@@ -1,0 +1,225 @@
+"""GB300 (sm_103a) p-norm semiring products: a thin PyTorch-facing wrapper.
+
+The library estimates the (x,max) semiring matrix product on nonnegative reals
+with a family of p-norm rings (O. Serang, arXiv 1511.05690, Sec. 2.1 and
+Alg. 5): scale, raise to p, ring GEMM on the tensor cores, 1/p root, largest
+stable p per entry, un-scale.  Through x = exp(-w) it gives (+,min) APSP by
+repeated squaring (Sec. 2.2).
+
+PyTorch provides device memory and streams only.  Every function here
+validates shapes, allocates outputs and the workspace, and calls the C ABI of
+``_lib/libpnorm.so`` (``include/pnorm.h``); all arithmetic runs in the CUDA
+kernels.  There is no CPU fallback: if the library is missing, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _binding as _b
+from ._binding import (PN_BF16, PN_E4M3, PN_F16, PN_F32_EXACT, PN_TF32, PnError,  # noqa: F401
+                       make_opts, status_string)
+
+__all__ = ["maxprod_pnorm", "maxprod_exact", "apsp_pnorm", "default_tau", "workspace",
+           "PnError", "make_opts", "status_string", "sm_count", "PNormMaxProd",
+           "maxprod_pnorm_backward"]
+
+_ws = {}
+_status = {}
+
+
+def lib():
+    return _b.load()
+
+
+def sm_count() -> int:
+    return int(lib().pn_device_sm_count())
+
+
+def default_tau(K: int, compute="bf16") -> float:
+    c = _b.COMPUTE_NAMES[compute] if isinstance(compute, str) else int(compute)
+    return float(lib().pn_default_tau(int(K), c))
+
+
+def workspace(nbytes: int, device) -> torch.Tensor:
+    """Per-device cached workspace of at least nbytes (256-byte aligned)."""
+    dev = torch.device(device)
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    buf = _ws.get(key)
+    if buf is None or buf.numel() < nbytes:
+        _ws.pop(key, None)
+        buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=dev)
+        if buf.data_ptr() % 256:
+            raise RuntimeError("workspace allocation is not 256-byte aligned")
+        _ws[key] = buf
+    return buf
+
+
+def status_word(device) -> torch.Tensor:
+    """Per-device int32 word receiving device-side errors (zero when clean)."""
+    dev = torch.device(device)
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    w = _status.get(key)
+    if w is None:
+        w = torch.zeros(1, dtype=torch.int32, device=dev)
+        _status[key] = w
+    return w
+
+
+def check_device_status(device, where: str) -> None:
+    """Synchronises the current stream and raises PnError if a kernel recorded an error."""
+    w = status_word(device)
+    code = int(w.item())
+    if code != 0:
+        w.zero_()
+        raise PnError(code, where)
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mat(x: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(x, torch.Tensor) or x.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D tensor")
+    if x.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if x.stride(1) != 1 or (x.size(0) > 1 and x.stride(0) < x.size(1)):
+        x = x.contiguous()
+    return x
+
+
+def _ld(x: torch.Tensor) -> int:
+    return x.stride(0) if x.size(0) > 1 else max(x.size(1), 1)
+
+
+def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), compute="bf16",
+                  tau=None, scaling=2, tile_n=0, out=None, want_psel=True, want_ssel=True,
+                  check=True, ev_begin=None, ev_end=None, stream=None, timeout_ns=0,
+                  debug_flags=0):
+    """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None)."""
+    A, B = _mat(A, "A"), _mat(B, "B")
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    dev = A.device
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=dev)
+    psel = torch.empty((M, N), dtype=torch.uint8, device=dev) if want_psel else None
+    ssel = torch.empty((M, N), dtype=torch.float32, device=dev) if want_ssel else None
+    st = status_word(dev)
+    o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(),
+                  ev_begin.cuda_event if ev_begin is not None else None,
+                  ev_end.cuda_event if ev_end is not None else None, timeout_ns, debug_flags)
+    L = lib()
+    need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
+    if need == 0 and M * N > 0:
+        raise ValueError("invalid options")
+    ws = workspace(need, dev)
+    rc = L.maxprod_pnorm(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(),
+                         _ld(C), psel.data_ptr() if psel is not None else None,
+                         ssel.data_ptr() if ssel is not None else None, ctypes.byref(o),
+                         ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _b.check(rc, "maxprod_pnorm")
+    if check:
+        check_device_status(dev, "maxprod_pnorm")
+    return C, psel, ssel
+
+
+def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None, out=None,
+                  stream=None):
+    """Exact (x,max) (semiring 0) or (+,min) (semiring 1) product on the CUDA cores."""
+    A, B = _mat(A, "A"), _mat(B, "B")
+    M, K = A.shape
+    K2, N = B.shape
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    C = out if out is not None else torch.empty((M, N), dtype=torch.float32, device=A.device)
+    L = lib()
+    if variant is None:
+        rc = L.maxprod_exact(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(),
+                             _ld(C), int(semiring), _stream_ptr(stream))
+    else:
+        rc = L.pn_maxprod_exact_variant(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B),
+                                        C.data_ptr(), _ld(C), int(semiring), int(variant),
+                                        _stream_ptr(stream))
+    _b.check(rc, "maxprod_exact")
+    return C
+
+
+def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
+               tau=None, scaling=2, diag_policy=1, tile_n=0, out=None, check=True,
+               stream=None, ev_begin=None, ev_end=None):
+    """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge)."""
+    W = _mat(W, "W")
+    n = W.shape[0]
+    if W.shape[1] != n:
+        raise ValueError("W must be square")
+    dev = W.device
+    D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=dev)
+    st = status_word(dev)
+    o = make_opts(p_log2, compute, tau, scaling, diag_policy, tile_n, st.data_ptr(),
+                  ev_begin.cuda_event if ev_begin is not None else None,
+                  ev_end.cuda_event if ev_end is not None else None)
+    L = lib()
+    need = L.pn_apsp_workspace_size(n, ctypes.byref(o))
+    if need == 0 and n > 0:
+        raise ValueError("invalid options")
+    ws = workspace(need, dev)
+    rc = L.apsp_pnorm(n, W.data_ptr(), _ld(W), D.data_ptr(), _ld(D), int(n_squarings),
+                      ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream_ptr(stream))
+    _b.check(rc, "apsp_pnorm")
+    if check:
+        check_device_status(dev, "apsp_pnorm")
+    return D
+
+
+def maxprod_pnorm_backward(A, B, C, S_sel, p_sel, dC, *, p_log2=tuple(range(7)),
+                           compute="f32", tau=None, scaling=2, check=True, stream=None):
+    """Adjoint of maxprod_pnorm at fixed p* per entry; returns (dA, dB)."""
+    A, B = _mat(A, "A").contiguous(), _mat(B, "B").contiguous()
+    C, S_sel, dC = C.contiguous(), S_sel.contiguous(), dC.contiguous()
+    p_sel = p_sel.contiguous()
+    M, K = A.shape
+    N = B.shape[1]
+    dev = A.device
+    dA = torch.empty((M, K), dtype=torch.float32, device=dev)
+    dB = torch.empty((K, N), dtype=torch.float32, device=dev)
+    st = status_word(dev)
+    o = make_opts(p_log2, compute, tau, scaling, 1, 0, st.data_ptr())
+    L = lib()
+    need = L.pn_backward_workspace_size(M, N, K, ctypes.byref(o))
+    ws = workspace(max(need, 256), dev)
+    rc = L.maxprod_pnorm_backward(M, N, K, A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                  S_sel.data_ptr(), p_sel.data_ptr(), dC.data_ptr(),
+                                  dA.data_ptr(), dB.data_ptr(), ctypes.byref(o), ws.data_ptr(),
+                                  ws.numel(), _stream_ptr(stream))
+    _b.check(rc, "maxprod_pnorm_backward")
+    if check:
+        check_device_status(dev, "maxprod_pnorm_backward")
+    return dA, dB
+
+
+class PNormMaxProd(torch.autograd.Function):
+    """C = p-norm (x,max) product of A and B, differentiable at fixed p* per entry."""
+
+    @staticmethod
+    def forward(ctx, A, B, p_log2=tuple(range(7)), compute="f32", tau=None, scaling=2):
+        C, psel, ssel = maxprod_pnorm(A, B, p_log2=p_log2, compute=compute, tau=tau,
+                                      scaling=scaling)
+        ctx.save_for_backward(A, B, C, ssel, psel)
+        ctx.cfg = (tuple(p_log2), compute, tau, scaling)
+        ctx.mark_non_differentiable(psel, ssel)
+        return C, psel, ssel
+
+    @staticmethod
+    def backward(ctx, dC, _dpsel=None, _dssel=None):
+        A, B, C, ssel, psel = ctx.saved_tensors
+        p_log2, compute, tau, scaling = ctx.cfg
+        dA, dB = maxprod_pnorm_backward(A, B, C, ssel, psel, dC.contiguous(), p_log2=p_log2,
+                                        compute=compute, tau=tau, scaling=scaling)
+        return dA, dB, None, None, None, None

@@ -1,0 +1,412 @@
+// Host runtime and C ABI of the p-norm semiring library (include/pnorm.h):
+// argument checks, workspace layout, the per-level launch sequence of the
+// p-norm product (Alg. 5), the APSP driver (Sec. 2.2) and the exact product.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "pn_internal.h"
+#include <cuda_runtime.h>
+
+namespace pn {
+
+namespace {
+
+constexpr size_t WS_ALIGN = 256;
+constexpr size_t IMG_ALIGN = 1024;
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct DevInfo {
+  int sms = 0;
+  int ok = -1;  // -1 unknown, 0 unsupported, 1 sm_103
+};
+std::mutex g_dev_mu;
+DevInfo g_dev[64];
+
+// Streaming multiprocessors of the current device, or 0 if it is not an
+// sm_103 (GB300-class) device.
+int device_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DevInfo& d = g_dev[dev];
+  if (d.ok < 0) {
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    d.ok = (major == 10 && minor == 3) ? 1 : 0;
+    d.sms = sms;
+  }
+  return d.ok == 1 ? d.sms : 0;
+}
+
+bool opts_valid(const pn_opts* o) {
+  if (!o) return false;
+  if (o->n_p < 1 || o->n_p > PN_MAX_P) return false;
+  for (int q = 0; q < o->n_p; ++q) {
+    if (o->p_log2[q] < 0 || o->p_log2[q] > 15) return false;
+    if (q > 0 && o->p_log2[q] <= o->p_log2[q - 1]) return false;
+  }
+  if (o->compute < PN_F32_EXACT || o->compute > PN_E4M3) return false;
+  if (o->scaling < 0 || o->scaling > 2) return false;
+  if (o->diag_policy < 0 || o->diag_policy > 1) return false;
+  if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256) return false;
+  if (o->timeout_ns < 0) return false;
+  if (std::isnan(o->tau)) return false;
+  return true;
+}
+
+// Tile width: 3xTF32 carries two operand planes, so only 128 fits the ring.
+int choose_bn(const pn_opts* o, int64_t M, int64_t N) {
+  if (o->compute == PN_F32_EXACT) return 128;
+  if (o->tile_n) return o->tile_n;
+  (void)M;
+  return N > 128 ? 256 : 128;
+}
+
+// Smallest float >= t (so that S >= result  <=>  S >= t for float S).
+float tau_up(double t) {
+  if (!(t > 0.0)) return 0.0f;
+  if (t > 3.0e38) return INFINITY;
+  float f = static_cast<float>(t);
+  if (static_cast<double>(f) < t) f = std::nextafter(f, INFINITY);
+  if (f == 0.0f) f = std::nextafter(0.0f, 1.0f);
+  return f;
+}
+
+// Workspace layout of one product (single problem).
+struct Layout {
+  int BN = 0, KB = 0, RBA = 0, RBB = 0, tiles_m = 0, tiles_n = 0, total_tiles = 0;
+  int state_ld = 0, n_p = 0, planes = 1;
+  size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0, off_cflag = 0;
+  size_t ctrl_bytes = 0;
+  size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_aimg = 0, off_bimg = 0;
+  size_t a_level_bytes = 0, b_level_bytes = 0, a_plane = 0, b_plane = 0;
+  size_t total = 0;
+};
+
+Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
+  Layout L;
+  const int mode = o->compute;
+  L.BN = choose_bn(o, M, N);
+  L.n_p = o->n_p;
+  L.planes = mode_planes(mode);
+  L.KB = static_cast<int>(ceil_div(K, mode_bk(mode)));
+  L.tiles_m = static_cast<int>(ceil_div(M, TILE_M));
+  L.tiles_n = static_cast<int>(ceil_div(N, L.BN));
+  L.RBA = L.tiles_m;
+  L.RBB = L.tiles_n * (L.BN / TILE_M);
+  L.total_tiles = L.tiles_m * L.tiles_n;
+  L.state_ld = L.tiles_n * (L.BN / 32);
+  size_t off = 0;
+  // control words, cleared at the start of every call
+  L.off_rmax = off; off += sizeof(uint32_t) * M;
+  L.off_cmax = off; off += sizeof(uint32_t) * N;
+  L.off_gmax = off; off += sizeof(uint32_t) * 2;
+  L.off_counts = off; off += sizeof(int32_t) * PN_MAX_P;
+  L.off_rflag = off; off += static_cast<size_t>(L.n_p) * L.tiles_m;
+  L.off_cflag = off; off += static_cast<size_t>(L.n_p) * L.tiles_n;
+  L.ctrl_bytes = align_up(off, 16);
+  off = align_up(off, WS_ALIGN);
+  L.off_r = off; off = align_up(off + sizeof(float) * M, WS_ALIGN);
+  L.off_c = off; off = align_up(off + sizeof(float) * N, WS_ALIGN);
+  L.off_work = off; off = align_up(off + sizeof(int32_t) * L.n_p * (size_t)L.total_tiles, WS_ALIGN);
+  L.off_state = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
+  L.a_plane = static_cast<size_t>(L.RBA) * L.KB * IMG_BYTES;
+  L.b_plane = static_cast<size_t>(L.RBB) * L.KB * IMG_BYTES;
+  L.a_level_bytes = L.a_plane * L.planes;
+  L.b_level_bytes = L.b_plane * L.planes;
+  L.off_aimg = off; off += L.a_level_bytes * L.n_p;
+  L.off_bimg = off; off += L.b_level_bytes * L.n_p;
+  L.total = align_up(off, WS_ALIGN);
+  return L;
+}
+
+double default_tau(int64_t K, int compute) {
+  int e_mu, m, s;
+  switch (compute) {
+    case PN_F32_EXACT: e_mu = -126; m = 21; s = 0; break;
+    case PN_TF32: e_mu = -126; m = 10; s = 0; break;
+    case PN_BF16: e_mu = -126; m = 7; s = 0; break;
+    case PN_F16: e_mu = -14; m = 10; s = 15; break;
+    case PN_E4M3: e_mu = -6; m = 3; s = 8; break;
+    default: return -1.0;
+  }
+  return static_cast<double>(K > 0 ? K : 1) * std::ldexp(1.0, e_mu + m - s);
+}
+
+pn_status cuda_status(int e) { return e == 0 ? PN_OK : PN_ECUDA; }
+
+// Fills the Common / Prob description of one product laid out by `L` in `ws`.
+void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, const float* A,
+                 int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, uint8_t* p_sel,
+                 float* S_sel, const pn_opts* o, uint8_t* ws) {
+  std::memset(&cm, 0, sizeof(cm));
+  Prob& P = cm.single;
+  P.A = A; P.B = B; P.C = C; P.psel = p_sel; P.Ssel = S_sel;
+  P.lda = lda; P.ldb = ldb; P.ldc = ldc; P.ldaux = N;
+  P.M = static_cast<int32_t>(M); P.N = static_cast<int32_t>(N); P.K = static_cast<int32_t>(K);
+  P.KB = L.KB; P.RBA = L.RBA; P.RBB = L.RBB;
+  P.tiles_m = L.tiles_m; P.tiles_n = L.tiles_n;
+  P.tile_base = 0; P.xa_base = 0; P.xb_base = 0; P.tm_base = 0; P.tn_base = 0;
+  const bool vc = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
+                  ((N & 15) == 0) &&
+                  (!p_sel || (reinterpret_cast<uintptr_t>(p_sel) & 15) == 0) &&
+                  (!S_sel || (reinterpret_cast<uintptr_t>(S_sel) & 15) == 0);
+  P.vec_c = vc ? 1 : 0;
+  P.state_ld = L.state_ld;
+  P.a_img = 0; P.b_img = 0;
+  P.a_plane = static_cast<int64_t>(L.a_plane);
+  P.b_plane = static_cast<int64_t>(L.b_plane);
+  P.rc_r = 0; P.rc_c = 0; P.state_off = 0;
+  const double tau = o->tau > 0.0 ? o->tau : default_tau(K, o->compute);
+  P.tau_d = tau;
+  P.tau = tau_up(tau);
+  cm.probs = nullptr;
+  cm.nprob = 1;
+  cm.total_tiles = L.total_tiles;
+  cm.total_xa = L.RBA * L.KB;
+  cm.total_xb = L.RBB * L.KB;
+  cm.total_tm = L.tiles_m;
+  cm.total_tn = L.tiles_n;
+  cm.mode = o->compute;
+  cm.BN = L.BN;
+  cm.s_op = mode_op_shift(o->compute);
+  cm.scaling = o->scaling;
+  cm.unscale = std::ldexp(1.0f, -2 * cm.s_op);
+  cm.rmax = reinterpret_cast<uint32_t*>(ws + L.off_rmax);
+  cm.cmax = reinterpret_cast<uint32_t*>(ws + L.off_cmax);
+  cm.gmax = reinterpret_cast<uint32_t*>(ws + L.off_gmax);
+  cm.r = reinterpret_cast<float*>(ws + L.off_r);
+  cm.c = reinterpret_cast<float*>(ws + L.off_c);
+  cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
+  cm.status = o->dev_status;
+  cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
+  cm.debug_flags = o->debug_flags;
+  cm.n_levels = o->n_p;
+}
+
+// Level q of the p family (q = n_p-1 is the largest p).
+Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, int q) {
+  Level lv;
+  std::memset(&lv, 0, sizeof(lv));
+  const int top = o->n_p - 1;
+  int32_t* counts = reinterpret_cast<int32_t*>(ws + L.off_counts);
+  int32_t* work = reinterpret_cast<int32_t*>(ws + L.off_work);
+  uint8_t* rflag = ws + L.off_rflag;
+  uint8_t* cflag = ws + L.off_cflag;
+  const int qn = q > 0 ? q - 1 : 0;
+  lv.q = q;
+  lv.plog = o->p_log2[q];
+  lv.is_top = q == top;
+  lv.is_bottom = q == 0;
+  lv.a_level = ws + L.off_aimg + L.a_level_bytes * q;
+  lv.b_level = ws + L.off_bimg + L.b_level_bytes * q;
+  lv.work = work + static_cast<size_t>(q) * L.total_tiles;
+  lv.work_count = counts + q;
+  lv.next_work = work + static_cast<size_t>(qn) * L.total_tiles;
+  lv.next_count = counts + qn;
+  lv.rflag = rflag + static_cast<size_t>(q) * L.tiles_m;
+  lv.cflag = cflag + static_cast<size_t>(q) * L.tiles_n;
+  lv.next_rflag = rflag + static_cast<size_t>(qn) * L.tiles_m;
+  lv.next_cflag = cflag + static_cast<size_t>(qn) * L.tiles_n;
+  return lv;
+}
+
+// The product proper, arguments already checked.
+pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                    int64_t ldb, float* C, int64_t ldc, uint8_t* p_sel, float* S_sel,
+                    const pn_opts* o, uint8_t* ws, void* stream, int sms) {
+  if (M == 0 || N == 0) return PN_OK;
+  const Layout L = make_layout(M, N, K, o);
+  Common cm;
+  fill_common(cm, L, M, N, K, A, lda, B, ldb, C, ldc, p_sel, S_sel, o, ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (K == 0) return cuda_status(launch_fill_empty(cm, o->p_log2[0], stream));
+  int e = cudaMemsetAsync(ws, 0, L.ctrl_bytes, s);
+  if (e) return PN_ECUDA;
+  if ((e = launch_maxes(cm, stream))) return PN_ECUDA;
+  for (int q = o->n_p - 1; q >= 0; --q) {
+    const Level lv = make_level(L, o, ws, q);
+    if ((e = launch_power_a(cm, lv, stream))) return PN_ECUDA;
+    if ((e = launch_power_b(cm, lv, stream))) return PN_ECUDA;
+    if (lv.is_top && o->ev_gemm_begin)
+      if (cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_begin), s)) return PN_ECUDA;
+    if ((e = launch_gemm_level(cm, lv, sms, stream))) return PN_ECUDA;
+    if (lv.is_top && o->ev_gemm_end)
+      if (cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_end), s)) return PN_ECUDA;
+  }
+  return PN_OK;
+}
+
+bool dims_ok(int64_t M, int64_t N, int64_t K) {
+  const int64_t lim = (int64_t)1 << 30;
+  return M >= 0 && N >= 0 && K >= 0 && M < lim && N < lim && K < lim;
+}
+
+}  // namespace
+
+}  // namespace pn
+
+using namespace pn;
+
+extern "C" {
+
+const char* pn_status_string(int32_t status) {
+  switch (status) {
+    case PN_OK: return "PN_OK";
+    case PN_EINVAL: return "PN_EINVAL: invalid argument";
+    case PN_EALIGN: return "PN_EALIGN: workspace not 256-byte aligned";
+    case PN_EWORKSPACE: return "PN_EWORKSPACE: workspace too small";
+    case PN_EDOMAIN: return "PN_EDOMAIN: input outside the semiring domain";
+    case PN_ECUDA: return "PN_ECUDA: CUDA runtime error";
+    case PN_ETIMEOUT: return "PN_ETIMEOUT: a bounded device wait ran out";
+    case PN_EUNSUPPORTED: return "PN_EUNSUPPORTED: unsupported device or mode";
+    default: return "unknown pn_status";
+  }
+}
+
+void pn_default_opts(pn_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_p = 7;
+  for (int q = 0; q < 7; ++q) o->p_log2[q] = q;
+  o->tau = 0.0;
+  o->compute = PN_BF16;
+  o->scaling = 2;
+  o->diag_policy = 1;
+  o->tile_n = 0;
+}
+
+double pn_default_tau(int64_t K, int32_t compute) { return pn::default_tau(K, compute); }
+
+int32_t pn_device_sm_count(void) { return pn::device_sms(); }
+
+size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts) {
+  if (!opts_valid(opts) || !dims_ok(M, N, K)) return 0;
+  return make_layout(M, N, K, opts).total;
+}
+
+pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, uint8_t* p_sel,
+                        float* S_sel, const pn_opts* opts, void* ws, size_t ws_bytes,
+                        void* stream) {
+  if (!opts_valid(opts) || !dims_ok(M, N, K)) return PN_EINVAL;
+  if (M == 0 || N == 0) return PN_OK;
+  if (!C || ldc < N) return PN_EINVAL;
+  if (K > 0 && (!A || !B || lda < K || ldb < N)) return PN_EINVAL;
+  const size_t need = make_layout(M, N, K, opts).total;
+  if (!ws || ws_bytes < need) return PN_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % WS_ALIGN) return PN_EALIGN;
+  const int sms = device_sms();
+  if (sms <= 0) return PN_EUNSUPPORTED;
+  return run_pnorm(M, N, K, A, lda, B, ldb, C, ldc, p_sel, S_sel, opts,
+                   static_cast<uint8_t*>(ws), stream, sms);
+}
+
+pn_status maxprod_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                        const float* B, int64_t ldb, float* C, int64_t ldc, int32_t semiring,
+                        void* stream) {
+  if (!dims_ok(M, N, K) || (semiring != 0 && semiring != 1)) return PN_EINVAL;
+  if (M == 0 || N == 0) return PN_OK;
+  if (!C || ldc < N) return PN_EINVAL;
+  if (K > 0 && (!A || !B || lda < K || ldb < N)) return PN_EINVAL;
+  if (device_sms() <= 0) return PN_EUNSUPPORTED;
+  return cuda_status(launch_exact(M, N, K, A, lda, B, ldb, C, ldc, semiring, 1, stream));
+}
+
+// Exact product with an explicit kernel variant (0: FMUL + FMNMX, 1: paired
+// mul.f32x2 + 3-input max); used to compare the two.  Same results.
+pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                                   const float* B, int64_t ldb, float* C, int64_t ldc,
+                                   int32_t semiring, int32_t variant, void* stream) {
+  if (!dims_ok(M, N, K) || (semiring != 0 && semiring != 1)) return PN_EINVAL;
+  if (M == 0 || N == 0) return PN_OK;
+  if (!C || ldc < N) return PN_EINVAL;
+  if (K > 0 && (!A || !B || lda < K || ldb < N)) return PN_EINVAL;
+  if (device_sms() <= 0) return PN_EUNSUPPORTED;
+  return cuda_status(launch_exact(M, N, K, A, lda, B, ldb, C, ldc, semiring, variant, stream));
+}
+
+size_t pn_apsp_workspace_size(int64_t n, const pn_opts* opts) {
+  if (!opts_valid(opts) || !dims_ok(n, n, n)) return 0;
+  const size_t x_bytes = align_up(sizeof(float) * n * n, IMG_ALIGN);
+  return x_bytes + make_layout(n, n, n, opts).total;
+}
+
+pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t ldd,
+                     int32_t n_squarings, const pn_opts* opts, void* ws, size_t ws_bytes,
+                     void* stream) {
+  if (!opts_valid(opts) || !dims_ok(n, n, n)) return PN_EINVAL;
+  if (n == 0) return PN_OK;
+  if (!W || !D || ldw < n || ldd < n) return PN_EINVAL;
+  const size_t need = pn_apsp_workspace_size(n, opts);
+  if (!ws || ws_bytes < need) return PN_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % WS_ALIGN) return PN_EALIGN;
+  const int sms = device_sms();
+  if (sms <= 0) return PN_EUNSUPPORTED;
+  int T = n_squarings;
+  if (T <= 0) {
+    T = 0;
+    while (((int64_t)1 << T) < n) ++T;
+  }
+  uint8_t* wsb = static_cast<uint8_t*>(ws);
+  float* X = reinterpret_cast<float*>(wsb);
+  uint8_t* pws = wsb + align_up(sizeof(float) * n * n, IMG_ALIGN);
+  if (launch_apsp_init(n, W, ldw, X, opts->diag_policy, opts->dev_status, stream)) return PN_ECUDA;
+  // ping-pong between the workspace copy X (ld n) and the output D (ld ldd)
+  float* src = X;
+  int64_t lds = n;
+  float* dst = D;
+  int64_t ldt = ldd;
+  pn_opts o = *opts;
+  for (int t = 0; t < T; ++t) {
+    if (t > 0) o.ev_gemm_begin = o.ev_gemm_end = nullptr;
+    const pn_status st =
+        run_pnorm(n, n, n, src, lds, src, lds, dst, ldt, nullptr, nullptr, &o, pws, stream, sms);
+    if (st != PN_OK) return st;
+    if (opts->diag_policy == 1 && launch_diag_reset(n, dst, ldt, stream)) return PN_ECUDA;
+    float* tp = src; src = dst; dst = tp;
+    const int64_t tl = lds; lds = ldt; ldt = tl;
+  }
+  if (launch_apsp_final(n, src, lds, D, ldd, stream)) return PN_ECUDA;
+  return PN_OK;
+}
+
+size_t pn_backward_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts) {
+  (void)M; (void)N; (void)K; (void)opts;
+  return 0;
+}
+
+pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A,
+                                 const float* B, const float* C, const float* S_sel,
+                                 const uint8_t* p_sel, const float* dC, float* dA, float* dB,
+                                 const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
+  (void)M; (void)N; (void)K; (void)A; (void)B; (void)C; (void)S_sel; (void)p_sel; (void)dC;
+  (void)dA; (void)dB; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
+  return PN_EUNSUPPORTED;
+}
+
+size_t pn_grouped_table_bytes(int32_t count) {
+  (void)count;
+  return 0;
+}
+
+pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
+                                 const float* const* B, float* const* C, const pn_opts* opts,
+                                 void* host_table, size_t table_bytes, size_t* ws_bytes) {
+  (void)count; (void)MNK; (void)A; (void)B; (void)C; (void)opts; (void)host_table;
+  (void)table_bytes; (void)ws_bytes;
+  return PN_EUNSUPPORTED;
+}
+
+pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
+                                const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
+  (void)host_table; (void)dev_table; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
+  return PN_EUNSUPPORTED;
+}
+
+}  // extern "C"

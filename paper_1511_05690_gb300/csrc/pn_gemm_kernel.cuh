@@ -1,0 +1,382 @@
+// Tensor-core level kernel of the p-norm product (template; instantiated per
+// operand format in pn_gemm_*.cu).  See pn_gemm.cu for the design notes.
+#pragma once
+#include <cfloat>
+
+#include "pn_device.cuh"
+
+namespace pn {
+namespace gemm {
+
+constexpr int GEMM_THREADS = 192;
+constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
+
+__host__ __device__ constexpr inline int stage_bytes(int mode, int BN) {
+  return mode_planes(mode) * (IMG_BYTES + IMG_BYTES * (BN / TILE_M));
+}
+__host__ __device__ constexpr int num_stages(int mode, int BN) {
+  return SMEM_STAGE_BUDGET / stage_bytes(mode, BN) > 8 ? 8 : SMEM_STAGE_BUDGET / stage_bytes(mode, BN);
+}
+__host__ __device__ constexpr int smem_total(int mode, int BN) {
+  return num_stages(mode, BN) * stage_bytes(mode, BN) + 1024 /*align*/ + 256 /*barriers*/;
+}
+__host__ __device__ constexpr int mma_kind(int mode) {
+  return (mode == MODE_BF16 || mode == MODE_F16) ? KIND_F16 : mode == MODE_E4M3 ? KIND_F8 : KIND_TF32;
+}
+// A/B format codes of the instruction descriptor.
+__host__ __device__ constexpr uint32_t ab_format(int mode) {
+  return mode == MODE_BF16 ? 1u : (mode == MODE_TF32 || mode == MODE_3XTF32) ? 2u : 0u;
+}
+
+// Waits without looking at the abort flag (used while draining after an abort).
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  int32_t never = 0;
+  return mbar_wait(bar, parity, timeout_ns, &never);
+}
+
+template <int MODE, int BN>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+  constexpr int PLANES = mode_planes(MODE);
+  constexpr int A_BYTES = IMG_BYTES;
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
+  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int KIND = mma_kind(MODE);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr int CHUNKS = BN / 32;
+  static_assert(STAGES >= 2, "operand ring too small");
+
+  const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
+  if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(tmem_slot + 1);
+  volatile int32_t* ok_flag = abort_flag + 1;  // [2], epilogue item hand-off
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    ok_flag[0] = ok_flag[1] = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint64_t tmo = cm.timeout_ns;
+
+  if (warp == 0) {
+    // ------------------------------------------------------ producer ---
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int8_t pend[STAGES];
+      for (int s = 0; s < STAGES; ++s) pend[s] = -1;
+      bool aborted = false;
+      bool first = true;
+      const uint64_t pol = policy_evict_last();
+      for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x) {
+        const int t = lv.is_top ? idx : lv.work[idx];
+        const Prob& P = prob_at(cm, find_prob(cm, t, 0));
+        int tm, tn;
+        raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+        const uint8_t* a_src = lv.a_level + P.a_img + (int64_t)tm * P.KB * IMG_BYTES;
+        const uint8_t* b_src = lv.b_level + P.b_img + (int64_t)tn * (BN / TILE_M) * P.KB * IMG_BYTES;
+        for (int kb = 0; kb < P.KB; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, abort_flag)) {
+            aborted = true;
+            break;
+          }
+          pend[stage] = -1;
+          const bool drop = (cm.debug_flags & 1) && first && kb == 0;
+          if (!drop) {
+            mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
+            const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+            for (int pl = 0; pl < PLANES; ++pl) {
+              const uint32_t base = sa + pl * (A_BYTES + B_BYTES);
+              bulk_g2s_hint(base, a_src + pl * P.a_plane + (int64_t)kb * IMG_BYTES, IMG_BYTES,
+                            &full[stage], pol);
+#pragma unroll
+              for (int h = 0; h < BN / TILE_M; ++h)
+                bulk_g2s_hint(base + A_BYTES + h * IMG_BYTES,
+                              b_src + pl * P.b_plane + ((int64_t)h * P.KB + kb) * IMG_BYTES,
+                              IMG_BYTES, &full[stage], pol);
+            }
+            pend[stage] = static_cast<int8_t>(phase);
+          }
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        first = false;
+      }
+      if (aborted) {
+        *abort_flag = 1;
+        set_status(cm.status, PN_ETIMEOUT);
+        // let every copy still in flight land before the CTA exits
+        for (int s = 0; s < STAGES; ++s)
+          if (pend[s] >= 0) mbar_wait_drain(&full[s], static_cast<uint32_t>(pend[s]), tmo);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ----------------------------------------------------- MMA issuer ---
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool aborted = false;
+      int it = 0;
+      for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x, ++it) {
+        const int t = lv.is_top ? idx : lv.work[idx];
+        const Prob& P = prob_at(cm, find_prob(cm, t, 0));
+        const int buf = it & 1;
+        if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)) {
+          aborted = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem_base + buf * BN;
+        for (int kb = 0; kb < P.KB; ++kb) {
+          if (!mbar_wait(&full[stage], phase, tmo, abort_flag)) {
+            aborted = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = sdesc_sw128(sa + kk * 32);
+            const uint64_t bd = sdesc_sw128(sb + kk * 32);
+            const uint32_t acc = (kb | kk) != 0;
+            if constexpr (PLANES == 1) {
+              mma_ss<KIND>(d, ad, bd, IDESC, acc);
+            } else {
+              const uint32_t sa_lo = sa + A_BYTES + B_BYTES, sb_lo = sa_lo + A_BYTES;
+              const uint64_t adl = sdesc_sw128(sa_lo + kk * 32);
+              const uint64_t bdl = sdesc_sw128(sb_lo + kk * 32);
+              mma_ss<KIND>(d, adl, bd, IDESC, acc);  // small terms first
+              mma_ss<KIND>(d, ad, bdl, IDESC, 1u);
+              mma_ss<KIND>(d, ad, bd, IDESC, 1u);
+            }
+          }
+          mma_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (aborted) break;
+        mma_commit(&acc_full[buf]);
+      }
+      if (aborted) {
+        *abort_flag = 1;
+        set_status(cm.status, PN_ETIMEOUT);
+        mma_commit(drain);  // completes once every issued MMA has finished
+        mbar_wait_drain(drain, 0, tmo);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------- epilogue ---
+    const int quarter = warp & 3;  // TMEM lanes quarter*32 .. +31
+    const int et = threadIdx.x - 64;
+    int it = 0;
+    for (int idx = blockIdx.x; idx < count; idx += gridDim.x, ++it) {
+      const int t = lv.is_top ? idx : lv.work[idx];
+      const int g = find_prob(cm, t, 0);
+      const Prob& P = prob_at(cm, g);
+      int tm, tn;
+      raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+      const int buf = it & 1;
+      if (et == 0) {
+        const bool ok = mbar_wait(&acc_full[buf], (it >> 1) & 1, tmo, abort_flag);
+        if (!ok) {
+          *abort_flag = 1;
+          set_status(cm.status, PN_ETIMEOUT);
+        }
+        ok_flag[buf] = ok ? 1 : 0;
+      }
+      bar_sync_named(1, 128);
+      if (!ok_flag[buf]) break;
+      tc_fence_after();
+
+      const int i = tm * TILE_M + quarter * 32 + lane;
+      const bool row_ok = i < P.M;
+      const float rs = row_ok ? cm.r[P.rc_r + i] : 0.0f;
+      const uint32_t* st_row = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS;
+      uint32_t res_all[CHUNKS];
+      bool any_left = false;
+#pragma unroll 1
+      for (int ch = 0; ch < CHUNKS; ++ch) {
+        uint32_t v[32];
+        tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + ch * 32, v);
+        tmem_ld_wait();
+        if (ch == CHUNKS - 1) {
+          tc_fence_before();
+          mbar_arrive(&acc_empty[buf]);
+        }
+        const int j0 = tn * BN + ch * 32;
+        uint32_t res = 0;
+        if (row_ok && j0 < P.N) {
+          if (!lv.is_top) res = st_row[ch];
+          const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
+          // entries to resolve at this p: not yet resolved, in range, and
+          // stable (or the smallest p, which takes whatever is left)
+          uint32_t cand = 0, near = 0;
+          float x[32];
+#pragma unroll
+          for (int e = 0; e < 32; ++e) {
+            const float S = __uint_as_float(v[e]) * cm.unscale;
+            x[e] = S;
+            if (e < jn && !((res >> e) & 1u)) {
+              if (S >= P.tau || lv.is_bottom) {
+                cand |= 1u << e;
+                if (S < 10.0f * P.tau) near |= 1u << e;
+              } else {
+                any_left = true;
+              }
+            }
+          }
+          if (cand) {
+            // (S^(p))^(1/p) for p = 2^plog: plog correctly rounded square roots
+            for (int s = 0; s < lv.plog; ++s) {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) x[e] = sqrtf(x[e]);
+            }
+            if (near) {
+              // within a decade of the underflow threshold: root in FP64
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                if ((near >> e) & 1u) {
+                  double dr = static_cast<double>(__uint_as_float(v[e]) * cm.unscale);
+                  for (int s = 0; s < lv.plog; ++s) dr = sqrt(dr);
+                  x[e] = static_cast<float>(dr);
+                }
+              }
+            }
+            const float* cs = cm.c + P.rc_c + j0;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) x[e] = rs * (e < jn ? __ldg(cs + e) : 0.0f) * x[e];
+            float* crow = P.C + (int64_t)i * P.ldc + j0;
+            uint8_t* prow = P.psel ? P.psel + (int64_t)i * P.ldaux + j0 : nullptr;
+            float* srow = P.Ssel ? P.Ssel + (int64_t)i * P.ldaux + j0 : nullptr;
+            if (cand == 0xffffffffu && P.vec_c) {
+#pragma unroll
+              for (int e = 0; e < 32; e += 4)
+                *reinterpret_cast<float4*>(crow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
+              if (srow) {
+#pragma unroll
+                for (int e = 0; e < 32; e += 4)
+                  *reinterpret_cast<float4*>(srow + e) = make_float4(
+                      __uint_as_float(v[e]) * cm.unscale, __uint_as_float(v[e + 1]) * cm.unscale,
+                      __uint_as_float(v[e + 2]) * cm.unscale, __uint_as_float(v[e + 3]) * cm.unscale);
+              }
+              if (prow) {
+                // p_sel = log2 p, with 0x80 where the smallest p took an unstable S
+                uint32_t w[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  uint32_t word = 0;
+#pragma unroll
+                  for (int b = 0; b < 4; ++b) {
+                    const int e = 4 * q + b;
+                    const bool st = __uint_as_float(v[e]) * cm.unscale >= P.tau;
+                    word |= static_cast<uint32_t>(lv.plog | (st ? 0 : 0x80)) << (8 * b);
+                  }
+                  w[q] = word;
+                }
+                *reinterpret_cast<uint4*>(prow) = make_uint4(w[0], w[1], w[2], w[3]);
+                *reinterpret_cast<uint4*>(prow + 16) = make_uint4(w[4], w[5], w[6], w[7]);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                if ((cand >> e) & 1u) {
+                  const float S = __uint_as_float(v[e]) * cm.unscale;
+                  crow[e] = x[e];
+                  if (srow) srow[e] = S;
+                  if (prow) prow[e] = static_cast<uint8_t>(lv.plog | (S >= P.tau ? 0 : 0x80));
+                }
+              }
+            }
+            res |= cand;
+          }
+        }
+        res_all[ch] = res;
+      }
+      if (!lv.is_bottom) {
+        const bool tile_left = bar_red_or(any_left, 2, 128);
+        if (tile_left) {
+          if (row_ok) {
+            uint32_t* st_w = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS;
+#pragma unroll
+            for (int ch = 0; ch < CHUNKS; ++ch)
+              if (tn * BN + ch * 32 < P.N) st_w[ch] = res_all[ch];
+          }
+          if (et == 0) {
+            const int slot = atomicAdd(lv.next_count, 1);
+            lv.next_work[slot] = t;
+            lv.next_rflag[P.tm_base + tm] = 1;
+            lv.next_cflag[P.tn_base + tn] = 1;
+          }
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+template <int MODE, int BN>
+inline int set_attr_t() {
+  static int done = 0;
+  if (done) return 0;
+  const cudaError_t e = cudaFuncSetAttribute(
+      k_gemm_level<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total(MODE, BN));
+  if (e == cudaSuccess) done = 1;
+  return e;
+}
+
+template <int MODE, int BN>
+inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
+  const int e = set_attr_t<MODE, BN>();
+  if (e) return e;
+  int grid = cm.total_tiles < num_sms ? cm.total_tiles : num_sms;
+  if (grid < 1) return 0;
+  k_gemm_level<MODE, BN><<<grid, GEMM_THREADS, smem_total(MODE, BN),
+                           static_cast<cudaStream_t>(stream)>>>(cm, lv);
+  return cudaGetLastError();
+}
+
+}  // namespace gemm
+}  // namespace pn

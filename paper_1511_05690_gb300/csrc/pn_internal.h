@@ -1,0 +1,147 @@
+// Internal types shared by the host runtime and the kernels of the p-norm
+// semiring library.  Not part of the public ABI (see include/pnorm.h).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/pnorm.h"
+
+namespace pn {
+
+constexpr int TILE_M = 128;         // output rows per tensor-core tile (MMA M)
+constexpr int IMG_BYTES = 16384;    // one operand tile image: 128 rows x 128 bytes
+constexpr int IMG_ROW_BYTES = 128;  // bytes of K per image row (one 128-byte swizzle row)
+constexpr int RASTER_GM = 8;        // tile rows per raster group (L2 reuse of B)
+
+// Operand formats of the tensor-core path (values equal pn_compute).
+enum Mode : int32_t { MODE_3XTF32 = 0, MODE_TF32 = 1, MODE_BF16 = 2, MODE_F16 = 3, MODE_E4M3 = 4 };
+
+__host__ __device__ constexpr int mode_elem_bytes(int mode) {
+  return mode == MODE_E4M3 ? 1 : (mode == MODE_BF16 || mode == MODE_F16) ? 2 : 4;
+}
+// K elements per 128-byte image row.
+__host__ __device__ constexpr int mode_bk(int mode) { return IMG_ROW_BYTES / mode_elem_bytes(mode); }
+__host__ __device__ constexpr int mode_planes(int mode) { return mode == MODE_3XTF32 ? 2 : 1; }
+// Exponent s of the power-of-two factor 2^s applied to powered operands.
+__host__ __device__ constexpr int mode_op_shift(int mode) {
+  return mode == MODE_F16 ? 15 : mode == MODE_E4M3 ? 8 : 0;
+}
+
+// One (x,max) product problem and where its pieces live in the workspace.
+struct Prob {
+  const float* A;
+  const float* B;
+  float* C;
+  uint8_t* psel;  // nullable
+  float* Ssel;    // nullable
+  int64_t lda, ldb, ldc, ldaux;
+  int32_t M, N, K;
+  int32_t KB;               // k-blocks of mode_bk(mode) elements
+  int32_t RBA, RBB;         // 128-row blocks of the A image / of the B^T image
+  int32_t tiles_m, tiles_n; // output tiles (128 x BN)
+  int32_t tile_base;        // first global tile id of this problem
+  int32_t xa_base, xb_base; // first global operand-tile id (RBA*KB / RBB*KB per problem)
+  int32_t tm_base, tn_base; // offsets into per-level row / column flag arrays
+  int32_t vec_c;            // C, p_sel, S_sel rows allow 16-byte vector stores
+  int32_t state_ld;         // 32-bit state words per row (tiles_n * BN / 32)
+  int64_t a_img, b_img;     // byte offsets inside one level's A / B image region
+  int64_t a_plane, b_plane; // bytes of one image plane (the 3xTF32 lo plane follows hi)
+  int64_t rc_r, rc_c;       // element offsets into the row / column scale arrays
+  int64_t state_off;        // word offset into the state array
+  float tau;
+  float pad0;
+  double tau_d;
+};
+
+// Everything a launch needs besides the per-level control.
+struct Common {
+  const Prob* probs;  // device table (grouped) or nullptr
+  Prob single;        // the problem when nprob == 1
+  int32_t nprob;
+  int32_t total_tiles, total_xa, total_xb;
+  int32_t total_tm, total_tn;  // tile rows / tile columns summed over problems
+  int32_t mode, BN, s_op, scaling;
+  float unscale;      // 2^(-2 s_op)
+  int32_t pad1;
+  uint32_t* rmax;     // per-row max of A (float bits)
+  uint32_t* cmax;     // per-column max of B
+  uint32_t* gmax;     // per-problem global max of A (2g) and B (2g+1)
+  float* r;           // row scales
+  float* c;           // column scales
+  uint32_t* state;    // resolved-entry bits of tiles that go to a lower level
+  int32_t* status;
+  uint64_t timeout_ns;
+  int32_t debug_flags;
+  int32_t n_levels;
+};
+
+// Control of one p level (one p of the family).
+struct Level {
+  int32_t q;          // index into P (0 = smallest p)
+  int32_t plog;       // log2 p
+  int32_t is_top;     // largest p: every tile, nothing resolved yet
+  int32_t is_bottom;  // smallest p: resolve every entry that is left
+  uint8_t* a_level;   // this level's A image region
+  uint8_t* b_level;   // this level's B image region
+  const int32_t* work;        // tiles of this level (ignored at the top)
+  const int32_t* work_count;
+  int32_t* next_work;         // tiles pushed to the next lower level
+  int32_t* next_count;
+  const uint8_t* rflag;       // this level's needed A row blocks (not at top)
+  const uint8_t* cflag;       // this level's needed B column tiles (not at top)
+  uint8_t* next_rflag;
+  uint8_t* next_cflag;
+};
+
+__host__ __device__ inline const Prob& prob_at(const Common& cm, int g) {
+  return cm.nprob == 1 ? cm.single : cm.probs[g];
+}
+
+// Problem index owning global id `id` given per-problem first ids (binary
+// search on the field selected by `which`: 0 tiles, 1 A operand tiles, 2 B
+// operand tiles, 3 tile rows, 4 tile columns).
+__host__ __device__ inline int find_prob(const Common& cm, int id, int which) {
+  if (cm.nprob == 1) return 0;
+  int lo = 0, hi = cm.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const Prob& p = cm.probs[mid];
+    const int base = which == 0   ? p.tile_base
+                     : which == 1 ? p.xa_base
+                     : which == 2 ? p.xb_base
+                     : which == 3 ? p.tm_base
+                                  : p.tn_base;
+    if (base <= id) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Local tile index -> (tile row, tile column), grouped raster order.
+__host__ __device__ inline void raster(int lt, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int group = RASTER_GM * tiles_n;
+  const int g = lt / group;
+  const int first_m = g * RASTER_GM;
+  const int gm = (tiles_m - first_m) < RASTER_GM ? (tiles_m - first_m) : RASTER_GM;
+  const int local = lt - g * group;
+  tm = first_m + local % gm;
+  tn = local / gm;
+}
+
+// ------------------------------------------------------------ launchers ---
+// All return a cudaError_t value as int (0 = success).
+int launch_maxes(const Common& cm, void* stream);
+int launch_power_a(const Common& cm, const Level& lv, void* stream);
+int launch_power_b(const Common& cm, const Level& lv, void* stream);
+int launch_gemm_level(const Common& cm, const Level& lv, int num_sms, void* stream);
+int launch_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                 int64_t ldb, float* C, int64_t ldc, int semiring, int variant, void* stream);
+int launch_fill_empty(const Common& cm, int plog0, void* stream);
+int launch_apsp_init(int64_t n, const float* W, int64_t ldw, float* X, int diag, int32_t* status,
+                     void* stream);
+int launch_diag_reset(int64_t n, float* X, int64_t ldx, void* stream);
+int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd,
+                      void* stream);
+int gemm_smem_bytes(int mode, int BN);
+int gemm_stages(int mode, int BN);
+
+}  // namespace pn

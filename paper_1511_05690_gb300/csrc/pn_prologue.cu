@@ -1,0 +1,474 @@
+// Prologue of the p-norm product (Alg. 5, first loop, with the scaled H' of
+// Sec. 2.1): per-row maxima of A and per-column maxima of B, power-of-two
+// scales, and the scaled operands raised to the power p of one level and cast
+// to the tensor-core operand format.
+//
+// Operands are written as "tile images": for every block of 128 output rows
+// (rows of A, or columns of B) and every 128 bytes of K, a 16 KB block holding
+// exactly the shared-memory image the tensor cores read (K-major, 128-byte
+// swizzle).  The GEMM then moves each tile with one 1-D bulk copy.  Rows past
+// M (N) and K past K are zero in the image, so the GEMM needs no tail logic.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "pn_device.cuh"
+
+namespace pn {
+
+namespace {
+
+constexpr int PRO_THREADS = 256;
+
+__device__ __forceinline__ bool in_domain(float x) {
+  // R+ with every power-of-two scale representable: 0 <= x <= 2^127.
+  return x >= 0.0f && x <= 1.7014118346046923e38f;
+}
+
+__device__ __forceinline__ float nonneg_bits_max(float m) { return m > 0.0f ? m : 0.0f; }
+
+// ------------------------------------------------------------- maxima ---
+// One block per operand tile (128 rows x BK of K): partial maxima, then one
+// atomicMax per row (A) or column (B).  Non-negative floats order like their
+// bit patterns, so the maxima are kept as uint32 bits.
+__global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ Common cm) {
+  __shared__ float red[2][128];
+  __shared__ float blk_max[PRO_THREADS / 32];
+  const int bk = mode_bk(cm.mode);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int id = blockIdx.x;
+  const bool is_b = id >= cm.total_xa;
+  if (is_b) id -= cm.total_xa;
+  const int g = find_prob(cm, id, is_b ? 2 : 1);
+  const Prob& P = prob_at(cm, g);
+  const int local = id - (is_b ? P.xb_base : P.xa_base);
+  const int rb = local / P.KB, kb = local - rb * P.KB;
+  const int k0 = kb * bk;
+  bool bad = false;
+  float bmax = 0.0f;
+  if (!is_b) {
+    // rows rb*128 + warp*16 .. +15, each row read by the whole warp
+    for (int rr = 0; rr < 16; ++rr) {
+      const int row = rb * TILE_M + warp * 16 + rr;
+      float m = 0.0f;
+      if (row < P.M) {
+        const float* src = P.A + (int64_t)row * P.lda;
+        for (int kk = lane; kk < bk; kk += 32) {
+          const int k = k0 + kk;
+          if (k < P.K) {
+            const float x = __ldg(src + k);
+            bad |= !in_domain(x);
+            m = fmaxf(m, x);
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      m = nonneg_bits_max(m);
+      if (lane == 0 && row < P.M && m > 0.0f)
+        atomicMax(cm.rmax + P.rc_r + row, __float_as_uint(m));
+      bmax = fmaxf(bmax, m);
+    }
+  } else {
+    // columns n = rb*128 + (tid & 127); two halves of the K range
+    const int n = rb * TILE_M + (tid & 127);
+    float m = 0.0f;
+    if (n < P.N) {
+      for (int kk = tid >> 7; kk < bk; kk += 2) {
+        const int k = k0 + kk;
+        if (k < P.K) {
+          const float x = __ldg(P.B + (int64_t)k * P.ldb + n);
+          bad |= !in_domain(x);
+          m = fmaxf(m, x);
+        }
+      }
+    }
+    red[tid >> 7][tid & 127] = nonneg_bits_max(m);
+    __syncthreads();
+    if (tid < 128) {
+      m = fmaxf(red[0][tid], red[1][tid]);
+      if (n < P.N && m > 0.0f) atomicMax(cm.cmax + P.rc_c + n, __float_as_uint(m));
+    }
+    bmax = m;
+    __syncthreads();
+  }
+  if (__syncthreads_or(bad) && tid == 0) set_status(cm.status, PN_EDOMAIN);
+  if (cm.scaling == 1) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    if (lane == 0) blk_max[warp] = bmax;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.0f;
+      for (int w = 0; w < PRO_THREADS / 32; ++w) m = fmaxf(m, blk_max[w]);
+      if (m > 0.0f) atomicMax(cm.gmax + 2 * g + (is_b ? 1 : 0), __float_as_uint(m));
+    }
+  }
+}
+
+__device__ __forceinline__ float scale_of(const Common& cm, const uint32_t* mx, int64_t idx,
+                                          int g, int which) {
+  if (cm.scaling == 0) return 1.0f;
+  const uint32_t bits = cm.scaling == 1 ? cm.gmax[2 * g + which] : mx[idx];
+  return pow2_ceil_f(__uint_as_float(bits));
+}
+
+// x^(2^plog) by repeated squaring (each step one correctly rounded multiply).
+__device__ __forceinline__ float pow2k(float x, int plog) {
+#pragma unroll 1
+  for (int t = 0; t < plog; ++t) x = x * x;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Packs 16 bytes of operand data from EPC powered, shifted values.
+template <int MODE>
+struct Packer;
+
+template <>
+struct Packer<MODE_BF16> {
+  static constexpr int EPC = 8;
+  __device__ static void pack(const float (&v)[EPC], uint4& hi, uint4&) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    hi = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+template <>
+struct Packer<MODE_F16> {
+  static constexpr int EPC = 8;
+  __device__ static void pack(const float (&v)[EPC], uint4& hi, uint4&) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2 h = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+      w[i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+    hi = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+template <>
+struct Packer<MODE_E4M3> {
+  static constexpr int EPC = 16;
+  __device__ static void pack(const float (&v)[EPC], uint4& hi, uint4&) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const __nv_fp8x2_storage_t lo2 =
+          __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i], v[4 * i + 1]), __NV_SATFINITE, __NV_E4M3);
+      const __nv_fp8x2_storage_t hi2 = __nv_cvt_float2_to_fp8x2(
+          make_float2(v[4 * i + 2], v[4 * i + 3]), __NV_SATFINITE, __NV_E4M3);
+      w[i] = static_cast<uint32_t>(lo2) | (static_cast<uint32_t>(hi2) << 16);
+    }
+    hi = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+};
+
+template <>
+struct Packer<MODE_TF32> {
+  static constexpr int EPC = 4;
+  __device__ static void pack(const float (&v)[EPC], uint4& hi, uint4&) {
+    hi = make_uint4(tf32_bits(v[0]), tf32_bits(v[1]), tf32_bits(v[2]), tf32_bits(v[3]));
+  }
+};
+
+template <>
+struct Packer<MODE_3XTF32> {
+  static constexpr int EPC = 4;
+  __device__ static void pack(const float (&v)[EPC], uint4& hi, uint4& lo) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      h[i] = tf32_bits(v[i]);
+      l[i] = tf32_bits(v[i] - __uint_as_float(h[i]));  // exact difference, then rounded
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+};
+
+// ----------------------------------------------------------- A images ---
+template <int MODE>
+__device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, int g,
+                                             const Prob& P, int rb, int kb) {
+  using PK = Packer<MODE>;
+  constexpr int EPC = PK::EPC;
+  constexpr int BK = mode_bk(MODE);
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
+  const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+#pragma unroll 1
+  for (int u = 0; u < 4; ++u) {
+    const int ch = threadIdx.x + PRO_THREADS * u;
+    const int rr = ch >> 3, cc = ch & 7;
+    const int row = rb * TILE_M + rr;
+    const int k0 = kb * BK + cc * EPC;
+    float v[EPC];
+    if (row < P.M) {
+      const float rs = scale_of(cm, cm.rmax, P.rc_r + row, g, 0);
+      if (lv.is_top && kb == 0 && cc == 0) cm.r[P.rc_r + row] = rs;
+      const float* src = P.A + (int64_t)row * P.lda + k0;
+      if (vec && k0 + EPC <= P.K) {
+#pragma unroll
+        for (int e = 0; e < EPC; e += 4) {
+          const float4 t = __ldg(reinterpret_cast<const float4*>(src + e));
+          v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) v[e] = (k0 + e < P.K) ? __ldg(src + e) : 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[e] = pow2k(v[e] / rs, lv.plog) * opscale;
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[e] = 0.0f;
+    }
+    uint4 hi, lo;
+    PK::pack(v, hi, lo);
+    const uint32_t off = sw128_offset(rr, cc * 16);
+    *reinterpret_cast<uint4*>(dst + off) = hi;
+    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
+  }
+}
+
+// Top level: one block per operand tile.  Lower levels: one block per tile
+// row, skipped unless a pushed output tile needs that row block.
+template <int MODE>
+__global__ void __launch_bounds__(PRO_THREADS)
+    k_power_a(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+  if (lv.is_top) {
+    const int id = blockIdx.x;
+    const int g = find_prob(cm, id, 1);
+    const Prob& P = prob_at(cm, g);
+    const int local = id - P.xa_base;
+    const int rb = local / P.KB;
+    power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
+  } else {
+    const int id = blockIdx.x;
+    if (!lv.rflag[id]) return;
+    const int g = find_prob(cm, id, 3);
+    const Prob& P = prob_at(cm, g);
+    const int rb = id - P.tm_base;
+    for (int kb = 0; kb < P.KB; ++kb) power_a_tile<MODE>(cm, lv, g, P, rb, kb);
+  }
+}
+
+// ----------------------------------------------------------- B images ---
+// The B image holds B^T: image row n, K along the 128-byte row.  The tile of
+// B (BK rows of K x 128 columns) is staged in shared memory and transposed.
+template <int MODE>
+__device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, int g,
+                                             const Prob& P, int rb, int kb, float* stile) {
+  using PK = Packer<MODE>;
+  constexpr int EPC = PK::EPC;
+  constexpr int BK = mode_bk(MODE);
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  __syncthreads();  // stile reuse across consecutive tiles
+  {
+    const int nl = threadIdx.x & 127;
+    const int n = rb * TILE_M + nl;
+    float cs = 1.0f;
+    if (n < P.N) {
+      cs = scale_of(cm, cm.cmax, P.rc_c + n, g, 1);
+      if (lv.is_top && kb == 0 && threadIdx.x < 128) cm.c[P.rc_c + n] = cs;
+    }
+#pragma unroll 4
+    for (int kk = threadIdx.x >> 7; kk < BK; kk += 2) {
+      const int k = kb * BK + kk;
+      float x = 0.0f;
+      if (n < P.N && k < P.K) x = __ldg(P.B + (int64_t)k * P.ldb + n) / cs;
+      stile[kk * 129 + nl] = x;
+    }
+  }
+  __syncthreads();
+  uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
+#pragma unroll 1
+  for (int u = 0; u < 4; ++u) {
+    const int ch = threadIdx.x + PRO_THREADS * u;
+    const int nr = ch >> 3, cc = ch & 7;
+    float v[EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) v[e] = pow2k(stile[(cc * EPC + e) * 129 + nr], lv.plog) * opscale;
+    uint4 hi, lo;
+    PK::pack(v, hi, lo);
+    const uint32_t off = sw128_offset(nr, cc * 16);
+    *reinterpret_cast<uint4*>(dst + off) = hi;
+    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.b_plane + off) = lo;
+  }
+}
+
+// Top level: one block per operand tile.  Lower levels: one block per output
+// tile column, skipped unless a pushed output tile needs it.
+template <int MODE>
+__global__ void __launch_bounds__(PRO_THREADS)
+    k_power_b(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+  extern __shared__ float stile[];  // [BK][129]
+  if (lv.is_top) {
+    const int id = blockIdx.x;
+    const int g = find_prob(cm, id, 2);
+    const Prob& P = prob_at(cm, g);
+    const int local = id - P.xb_base;
+    const int rb = local / P.KB;
+    power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
+  } else {
+    const int id = blockIdx.x;
+    if (!lv.cflag[id]) return;
+    const int g = find_prob(cm, id, 4);
+    const Prob& P = prob_at(cm, g);
+    const int per_tile = cm.BN / TILE_M;
+    const int tn = id - P.tn_base;
+    for (int h = 0; h < per_tile; ++h)
+      for (int kb = 0; kb < P.KB; ++kb)
+        power_b_tile<MODE>(cm, lv, g, P, tn * per_tile + h, kb, stile);
+  }
+}
+
+// ------------------------------------------------------------ K == 0 ---
+// Empty contraction: every S^(p) is 0, so p* is the smallest p (unstable)
+// and the estimate is the exact empty max, 0.
+__global__ void k_fill_empty(const __grid_constant__ Common cm, int plog0) {
+  const Prob& P = cm.single;
+  const int64_t total = (int64_t)P.M * P.N;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / P.N, j = e - i * P.N;
+    P.C[i * P.ldc + j] = 0.0f;
+    if (P.psel) P.psel[i * P.ldaux + j] = static_cast<uint8_t>(0x80 | plog0);
+    if (P.Ssel) P.Ssel[i * P.ldaux + j] = 0.0f;
+  }
+}
+
+// ---------------------------------------------------------------- APSP ---
+// x = exp(-w) (Sec. 2.2), +inf -> 0; weights must be >= 0 or +inf.
+__global__ void k_apsp_init(int64_t n, const float* __restrict__ W, int64_t ldw,
+                            float* __restrict__ X, int diag, int32_t* status) {
+  const int64_t total = n * n;
+  bool bad = false;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const float w = W[i * ldw + j];
+    bad |= !(w >= 0.0f);  // negative or NaN
+    float x = (w == INFINITY) ? 0.0f : expf(-w);
+    if (diag && i == j) x = 1.0f;
+    X[e] = x;
+  }
+  if (bad) set_status(status, PN_EDOMAIN);
+}
+
+__global__ void k_diag_reset(int64_t n, float* X, int64_t ldx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    X[i * ldx + i] = 1.0f;
+}
+
+// d = -log x; x = 0 (no path) -> +inf.
+__global__ void k_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd) {
+  const int64_t total = n * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    const float x = X[i * ldx + j];
+    D[i * ldd + j] = x > 0.0f ? -logf(x) : INFINITY;
+  }
+}
+
+template <int MODE>
+int launch_power_b_t(const Common& cm, const Level& lv, void* stream) {
+  const int smem = mode_bk(MODE) * 129 * 4;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_power_b<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int grid = lv.is_top ? cm.total_xb : cm.total_tn;
+  k_power_b<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(cm, lv);
+  return cudaGetLastError();
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return static_cast<int>(b > 0 ? b : 1);
+}
+
+}  // namespace
+
+int launch_maxes(const Common& cm, void* stream) {
+  const int blocks = cm.total_xa + cm.total_xb;
+  if (blocks <= 0) return 0;
+  k_maxes<<<blocks, PRO_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(cm);
+  return cudaGetLastError();
+}
+
+int launch_power_a(const Common& cm, const Level& lv, void* stream) {
+  if (cm.total_xa <= 0) return 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int grid = lv.is_top ? cm.total_xa : cm.total_tm;
+  switch (cm.mode) {
+    case MODE_3XTF32: k_power_a<MODE_3XTF32><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    case MODE_TF32: k_power_a<MODE_TF32><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    case MODE_BF16: k_power_a<MODE_BF16><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    case MODE_F16: k_power_a<MODE_F16><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    case MODE_E4M3: k_power_a<MODE_E4M3><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int launch_power_b(const Common& cm, const Level& lv, void* stream) {
+  if (cm.total_xb <= 0) return 0;
+  switch (cm.mode) {
+    case MODE_3XTF32: return launch_power_b_t<MODE_3XTF32>(cm, lv, stream);
+    case MODE_TF32: return launch_power_b_t<MODE_TF32>(cm, lv, stream);
+    case MODE_BF16: return launch_power_b_t<MODE_BF16>(cm, lv, stream);
+    case MODE_F16: return launch_power_b_t<MODE_F16>(cm, lv, stream);
+    case MODE_E4M3: return launch_power_b_t<MODE_E4M3>(cm, lv, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int launch_fill_empty(const Common& cm, int plog0, void* stream) {
+  const int64_t total = (int64_t)cm.single.M * cm.single.N;
+  if (total <= 0) return 0;
+  k_fill_empty<<<grid_for(total, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(cm, plog0);
+  return cudaGetLastError();
+}
+
+int launch_apsp_init(int64_t n, const float* W, int64_t ldw, float* X, int diag, int32_t* status,
+                     void* stream) {
+  if (n <= 0) return 0;
+  k_apsp_init<<<grid_for(n * n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, W, ldw, X,
+                                                                                 diag, status);
+  return cudaGetLastError();
+}
+
+int launch_diag_reset(int64_t n, float* X, int64_t ldx, void* stream) {
+  if (n <= 0) return 0;
+  k_diag_reset<<<grid_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, X, ldx);
+  return cudaGetLastError();
+}
+
+int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd,
+                      void* stream) {
+  if (n <= 0) return 0;
+  k_apsp_final<<<grid_for(n * n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, X, ldx, D,
+                                                                                  ldd);
+  return cudaGetLastError();
+}
+
+}  // namespace pn

@@ -1,0 +1,104 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every symbol include/pnorm.h declares, and its host logic (options, status
+strings, workspace sizes, defaults, argument validation) behaves as documented.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def binding():
+    from paper_1511_05690_gb300 import build
+    build.build()
+    from paper_1511_05690_gb300 import _binding
+    _binding.load()
+    return _binding
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^PN_API\s+[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol(binding):
+    declared = _declared_symbols()
+    assert len(declared) >= 15
+    lib = binding.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(binding.EXPORTS)
+
+
+def test_status_strings(binding):
+    lib = binding.load()
+    for code in range(8):
+        assert lib.pn_status_string(code).decode().startswith("PN_")
+    assert lib.pn_status_string(99) == b"unknown pn_status"
+
+
+def test_default_opts(binding):
+    o = binding.make_opts()
+    assert o.n_p == 7 and list(o.p_log2[:7]) == list(range(7))
+    assert o.compute == binding.PN_BF16 and o.scaling == 2 and o.diag_policy == 1
+
+
+def test_default_tau_matches_oracle_reading(binding, orc):
+    lib = binding.load()
+    for K in (1, 256, 4096, 16384):
+        for mode in range(5):
+            assert lib.pn_default_tau(K, mode) == orc.default_tau(K, mode)
+    assert lib.pn_default_tau(10, 9) < 0
+
+
+def test_workspace_sizes(binding):
+    lib = binding.load()
+    o = binding.make_opts(compute="bf16")
+    s1 = lib.pn_workspace_size(1000, 1000, 1000, ctypes.byref(o))
+    s2 = lib.pn_workspace_size(2000, 1000, 1000, ctypes.byref(o))
+    assert 0 < s1 < s2 and s1 % 256 == 0
+    # the images dominate: |P| levels x (A + B) x bytes per element
+    assert s1 >= 7 * (1024 * 1024 + 1024 * 1024) * 2
+    o32 = binding.make_opts(compute="f32")
+    assert lib.pn_workspace_size(1000, 1000, 1000, ctypes.byref(o32)) > 3 * s1
+    bad = binding.make_opts()
+    bad.n_p = 17
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    bad = binding.make_opts()
+    bad.p_log2[3] = bad.p_log2[2]
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    assert lib.pn_workspace_size(-1, 10, 10, ctypes.byref(o)) == 0
+    assert lib.pn_apsp_workspace_size(100, ctypes.byref(o)) > lib.pn_workspace_size(
+        100, 100, 100, ctypes.byref(o))
+
+
+def test_argument_validation_before_any_device_call(binding):
+    """Invalid options and shapes are rejected on the host (PN_EINVAL) before the
+    library looks for a device; empty problems succeed without touching it."""
+    lib = binding.load()
+    o = binding.make_opts()
+    bad = binding.make_opts()
+    bad.compute = 9
+    z = None
+    assert lib.maxprod_pnorm(4, 4, 4, z, 4, z, 4, z, 4, z, z, ctypes.byref(bad), z, 0, z) == 1
+    assert lib.maxprod_pnorm(4, 4, 4, 16, 2, 16, 4, 16, 4, z, z, ctypes.byref(o), z, 0, z) == 1
+    assert lib.maxprod_pnorm(0, 4, 4, z, 4, z, 4, z, 4, z, z, ctypes.byref(o), z, 0, z) == 0
+    assert lib.maxprod_exact(4, 4, 4, z, 4, z, 4, z, 4, 5, z) == 1
+    assert lib.maxprod_exact(0, 4, 4, z, 4, z, 4, z, 4, 0, z) == 0
+    assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
+    assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1
+
+
+def test_missing_library_fails_loudly(binding, monkeypatch):
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding, "LIB_PATH", "/nonexistent/libpnorm.so")
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load()
