@@ -1,0 +1,424 @@
+#!/usr/bin/env python3
+"""Benchmark of the p-norm (x,max) semiring product on GB300.
+
+Metric: effective semiring Gop/s, counted as M*N*K (n^3) per product, of the
+p-norm tensor-core estimate, next to the exact CUDA-core product and the FP64
+CPU oracle, with the estimate's error stated against the exact product.
+
+Workload (default): one square product, n = 16384, entries exp(-Exponential(4))
+(= U^(1/4)), BF16 powered operands, P = {1, 2, ..., 64}.  A step is one full
+call: maxima and scales, powered operand images, the tensor-core level
+launches with the fused stable-p epilogue, writing C and p_sel.  Inputs (1 GiB
+each) are larger than L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch under torch.distributed.run; every rank computes its own
+product (independent replicas, weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--compute", default="bf16")
+    ap.add_argument("--tile-n", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--err-samples", type=int, default=4096)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-exact", action="store_true")
+    return ap.parse_args()
+
+
+P_LOG2 = list(range(7))
+LAUNCHES_PER_STEP = 1 + 3 * len(P_LOG2)  # maxima + (A images, B images, GEMM) per level
+
+
+def workload_name(n, compute):
+    return (f"maxprod_pnorm n={n} {compute} P={{1..64}} entries exp(-Exp(4)); "
+            f"exact CUDA-core (x,max) product as the comparison")
+
+
+# ---------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """Samples nvidia-smi (SM clock, throttle reasons) every 100 ms; only the
+    samples whose timestamps fall inside the timed region are reported (the
+    nearest one if the region is shorter than the sampling period)."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.idx), "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def mark_begin(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        from datetime import datetime
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        samples = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    samples.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        inside = [x for x in samples if self.t0 <= x[0] <= self.t1]
+        how = "inside timed region"
+        if not inside:
+            mid = 0.5 * (self.t0 + self.t1)
+            inside = [min(samples, key=lambda x: abs(x[0] - mid))]
+            how = "nearest sample (timed region shorter than the 100 ms period)"
+        reasons = set()
+        for x in inside:
+            for nm, val in zip(self.NAMES, x[3]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(x[1] for x in inside),
+                "sm_max_mhz": max(x[2] for x in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "sampling": how}
+
+
+# --------------------------------------------------------------- helpers ---
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def gemm_peak_tflops(compute, peaks):
+    """Dense tensor peak of the operand format: the measured BF16 figure (sustained:
+    the kernel runs inside a seconds-long loop) times the nominal format ratio."""
+    ratio = {"bf16": 1.0, "f16": 1.0, "tf32": 0.5, "f32": 0.5 / 3, "e4m3": 2.0}[compute]
+    return peaks["bf16_tflops_sustained"] * ratio
+
+
+def traffic_from_profile(compute):
+    """DRAM bytes per top-level GEMM launch recorded by ncu in profiles/, if the
+    kernel source is unchanged since the capture (else None)."""
+    src = os.path.join(ROOT, "paper_1511_05690_gb300", "csrc", "pn_gemm_kernel.cuh")
+    prof = os.path.join(ROOT, "profiles", f"gemm_level_{compute}_n16384.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(prof).read()
+    except OSError:
+        return None
+    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != sha:
+        return None
+    return float(m_b.group(1))
+
+
+def cpu_baseline(A_h, B_h, n, seconds, oracle):
+    """The FP64 oracle (exact max + every p-sum) on sampled output entries,
+    sized to about `seconds` of CPU time; Gop/s counted as K per entry."""
+    g = workloads.rng(None, 99)
+    rows = np.unique(g.integers(0, n, 64))
+    A64 = A_h[rows].astype(np.float64)  # only sampled rows are read
+    B64 = B_h.astype(np.float64)
+    r = oracle.row_scales(A64)
+    c = oracle.col_scales(B64)
+
+    def run(E):
+        loc = g.integers(0, len(rows), E)
+        jj = g.integers(0, n, E)
+        t0 = time.perf_counter()
+        oracle.entries(A64, B64, loc, jj, P_LOG2, r, c)
+        return time.perf_counter() - t0
+
+    E0 = 64
+    t0 = run(E0)
+    E = max(E0, int(E0 * seconds / max(t0, 1e-3)))
+    t = run(E)
+    return {"value": E * n / t / 1e9, "unit": "Gop/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{E} random output entries of the n={n} product (exact max and "
+                      f"the {len(P_LOG2)} p-sums each, FP64); {t:.1f} s"}
+
+
+# ----------------------------------------------------------------- ours ---
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1511_05690_gb300 as pn
+
+    n = args.n
+    A_h, B_h = workloads.wide_range_pair(n, n, n)
+    A = torch.from_numpy(A_h).cuda()
+    B = torch.from_numpy(B_h).cuda()
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev0=None, ev1=None):
+        return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n,
+                                out=C, want_ssel=False, check=False, ev_begin=ev0, ev_end=ev1)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    pn.check_device_status(A.device, "warmup")
+    K = args.steps
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)]
+    t_begin, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)  # let the sampler come up before the timed region
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_begin()
+    t_begin.record(stream)
+    for s in range(K):
+        _, psel, _ = step(*gev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    pn.check_device_status(A.device, "timed steps")
+    ms = t_begin.elapsed_time(t_end)
+    gemm_ms = [a.elapsed_time(b) for a, b in gev]
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ops = float(n) ** 3
+    value = world * ops * K / (ms_max / 1e3) / 1e9
+
+    # error of the estimate at sampled entries: vs exact and vs the FP64 p-norm
+    err = None
+    if rank == 0 and args.err_samples > 0:
+        import oracle
+        ii, jj = workloads.wide_range_entries(n, args.err_samples)
+        rows = np.unique(ii)
+        A64 = A_h[rows].astype(np.float64)
+        B64 = B_h.astype(np.float64)
+        r = np.ones(n)
+        r[rows] = oracle.row_scales(A64)
+        c = oracle.col_scales(B64)
+        loc = np.searchsorted(rows, ii)
+        exact, S = oracle.entries(A64, B64, loc, jj, P_LOG2, r[rows], c)
+        del B64
+        ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
+        Cs = C[ti, tj].double().cpu().numpy()
+        ps = (psel[ti, tj].cpu().numpy() & 0x7F).astype(np.int64)
+        S_at = S[np.arange(len(ii)), ps]
+        pn_ref = r[ii] * c[jj] * np.power(S_at, 1.0 / 2.0 ** ps)
+        e_exact = np.abs(Cs - exact) / exact
+        e_orc = np.abs(Cs - pn_ref) / pn_ref
+        err = {"samples": int(len(ii)), "max_rel_vs_exact": float(e_exact.max()),
+               "median_rel_vs_exact": float(np.median(e_exact)),
+               "max_rel_vs_fp64_pnorm": float(e_orc.max()),
+               "median_rel_vs_fp64_pnorm": float(np.median(e_orc)),
+               "p_sel_histogram": {str(2 ** int(k)): int(v) for k, v in
+                                   zip(*np.unique(ps, return_counts=True))}}
+
+    # exact CUDA-core product of the same inputs, for the comparison in the metric
+    exact_info = None
+    if rank == 0 and not args.no_exact:
+        E = torch.empty_like(C)
+        pn.maxprod_exact(A, B, out=E)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pn.maxprod_exact(A, B, out=E)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ems = e0.elapsed_time(e1)
+        exact_info = {"ms": ems, "gops": ops / (ems / 1e3) / 1e9,
+                      "speedup_of_pnorm": (ops / (ms_max / K / 1e3) / 1e9) / (ops / (ems / 1e3) / 1e9)}
+        del E
+
+    # end to end through the public API from pinned host buffers
+    Ah = torch.from_numpy(A_h).pin_memory()
+    Bh = torch.from_numpy(B_h).pin_memory()
+    Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    Ad, Bd = torch.empty_like(A), torch.empty_like(B)
+
+    def e2e_step():
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        pn.maxprod_pnorm(Ad, Bd, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n, out=C,
+                         want_psel=False, want_ssel=False, check=False)
+        Ch.copy_(C, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    KE = max(1, args.e2e_steps)
+    if world > 1:
+        dist.barrier()
+    x0.record(stream)
+    for _ in range(KE):
+        e2e_step()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = torch.tensor([x0.elapsed_time(x1) / KE], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = world * ops / (float(e2e_ms.item()) / 1e3) / 1e9
+    pn.check_device_status(A.device, "e2e")
+
+    peaks, peak_src = measured_peaks()
+    gemm_avg = statistics.mean(gemm_ms)
+    achieved = 2.0 * ops / (gemm_avg / 1e3) / 1e12
+    peak = gemm_peak_tflops(args.compute, peaks)
+    line = {
+        "metric": "Effective semiring Gop/s (n^3/s): p-norm TC vs exact GPU kernel at stated err",
+        "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
+        "config": {"workload": workload_name(n, args.compute), "n": n, "p_log2": P_LOG2,
+                   "outputs": "C and p_sel", "l2": "inputs larger than L2 (1 GiB each), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * n,
+                "d2h_bytes_per_step": 4 * n * n, "steps": KE},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(args.compute),
+                     "kernel": "k_gemm_level (largest p), 2*n^3 FLOP per launch",
+                     "launch_ms": gemm_avg,
+                     "peak_source": f"{peak_src} bf16_tflops_sustained x format ratio"},
+        "clocks": clk,
+        "gpu_launches": LAUNCHES_PER_STEP * K,
+        "err": err,
+        "exact_kernel": exact_info,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        line["cpu_baseline"] = cpu_baseline(A_h, B_h, n, args.cpu_seconds, oracle)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ reference ---
+def run_reference(args):
+    """The FP64 oracle as the reference arm, on a bounded sample per step."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    g = workloads.rng(None, 98)
+    rows = np.unique(g.integers(0, n, 16))
+    # only the sampled rows of A and all of B are needed: draw the full pair once
+    A_h, B_h = workloads.wide_range_pair(n, n, n)
+    A64 = A_h[rows].astype(np.float64)
+    B64 = B_h.astype(np.float64)
+    r = oracle.row_scales(A64)
+    c = oracle.col_scales(B64)
+    per_step_s = 4.0
+
+    def run(E):
+        ii = g.integers(0, len(rows), E)
+        jj = g.integers(0, n, E)
+        t0 = time.perf_counter()
+        oracle.entries(A64, B64, ii, jj, P_LOG2, r, c)
+        return time.perf_counter() - t0
+
+    t0 = run(32)
+    E = max(32, int(32 * per_step_s / max(t0, 1e-3)))
+    for _ in range(max(args.warmup, 0)):
+        run(max(8, E // 8))
+    t_total = 0.0
+    for _ in range(args.steps):
+        t_total += run(E)
+    value = args.steps * E * n / t_total / 1e9
+    sample = (f"{E} random output entries per step of the n={n} product (exact max and "
+              f"{len(P_LOG2)} p-sums each, FP64)")
+    line = {
+        "metric": "Effective semiring Gop/s (n^3/s): p-norm TC vs exact GPU kernel at stated err",
+        "impl": "reference", "value": value, "unit": "Gop/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(n, args.compute), "n": n, "p_log2": P_LOG2},
+        "cpu_baseline": {"value": value, "unit": "Gop/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Gop/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,15 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _event(ev):
+    """Raw cudaEvent_t of a torch.cuda.Event (created on first use)."""
+    if ev is None:
+        return None
+    if not ev.cuda_event:
+        ev.record()  # torch creates the underlying event lazily
+    return ev.cuda_event
+
+
 def _mat(x: torch.Tensor, name: str) -> torch.Tensor:
     if not isinstance(x, torch.Tensor) or x.dim() != 2:
         raise ValueError(f"{name} must be a 2-D tensor")
@@ -112,9 +121,8 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
     psel = torch.empty((M, N), dtype=torch.uint8, device=dev) if want_psel else None
     ssel = torch.empty((M, N), dtype=torch.float32, device=dev) if want_ssel else None
     st = status_word(dev)
-    o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(),
-                  ev_begin.cuda_event if ev_begin is not None else None,
-                  ev_end.cuda_event if ev_end is not None else None, timeout_ns, debug_flags)
+    o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(), _event(ev_begin),
+                  _event(ev_end), timeout_ns, debug_flags)
     L = lib()
     need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
     if need == 0 and M * N > 0:
@@ -163,8 +171,7 @@ def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), comput
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=dev)
     st = status_word(dev)
     o = make_opts(p_log2, compute, tau, scaling, diag_policy, tile_n, st.data_ptr(),
-                  ev_begin.cuda_event if ev_begin is not None else None,
-                  ev_end.cuda_event if ev_end is not None else None)
+                  _event(ev_begin), _event(ev_end))
     L = lib()
     need = L.pn_apsp_workspace_size(n, ctypes.byref(o))
     if need == 0 and n > 0:

@@ -152,6 +152,9 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   P.KB = L.KB; P.RBA = L.RBA; P.RBB = L.RBB;
   P.tiles_m = L.tiles_m; P.tiles_n = L.tiles_n;
   P.tile_base = 0; P.xa_base = 0; P.xb_base = 0; P.tm_base = 0; P.tn_base = 0;
+  P.KMA = static_cast<int32_t>(ceil_div(K, MAXSEG_A));
+  P.KMB = static_cast<int32_t>(ceil_div(K, MAXSEG_B));
+  P.ma_base = 0; P.mb_base = 0;
   const bool vc = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
                   ((N & 15) == 0) &&
                   (!p_sel || (reinterpret_cast<uintptr_t>(p_sel) & 15) == 0) &&
@@ -172,6 +175,8 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.total_xb = L.RBB * L.KB;
   cm.total_tm = L.tiles_m;
   cm.total_tn = L.tiles_n;
+  cm.total_ma = L.RBA * P.KMA;
+  cm.total_mb = L.RBB * P.KMB;
   cm.mode = o->compute;
   cm.BN = L.BN;
   cm.s_op = mode_op_shift(o->compute);
@@ -187,6 +192,12 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
   cm.debug_flags = o->debug_flags;
   cm.n_levels = o->n_p;
+  // For operand formats with the FP32 exponent range (3xTF32, TF32, BF16) the
+  // threshold tau = K mu 2^(m-s) lies near FP32 underflow, and entries within
+  // a decade of it are selected and rooted in FP64.  FP16 / E4M3 thresholds
+  // lie far above FP32 underflow, where an FP32 S is exact to 2^-24, far
+  // finer than the operands' own 2^-11 / 2^-4.
+  cm.fp64_near = (o->compute == PN_F32_EXACT || o->compute == PN_TF32 || o->compute == PN_BF16);
 }
 
 // Level q of the p family (q = n_p-1 is the largest p).

@@ -206,6 +206,18 @@ __device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Hardware base-2 logarithm / exponential (MUFU), subnormals supported.
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // OR-reduction across the `count` threads of named barrier `id`.
 __device__ __forceinline__ bool bar_red_or(bool v, uint32_t id, uint32_t count) {
   uint32_t r;

@@ -8,7 +8,9 @@
 namespace pn {
 namespace gemm {
 
-constexpr int GEMM_THREADS = 192;
+constexpr int EPI_WARPS = 8;                       // two per TMEM lane quarter
+constexpr int EPI_THREADS = EPI_WARPS * 32;
+constexpr int GEMM_THREADS = 64 + EPI_THREADS;     // producer, MMA, epilogue
 constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
 
 __host__ __device__ constexpr inline int stage_bytes(int mode, int BN) {
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], EPI_THREADS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -204,8 +206,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------- epilogue ---
-    const int quarter = warp & 3;  // TMEM lanes quarter*32 .. +31
+    // Warp w may only read TMEM lanes 32*(w%4)..+31 (one output row each);
+    // the two warps of a lane quarter split the tile's columns in halves.
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
     const int et = threadIdx.x - 64;
+    constexpr int HCH = CHUNKS / 2;  // 32-column chunks per warp
     int it = 0;
     for (int idx = blockIdx.x; idx < count; idx += gridDim.x, ++it) {
       const int t = lv.is_top ? idx : lv.work[idx];
@@ -222,122 +229,132 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         ok_flag[buf] = ok ? 1 : 0;
       }
-      bar_sync_named(1, 128);
+      bar_sync_named(1, EPI_THREADS);
       if (!ok_flag[buf]) break;
       tc_fence_after();
 
       const int i = tm * TILE_M + quarter * 32 + lane;
       const bool row_ok = i < P.M;
       const float rs = row_ok ? cm.r[P.rc_r + i] : 0.0f;
-      const uint32_t* st_row = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS;
-      uint32_t res_all[CHUNKS];
+      const int ch0 = half * HCH;
+      const uint32_t* st_row = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
+      const float inv_p = __uint_as_float((127u - (uint32_t)lv.plog) << 23);  // 2^-plog
+      uint32_t res_all[HCH];
       bool any_left = false;
 #pragma unroll 1
-      for (int ch = 0; ch < CHUNKS; ++ch) {
+      for (int hc = 0; hc < HCH; ++hc) {
+        const int ch = ch0 + hc;
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + ch * 32, v);
         tmem_ld_wait();
-        if (ch == CHUNKS - 1) {
+        if (hc == HCH - 1) {
           tc_fence_before();
           mbar_arrive(&acc_empty[buf]);
         }
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
         if (row_ok && j0 < P.N) {
-          if (!lv.is_top) res = st_row[ch];
+          if (!lv.is_top) res = st_row[hc];
           const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
-          // entries to resolve at this p: not yet resolved, in range, and
-          // stable (or the smallest p, which takes whatever is left)
-          uint32_t cand = 0, near = 0;
+          const uint32_t inrange = jn == 32 ? 0xffffffffu : ((1u << jn) - 1u);
+          // entries to resolve at this p: not yet resolved, in range, and stable
+          // (or the smallest p, which takes whatever is left)
+          uint32_t stable = 0, near = 0;
           float x[32];
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            const float S = __uint_as_float(v[e]) * cm.unscale;
-            x[e] = S;
-            if (e < jn && !((res >> e) & 1u)) {
-              if (S >= P.tau || lv.is_bottom) {
-                cand |= 1u << e;
-                if (S < 10.0f * P.tau) near |= 1u << e;
+            x[e] = __uint_as_float(v[e]) * cm.unscale;
+            stable |= (x[e] >= P.tau ? 1u : 0u) << e;
+            near |= (x[e] < 10.0f * P.tau ? 1u : 0u) << e;
+          }
+          const uint32_t open = inrange & ~res;
+          const uint32_t cand = lv.is_bottom ? open : (open & stable);
+          any_left |= (open & ~cand) != 0u;
+          near &= cand & (cm.fp64_near ? 0xffffffffu : 0u);
+          if (cand) {
+            const uint32_t pbits = lv.plog * 0x01010101u;
+            uint32_t pw[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const uint32_t nb = (~stable >> (4 * q)) & 0xfu;  // unstable bytes
+              const uint32_t flag = (nb & 1u) | ((nb & 2u) << 7) | ((nb & 4u) << 14) | ((nb & 8u) << 21);
+              pw[q] = pbits | (flag << 7);
+            }
+            // S_sel before x is overwritten by the root
+            float* srow = P.Ssel ? P.Ssel + (int64_t)i * P.ldaux + j0 : nullptr;
+            const bool full_vec = cand == 0xffffffffu && P.vec_c;
+            if (srow) {
+              if (full_vec) {
+#pragma unroll
+                for (int e = 0; e < 32; e += 4)
+                  *reinterpret_cast<float4*>(srow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
               } else {
-                any_left = true;
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                  if ((cand >> e) & 1u) srow[e] = x[e];
               }
             }
-          }
-          if (cand) {
-            // (S^(p))^(1/p) for p = 2^plog: plog correctly rounded square roots
-            for (int s = 0; s < lv.plog; ++s) {
+            // (S^(p))^(1/p) = 2^(log2(S) / p): two MUFU operations, relative
+            // error ~2^-22 (p = 1 is exact)
+            if (lv.plog > 0) {
 #pragma unroll
-              for (int e = 0; e < 32; ++e) x[e] = sqrtf(x[e]);
+              for (int e = 0; e < 32; ++e) x[e] = ex2_approx(lg2_approx(x[e]) * inv_p);
             }
             if (near) {
-              // within a decade of the underflow threshold: root in FP64
+              // within a decade of tau, which for these formats sits near the
+              // FP32 underflow range: root in FP64
 #pragma unroll
               for (int e = 0; e < 32; ++e) {
                 if ((near >> e) & 1u) {
                   double dr = static_cast<double>(__uint_as_float(v[e]) * cm.unscale);
-                  for (int s = 0; s < lv.plog; ++s) dr = sqrt(dr);
+                  for (int s2 = 0; s2 < lv.plog; ++s2) dr = sqrt(dr);
                   x[e] = static_cast<float>(dr);
                 }
               }
             }
             const float* cs = cm.c + P.rc_c + j0;
+            if (jn == 32 && P.vec_c) {
 #pragma unroll
-            for (int e = 0; e < 32; ++e) x[e] = rs * (e < jn ? __ldg(cs + e) : 0.0f) * x[e];
+              for (int e = 0; e < 32; e += 4) {
+                const float4 cv = __ldg(reinterpret_cast<const float4*>(cs + e));
+                x[e] *= rs * cv.x; x[e + 1] *= rs * cv.y; x[e + 2] *= rs * cv.z; x[e + 3] *= rs * cv.w;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) x[e] *= rs * (e < jn ? __ldg(cs + e) : 0.0f);
+            }
             float* crow = P.C + (int64_t)i * P.ldc + j0;
             uint8_t* prow = P.psel ? P.psel + (int64_t)i * P.ldaux + j0 : nullptr;
-            float* srow = P.Ssel ? P.Ssel + (int64_t)i * P.ldaux + j0 : nullptr;
-            if (cand == 0xffffffffu && P.vec_c) {
+            if (full_vec) {
 #pragma unroll
               for (int e = 0; e < 32; e += 4)
                 *reinterpret_cast<float4*>(crow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
-              if (srow) {
-#pragma unroll
-                for (int e = 0; e < 32; e += 4)
-                  *reinterpret_cast<float4*>(srow + e) = make_float4(
-                      __uint_as_float(v[e]) * cm.unscale, __uint_as_float(v[e + 1]) * cm.unscale,
-                      __uint_as_float(v[e + 2]) * cm.unscale, __uint_as_float(v[e + 3]) * cm.unscale);
-              }
               if (prow) {
-                // p_sel = log2 p, with 0x80 where the smallest p took an unstable S
-                uint32_t w[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                  uint32_t word = 0;
-#pragma unroll
-                  for (int b = 0; b < 4; ++b) {
-                    const int e = 4 * q + b;
-                    const bool st = __uint_as_float(v[e]) * cm.unscale >= P.tau;
-                    word |= static_cast<uint32_t>(lv.plog | (st ? 0 : 0x80)) << (8 * b);
-                  }
-                  w[q] = word;
-                }
-                *reinterpret_cast<uint4*>(prow) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(prow + 16) = make_uint4(w[4], w[5], w[6], w[7]);
+                *reinterpret_cast<uint4*>(prow) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+                *reinterpret_cast<uint4*>(prow + 16) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
               }
             } else {
 #pragma unroll
               for (int e = 0; e < 32; ++e) {
                 if ((cand >> e) & 1u) {
-                  const float S = __uint_as_float(v[e]) * cm.unscale;
                   crow[e] = x[e];
-                  if (srow) srow[e] = S;
-                  if (prow) prow[e] = static_cast<uint8_t>(lv.plog | (S >= P.tau ? 0 : 0x80));
+                  if (prow) prow[e] = static_cast<uint8_t>(pw[e >> 2] >> (8 * (e & 3)));
                 }
               }
             }
             res |= cand;
           }
         }
-        res_all[ch] = res;
+        res_all[hc] = res;
       }
       if (!lv.is_bottom) {
-        const bool tile_left = bar_red_or(any_left, 2, 128);
+        const bool tile_left = bar_red_or(any_left, 2, EPI_THREADS);
         if (tile_left) {
           if (row_ok) {
-            uint32_t* st_w = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS;
+            uint32_t* st_w = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
 #pragma unroll
-            for (int ch = 0; ch < CHUNKS; ++ch)
-              if (tn * BN + ch * 32 < P.N) st_w[ch] = res_all[ch];
+            for (int hc = 0; hc < HCH; ++hc)
+              if (tn * BN + (ch0 + hc) * 32 < P.N) st_w[hc] = res_all[hc];
           }
           if (et == 0) {
             const int slot = atomicAdd(lv.next_count, 1);

@@ -12,6 +12,8 @@ constexpr int TILE_M = 128;         // output rows per tensor-core tile (MMA M)
 constexpr int IMG_BYTES = 16384;    // one operand tile image: 128 rows x 128 bytes
 constexpr int IMG_ROW_BYTES = 128;  // bytes of K per image row (one 128-byte swizzle row)
 constexpr int RASTER_GM = 8;        // tile rows per raster group (L2 reuse of B)
+constexpr int MAXSEG_A = 1024;      // columns of A per max-pass unit
+constexpr int MAXSEG_B = 256;       // rows of B per max-pass unit
 
 // Operand formats of the tensor-core path (values equal pn_compute).
 enum Mode : int32_t { MODE_3XTF32 = 0, MODE_TF32 = 1, MODE_BF16 = 2, MODE_F16 = 3, MODE_E4M3 = 4 };
@@ -42,6 +44,8 @@ struct Prob {
   int32_t tile_base;        // first global tile id of this problem
   int32_t xa_base, xb_base; // first global operand-tile id (RBA*KB / RBB*KB per problem)
   int32_t tm_base, tn_base; // offsets into per-level row / column flag arrays
+  int32_t KMA, KMB;         // max-pass segments: 1024 columns of A / 256 rows of B
+  int32_t ma_base, mb_base; // first global max-pass unit (RBA*KMA / RBB*KMB per problem)
   int32_t vec_c;            // C, p_sel, S_sel rows allow 16-byte vector stores
   int32_t state_ld;         // 32-bit state words per row (tiles_n * BN / 32)
   int64_t a_img, b_img;     // byte offsets inside one level's A / B image region
@@ -60,6 +64,7 @@ struct Common {
   int32_t nprob;
   int32_t total_tiles, total_xa, total_xb;
   int32_t total_tm, total_tn;  // tile rows / tile columns summed over problems
+  int32_t total_ma, total_mb;  // max-pass units summed over problems
   int32_t mode, BN, s_op, scaling;
   float unscale;      // 2^(-2 s_op)
   int32_t pad1;
@@ -73,6 +78,8 @@ struct Common {
   uint64_t timeout_ns;
   int32_t debug_flags;
   int32_t n_levels;
+  int32_t fp64_near;  // FP64 selection/root for entries with S < 10 tau (FP32-range formats)
+  int32_t pad2;
 };
 
 // Control of one p level (one p of the family).
@@ -99,7 +106,7 @@ __host__ __device__ inline const Prob& prob_at(const Common& cm, int g) {
 
 // Problem index owning global id `id` given per-problem first ids (binary
 // search on the field selected by `which`: 0 tiles, 1 A operand tiles, 2 B
-// operand tiles, 3 tile rows, 4 tile columns).
+// operand tiles, 3 tile rows, 4 tile columns, 5 A max units, 6 B max units).
 __host__ __device__ inline int find_prob(const Common& cm, int id, int which) {
   if (cm.nprob == 1) return 0;
   int lo = 0, hi = cm.nprob - 1;
@@ -110,7 +117,9 @@ __host__ __device__ inline int find_prob(const Common& cm, int id, int which) {
                      : which == 1 ? p.xa_base
                      : which == 2 ? p.xb_base
                      : which == 3 ? p.tm_base
-                                  : p.tn_base;
+                     : which == 4 ? p.tn_base
+                     : which == 5 ? p.ma_base
+                                  : p.mb_base;
     if (base <= id) lo = mid; else hi = mid - 1;
   }
   return lo;

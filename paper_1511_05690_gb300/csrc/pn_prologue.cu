@@ -28,37 +28,52 @@ __device__ __forceinline__ bool in_domain(float x) {
 __device__ __forceinline__ float nonneg_bits_max(float m) { return m > 0.0f ? m : 0.0f; }
 
 // ------------------------------------------------------------- maxima ---
-// One block per operand tile (128 rows x BK of K): partial maxima, then one
-// atomicMax per row (A) or column (B).  Non-negative floats order like their
-// bit patterns, so the maxima are kept as uint32 bits.
+// A unit: 128 rows x 1024 columns of A; each warp reduces 16 rows (float4
+// loads, 8 in flight per lane per row).  B unit: 128 columns x 256 rows of B;
+// each thread keeps the maxima of 4 columns over 32 rows, then the 8 row
+// groups are combined in shared memory.  One atomicMax per row / column per
+// unit.  Non-negative floats order like their bit patterns, so maxima are
+// kept as uint32 bits.
 __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ Common cm) {
-  __shared__ float red[2][128];
+  __shared__ float red[8][128];
   __shared__ float blk_max[PRO_THREADS / 32];
-  const int bk = mode_bk(cm.mode);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int id = blockIdx.x;
-  const bool is_b = id >= cm.total_xa;
-  if (is_b) id -= cm.total_xa;
-  const int g = find_prob(cm, id, is_b ? 2 : 1);
+  const bool is_b = id >= cm.total_ma;
+  if (is_b) id -= cm.total_ma;
+  const int g = find_prob(cm, id, is_b ? 6 : 5);
   const Prob& P = prob_at(cm, g);
-  const int local = id - (is_b ? P.xb_base : P.xa_base);
-  const int rb = local / P.KB, kb = local - rb * P.KB;
-  const int k0 = kb * bk;
   bool bad = false;
   float bmax = 0.0f;
   if (!is_b) {
-    // rows rb*128 + warp*16 .. +15, each row read by the whole warp
+    const int local = id - P.ma_base;
+    const int rb = local / P.KMA, seg = local - rb * P.KMA;
+    const int k0 = seg * MAXSEG_A;
+    const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
     for (int rr = 0; rr < 16; ++rr) {
       const int row = rb * TILE_M + warp * 16 + rr;
       float m = 0.0f;
       if (row < P.M) {
         const float* src = P.A + (int64_t)row * P.lda;
-        for (int kk = lane; kk < bk; kk += 32) {
-          const int k = k0 + kk;
-          if (k < P.K) {
-            const float x = __ldg(src + k);
-            bad |= !in_domain(x);
-            m = fmaxf(m, x);
+        if (vec && k0 + MAXSEG_A <= P.K) {
+          float4 t[MAXSEG_A / 128];
+#pragma unroll
+          for (int it = 0; it < MAXSEG_A / 128; ++it)
+            t[it] = __ldg(reinterpret_cast<const float4*>(src + k0 + it * 128 + lane * 4));
+#pragma unroll
+          for (int it = 0; it < MAXSEG_A / 128; ++it) {
+            bad |= !in_domain(t[it].x) | !in_domain(t[it].y) | !in_domain(t[it].z) |
+                   !in_domain(t[it].w);
+            m = fmaxf(m, fmaxf(fmaxf(t[it].x, t[it].y), fmaxf(t[it].z, t[it].w)));
+          }
+        } else {
+          for (int kk = lane; kk < MAXSEG_A; kk += 32) {
+            const int k = k0 + kk;
+            if (k < P.K) {
+              const float x = __ldg(src + k);
+              bad |= !in_domain(x);
+              m = fmaxf(m, x);
+            }
           }
         }
       }
@@ -70,27 +85,46 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
       bmax = fmaxf(bmax, m);
     }
   } else {
-    // columns n = rb*128 + (tid & 127); two halves of the K range
-    const int n = rb * TILE_M + (tid & 127);
-    float m = 0.0f;
-    if (n < P.N) {
-      for (int kk = tid >> 7; kk < bk; kk += 2) {
-        const int k = k0 + kk;
-        if (k < P.K) {
-          const float x = __ldg(P.B + (int64_t)k * P.ldb + n);
-          bad |= !in_domain(x);
-          m = fmaxf(m, x);
+    const int local = id - P.mb_base;
+    const int rb = local / P.KMB, seg = local - rb * P.KMB;
+    const int k0 = seg * MAXSEG_B;
+    const int n4 = rb * TILE_M + lane * 4;
+    const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0);
+    float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (vec && n4 + 4 <= P.N && k0 + MAXSEG_B <= P.K) {
+#pragma unroll 8
+      for (int it = 0; it < MAXSEG_B / 8; ++it) {
+        const int k = k0 + warp + 8 * it;
+        const float4 t = __ldg(reinterpret_cast<const float4*>(P.B + (int64_t)k * P.ldb + n4));
+        bad |= !in_domain(t.x) | !in_domain(t.y) | !in_domain(t.z) | !in_domain(t.w);
+        m4[0] = fmaxf(m4[0], t.x); m4[1] = fmaxf(m4[1], t.y);
+        m4[2] = fmaxf(m4[2], t.z); m4[3] = fmaxf(m4[3], t.w);
+      }
+    } else {
+      for (int it = 0; it < MAXSEG_B / 8; ++it) {
+        const int k = k0 + warp + 8 * it;
+        if (k >= P.K) break;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if (n4 + c < P.N) {
+            const float x = __ldg(P.B + (int64_t)k * P.ldb + n4 + c);
+            bad |= !in_domain(x);
+            m4[c] = fmaxf(m4[c], x);
+          }
         }
       }
     }
-    red[tid >> 7][tid & 127] = nonneg_bits_max(m);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = nonneg_bits_max(m4[c]);
     __syncthreads();
     if (tid < 128) {
-      m = fmaxf(red[0][tid], red[1][tid]);
+      float m = red[0][tid];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w][tid]);
+      const int n = rb * TILE_M + tid;
       if (n < P.N && m > 0.0f) atomicMax(cm.cmax + P.rc_c + n, __float_as_uint(m));
+      bmax = m;
     }
-    bmax = m;
-    __syncthreads();
   }
   if (__syncthreads_or(bad) && tid == 0) set_status(cm.status, PN_EDOMAIN);
   if (cm.scaling == 1) {
@@ -111,6 +145,12 @@ __device__ __forceinline__ float scale_of(const Common& cm, const uint32_t* mx, 
   if (cm.scaling == 0) return 1.0f;
   const uint32_t bits = cm.scaling == 1 ? cm.gmax[2 * g + which] : mx[idx];
   return pow2_ceil_f(__uint_as_float(bits));
+}
+
+// x / s for a power of two s: a multiply by the exact reciprocal when 1/s is
+// a normal float (identical rounding), else a division.
+__device__ __forceinline__ float div_pow2(float x, float s, float inv, bool inv_ok) {
+  return inv_ok ? x * inv : x / s;
 }
 
 // x^(2^plog) by repeated squaring (each step one correctly rounded multiply).
@@ -208,35 +248,41 @@ __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, 
   const float opscale = ldexpf(1.0f, cm.s_op);
   uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
   const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
-#pragma unroll 1
+  // 1024 16-byte output chunks per tile, 4 per thread: chunk = tid + 256 u,
+  // row = chunk / 8 (8 threads cover one 128-byte image row), 16-byte slot
+  // = chunk % 8.  All loads are issued before any arithmetic.
+  float v[4][EPC];
+  const int cc = threadIdx.x & 7;
+  const int k0 = kb * BK + cc * EPC;
+#pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const int ch = threadIdx.x + PRO_THREADS * u;
-    const int rr = ch >> 3, cc = ch & 7;
+    const int row = rb * TILE_M + (threadIdx.x >> 3) + 32 * u;
+    const float* src = P.A + (int64_t)row * P.lda + k0;
+    if (row < P.M && vec && k0 + EPC <= P.K) {
+#pragma unroll
+      for (int e = 0; e < EPC; e += 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(src + e));
+        v[u][e] = t.x; v[u][e + 1] = t.y; v[u][e + 2] = t.z; v[u][e + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[u][e] = (row < P.M && k0 + e < P.K) ? __ldg(src + e) : 0.0f;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int rr = (threadIdx.x >> 3) + 32 * u;
     const int row = rb * TILE_M + rr;
-    const int k0 = kb * BK + cc * EPC;
-    float v[EPC];
     if (row < P.M) {
       const float rs = scale_of(cm, cm.rmax, P.rc_r + row, g, 0);
       if (lv.is_top && kb == 0 && cc == 0) cm.r[P.rc_r + row] = rs;
-      const float* src = P.A + (int64_t)row * P.lda + k0;
-      if (vec && k0 + EPC <= P.K) {
+      const float inv = 1.0f / rs;
+      const bool inv_ok = rs >= 1.1754944e-38f && rs <= 8.507059e37f;
 #pragma unroll
-        for (int e = 0; e < EPC; e += 4) {
-          const float4 t = __ldg(reinterpret_cast<const float4*>(src + e));
-          v[e] = t.x; v[e + 1] = t.y; v[e + 2] = t.z; v[e + 3] = t.w;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < EPC; ++e) v[e] = (k0 + e < P.K) ? __ldg(src + e) : 0.0f;
-      }
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[e] = pow2k(v[e] / rs, lv.plog) * opscale;
-    } else {
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[e] = 0.0f;
+      for (int e = 0; e < EPC; ++e) v[u][e] = pow2k(div_pow2(v[u][e], rs, inv, inv_ok), lv.plog) * opscale;
     }
     uint4 hi, lo;
-    PK::pack(v, hi, lo);
+    PK::pack(v[u], hi, lo);
     const uint32_t off = sw128_offset(rr, cc * 16);
     *reinterpret_cast<uint4*>(dst + off) = hi;
     if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
@@ -277,24 +323,48 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
   const float opscale = ldexpf(1.0f, cm.s_op);
   __syncthreads();  // stile reuse across consecutive tiles
   {
-    const int nl = threadIdx.x & 127;
-    const int n = rb * TILE_M + nl;
-    float cs = 1.0f;
-    if (n < P.N) {
-      cs = scale_of(cm, cm.cmax, P.rc_c + n, g, 1);
-      if (lv.is_top && kb == 0 && threadIdx.x < 128) cm.c[P.rc_c + n] = cs;
+    // BK rows of K x 128 columns: thread = (row group tid/32, 4 columns),
+    // float4 loads, all issued before the scaled values go to shared memory.
+    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+    const int n4 = rb * TILE_M + lane * 4;
+    const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0) &&
+                     n4 + 4 <= P.N;
+    float cs[4], inv[4];
+    bool inv_ok[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int n = n4 + c;
+      cs[c] = n < P.N ? scale_of(cm, cm.cmax, P.rc_c + n, g, 1) : 1.0f;
+      inv[c] = 1.0f / cs[c];
+      inv_ok[c] = cs[c] >= 1.1754944e-38f && cs[c] <= 8.507059e37f;
+      if (lv.is_top && kb == 0 && rg == 0 && n < P.N) cm.c[P.rc_c + n] = cs[c];
     }
-#pragma unroll 4
-    for (int kk = threadIdx.x >> 7; kk < BK; kk += 2) {
-      const int k = kb * BK + kk;
-      float x = 0.0f;
-      if (n < P.N && k < P.K) x = __ldg(P.B + (int64_t)k * P.ldb + n) / cs;
-      stile[kk * 129 + nl] = x;
+    float4 t[BK / 8];
+#pragma unroll
+    for (int it = 0; it < BK / 8; ++it) {
+      const int k = kb * BK + rg + 8 * it;
+      if (vec && k < P.K) {
+        t[it] = __ldg(reinterpret_cast<const float4*>(P.B + (int64_t)k * P.ldb + n4));
+      } else {
+        const float* src = P.B + (int64_t)k * P.ldb;
+        t[it].x = (k < P.K && n4 < P.N) ? __ldg(src + n4) : 0.0f;
+        t[it].y = (k < P.K && n4 + 1 < P.N) ? __ldg(src + n4 + 1) : 0.0f;
+        t[it].z = (k < P.K && n4 + 2 < P.N) ? __ldg(src + n4 + 2) : 0.0f;
+        t[it].w = (k < P.K && n4 + 3 < P.N) ? __ldg(src + n4 + 3) : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < BK / 8; ++it) {
+      float* rowp = stile + (rg + 8 * it) * 129 + lane * 4;
+      rowp[0] = div_pow2(t[it].x, cs[0], inv[0], inv_ok[0]);
+      rowp[1] = div_pow2(t[it].y, cs[1], inv[1], inv_ok[1]);
+      rowp[2] = div_pow2(t[it].z, cs[2], inv[2], inv_ok[2]);
+      rowp[3] = div_pow2(t[it].w, cs[3], inv[3], inv_ok[3]);
     }
   }
   __syncthreads();
   uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
-#pragma unroll 1
+#pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int ch = threadIdx.x + PRO_THREADS * u;
     const int nr = ch >> 3, cc = ch & 7;
@@ -409,7 +479,7 @@ int grid_for(int64_t total, int threads) {
 }  // namespace
 
 int launch_maxes(const Common& cm, void* stream) {
-  const int blocks = cm.total_xa + cm.total_xb;
+  const int blocks = cm.total_ma + cm.total_mb;
   if (blocks <= 0) return 0;
   k_maxes<<<blocks, PRO_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(cm);
   return cudaGetLastError();
