@@ -140,6 +140,29 @@ PN_API pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, 
                         float* S_sel, const pn_opts* opts, void* ws, size_t ws_bytes,
                         void* stream);
 
+/* Size of the scratch array behind maxprod_pnorm_static: 64 MiB of device
+ * memory, reserved on every GPU that loads this library until the process
+ * exits. */
+#define PN_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* maxprod_pnorm for callers that cannot allocate device memory (no citation:
+ * the paper has no counterpart; this is a library convenience).  Some callers
+ * are handed only their inputs and outputs and may not call cudaMalloc -- for
+ * instance a plugin whose host framework owns all device memory, or code on
+ * a path where an allocation would stall.  This call takes no workspace: it
+ * uses a fixed array of PN_STATIC_SCRATCH_BYTES inside the library and
+ * allocates nothing.  Arguments and results are those of maxprod_pnorm.
+ * Returns PN_EWORKSPACE when pn_workspace_size(M, N, K, opts) exceeds
+ * PN_STATIC_SCRATCH_BYTES (with P = {1..64}, square products fit up to about
+ * n = 1500 with BF16 operands and n = 700 with PN_F32_EXACT).  The first call on a device looks up the array's device
+ * address; make it before any stream capture.  Every call uses the same array,
+ * so calls whose GPU work can overlap (other streams, other host threads) race
+ * and must be serialised by the caller. */
+PN_API pn_status maxprod_pnorm_static(int64_t M, int64_t N, int64_t K, const float* A,
+                                      int64_t lda, const float* B, int64_t ldb, float* C,
+                                      int64_t ldc, uint8_t* p_sel, float* S_sel,
+                                      const pn_opts* opts, void* stream);
+
 /* Exact semiring product on the CUDA cores (FP32, the plain comparison):
  * semiring 0: C_ij = max_k a_ik * b_kj  (Alg. 2; empty max = 0)
  * semiring 1: C_ij = min_k a_ik + b_kj  (Alg. 1; empty min = +inf)

@@ -27,7 +27,7 @@ EXPORTS = (
     "pn_workspace_size", "maxprod_pnorm", "maxprod_exact", "pn_maxprod_exact_variant",
     "pn_apsp_workspace_size", "apsp_pnorm", "pn_backward_workspace_size",
     "maxprod_pnorm_backward", "pn_grouped_table_bytes", "pn_grouped_build_table",
-    "maxprod_pnorm_grouped",
+    "maxprod_pnorm_grouped", "maxprod_pnorm_static",
 )
 
 
@@ -85,6 +85,9 @@ def load():
         lib.maxprod_pnorm.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp, optp,
                                       vp, sz, vp]
         lib.maxprod_pnorm.restype = i32
+        lib.maxprod_pnorm_static.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, vp, vp,
+                                             optp, vp]
+        lib.maxprod_pnorm_static.restype = i32
         lib.maxprod_exact.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp]
         lib.maxprod_exact.restype = i32
         lib.pn_maxprod_exact_variant.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32,
