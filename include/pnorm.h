@@ -154,7 +154,7 @@ PN_API pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, 
  * allocates nothing.  Arguments and results are those of maxprod_pnorm.
  * Returns PN_EWORKSPACE when pn_workspace_size(M, N, K, opts) exceeds
  * PN_STATIC_SCRATCH_BYTES (with P = {1..64}, square products fit up to about
- * n = 1500 with BF16 operands and n = 700 with PN_F32_EXACT).  The first call on a device looks up the array's device
+ * n = 3900 with BF16 operands and n = 2000 with PN_F32_EXACT).  The first call on a device looks up the array's device
  * address; make it before any stream capture.  Every call uses the same array,
  * so calls whose GPU work can overlap (other streams, other host threads) race
  * and must be serialised by the caller. */

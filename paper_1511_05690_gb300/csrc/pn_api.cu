@@ -119,8 +119,11 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.b_plane = static_cast<size_t>(L.RBB) * L.KB * IMG_BYTES;
   L.a_level_bytes = L.a_plane * L.planes;
   L.b_level_bytes = L.b_plane * L.planes;
-  L.off_aimg = off; off += L.a_level_bytes * L.n_p;
-  L.off_bimg = off; off += L.b_level_bytes * L.n_p;
+  // One image buffer per operand serves every level: level q reads only the
+  // images written for level q, after the previous level's GEMM has finished
+  // (stream order).
+  L.off_aimg = off; off += L.a_level_bytes;
+  L.off_bimg = off; off += L.b_level_bytes;
   L.total = align_up(off, WS_ALIGN);
   return L;
 }
@@ -214,8 +217,8 @@ Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, int q) {
   lv.plog = o->p_log2[q];
   lv.is_top = q == top;
   lv.is_bottom = q == 0;
-  lv.a_level = ws + L.off_aimg + L.a_level_bytes * q;
-  lv.b_level = ws + L.off_bimg + L.b_level_bytes * q;
+  lv.a_level = ws + L.off_aimg;
+  lv.b_level = ws + L.off_bimg;
   lv.work = work + static_cast<size_t>(q) * L.total_tiles;
   lv.work_count = counts + q;
   lv.next_work = work + static_cast<size_t>(qn) * L.total_tiles;
