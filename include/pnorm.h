@@ -82,8 +82,14 @@ typedef struct pn_opts {
   /* Operand scaling (Sec. 2.1, H'): 2 = per-row (A) / per-column (B) powers
    * of two (default); 1 = one global power of two per operand; 0 = none. */
   int32_t scaling;
-  /* APSP only: 1 = reset the diagonal to x = 1 (distance 0) after each
-   * squaring (default); 0 = leave it. */
+  /* APSP only (reading of Sec. 2.2; the paper is silent): 1 = set the
+   * diagonal to x = 1 (distance 0) after the transform and after each
+   * squaring; 2 (default) = that, and clamp every entry to x <= 1 (distance
+   * >= 0); 0 = neither.  Both are exact facts for nonnegative weights, and
+   * since the p-norm estimate only overestimates x, the clamped estimate still
+   * lies between the exact x and the unclamped one.  Without the clamp,
+   * overestimated entries above 1 form cycles whose value grows with every
+   * squaring. */
   int32_t diag_policy;
   /* Output tile width of the tensor-core kernel: 0 = autotuned, else 128 or
    * 256 (PN_F32_EXACT always uses 128). */
@@ -105,7 +111,8 @@ typedef struct pn_opts {
 PN_API const char* pn_status_string(int32_t status);
 
 /* P = {1, 2, 4, ..., 64}, PN_BF16, default tau, per-row/column scaling,
- * diagonal reset, autotuned tiles, no status word, no events. */
+ * diagonal reset and clamp (diag_policy 2), autotuned tiles, no status word,
+ * no events. */
 PN_API void pn_default_opts(pn_opts* opts);
 
 /* Default tau for contraction length K and compute mode (reading of Sec. 2.1,
@@ -186,9 +193,9 @@ PN_API pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const
 PN_API size_t pn_apsp_workspace_size(int64_t n, const pn_opts* opts);
 
 /* All-pairs shortest distances estimated with p-norm squarings (Sec. 2.2):
- * X = exp(-W) with +inf -> 0, X_ii = 1 (diag_policy 1); then n_squarings
- * times X <- maxprod_pnorm(X, X) followed by the diagonal reset; finally
- * D = -log X (0 -> +inf).  W: n x n FP32, ldw >= n, entries >= 0 or +inf
+ * X = exp(-W) with +inf -> 0, X_ii = 1 (diag_policy >= 1); then n_squarings
+ * times X <- maxprod_pnorm(X, X) followed by the diag_policy rule (fused
+ * into the product's epilogue); finally D = -log X (0 -> +inf).  W: n x n FP32, ldw >= n, entries >= 0 or +inf
  * (else PN_EDOMAIN); D: n x n FP32, ldd >= n.  n_squarings <= 0 selects
  * ceil(log2 n), which covers every path of up to n edges (Sec. 1, A^n by
  * powers of two). */

@@ -21,7 +21,8 @@ passages they follow:
 * ``entries`` -- exact max and p-sums at selected entries only.
 * ``floyd_warshall`` -- exact APSP (the comparison of Sec. 3.1).
 * ``apsp_pnorm`` -- Sec. 2.2: exp(-W), repeated p-norm squaring, -log.
-* ``pnorm_grad`` -- gradient of the p-norm product at fixed p per entry.
+* ``pnorm_grad`` / ``pnorm_grad_entries`` -- gradient of the p-norm product at
+  fixed p per entry (all entries / selected entries).
 * ``default_tau`` -- the stability threshold reading (Sec. 2.1, tau).
 """
 from __future__ import annotations
@@ -84,6 +85,8 @@ def _load():
             lib.orc_apsp_pnorm.argtypes = [i64, vp, i64, ci, ci, vp, dbl, ci, ci, vp, i64, vp]
             lib.orc_apsp_pnorm.restype = ci
             lib.orc_pnorm_grad.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+            lib.orc_pnorm_grad_entries.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, i64, vp,
+                                                   vp, vp, i64, vp, vp, vp]
             lib.orc_row_logloss.argtypes = [i64, i64, vp, vp, vp]
             lib.orc_row_logloss.restype = dbl
             lib.orc_col_logloss.argtypes = [i64, i64, vp, vp, vp]
@@ -254,7 +257,7 @@ def floyd_warshall(W):
 
 
 def apsp_pnorm(W, p_log2, tau: float, n_squarings: int = 0, scaling: int = 2,
-               diag_policy: int = 1):
+               diag_policy: int = 2):
     W = _f64(W)
     n = W.shape[0]
     D = np.empty((n, n), dtype=np.float64)
@@ -278,6 +281,23 @@ def pnorm_grad(A, B, plog, G, scaling: int = 2):
     dA = np.empty((M, K), dtype=np.float64)
     dB = np.empty((K, N), dtype=np.float64)
     _load().orc_pnorm_grad(M, N, K, _p(A), _p(B), _p(r), _p(c), _p(pl), _p(G), _p(dA), _p(dB))
+    return dA, dB
+
+
+def pnorm_grad_entries(A, B, plog, G, ia, ka, kb, jb, scaling: int = 2):
+    """Sampled entries dA[ia, ka] and dB[kb, jb] of pnorm_grad (same definitions)."""
+    A, B, G = _f64(A), _f64(B), _f64(G)
+    M, K = A.shape
+    _, N = B.shape
+    r = row_scales(A, scaling)
+    c = col_scales(B, scaling)
+    pl = np.ascontiguousarray(np.asarray(plog) & 0x7F, dtype=np.uint8)
+    ia, ka = np.ascontiguousarray(ia, np.int64), np.ascontiguousarray(ka, np.int64)
+    kb, jb = np.ascontiguousarray(kb, np.int64), np.ascontiguousarray(jb, np.int64)
+    dA = np.empty(len(ia), dtype=np.float64)
+    dB = np.empty(len(kb), dtype=np.float64)
+    _load().orc_pnorm_grad_entries(M, N, K, _p(A), _p(B), _p(r), _p(c), _p(pl), _p(G), len(ia),
+                                   _p(ia), _p(ka), _p(dA), len(kb), _p(kb), _p(jb), _p(dB))
     return dA, dB
 
 

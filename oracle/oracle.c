@@ -21,7 +21,8 @@
  *     If no p passes, p* is the smallest p in P and the result carries an
  *     "unstable" flag (0x80 in p_sel).
  *   - APSP (Sec. 2.2, Eq. for A^n): the diagonal is reset to 1 (distance 0)
- *     after each squaring when diag_policy == 1.
+ *     after each squaring when diag_policy >= 1; with diag_policy == 2 every
+ *     entry is also clamped to <= 1 (distance >= 0).
  *
  * Build: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC oracle.c
  * (-ffp-contract=off keeps every product and sum separately rounded.)
@@ -344,9 +345,13 @@ void orc_floyd_warshall(int64_t n, double* D, int64_t ldd) {
   }
 }
 
-/* p-norm APSP (Sec. 2.2): X = exp(-W) (+inf -> 0), X_ii = 1 if diag_policy,*/
-/* then n_sq times X <- E(X, X) (the p-norm product above) with the same    */
-/* diagonal reset, and D = -log X.  n_sq <= 0 means ceil(log2 n).           */
+/* p-norm APSP (Sec. 2.2): X = exp(-W) (+inf -> 0), then n_sq times         */
+/* X <- E(X, X) (the p-norm product above), and D = -log X.                 */
+/* n_sq <= 0 means ceil(log2 n).  After the transform and after each         */
+/* squaring, diag_policy >= 1 sets X_ii = 1 (distance 0); diag_policy == 2   */
+/* also clamps every entry to X <= 1 (distance >= 0): with nonnegative       */
+/* weights both are exact facts, and since E only overestimates X the        */
+/* clamped estimate still lies between the exact X and the unclamped one.   */
 int orc_apsp_pnorm(int64_t n, const double* W, int64_t ldw, int n_sq, int n_p, const int* p_log2,
                    double tau, int scaling, int diag_policy, double* D, int64_t ldd,
                    uint8_t* psel_last) {
@@ -363,13 +368,16 @@ int orc_apsp_pnorm(int64_t n, const double* W, int64_t ldw, int n_sq, int n_p, c
       double w = W[i * ldw + j];
       X[i * n + j] = (w == INFINITY) ? 0.0 : exp(-w);
     }
-  if (diag_policy == 1)
+  if (diag_policy >= 1)
     for (int64_t i = 0; i < n; ++i) X[i * n + i] = 1.0;
   for (int t = 0; t < n_sq; ++t) {
     int rc = orc_pnorm(n, n, n, X, n, X, n, n_p, p_log2, tau, scaling, Y,
                        (t == n_sq - 1) ? psel_last : NULL, NULL, NULL, NULL, NULL);
     if (rc) return rc;
-    if (diag_policy == 1)
+    if (diag_policy == 2)
+      for (int64_t e = 0; e < n * n; ++e)
+        if (Y[e] > 1.0) Y[e] = 1.0;
+    if (diag_policy >= 1)
       for (int64_t i = 0; i < n; ++i) Y[i * n + i] = 1.0;
     double* tmp = X;
     X = Y;
@@ -439,6 +447,47 @@ void orc_pnorm_grad(int64_t M, int64_t N, int64_t K, const double* A, const doub
     }
   }
   free(Wt);
+}
+
+/* Selected entries of the same gradient: dA at (ia[e], ka[e]) for e < n_a   */
+/* and dB at (kb[e], jb[e]) for e < n_b.  A dA entry needs row i of W, i.e.  */
+/* S_ij for every j (O(N K) terms); a dB entry needs column j (O(M K)).     */
+void orc_pnorm_grad_entries(int64_t M, int64_t N, int64_t K, const double* A, const double* B,
+                            const double* r, const double* c, const uint8_t* plog,
+                            const double* G, int64_t n_a, const int64_t* ia, const int64_t* ka,
+                            double* dA, int64_t n_b, const int64_t* kb, const int64_t* jb,
+                            double* dB) {
+  int64_t e;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (e = 0; e < n_a; ++e) {
+    const int64_t i = ia[e], k = ka[e];
+    double acc = 0.0;
+    for (int64_t j = 0; j < N; ++j) {
+      double p = ldexp(1.0, plog[i * N + j]);
+      double s = 0.0;
+      for (int64_t t = 0; t < K; ++t) s += pow((A[i * K + t] / r[i]) * (B[t * N + j] / c[j]), p);
+      if (!(s > 0.0)) continue;
+      double C = r[i] * c[j] * pow(s, 1.0 / p);
+      double W = G[i * N + j] * C / s;
+      acc += W * pow(A[i * K + k] / r[i], p - 1.0) / r[i] * pow(B[k * N + j] / c[j], p);
+    }
+    dA[e] = acc;
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (e = 0; e < n_b; ++e) {
+    const int64_t k = kb[e], j = jb[e];
+    double acc = 0.0;
+    for (int64_t i = 0; i < M; ++i) {
+      double p = ldexp(1.0, plog[i * N + j]);
+      double s = 0.0;
+      for (int64_t t = 0; t < K; ++t) s += pow((A[i * K + t] / r[i]) * (B[t * N + j] / c[j]), p);
+      if (!(s > 0.0)) continue;
+      double C = r[i] * c[j] * pow(s, 1.0 / p);
+      double W = G[i * N + j] * C / s;
+      acc += W * pow(A[i * K + k] / r[i], p) * pow(B[k * N + j] / c[j], p - 1.0) / c[j];
+    }
+    dB[e] = acc;
+  }
 }
 
 /* Loss L = sum_j log C_ij over one row i of the product, at fixed p per    */

@@ -160,7 +160,7 @@ def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None,
 
 
 def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
-               tau=None, scaling=2, diag_policy=1, tile_n=0, out=None, check=True,
+               tau=None, scaling=2, diag_policy=2, tile_n=0, out=None, check=True,
                stream=None, ev_begin=None, ev_end=None):
     """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge)."""
     W = _mat(W, "W")

@@ -122,7 +122,7 @@ def check(status: int, where: str = "") -> None:
         raise PnError(status, where)
 
 
-def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_policy=1,
+def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_policy=2,
               tile_n=0, dev_status=None, ev_begin=None, ev_end=None, timeout_ns=0,
               debug_flags=0) -> PnOpts:
     o = PnOpts()

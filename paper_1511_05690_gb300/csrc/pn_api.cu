@@ -52,7 +52,7 @@ bool opts_valid(const pn_opts* o) {
   }
   if (o->compute < PN_F32_EXACT || o->compute > PN_E4M3) return false;
   if (o->scaling < 0 || o->scaling > 2) return false;
-  if (o->diag_policy < 0 || o->diag_policy > 1) return false;
+  if (o->diag_policy < 0 || o->diag_policy > 2) return false;
   if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256) return false;
   if (o->timeout_ns < 0) return false;
   if (std::isnan(o->tau)) return false;
@@ -233,11 +233,12 @@ Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, int q) {
 // The product proper, arguments already checked.
 pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
                     int64_t ldb, float* C, int64_t ldc, uint8_t* p_sel, float* S_sel,
-                    const pn_opts* o, uint8_t* ws, void* stream, int sms) {
+                    const pn_opts* o, uint8_t* ws, void* stream, int sms, int post = 0) {
   if (M == 0 || N == 0) return PN_OK;
   const Layout L = make_layout(M, N, K, o);
   Common cm;
   fill_common(cm, L, M, N, K, A, lda, B, ldb, C, ldc, p_sel, S_sel, o, ws);
+  cm.post = post;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (K == 0) return cuda_status(launch_fill_empty(cm, o->p_log2[0], stream));
   int e = cudaMemsetAsync(ws, 0, L.ctrl_bytes, s);
@@ -254,6 +255,53 @@ pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
       if (cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_end), s)) return PN_ECUDA;
   }
   return PN_OK;
+}
+
+// Adjoint: supported operand formats (FP32 exponent range; W is not scaled).
+bool bw_mode_ok(int compute) {
+  return compute == PN_F32_EXACT || compute == PN_TF32 || compute == PN_BF16;
+}
+
+// Workspace of the adjoint: control words, scales and the four operand images
+// of one p (reused for every p, stream order).
+struct BwLayout {
+  int BN = 0, KB1 = 0, KB2 = 0, RB1a = 0, RB1b = 0, RB2a = 0, RB2b = 0;
+  size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_mask = 0, ctrl_bytes = 0;
+  size_t off_r = 0, off_c = 0, off_w1 = 0, off_b1 = 0, off_a2 = 0, off_w2 = 0;
+  size_t plane_w1 = 0, plane_b1 = 0, plane_a2 = 0, plane_w2 = 0, total = 0;
+};
+
+BwLayout make_bw_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
+  BwLayout L;
+  const int mode = o->compute;
+  const int bk = mode_bk(mode), planes = mode_planes(mode);
+  L.BN = mode == PN_F32_EXACT ? 128 : (o->tile_n ? o->tile_n : 256);
+  const int per = L.BN / TILE_M;
+  L.KB1 = static_cast<int>(ceil_div(N, bk));
+  L.KB2 = static_cast<int>(ceil_div(M, bk));
+  L.RB1a = static_cast<int>(ceil_div(M, TILE_M));
+  L.RB1b = static_cast<int>(ceil_div(K, L.BN)) * per;
+  L.RB2a = static_cast<int>(ceil_div(K, TILE_M));
+  L.RB2b = static_cast<int>(ceil_div(N, L.BN)) * per;
+  size_t off = 0;
+  L.off_rmax = off; off += sizeof(uint32_t) * M;
+  L.off_cmax = off; off += sizeof(uint32_t) * N;
+  L.off_gmax = off; off += sizeof(uint32_t) * 2;
+  L.off_mask = off; off += sizeof(uint32_t);
+  L.ctrl_bytes = align_up(off, 16);
+  off = align_up(off, WS_ALIGN);
+  L.off_r = off; off = align_up(off + sizeof(float) * M, WS_ALIGN);
+  L.off_c = off; off = align_up(off + sizeof(float) * N, IMG_ALIGN);
+  L.plane_w1 = static_cast<size_t>(L.RB1a) * L.KB1 * IMG_BYTES;
+  L.plane_b1 = static_cast<size_t>(L.RB1b) * L.KB1 * IMG_BYTES;
+  L.plane_a2 = static_cast<size_t>(L.RB2a) * L.KB2 * IMG_BYTES;
+  L.plane_w2 = static_cast<size_t>(L.RB2b) * L.KB2 * IMG_BYTES;
+  L.off_w1 = off; off += L.plane_w1 * planes;
+  L.off_b1 = off; off += L.plane_b1 * planes;
+  L.off_a2 = off; off += L.plane_a2 * planes;
+  L.off_w2 = off; off += L.plane_w2 * planes;
+  L.total = align_up(off, WS_ALIGN);
+  return L;
 }
 
 bool dims_ok(int64_t M, int64_t N, int64_t K) {
@@ -291,7 +339,7 @@ void pn_default_opts(pn_opts* o) {
   o->tau = 0.0;
   o->compute = PN_BF16;
   o->scaling = 2;
-  o->diag_policy = 1;
+  o->diag_policy = 2;
   o->tile_n = 0;
 }
 
@@ -379,10 +427,10 @@ pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t l
   pn_opts o = *opts;
   for (int t = 0; t < T; ++t) {
     if (t > 0) o.ev_gemm_begin = o.ev_gemm_end = nullptr;
-    const pn_status st =
-        run_pnorm(n, n, n, src, lds, src, lds, dst, ldt, nullptr, nullptr, &o, pws, stream, sms);
+    // the diagonal reset / clamp of diag_policy is applied by the epilogue
+    const pn_status st = run_pnorm(n, n, n, src, lds, src, lds, dst, ldt, nullptr, nullptr, &o,
+                                   pws, stream, sms, opts->diag_policy);
     if (st != PN_OK) return st;
-    if (opts->diag_policy == 1 && launch_diag_reset(n, dst, ldt, stream)) return PN_ECUDA;
     float* tp = src; src = dst; dst = tp;
     const int64_t tl = lds; lds = ldt; ldt = tl;
   }
@@ -391,17 +439,127 @@ pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t l
 }
 
 size_t pn_backward_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts) {
-  (void)M; (void)N; (void)K; (void)opts;
-  return 0;
+  if (!opts_valid(opts) || !dims_ok(M, N, K) || !bw_mode_ok(opts->compute)) return 0;
+  return make_bw_layout(M, N, K, opts).total;
 }
 
 pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A,
                                  const float* B, const float* C, const float* S_sel,
                                  const uint8_t* p_sel, const float* dC, float* dA, float* dB,
                                  const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
-  (void)M; (void)N; (void)K; (void)A; (void)B; (void)C; (void)S_sel; (void)p_sel; (void)dC;
-  (void)dA; (void)dB; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
-  return PN_EUNSUPPORTED;
+  if (!opts_valid(opts) || !dims_ok(M, N, K)) return PN_EINVAL;
+  if (!bw_mode_ok(opts->compute)) return PN_EUNSUPPORTED;
+  if (K == 0) return PN_OK;  // dA and dB are empty
+  if ((M > 0 && !dA) || (N > 0 && !dB)) return PN_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (M == 0 || N == 0) {
+    // no output entry depends on the other operand: the gradient is zero
+    if (M > 0 && cudaMemsetAsync(dA, 0, sizeof(float) * M * K, s)) return PN_ECUDA;
+    if (N > 0 && cudaMemsetAsync(dB, 0, sizeof(float) * K * N, s)) return PN_ECUDA;
+    return PN_OK;
+  }
+  if (!A || !B || !C || !S_sel || !p_sel || !dC) return PN_EINVAL;
+  const BwLayout L = make_bw_layout(M, N, K, opts);
+  if (!ws || ws_bytes < L.total) return PN_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % WS_ALIGN) return PN_EALIGN;
+  const int sms = device_sms();
+  if (sms <= 0) return PN_EUNSUPPORTED;
+  uint8_t* w = static_cast<uint8_t*>(ws);
+
+  // scales of the forward operands (same rule as maxprod_pnorm)
+  const Layout FL = make_layout(M, N, K, opts);
+  Common fw;
+  fill_common(fw, FL, M, N, K, A, K, B, N, nullptr, N, nullptr, nullptr, opts, w);
+  fw.rmax = reinterpret_cast<uint32_t*>(w + L.off_rmax);
+  fw.cmax = reinterpret_cast<uint32_t*>(w + L.off_cmax);
+  fw.gmax = reinterpret_cast<uint32_t*>(w + L.off_gmax);
+  fw.r = reinterpret_cast<float*>(w + L.off_r);
+  fw.c = reinterpret_cast<float*>(w + L.off_c);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(w + L.off_mask);
+  if (cudaMemsetAsync(w, 0, L.ctrl_bytes, s)) return PN_ECUDA;
+  if (launch_maxes(fw, stream)) return PN_ECUDA;
+  if (launch_scales(fw, stream)) return PN_ECUDA;
+  if (launch_bw_mask(p_sel, M * N, opts->p_log2, opts->n_p, mask, stream)) return PN_ECUDA;
+
+  // G1: dA (M x K) = W^(p) (M x N) . B'^p^T, contraction over N
+  Common g1;
+  std::memset(&g1, 0, sizeof(g1));
+  {
+    Prob& P = g1.single;
+    P.A = A; P.lda = K; P.C = dA; P.ldc = K;
+    P.M = static_cast<int32_t>(M); P.N = static_cast<int32_t>(K); P.K = static_cast<int32_t>(N);
+    P.KB = L.KB1; P.RBA = L.RB1a; P.RBB = L.RB1b;
+    P.tiles_m = static_cast<int32_t>(ceil_div(M, TILE_M));
+    P.tiles_n = static_cast<int32_t>(ceil_div(K, L.BN));
+    P.a_plane = static_cast<int64_t>(L.plane_w1);
+    P.b_plane = static_cast<int64_t>(L.plane_b1);
+    P.vec_c = (K % 4 == 0) && (reinterpret_cast<uintptr_t>(dA) % 16 == 0) &&
+              (reinterpret_cast<uintptr_t>(A) % 16 == 0);
+    g1.total_tiles = P.tiles_m * P.tiles_n;
+  }
+  // G2: dB (K x N) = A'^p^T (K x M) . W^(p), contraction over M
+  Common g2;
+  std::memset(&g2, 0, sizeof(g2));
+  {
+    Prob& P = g2.single;
+    P.A = B; P.lda = N; P.C = dB; P.ldc = N;
+    P.M = static_cast<int32_t>(K); P.N = static_cast<int32_t>(N); P.K = static_cast<int32_t>(M);
+    P.KB = L.KB2; P.RBA = L.RB2a; P.RBB = L.RB2b;
+    P.tiles_m = static_cast<int32_t>(ceil_div(K, TILE_M));
+    P.tiles_n = static_cast<int32_t>(ceil_div(N, L.BN));
+    P.a_plane = static_cast<int64_t>(L.plane_a2);
+    P.b_plane = static_cast<int64_t>(L.plane_w2);
+    P.vec_c = (N % 4 == 0) && (reinterpret_cast<uintptr_t>(dB) % 16 == 0) &&
+              (reinterpret_cast<uintptr_t>(B) % 16 == 0);
+    g2.total_tiles = P.tiles_m * P.tiles_n;
+  }
+  for (Common* g : {&g1, &g2}) {
+    g->nprob = 1;
+    g->mode = opts->compute;
+    g->BN = L.BN;
+    g->r = fw.r;
+    g->c = fw.c;
+    g->status = opts->dev_status;
+    g->timeout_ns = fw.timeout_ns;
+    g->debug_flags = 0;
+    g->unscale = 1.0f;
+  }
+  g1.grad_axis = 0;
+  g2.grad_axis = 1;
+
+  for (int q = opts->n_p - 1; q >= 0; --q) {
+    const int plog = opts->p_log2[q];
+    BwImage im;
+    std::memset(&im, 0, sizeof(im));
+    im.plog = plog; im.q = q; im.pmask = mask;
+    im.dC = dC; im.Cv = C; im.S = S_sel; im.psel = p_sel;
+    // W^(p) rows (i, contraction j) and B'^p rows (k, contraction j)
+    im.kind = 1; im.trans = 0; im.srows = static_cast<int32_t>(M); im.scols = static_cast<int32_t>(N);
+    im.dst = w + L.off_w1; im.plane = static_cast<int64_t>(L.plane_w1); im.RB = L.RB1a; im.KB = L.KB1;
+    if (launch_bw_image(opts->compute, im, stream)) return PN_ECUDA;
+    im.kind = 0; im.trans = 0; im.src = B; im.lds = N; im.scale = fw.c;
+    im.srows = static_cast<int32_t>(K); im.scols = static_cast<int32_t>(N);
+    im.dst = w + L.off_b1; im.plane = static_cast<int64_t>(L.plane_b1); im.RB = L.RB1b; im.KB = L.KB1;
+    if (launch_bw_image(opts->compute, im, stream)) return PN_ECUDA;
+    // A'^p transposed (k, contraction i) and W^(p) transposed (j, contraction i)
+    im.kind = 0; im.trans = 1; im.src = A; im.lds = K; im.scale = fw.r;
+    im.srows = static_cast<int32_t>(M); im.scols = static_cast<int32_t>(K);
+    im.dst = w + L.off_a2; im.plane = static_cast<int64_t>(L.plane_a2); im.RB = L.RB2a; im.KB = L.KB2;
+    if (launch_bw_image(opts->compute, im, stream)) return PN_ECUDA;
+    im.kind = 1; im.trans = 1; im.src = nullptr; im.scale = nullptr;
+    im.srows = static_cast<int32_t>(M); im.scols = static_cast<int32_t>(N);
+    im.dst = w + L.off_w2; im.plane = static_cast<int64_t>(L.plane_w2); im.RB = L.RB2b; im.KB = L.KB2;
+    if (launch_bw_image(opts->compute, im, stream)) return PN_ECUDA;
+
+    Level lv;
+    std::memset(&lv, 0, sizeof(lv));
+    lv.q = q; lv.plog = plog; lv.is_top = 1; lv.is_bottom = 1; lv.pmask = mask;
+    lv.a_level = w + L.off_w1; lv.b_level = w + L.off_b1;
+    if (launch_gemm_grad(g1, lv, sms, stream)) return PN_ECUDA;
+    lv.a_level = w + L.off_a2; lv.b_level = w + L.off_w2;
+    if (launch_gemm_grad(g2, lv, sms, stream)) return PN_ECUDA;
+  }
+  return PN_OK;
 }
 
 size_t pn_grouped_table_bytes(int32_t count) {

@@ -241,6 +241,26 @@ __host__ __device__ __forceinline__ uint32_t sw128_offset(uint32_t r, uint32_t b
   return r * 128u + ((((b >> 4) ^ (r & 7u)) & 7u) << 4) + (b & 15u);
 }
 
+// x / s for a power of two s: a multiply by the exact reciprocal when 1/s is
+// a normal float (identical rounding), else a division.
+__device__ __forceinline__ float div_pow2(float x, float s, float inv, bool inv_ok) {
+  return inv_ok ? x * inv : x / s;
+}
+__device__ __forceinline__ bool recip_exact(float s) {
+  return s >= 1.1754944e-38f && s <= 8.507059e37f;
+}
+
+// x^(2^k - 1) = x * x^2 * x^4 * ... * x^(2^(k-1)) (k correctly rounded
+// squarings and products); 1 for k = 0.
+__device__ __forceinline__ float pow_pm1(float x, int k) {
+  float r = 1.0f;
+  for (int t = 0; t < k; ++t) {
+    r *= x;
+    x *= x;
+  }
+  return r;
+}
+
 // Smallest power of two >= m (m > 0, finite); 1 for m == 0.  Returns +inf
 // when that power is beyond the float range.
 __device__ __forceinline__ float pow2_ceil_f(float m) {

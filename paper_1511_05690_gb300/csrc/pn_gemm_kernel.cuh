@@ -36,7 +36,11 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, 
   return mbar_wait(bar, parity, timeout_ns, &never);
 }
 
-template <int MODE, int BN>
+// EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
+// lists).  EPI 1: gradient epilogue of the adjoint, out (+)= acc * x'^(p-1) / s
+// with x the source element at the output position and s its row (grad_axis
+// 0) or column (1) scale; the first p present overwrites, later ones add.
+template <int MODE, int BN, int EPI>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
   constexpr int PLANES = mode_planes(MODE);
@@ -50,6 +54,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   constexpr int CHUNKS = BN / 32;
   static_assert(STAGES >= 2, "operand ring too small");
 
+  if constexpr (EPI == 1) {
+    if (!((*lv.pmask >> lv.q) & 1u)) return;  // no entry selected this p
+  }
   const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
   if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
 
@@ -235,7 +242,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 
       const int i = tm * TILE_M + quarter * 32 + lane;
       const bool row_ok = i < P.M;
-      const float rs = row_ok ? cm.r[P.rc_r + i] : 0.0f;
+      // row scale: the p-norm epilogue, or the dA gradient (grad_axis 0)
+      const bool use_rs = row_ok && (EPI == 0 || cm.grad_axis == 0);
+      const float rs = use_rs ? cm.r[P.rc_r + i] : 0.0f;
       const int ch0 = half * HCH;
       const uint32_t* st_row = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
       const float inv_p = __uint_as_float((127u - (uint32_t)lv.plog) << 23);  // 2^-plog
@@ -253,7 +262,64 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
-        if (row_ok && j0 < P.N) {
+        if constexpr (EPI == 1) {
+          if (row_ok && j0 < P.N) {
+            const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
+            const float* erow = P.A + (int64_t)i * P.lda + j0;
+            float* orow = P.C + (int64_t)i * P.ldc + j0;
+            const bool vec = jn == 32 && P.vec_c;
+            const bool first = (*lv.pmask >> (lv.q + 1)) == 0u;
+            float x[32], sv[32];
+            if (vec) {
+#pragma unroll
+              for (int e = 0; e < 32; e += 4) {
+                const float4 t4 = __ldg(reinterpret_cast<const float4*>(erow + e));
+                x[e] = t4.x; x[e + 1] = t4.y; x[e + 2] = t4.z; x[e + 3] = t4.w;
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) x[e] = e < jn ? __ldg(erow + e) : 0.0f;
+            }
+            if (cm.grad_axis == 0) {
+#pragma unroll
+              for (int e = 0; e < 32; ++e) sv[e] = rs;
+            } else {
+              const float* cs = cm.c + P.rc_c + j0;
+#pragma unroll
+              for (int e = 0; e < 32; ++e) sv[e] = e < jn ? __ldg(cs + e) : 1.0f;
+            }
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              const float inv = 1.0f / sv[e];
+              const bool ok = recip_exact(sv[e]);
+              const float f = div_pow2(pow_pm1(div_pow2(x[e], sv[e], inv, ok), lv.plog), sv[e],
+                                       inv, ok);
+              x[e] = __uint_as_float(v[e]) * f;
+            }
+            if (!first) {
+              if (vec) {
+#pragma unroll
+                for (int e = 0; e < 32; e += 4) {
+                  const float4 o4 = *reinterpret_cast<const float4*>(orow + e);
+                  x[e] += o4.x; x[e + 1] += o4.y; x[e + 2] += o4.z; x[e + 3] += o4.w;
+                }
+              } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                  if (e < jn) x[e] += orow[e];
+              }
+            }
+            if (vec) {
+#pragma unroll
+              for (int e = 0; e < 32; e += 4)
+                *reinterpret_cast<float4*>(orow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 32; ++e)
+                if (e < jn) orow[e] = x[e];
+            }
+          }
+        } else if (row_ok && j0 < P.N) {
           if (!lv.is_top) res = st_row[hc];
           const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
           const uint32_t inrange = jn == 32 ? 0xffffffffu : ((1u << jn) - 1u);
@@ -294,9 +360,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                   if ((cand >> e) & 1u) srow[e] = x[e];
               }
             }
-            // (S^(p))^(1/p) = 2^(log2(S) / p): two MUFU operations, relative
-            // error ~2^-22 (p = 1 is exact)
-            if (lv.plog > 0) {
+            if constexpr (MODE == MODE_3XTF32) {
+              // FP32-accurate mode: (S^(p))^(1/p) for p = 2^plog as plog correctly
+              // rounded square roots (about one ulp in total); repeated APSP
+              // squarings double any bias each step, so no approximation here
+              for (int s2 = 0; s2 < lv.plog; ++s2) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) x[e] = sqrtf(x[e]);
+              }
+            } else if (lv.plog > 0) {
+              // (S^(p))^(1/p) = 2^(log2(S) / p): two MUFU operations, relative
+              // error ~2^-22, far below the operand rounding of these formats
 #pragma unroll
               for (int e = 0; e < 32; ++e) x[e] = ex2_approx(lg2_approx(x[e]) * inv_p);
             }
@@ -323,6 +397,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
               for (int e = 0; e < 32; ++e) x[e] *= rs * (e < jn ? __ldg(cs + e) : 0.0f);
             }
+            if (cm.post) {
+              // APSP squaring: distances are >= 0 (x <= 1) and d_ii = 0 (x_ii = 1)
+              if (cm.post == 2) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) x[e] = fminf(x[e], 1.0f);
+              }
+#pragma unroll
+              for (int e = 0; e < 32; ++e)
+                if (j0 + e == i) x[e] = 1.0f;
+            }
             float* crow = P.C + (int64_t)i * P.ldc + j0;
             uint8_t* prow = P.psel ? P.psel + (int64_t)i * P.ldaux + j0 : nullptr;
             if (full_vec) {
@@ -347,7 +431,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         res_all[hc] = res;
       }
-      if (!lv.is_bottom) {
+      if (EPI == 0 && !lv.is_bottom) {
         const bool tile_left = bar_red_or(any_left, 2, EPI_THREADS);
         if (tile_left) {
           if (row_ok) {
@@ -374,23 +458,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, int EPI>
 inline int set_attr_t() {
   static int done = 0;
   if (done) return 0;
-  const cudaError_t e = cudaFuncSetAttribute(
-      k_gemm_level<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_total(MODE, BN));
+  const cudaError_t e = cudaFuncSetAttribute(k_gemm_level<MODE, BN, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_total(MODE, BN));
   if (e == cudaSuccess) done = 1;
   return e;
 }
 
-template <int MODE, int BN>
+template <int MODE, int BN, int EPI = 0>
 inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
-  const int e = set_attr_t<MODE, BN>();
+  const int e = set_attr_t<MODE, BN, EPI>();
   if (e) return e;
   int grid = cm.total_tiles < num_sms ? cm.total_tiles : num_sms;
   if (grid < 1) return 0;
-  k_gemm_level<MODE, BN><<<grid, GEMM_THREADS, smem_total(MODE, BN),
+  k_gemm_level<MODE, BN, EPI><<<grid, GEMM_THREADS, smem_total(MODE, BN),
                            static_cast<cudaStream_t>(stream)>>>(cm, lv);
   return cudaGetLastError();
 }

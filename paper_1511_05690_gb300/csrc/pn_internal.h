@@ -79,7 +79,9 @@ struct Common {
   int32_t debug_flags;
   int32_t n_levels;
   int32_t fp64_near;  // FP64 selection/root for entries with S < 10 tau (FP32-range formats)
-  int32_t pad2;
+  int32_t grad_axis;  // gradient epilogue: 0 = scale per output row (r), 1 = per column (c)
+  int32_t post;       // APSP squaring: 1 = C_ii = 1, 2 = also C = min(C, 1)
+  int32_t pad3;
 };
 
 // Control of one p level (one p of the family).
@@ -98,6 +100,29 @@ struct Level {
   const uint8_t* cflag;       // this level's needed B column tiles (not at top)
   uint8_t* next_rflag;
   uint8_t* next_cflag;
+  const uint32_t* pmask;      // gradient launches: bit q set if some entry has p* = P[q]
+};
+
+// One operand image of the adjoint (maxprod_pnorm_backward).
+//   kind 0: (src / scale)^p with one scale per contraction index
+//   kind 1: W^(p) = dC * C / S where p_sel == p, else 0
+//   trans 0: image row r = source row r, contraction = source column
+//   trans 1: image row r = source column r, contraction = source row
+struct BwImage {
+  const float* src;
+  int64_t lds;
+  int32_t srows, scols;
+  const float* scale;
+  const float* dC;
+  const float* Cv;
+  const float* S;
+  const uint8_t* psel;
+  uint8_t* dst;
+  int64_t plane;           // bytes to the lo plane (3xTF32)
+  int32_t RB, KB;          // image row blocks (128 rows), contraction blocks
+  int32_t plog, q;
+  const uint32_t* pmask;
+  int32_t kind, trans;
 };
 
 __host__ __device__ inline const Prob& prob_at(const Common& cm, int g) {
@@ -147,9 +172,13 @@ int launch_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, c
 int launch_fill_empty(const Common& cm, int plog0, void* stream);
 int launch_apsp_init(int64_t n, const float* W, int64_t ldw, float* X, int diag, int32_t* status,
                      void* stream);
-int launch_diag_reset(int64_t n, float* X, int64_t ldx, void* stream);
 int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd,
                       void* stream);
+int launch_gemm_grad(const Common& cm, const Level& lv, int num_sms, void* stream);
+int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list, int n_p,
+                   uint32_t* mask, void* stream);
+int launch_scales(const Common& cm, void* stream);
+int launch_bw_image(int mode, const BwImage& im, void* stream);
 int gemm_smem_bytes(int mode, int BN);
 int gemm_stages(int mode, int BN);
 

@@ -48,7 +48,7 @@ def test_status_strings(binding):
 def test_default_opts(binding):
     o = binding.make_opts()
     assert o.n_p == 7 and list(o.p_log2[:7]) == list(range(7))
-    assert o.compute == binding.PN_BF16 and o.scaling == 2 and o.diag_policy == 1
+    assert o.compute == binding.PN_BF16 and o.scaling == 2 and o.diag_policy == 2
 
 
 def test_default_tau_matches_oracle_reading(binding, orc):

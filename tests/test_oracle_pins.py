@@ -355,3 +355,18 @@ def test_gradient_euler_homogeneity(orc):
         np.testing.assert_allclose(np.dot(A[i], dA[i]), out["C"][i, j], rtol=1e-12)
         np.testing.assert_allclose(np.dot(B[:, j], dB[:, j]), out["C"][i, j], rtol=1e-12)
         assert np.all(dA[np.arange(M) != i] == 0.0)
+
+
+def test_gradient_entries_match_full_gradient(orc):
+    """The sampled-entry gradient loops agree with the full-matrix ones."""
+    M, N, K = 7, 9, 5
+    A, B = workloads.uniform_pair(M, N, K, seed=23, dtype=np.float64)
+    out = orc.pnorm(A, B, [0, 3, 5], tau=1e-300)
+    plog = out["p_sel"] & 0x7F
+    G = workloads.rng(24).random((M, N)) + 0.5
+    dA, dB = orc.pnorm_grad(A, B, plog, G)
+    ia, ka = np.array([0, 3, 6, 6]), np.array([0, 4, 1, 2])
+    kb, jb = np.array([0, 4, 2]), np.array([8, 0, 5])
+    eA, eB = orc.pnorm_grad_entries(A, B, plog, G, ia, ka, kb, jb)
+    np.testing.assert_allclose(eA, dA[ia, ka], rtol=1e-13)
+    np.testing.assert_allclose(eB, dB[kb, jb], rtol=1e-13)
