@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--workload", default="pnorm",
+                    choices=["pnorm", "apsp", "backward", "grouped"],
+                    help="pnorm: the default product; the others measure the other paths")
     return ap.parse_args()
 
 
@@ -412,10 +415,111 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ other workloads ---
+def _timed(torch, fn, K, warmup, stream):
+    for _ in range(max(warmup, 1)):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / K
+
+
+def run_other(args):
+    """APSP n=4096 (12 squarings, 3xTF32), forward+backward n=2048 (3xTF32),
+    or 4096 grouped products (BF16, CUDA-graph replay).  One JSON line."""
+    import torch
+    import paper_1511_05690_gb300 as pn
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    line = {"metric": "Effective semiring Gop/s (n^3/s): p-norm TC vs exact GPU kernel at stated err",
+            "unit": "Gop/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic"}
+    if args.workload == "apsp":
+        n, T = 4096, 12
+        W = torch.from_numpy(workloads.apsp_weights(n, density=0.1, index=1)).cuda()
+        D = torch.empty_like(W)
+        pn.apsp_pnorm(W, out=D)
+        graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(graph, stream=s):
+                pn.apsp_pnorm(W, out=D, check=False, stream=s)
+        stream.wait_stream(s)
+        ms = _timed(torch, graph.replay, K, args.warmup, stream)
+        E = torch.empty_like(W)
+        ems = _timed(torch, lambda: [pn.maxprod_exact(W, W, semiring=1, out=E) for _ in range(1)],
+                     1, 1, stream)
+        line.update(value=T * n ** 3 / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 (3xTF32)",
+                    config={"workload": "apsp_pnorm n=4096 density 0.1 U[0,1] weights, 12 "
+                            "squarings, P={1..64}, diag reset + clamp, CUDA graph", "n": n},
+                    exact_kernel={"one_minplus_squaring_ms": ems,
+                                  "gops": n ** 3 / (ems / 1e3) / 1e9},
+                    gpu_launches=K * (1 + T * 22 + 1))
+    elif args.workload == "backward":
+        n = 2048
+        A_h, B_h = workloads.uniform_pair(n, n, n, index=2)
+        A, B = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+        out = {}
+        for name, pl in (("p16", [4]), ("p1_64", list(range(7)))):
+            C, psel, ssel = pn.maxprod_pnorm(A, B, p_log2=pl, compute="f32")
+            G = 1.0 / C
+            fwd = _timed(torch, lambda: pn.maxprod_pnorm(A, B, p_log2=pl, compute="f32",
+                                                         check=False), K, args.warmup, stream)
+            bwd = _timed(torch, lambda: pn.maxprod_pnorm_backward(A, B, C, ssel, psel, G,
+                                                                  p_log2=pl, compute="f32",
+                                                                  check=False),
+                         K, args.warmup, stream)
+            import ctypes
+            o = pn.make_opts(pl, "f32")
+            ws_b = pn.lib().pn_backward_workspace_size(n, n, n, ctypes.byref(o))
+            out[name] = {"fwd_ms": fwd, "bwd_ms": bwd,
+                         "fwd_bwd_gops": n ** 3 / ((fwd + bwd) / 1e3) / 1e9,
+                         "recompute_workspace_bytes": int(ws_b),
+                         "saved_powered_tiles_bytes": 2 * n * n * 4 * len(pl)}
+        line.update(value=out["p1_64"]["fwd_bwd_gops"],
+                    ms_per_step=out["p1_64"]["fwd_ms"] + out["p1_64"]["bwd_ms"],
+                    dtype="f32 (3xTF32)",
+                    config={"workload": "maxprod_pnorm forward + backward n=2048 U(0,1], "
+                            "loss sum log C, P={16} and P={1..64}", "n": n, "detail": out})
+    else:
+        sizes = workloads.grouped_sizes(4096)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(workloads.SEED_BASE + 3)
+        As = [1 - torch.rand((int(m), int(m)), generator=g, device="cuda") for m in sizes]
+        Bs = [1 - torch.rand((int(m), int(m)), generator=g, device="cuda") for m in sizes]
+        plan = pn.GroupedProduct(As, Bs, compute="bf16", tile_n=args.tile_n)
+        plan.run(check=True)
+        chosen = plan.autotune() if args.tile_n == 0 else args.tile_n
+        graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(graph, stream=s):
+                plan.run(stream=s)
+        stream.wait_stream(s)
+        ms = _timed(torch, graph.replay, K, args.warmup, stream)
+        ops = float(np.sum(sizes.astype(np.float64) ** 3))
+        line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="bf16",
+                    config={"workload": "4096 square products, n = round(16 * 64^U), BF16, "
+                            "P={1..64}, one launch per p level, CUDA graph replay",
+                            "sum_n3": ops, "tile_n": chosen})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "pnorm":
+        run_other(args)
     else:
         run_ours(args)
 

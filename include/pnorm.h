@@ -127,7 +127,8 @@ PN_API double pn_default_tau(int64_t K, int32_t compute);
 PN_API int32_t pn_device_sm_count(void);
 
 /* Bytes of workspace maxprod_pnorm needs for these sizes and options
- * (0 on invalid options).  The workspace must be 256-byte aligned. */
+ * (0 on invalid options); with tile_n = 0 it covers every tile width the
+ * autotuner may pick.  The workspace must be 256-byte aligned. */
 PN_API size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts);
 
 /* p-norm estimate of the (x, max) product C = A (x,max) B (Alg. 5 with H a
@@ -227,18 +228,39 @@ PN_API pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const f
  * copies host memory and can be captured in a CUDA graph:
  *  1. pn_grouped_build_table() (host only, no CUDA calls) writes a table
  *     describing `count` problems (sizes MNK[3g..3g+2] = M_g, N_g, K_g, and
- *     DEVICE pointers A[g], B[g], C[g] of contiguous row-major FP32 matrices)
- *     into host memory `host_table` of pn_grouped_table_bytes(count) bytes,
- *     and returns the workspace size in *ws_bytes.
+ *     DEVICE pointers A[g], B[g], C[g] of contiguous row-major FP32 matrices;
+ *     K_g >= 1 unless M_g or N_g is 0) into host memory `host_table` of
+ *     pn_grouped_table_bytes(count) bytes, and returns the workspace size in
+ *     *ws_bytes.  The table holds layouts for 128- and 256-wide tiles.
  *  2. The caller copies the table bytes unchanged to device memory
  *     `dev_table` (16-byte aligned) and calls maxprod_pnorm_grouped() with
- *     both copies; each C_g receives the same estimate as maxprod_pnorm. */
+ *     both copies and the same options; each C_g receives the estimate
+ *     maxprod_pnorm computes (no p_sel / S_sel).  opts->tile_n selects the
+ *     layout; 0 uses the autotuned choice for this table, else a size rule. */
 PN_API size_t pn_grouped_table_bytes(int32_t count);
 PN_API pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
-                                 const float* const* B, float* const* C, const pn_opts* opts,
-                                 void* host_table, size_t table_bytes, size_t* ws_bytes);
+                                        const float* const* B, float* const* C,
+                                        const pn_opts* opts, void* host_table,
+                                        size_t table_bytes, size_t* ws_bytes);
 PN_API pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
-                                const pn_opts* opts, void* ws, size_t ws_bytes, void* stream);
+                                       const pn_opts* opts, void* ws, size_t ws_bytes,
+                                       void* stream);
+
+/* Autotuner of the output tile width (no counterpart in the paper).  Times
+ * every candidate width (128, 256; 3xTF32 has only 128) on the caller's
+ * buffers with CUDA events -- three timed runs each after a warm-up -- and
+ * remembers the fastest for this device and shape class (ceil(log2) of M, N,
+ * K for a product; the table's sizes for a group).  Later calls with
+ * tile_n = 0 use it.  Synchronises the stream; not for use inside a stream
+ * capture.  The chosen width is returned in *chosen_tile_n (nullable).  The
+ * buffers are overwritten exactly as by the product itself. */
+PN_API pn_status pn_autotune(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
+                             const float* B, int64_t ldb, float* C, int64_t ldc,
+                             const pn_opts* opts, void* ws, size_t ws_bytes, void* stream,
+                             int32_t* chosen_tile_n);
+PN_API pn_status pn_grouped_autotune(const void* host_table, const void* dev_table,
+                                     const pn_opts* opts, void* ws, size_t ws_bytes,
+                                     void* stream, int32_t* chosen_tile_n);
 
 #ifdef __cplusplus
 }

@@ -23,7 +23,7 @@ from ._binding import (PN_BF16, PN_E4M3, PN_F16, PN_F32_EXACT, PN_TF32, PnError,
 
 __all__ = ["maxprod_pnorm", "maxprod_exact", "apsp_pnorm", "default_tau", "workspace",
            "PnError", "make_opts", "status_string", "sm_count", "PNormMaxProd",
-           "maxprod_pnorm_backward"]
+           "maxprod_pnorm_backward", "GroupedProduct", "autotune"]
 
 _ws = {}
 _status = {}
@@ -136,6 +136,85 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
     if check:
         check_device_status(dev, "maxprod_pnorm")
     return C, psel, ssel
+
+
+def autotune(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), compute="bf16",
+             tau=None, scaling=2, stream=None) -> int:
+    """Times the tile widths for this shape class and remembers the fastest
+    (later calls with tile_n=0 use it).  Synchronises; returns the width."""
+    A, B = _mat(A, "A"), _mat(B, "B")
+    M, K = A.shape
+    N = B.shape[1]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    o = make_opts(p_log2, compute, tau, scaling, 2, 0, status_word(A.device).data_ptr())
+    L = lib()
+    need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
+    ws = workspace(need, A.device)
+    chosen = ctypes.c_int32(0)
+    rc = L.pn_autotune(M, N, K, A.data_ptr(), _ld(A), B.data_ptr(), _ld(B), C.data_ptr(), _ld(C),
+                       ctypes.byref(o), ws.data_ptr(), ws.numel(), _stream_ptr(stream),
+                       ctypes.byref(chosen))
+    _b.check(rc, "pn_autotune")
+    return int(chosen.value)
+
+
+class GroupedProduct:
+    """Many independent p-norm (x,max) products C_g = A_g (x) B_g computed
+    together, one persistent launch per p level.  The problem table is built
+    and copied to the device once here; run() only launches kernels, so it can
+    be captured in a CUDA graph (the plan keeps its own workspace and outputs
+    alive for replays).  A_g: (M_g, K_g), B_g: (K_g, N_g), float32 CUDA."""
+
+    def __init__(self, As, Bs, *, p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2,
+                 tile_n=0):
+        import numpy as np
+        if len(As) != len(Bs):
+            raise ValueError("As and Bs differ in length")
+        self.As = [_mat(a, "A").contiguous() for a in As]
+        self.Bs = [_mat(b, "B").contiguous() for b in Bs]
+        dev = self.As[0].device if self.As else torch.device("cuda")
+        self.Cs = [torch.empty((a.shape[0], b.shape[1]), dtype=torch.float32, device=dev)
+                   for a, b in zip(self.As, self.Bs)]
+        count = len(self.As)
+        mnk = []
+        for a, b in zip(self.As, self.Bs):
+            if a.shape[1] != b.shape[0]:
+                raise ValueError("inner dimensions differ")
+            mnk += [a.shape[0], b.shape[1], a.shape[1]]
+        self.status = status_word(dev)
+        self.opts = make_opts(p_log2, compute, tau, scaling, 2, tile_n, self.status.data_ptr())
+        L = lib()
+        MNK = (ctypes.c_int64 * max(1, 3 * count))(*mnk)
+        vp = ctypes.c_void_p
+        Ap = (vp * max(1, count))(*[a.data_ptr() for a in self.As])
+        Bp = (vp * max(1, count))(*[b.data_ptr() for b in self.Bs])
+        Cp = (vp * max(1, count))(*[c.data_ptr() for c in self.Cs])
+        tb = L.pn_grouped_table_bytes(count)
+        self.host_table = np.zeros(tb, dtype=np.uint8)
+        ws_bytes = ctypes.c_size_t(0)
+        rc = L.pn_grouped_build_table(count, MNK, Ap, Bp, Cp, ctypes.byref(self.opts),
+                                      self.host_table.ctypes.data_as(vp), tb,
+                                      ctypes.byref(ws_bytes))
+        _b.check(rc, "pn_grouped_build_table")
+        self.dev_table = torch.from_numpy(self.host_table).to(dev)
+        self.ws = torch.empty(max(int(ws_bytes.value), 256), dtype=torch.uint8, device=dev)
+
+    def _args(self):
+        return (self.host_table.ctypes.data_as(ctypes.c_void_p), self.dev_table.data_ptr(),
+                ctypes.byref(self.opts), self.ws.data_ptr(), self.ws.numel())
+
+    def run(self, stream=None, check=False):
+        rc = lib().maxprod_pnorm_grouped(*self._args(), _stream_ptr(stream))
+        _b.check(rc, "maxprod_pnorm_grouped")
+        if check:
+            check_device_status(self.ws.device, "maxprod_pnorm_grouped")
+        return self.Cs
+
+    def autotune(self, stream=None) -> int:
+        chosen = ctypes.c_int32(0)
+        rc = lib().pn_grouped_autotune(*self._args(), _stream_ptr(stream), ctypes.byref(chosen))
+        _b.check(rc, "pn_grouped_autotune")
+        return int(chosen.value)
 
 
 def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None, out=None,

@@ -27,7 +27,7 @@ EXPORTS = (
     "pn_workspace_size", "maxprod_pnorm", "maxprod_exact", "pn_maxprod_exact_variant",
     "pn_apsp_workspace_size", "apsp_pnorm", "pn_backward_workspace_size",
     "maxprod_pnorm_backward", "pn_grouped_table_bytes", "pn_grouped_build_table",
-    "maxprod_pnorm_grouped", "maxprod_pnorm_static",
+    "maxprod_pnorm_grouped", "maxprod_pnorm_static", "pn_autotune", "pn_grouped_autotune",
 )
 
 
@@ -109,6 +109,11 @@ def load():
         lib.pn_grouped_build_table.restype = i32
         lib.maxprod_pnorm_grouped.argtypes = [vp, vp, optp, vp, sz, vp]
         lib.maxprod_pnorm_grouped.restype = i32
+        lib.pn_autotune.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, optp, vp, sz, vp,
+                                    ctypes.POINTER(i32)]
+        lib.pn_autotune.restype = i32
+        lib.pn_grouped_autotune.argtypes = [vp, vp, optp, vp, sz, vp, ctypes.POINTER(i32)]
+        lib.pn_grouped_autotune.restype = i32
         _lib = lib
         return lib
 

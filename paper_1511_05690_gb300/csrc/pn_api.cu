@@ -60,10 +60,11 @@ bool opts_valid(const pn_opts* o) {
 }
 
 // Tile width: 3xTF32 carries two operand planes, so only 128 fits the ring.
-int choose_bn(const pn_opts* o, int64_t M, int64_t N) {
+int choose_bn(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
   if (o->compute == PN_F32_EXACT) return 128;
   if (o->tile_n) return o->tile_n;
-  (void)M;
+  const int tuned = host_tuned_bn(o->compute, M, N, K);  // autotune cache
+  if (tuned) return tuned;
   return N > 128 ? 256 : 128;
 }
 
@@ -91,7 +92,7 @@ struct Layout {
 Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   Layout L;
   const int mode = o->compute;
-  L.BN = choose_bn(o, M, N);
+  L.BN = choose_bn(o, M, N, K);
   L.n_p = o->n_p;
   L.planes = mode_planes(mode);
   L.KB = static_cast<int>(ceil_div(K, mode_bk(mode)));
@@ -142,6 +143,16 @@ double default_tau(int64_t K, int compute) {
 }
 
 pn_status cuda_status(int e) { return e == 0 ? PN_OK : PN_ECUDA; }
+
+}  // namespace
+
+// Shared with the grouped and autotune code (pn_grouped.cu).
+int host_device_sms() { return device_sms(); }
+bool host_opts_valid(const pn_opts* o) { return opts_valid(o); }
+double host_default_tau(int64_t K, int compute) { return default_tau(K, compute); }
+float host_tau_up(double t) { return tau_up(t); }
+
+namespace {
 
 // Fills the Common / Prob description of one product laid out by `L` in `ws`.
 void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, const float* A,
@@ -349,7 +360,14 @@ int32_t pn_device_sm_count(void) { return pn::device_sms(); }
 
 size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts) {
   if (!opts_valid(opts) || !dims_ok(M, N, K)) return 0;
-  return make_layout(M, N, K, opts).total;
+  if (opts->tile_n != 0 || opts->compute == PN_F32_EXACT) return make_layout(M, N, K, opts).total;
+  // tile_n = 0: large enough for either width the autotuner may choose
+  pn_opts o = *opts;
+  o.tile_n = 128;
+  const size_t a = make_layout(M, N, K, &o).total;
+  o.tile_n = 256;
+  const size_t b = make_layout(M, N, K, &o).total;
+  return a > b ? a : b;
 }
 
 pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
@@ -560,25 +578,6 @@ pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A
     if (launch_gemm_grad(g2, lv, sms, stream)) return PN_ECUDA;
   }
   return PN_OK;
-}
-
-size_t pn_grouped_table_bytes(int32_t count) {
-  (void)count;
-  return 0;
-}
-
-pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
-                                 const float* const* B, float* const* C, const pn_opts* opts,
-                                 void* host_table, size_t table_bytes, size_t* ws_bytes) {
-  (void)count; (void)MNK; (void)A; (void)B; (void)C; (void)opts; (void)host_table;
-  (void)table_bytes; (void)ws_bytes;
-  return PN_EUNSUPPORTED;
-}
-
-pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
-                                const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
-  (void)host_table; (void)dev_table; (void)opts; (void)ws; (void)ws_bytes; (void)stream;
-  return PN_EUNSUPPORTED;
 }
 
 }  // extern "C"

@@ -161,6 +161,13 @@ __host__ __device__ inline void raster(int lt, int tiles_m, int tiles_n, int& tm
   tn = local / gm;
 }
 
+// --------------------------------------------------------- host helpers ---
+int host_device_sms();                      // SMs of the current sm_103 device, else 0
+bool host_opts_valid(const pn_opts* o);
+double host_default_tau(int64_t K, int compute);
+float host_tau_up(double t);                // smallest float >= t
+int host_tuned_bn(int mode, int64_t M, int64_t N, int64_t K);  // autotune cache, 0 if none
+
 // ------------------------------------------------------------ launchers ---
 // All return a cudaError_t value as int (0 = success).
 int launch_maxes(const Common& cm, void* stream);
