@@ -230,14 +230,16 @@ PN_API pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const f
  *     describing `count` problems (sizes MNK[3g..3g+2] = M_g, N_g, K_g, and
  *     DEVICE pointers A[g], B[g], C[g] of contiguous row-major FP32 matrices;
  *     K_g >= 1 unless M_g or N_g is 0) into host memory `host_table` of
- *     pn_grouped_table_bytes(count) bytes, and returns the workspace size in
- *     *ws_bytes.  The table holds layouts for 128- and 256-wide tiles.
+ *     pn_grouped_table_bytes(count, MNK, opts) bytes (0 on invalid
+ *     arguments), and returns the workspace size in *ws_bytes.  The table
+ *     holds layouts for 128- and 256-wide tiles and, per layout, lookup
+ *     tables from every tile / operand tile / max-pass unit to its problem.
  *  2. The caller copies the table bytes unchanged to device memory
  *     `dev_table` (16-byte aligned) and calls maxprod_pnorm_grouped() with
  *     both copies and the same options; each C_g receives the estimate
  *     maxprod_pnorm computes (no p_sel / S_sel).  opts->tile_n selects the
  *     layout; 0 uses the autotuned choice for this table, else a size rule. */
-PN_API size_t pn_grouped_table_bytes(int32_t count);
+PN_API size_t pn_grouped_table_bytes(int32_t count, const int64_t* MNK, const pn_opts* opts);
 PN_API pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
                                         const float* const* B, float* const* C,
                                         const pn_opts* opts, void* host_table,

@@ -189,7 +189,9 @@ class GroupedProduct:
         Ap = (vp * max(1, count))(*[a.data_ptr() for a in self.As])
         Bp = (vp * max(1, count))(*[b.data_ptr() for b in self.Bs])
         Cp = (vp * max(1, count))(*[c.data_ptr() for c in self.Cs])
-        tb = L.pn_grouped_table_bytes(count)
+        tb = L.pn_grouped_table_bytes(count, MNK, ctypes.byref(self.opts))
+        if tb == 0:
+            raise PnError(_b.PN_EINVAL, "pn_grouped_table_bytes")
         self.host_table = np.zeros(tb, dtype=np.uint8)
         ws_bytes = ctypes.c_size_t(0)
         rc = L.pn_grouped_build_table(count, MNK, Ap, Bp, Cp, ctypes.byref(self.opts),

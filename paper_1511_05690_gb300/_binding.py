@@ -102,7 +102,7 @@ def load():
         lib.maxprod_pnorm_backward.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp,
                                                optp, vp, sz, vp]
         lib.maxprod_pnorm_backward.restype = i32
-        lib.pn_grouped_table_bytes.argtypes = [i32]
+        lib.pn_grouped_table_bytes.argtypes = [i32, vp, optp]
         lib.pn_grouped_table_bytes.restype = sz
         lib.pn_grouped_build_table.argtypes = [i32, vp, vp, vp, vp, optp, vp, sz,
                                                ctypes.POINTER(sz)]

@@ -2,11 +2,11 @@
 //
 // Grouped: many independent (x,max) products in one launch per p level (the
 // problems and the p rings parallelise coarsely, Sec. 4).  Every kernel of the
-// product already maps a global id (operand tile, output tile, tile row /
-// column, max-pass unit) to its problem by a binary search over per-problem
-// first ids, so a group is a table of Prob records with running offsets into
-// one shared workspace.  The table is built on the host and copied to the
-// device by the caller once; the run step then only launches kernels and can
+// product works on global ids (operand tile, output tile, tile row / column,
+// max-pass unit); a group is a table of Prob records with running offsets
+// into one shared workspace, plus id -> problem lookup tables so that a kernel
+// finds the problem of an id with one load.  The table is built on the host
+// and copied to the device by the caller once; the run step then only launches kernels and can
 // be captured in a CUDA graph.  The table holds two layouts, for 128- and
 // 256-wide output tiles, so the autotuner can time both on the same buffers.
 //
@@ -38,7 +38,28 @@ struct GroupLayout {
   uint64_t off_rmax, off_cmax, off_gmax, off_counts, off_rflag, off_cflag, ctrl_bytes;
   uint64_t off_r, off_c, off_work, off_state, off_aimg, off_bimg, total;
   uint64_t probs_offset;  // bytes from the table start to this layout's Prob[count]
+  uint64_t lut_offset[7]; // bytes from the table start to each id -> problem table
 };
+
+// Id counts of a layout (tile width BN): tiles, A tiles, B tiles, tile rows,
+// tile columns, A max units, B max units.
+void id_counts(int32_t count, const int64_t* MNK, int mode, int BN, int64_t out[7]) {
+  const int bk = mode_bk(mode);
+  for (int w = 0; w < 7; ++w) out[w] = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    const int64_t M = MNK[3 * g], N = MNK[3 * g + 1], K = MNK[3 * g + 2];
+    if (M <= 0 || N <= 0) continue;
+    const int64_t tm = ceil_div(M, TILE_M), tn = ceil_div(N, BN), KB = ceil_div(K, bk);
+    const int64_t rbb = tn * (BN / TILE_M);
+    out[0] += tm * tn;
+    out[1] += tm * KB;
+    out[2] += rbb * KB;
+    out[3] += tm;
+    out[4] += tn;
+    out[5] += tm * ceil_div(K, MAXSEG_A);
+    out[6] += rbb * ceil_div(K, MAXSEG_B);
+  }
+}
 
 struct GroupHeader {
   uint64_t magic;
@@ -48,8 +69,14 @@ struct GroupHeader {
   GroupLayout layout[2];
 };
 
-size_t table_bytes(int32_t count) {
-  return align_up(sizeof(GroupHeader), 64) + 2 * static_cast<size_t>(count) * sizeof(Prob);
+size_t table_bytes(int32_t count, const int64_t* MNK, int mode) {
+  size_t b = align_up(sizeof(GroupHeader), 64) + 2 * static_cast<size_t>(count) * sizeof(Prob);
+  for (int l = 0; l < 2; ++l) {
+    int64_t ids[7];
+    id_counts(count, MNK, mode, (mode == MODE_3XTF32 || l == 0) ? 128 : 256, ids);
+    for (int w = 0; w < 7; ++w) b += align_up(sizeof(int32_t) * static_cast<size_t>(ids[w]), 16);
+  }
+  return b;
 }
 
 // -------------------------------------------------------------- autotune ---
@@ -102,16 +129,32 @@ using namespace pn;
 
 extern "C" {
 
-size_t pn_grouped_table_bytes(int32_t count) { return count < 0 ? 0 : table_bytes(count); }
+size_t pn_grouped_table_bytes(int32_t count, const int64_t* MNK, const pn_opts* opts) {
+  if (count < 0 || !host_opts_valid(opts) || (count > 0 && !MNK)) return 0;
+  for (int32_t g = 0; g < count; ++g)
+    for (int t = 0; t < 3; ++t)
+      if (MNK[3 * g + t] < 0 || MNK[3 * g + t] >= (int64_t(1) << 30)) return 0;
+  return table_bytes(count, MNK, opts->compute);
+}
 
 pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float* const* A,
                                  const float* const* B, float* const* C, const pn_opts* opts,
                                  void* host_table, size_t tbytes, size_t* ws_bytes) {
   if (count < 0 || !host_opts_valid(opts) || !host_table) return PN_EINVAL;
   if (count > 0 && (!MNK || !A || !B || !C)) return PN_EINVAL;
-  if (tbytes < table_bytes(count)) return PN_EINVAL;
   const int mode = opts->compute;
   const int bk = mode_bk(mode), planes = mode_planes(mode);
+  uint64_t sig = 1469598103934665603ull;
+  int64_t sum_cube = 0;
+  for (int32_t g = 0; g < count; ++g) {
+    const int64_t M = MNK[3 * g], N = MNK[3 * g + 1], K = MNK[3 * g + 2];
+    if (M < 0 || N < 0 || K < 0 || M >= (1 << 30) || N >= (1 << 30) || K >= (1 << 30))
+      return PN_EINVAL;
+    if (M > 0 && N > 0 && (K == 0 || !A[g] || !B[g] || !C[g])) return PN_EINVAL;
+    for (int t = 0; t < 3; ++t) sig = (sig ^ static_cast<uint64_t>(MNK[3 * g + t])) * 1099511628211ull;
+    sum_cube += M * N * K;
+  }
+  if (tbytes < table_bytes(count, MNK, mode)) return PN_EINVAL;
   auto* H = static_cast<GroupHeader*>(host_table);
   std::memset(H, 0, sizeof(GroupHeader));
   H->magic = GROUP_MAGIC;
@@ -119,17 +162,10 @@ pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float*
   H->n_p = opts->n_p;
   H->mode = mode;
   H->scaling = opts->scaling;
-  uint64_t sig = 1469598103934665603ull;
-  for (int32_t g = 0; g < count; ++g) {
-    const int64_t M = MNK[3 * g], N = MNK[3 * g + 1], K = MNK[3 * g + 2];
-    if (M < 0 || N < 0 || K < 0 || M >= (1 << 30) || N >= (1 << 30) || K >= (1 << 30))
-      return PN_EINVAL;
-    if (M > 0 && N > 0 && (K == 0 || !A[g] || !B[g] || !C[g])) return PN_EINVAL;
-    for (int t = 0; t < 3; ++t) sig = (sig ^ static_cast<uint64_t>(MNK[3 * g + t])) * 1099511628211ull;
-    H->sum_cube += M * N * K;
-  }
   H->signature = sig;
+  H->sum_cube = sum_cube;
   size_t off_probs = align_up(sizeof(GroupHeader), 64);
+  size_t off_lut = off_probs + 2 * static_cast<size_t>(count) * sizeof(Prob);
   size_t need = 0;
   for (int l = 0; l < 2; ++l) {
     GroupLayout& L = H->layout[l];
@@ -187,8 +223,29 @@ pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float*
       abytes += P.a_plane * planes;
       bbytes += P.b_plane * planes;
     }
-    if (tiles >= (int64_t(1) << 31) || xa >= (int64_t(1) << 31) || xb >= (int64_t(1) << 31))
+    if (tiles >= (int64_t(1) << 31) || xa >= (int64_t(1) << 31) || xb >= (int64_t(1) << 31) ||
+        ma >= (int64_t(1) << 31) || mb >= (int64_t(1) << 31))
       return PN_EINVAL;
+    // id -> problem lookup tables of this layout
+    const int64_t totals[7] = {tiles, xa, xb, tm, tn, ma, mb};
+    for (int w = 0; w < 7; ++w) {
+      L.lut_offset[w] = off_lut;
+      int32_t* lut = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(host_table) + off_lut);
+      for (int32_t g = 0; g < count; ++g) {
+        const Prob& P = probs[g];
+        const int64_t base = w == 0 ? P.tile_base : w == 1 ? P.xa_base : w == 2 ? P.xb_base
+                           : w == 3 ? P.tm_base : w == 4 ? P.tn_base : w == 5 ? P.ma_base : P.mb_base;
+        const int64_t cnt = w == 0 ? int64_t(P.tiles_m) * P.tiles_n
+                          : w == 1 ? int64_t(P.RBA) * P.KB
+                          : w == 2 ? int64_t(P.RBB) * P.KB
+                          : w == 3 ? P.tiles_m
+                          : w == 4 ? P.tiles_n
+                          : w == 5 ? int64_t(P.RBA) * P.KMA
+                                   : int64_t(P.RBB) * P.KMB;
+        for (int64_t e = 0; e < cnt; ++e) lut[base + e] = g;
+      }
+      off_lut += align_up(sizeof(int32_t) * static_cast<size_t>(totals[w]), 16);
+    }
     L.total_tiles = static_cast<int32_t>(tiles);
     L.total_xa = static_cast<int32_t>(xa);
     L.total_xb = static_cast<int32_t>(xb);
@@ -225,6 +282,8 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   Common cm;
   std::memset(&cm, 0, sizeof(cm));
   cm.probs = reinterpret_cast<const Prob*>(static_cast<const uint8_t*>(dev_table) + L.probs_offset);
+  for (int w = 0; w < 7; ++w)
+    cm.lut[w] = reinterpret_cast<const int32_t*>(static_cast<const uint8_t*>(dev_table) + L.lut_offset[w]);
   cm.nprob = H->count;
   cm.total_tiles = L.total_tiles;
   cm.total_xa = L.total_xa;

@@ -60,6 +60,9 @@ struct Prob {
 // Everything a launch needs besides the per-level control.
 struct Common {
   const Prob* probs;  // device table (grouped) or nullptr
+  // grouped: problem index of every global id, per id space (tiles, A operand
+  // tiles, B operand tiles, tile rows, tile columns, A / B max-pass units)
+  const int32_t* lut[7];
   Prob single;        // the problem when nprob == 1
   int32_t nprob;
   int32_t total_tiles, total_xa, total_xb;
@@ -129,25 +132,12 @@ __host__ __device__ inline const Prob& prob_at(const Common& cm, int g) {
   return cm.nprob == 1 ? cm.single : cm.probs[g];
 }
 
-// Problem index owning global id `id` given per-problem first ids (binary
-// search on the field selected by `which`: 0 tiles, 1 A operand tiles, 2 B
-// operand tiles, 3 tile rows, 4 tile columns, 5 A max units, 6 B max units).
+// Problem index owning global id `id` in id space `which` (0 tiles, 1 A
+// operand tiles, 2 B operand tiles, 3 tile rows, 4 tile columns, 5 A max
+// units, 6 B max units): a table lookup for groups.
 __host__ __device__ inline int find_prob(const Common& cm, int id, int which) {
   if (cm.nprob == 1) return 0;
-  int lo = 0, hi = cm.nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    const Prob& p = cm.probs[mid];
-    const int base = which == 0   ? p.tile_base
-                     : which == 1 ? p.xa_base
-                     : which == 2 ? p.xb_base
-                     : which == 3 ? p.tm_base
-                     : which == 4 ? p.tn_base
-                     : which == 5 ? p.ma_base
-                                  : p.mb_base;
-    if (base <= id) lo = mid; else hi = mid - 1;
-  }
-  return lo;
+  return cm.lut[which][id];
 }
 
 // Local tile index -> (tile row, tile column), grouped raster order.
