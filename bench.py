@@ -200,6 +200,23 @@ def cpu_baseline(A_h, B_h, n, seconds, oracle):
                       f"the {len(P_LOG2)} p-sums each, FP64); {t:.1f} s"}
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank number over all ranks (the slowest rank sets the time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, ops_per_step: float, steps: int, ms_max: float) -> float:
+    """Whole-job throughput in G ops/s: every rank computes its own product
+    (weak scaling), over the slowest rank's time."""
+    return world * ops_per_step * steps / (ms_max / 1e3) / 1e9
+
+
 # ----------------------------------------------------------------- ours ---
 def run_ours(args):
     import torch
@@ -250,12 +267,9 @@ def run_ours(args):
     pn.check_device_status(A.device, "timed steps")
     ms = t_begin.elapsed_time(t_end)
     gemm_ms = [a.elapsed_time(b) for a, b in gev]
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, device="cuda")
     ops = float(n) ** 3
-    value = world * ops * K / (ms_max / 1e3) / 1e9
+    value = job_value(world, ops, K, ms_max)
 
     # error of the estimate at sampled entries: vs exact and vs the FP64 p-norm
     err = None
@@ -325,10 +339,8 @@ def run_ours(args):
         e2e_step()
     x1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([x0.elapsed_time(x1) / KE], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = world * ops / (float(e2e_ms.item()) / 1e3) / 1e9
+    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / KE, world, device="cuda")
+    e2e_value = job_value(world, ops, 1, e2e_ms)
     pn.check_device_status(A.device, "e2e")
 
     peaks, peak_src = measured_peaks()

@@ -370,3 +370,16 @@ def test_gradient_entries_match_full_gradient(orc):
     eA, eB = orc.pnorm_grad_entries(A, B, plog, G, ia, ka, kb, jb)
     np.testing.assert_allclose(eA, dA[ia, ka], rtol=1e-13)
     np.testing.assert_allclose(eB, dB[kb, jb], rtol=1e-13)
+
+
+def test_entries_match_full_psums(orc):
+    """The selected-entry loops agree with the full p-sum and max-product loops."""
+    A, B = workloads.wide_range_pair(23, 17, 41, seed=25, dtype=np.float64)
+    pl = [0, 2, 4, 6]
+    r, c = orc.row_scales(A), orc.col_scales(B)
+    S = orc.psums(A, B, pl)
+    g = workloads.rng(26)
+    ii, jj = g.integers(0, 23, 50), g.integers(0, 17, 50)
+    ex, Se = orc.entries(A, B, ii, jj, pl, r, c)
+    np.testing.assert_array_equal(ex, orc.maxprod(A, B)[ii, jj])
+    np.testing.assert_allclose(Se, S[:, ii, jj].T, rtol=1e-14)
