@@ -156,13 +156,20 @@ def gemm_peak_tflops(compute, peaks):
     return peaks["bf16_tflops_sustained"] * ratio
 
 
+def gemm_source_sha():
+    """Hash of every source the tensor-core level kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("pn_gemm_kernel.cuh", "pn_device.cuh", "pn_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1511_05690_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profile(compute):
     """DRAM bytes per top-level GEMM launch recorded by ncu in profiles/, if the
     kernel source is unchanged since the capture (else None)."""
-    src = os.path.join(ROOT, "paper_1511_05690_gb300", "csrc", "pn_gemm_kernel.cuh")
     prof = os.path.join(ROOT, "profiles", f"gemm_level_{compute}_n16384.md")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = gemm_source_sha()
         text = open(prof).read()
     except OSError:
         return None

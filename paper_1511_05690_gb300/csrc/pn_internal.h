@@ -11,7 +11,7 @@ namespace pn {
 constexpr int TILE_M = 128;         // output rows per tensor-core tile (MMA M)
 constexpr int IMG_BYTES = 16384;    // one operand tile image: 128 rows x 128 bytes
 constexpr int IMG_ROW_BYTES = 128;  // bytes of K per image row (one 128-byte swizzle row)
-constexpr int RASTER_GM = 8;        // tile rows per raster group (L2 reuse of B)
+constexpr int RASTER_GM = 16;       // tile rows per raster group (L2 reuse of B)
 constexpr int MAXSEG_A = 1024;      // columns of A per max-pass unit
 constexpr int MAXSEG_B = 256;       // rows of B per max-pass unit
 

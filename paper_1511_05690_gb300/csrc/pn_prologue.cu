@@ -200,8 +200,16 @@ __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, 
 
 // Top level: one block per operand tile.  Lower levels: one block per tile
 // row, skipped unless a pushed output tile needs that row block.
+// Resident blocks per SM for the image kernels: as many as the registers of
+// the format's loads allow without heavy spilling -- more blocks keep more
+// loads in flight (the max pass, at HBM speed, keeps about 200 KB per SM).
 template <int MODE>
-__global__ void __launch_bounds__(PRO_THREADS)
+constexpr int img_min_blocks() {
+  return MODE == MODE_E4M3 ? 3 : (MODE == MODE_BF16 || MODE == MODE_F16) ? 4 : 5;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_a(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
   if (lv.is_top) {
     const int id = blockIdx.x;
@@ -291,7 +299,7 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
 // Top level: one block per operand tile.  Lower levels: one block per output
 // tile column, skipped unless a pushed output tile needs it.
 template <int MODE>
-__global__ void __launch_bounds__(PRO_THREADS)
+__global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_b(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
   extern __shared__ float stile[];  // [BK][129]
   if (lv.is_top) {
