@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--compute", default="bf16")
     ap.add_argument("--tile-n", type=int, default=0)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--err-samples", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -322,33 +322,27 @@ def run_ours(args):
                       "speedup_of_pnorm": (ops / (ms_max / K / 1e3) / 1e9) / (ops / (ems / 1e3) / 1e9)}
         del E
 
-    # end to end through the public API from pinned host buffers
+    # end to end through the public API from pinned host buffers: every step
+    # copies its inputs in, runs the product and copies C out; consecutive
+    # independent steps overlap on three streams (paper_1511_05690_gb300.pipeline)
+    from paper_1511_05690_gb300.pipeline import HostPipeline
     Ah = torch.from_numpy(A_h).pin_memory()
     Bh = torch.from_numpy(B_h).pin_memory()
     Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
-    Ad, Bd = torch.empty_like(A), torch.empty_like(B)
-
-    def e2e_step():
-        Ad.copy_(Ah, non_blocking=True)
-        Bd.copy_(Bh, non_blocking=True)
-        pn.maxprod_pnorm(Ad, Bd, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n, out=C,
-                         want_psel=False, want_ssel=False, check=False)
-        Ch.copy_(C, non_blocking=True)
-
-    e2e_step()
-    torch.cuda.synchronize()
-    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    del C
+    torch.cuda.empty_cache()
+    pipe = HostPipeline(n, n, n, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2)
     KE = max(1, args.e2e_steps)
+    pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         dist.barrier()
-    x0.record(stream)
-    for _ in range(KE):
-        e2e_step()
-    x1.record(stream)
     torch.cuda.synchronize()
+    pipe.run([(Ah, Bh, Ch)] * KE, ev_start=x0, ev_end=x1)
     e2e_ms = max_over_ranks(x0.elapsed_time(x1) / KE, world, device="cuda")
     e2e_value = job_value(world, ops, 1, e2e_ms)
     pn.check_device_status(A.device, "e2e")
+    del pipe
 
     peaks, peak_src = measured_peaks()
     gemm_avg = statistics.mean(gemm_ms)
@@ -363,7 +357,9 @@ def run_ours(args):
                    "outputs": "C and p_sel", "l2": "inputs larger than L2 (1 GiB each), no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * n,
-                "d2h_bytes_per_step": 4 * n * n, "steps": KE},
+                "d2h_bytes_per_step": 4 * n * n, "steps": KE,
+                "how": "pinned host A, B in / C out every step; steps overlap copy-in, "
+                       "compute and copy-out on three streams"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(args.compute),
                      "kernel": "k_gemm_level (largest p), 2*n^3 FLOP per launch",
