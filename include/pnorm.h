@@ -181,11 +181,13 @@ PN_API pn_status maxprod_exact(int64_t M, int64_t N, int64_t K, const float* A, 
                         const float* B, int64_t ldb, float* C, int64_t ldc, int32_t semiring,
                         void* stream);
 
-/* maxprod_exact with an explicit kernel variant, for comparing the two:
+/* maxprod_exact with an explicit kernel variant, for comparing them:
  * variant 0 issues one FP32 multiply (add) and one max (min) per semiring
- * operation; variant 1 (the default of maxprod_exact) forms two consecutive
- * products with one paired mul.rn.f32x2 (add.rn.f32x2) and folds both with
- * one 3-input max (min).  Both give identical results. */
+ * operation; variant 1 forms two consecutive products with one paired
+ * mul.rn.f32x2 (add.rn.f32x2) and folds both with one 3-input max (min);
+ * variant 2 (the default of maxprod_exact) issues variant 1's instructions in
+ * a software-pipelined order.  All give identical results.  A variant outside
+ * 0..2 returns PN_EINVAL. */
 PN_API pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                                    const float* B, int64_t ldb, float* C, int64_t ldc,
                                    int32_t semiring, int32_t variant, void* stream);

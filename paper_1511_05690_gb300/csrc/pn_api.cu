@@ -395,15 +395,17 @@ pn_status maxprod_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t
   if (!C || ldc < N) return PN_EINVAL;
   if (K > 0 && (!A || !B || lda < K || ldb < N)) return PN_EINVAL;
   if (device_sms() <= 0) return PN_EUNSUPPORTED;
-  return cuda_status(launch_exact(M, N, K, A, lda, B, ldb, C, ldc, semiring, 1, stream));
+  return cuda_status(launch_exact(M, N, K, A, lda, B, ldb, C, ldc, semiring, 2, stream));
 }
 
 // Exact product with an explicit kernel variant (0: FMUL + FMNMX, 1: paired
-// mul.f32x2 + 3-input max); used to compare the two.  Same results.
+// mul.f32x2 + 3-input max, 2: variant 1 software-pipelined); used to compare
+// them.  Same results.
 pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                                    const float* B, int64_t ldb, float* C, int64_t ldc,
                                    int32_t semiring, int32_t variant, void* stream) {
   if (!dims_ok(M, N, K) || (semiring != 0 && semiring != 1)) return PN_EINVAL;
+  if (variant < 0 || variant > 2) return PN_EINVAL;
   if (M == 0 || N == 0) return PN_OK;
   if (!C || ldc < N) return PN_EINVAL;
   if (K > 0 && (!A || !B || lda < K || ldb < N)) return PN_EINVAL;

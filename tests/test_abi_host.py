@@ -94,6 +94,8 @@ def test_argument_validation_before_any_device_call(binding):
     assert lib.maxprod_pnorm(0, 4, 4, z, 4, z, 4, z, 4, z, z, ctypes.byref(o), z, 0, z) == 0
     assert lib.maxprod_exact(4, 4, 4, z, 4, z, 4, z, 4, 5, z) == 1
     assert lib.maxprod_exact(0, 4, 4, z, 4, z, 4, z, 4, 0, z) == 0
+    assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, 3, z) == 1
+    assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
     assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1
 

@@ -55,7 +55,7 @@ EXACT_SHAPES = [(1, 1, 1), (7, 13, 5), (129, 257, 65), (300, 200, 1000), (128, 1
                 (64, 3, 130)]
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("shape", EXACT_SHAPES)
 def test_exact_maxprod_bit_exact(pn, orc, shape, variant):
     M, N, K = shape
@@ -64,7 +64,7 @@ def test_exact_maxprod_bit_exact(pn, orc, shape, variant):
     np.testing.assert_array_equal(C, orc.maxprod_f32(A, B))
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("shape", [(7, 13, 5), (129, 257, 65), (33, 70, 300)])
 def test_exact_minplus_bit_exact(pn, orc, shape, variant):
     M, N, K = shape
