@@ -76,9 +76,13 @@ def _load():
             lib.orc_col_scales.argtypes = [i64, i64, vp, i64, ci, vp]
             lib.orc_psums.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
             lib.orc_estimate.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, vp, vp, vp]
+            lib.orc_estimate_ex.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, ci, vp, vp, vp]
             lib.orc_pnorm.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci,
                                       vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm.restype = ci
+            lib.orc_pnorm_ex.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci, ci,
+                                         vp, vp, vp, vp, vp, vp]
+            lib.orc_pnorm_ex.restype = ci
             lib.orc_entries.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp,
                                         i64, vp, vp, vp, vp]
             lib.orc_floyd_warshall.argtypes = [i64, vp, i64]
@@ -190,8 +194,9 @@ def psums(A, B, p_log2, r=None, c=None, scaling: int = 2):
     return S
 
 
-def estimate(S, p_log2, r, c, tau: float):
-    """Largest stable p per entry; returns (Chat, p_sel, S_sel)."""
+def estimate(S, p_log2, r, c, tau: float, estimator: int = 0):
+    """Largest stable p per entry; returns (Chat, p_sel, S_sel).  estimator 1
+    replaces the root by the r = 1 projection from S^(p*/2) and S^(p*)."""
     S = _f64(S)
     n_p, M, N = S.shape
     pl = _plog(p_log2)
@@ -200,13 +205,15 @@ def estimate(S, p_log2, r, c, tau: float):
     Chat = np.empty((M, N), dtype=np.float64)
     psel = np.empty((M, N), dtype=np.uint8)
     Ssel = np.empty((M, N), dtype=np.float64)
-    _load().orc_estimate(M, N, n_p, _p(pl), _p(S), _p(r), _p(c), float(tau), _p(Chat),
-                         _p(psel), _p(Ssel))
+    _load().orc_estimate_ex(M, N, n_p, _p(pl), _p(S), _p(r), _p(c), float(tau), int(estimator),
+                            _p(Chat), _p(psel), _p(Ssel))
     return Chat, psel, Ssel
 
 
-def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False):
+def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
+          estimator: int = 0):
     """Full p-norm estimate of the (x,max) product (Alg. 5 with H = Alg. 3).
+    estimator 0 is the plain largest-stable-p norm, 1 the r = 1 projection.
 
     Returns a dict with Chat, p_sel, S_sel, r, c and (if want_S) S_all.
     """
@@ -221,15 +228,35 @@ def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False):
     r = np.empty(M, dtype=np.float64)
     c = np.empty(N, dtype=np.float64)
     S = np.empty((len(pl), M, N), dtype=np.float64) if want_S else None
-    rc = _load().orc_pnorm(M, N, K, _p(A), K, _p(B), N, len(pl), _p(pl), float(tau),
-                           int(scaling), _p(Chat), _p(psel), _p(Ssel),
-                           _p(S) if S is not None else None, _p(r), _p(c))
+    rc = _load().orc_pnorm_ex(M, N, K, _p(A), K, _p(B), N, len(pl), _p(pl), float(tau),
+                              int(scaling), int(estimator), _p(Chat), _p(psel), _p(Ssel),
+                              _p(S) if S is not None else None, _p(r), _p(c))
     if rc:
         raise MemoryError("oracle pnorm allocation failed")
     out = dict(C=Chat, p_sel=psel, S_sel=Ssel, r=r, c=c)
     if want_S:
         out["S"] = S
     return out
+
+
+def project(sums, p_prime: float, r: int):
+    """Multiset projection of Sec. 2.1 for one vector u.
+
+    sums[m-1] = ||u||_{m p'}^{m p'} = sum_i u_i^(m p') for m = 1 .. 2r.  The
+    r x (r+1) Hankel matrix H[i][j] = sums[i + j] (the paper's matrix of
+    power sums at p', 2p', ...) has a null vector gamma; the roots a of
+    sum_i gamma_i a^i are the projected values alpha^p', and the estimate of
+    max_i u_i is max alpha = max a^(1/p').  Returns all alpha (ascending).
+    """
+    sums = np.asarray(sums, dtype=np.float64)
+    assert len(sums) >= 2 * r
+    H = np.array([[sums[i + j] for j in range(r + 1)] for i in range(r)])
+    _, _, vt = np.linalg.svd(H)
+    gamma = vt[-1]                        # spans the null space when rank(H) = r
+    roots = np.roots(gamma[::-1])         # np.roots wants the highest power first
+    roots = np.real(roots[np.abs(np.imag(roots)) <= 1e-9 * np.maximum(1.0, np.abs(roots))])
+    roots = roots[roots > 0]
+    return np.sort(roots ** (1.0 / p_prime))
 
 
 def entries(A, B, ii, jj, p_log2, r, c):

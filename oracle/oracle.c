@@ -20,6 +20,12 @@
  *     plain form, (S^(p*))^(1/p*) at the largest p in P with S^(p) >= tau.
  *     If no p passes, p* is the smallest p in P and the result carries an
  *     "unstable" flag (0x80 in p_sel).
+ *   - projection estimator r = 1 (Sec. 2.1, multiset projection; the
+ *     printed r = 1 formula is garbled): the two evenly spaced norms are
+ *     taken at p'= p* / 2 and 2p' = p*, both stable; the estimate is the root
+ *     of the projection polynomial, (S^(2p') / S^(p'))^(1/p').  Entries
+ *     whose p* / 2 is not in P (including p* = min P and unstable entries)
+ *     keep the plain estimate.
  *   - APSP (Sec. 2.2, Eq. for A^n): the diagonal is reset to 1 (distance 0)
  *     after each squaring when diag_policy >= 1; with diag_policy == 2 every
  *     entry is also clamped to <= 1 (distance >= 0).
@@ -239,13 +245,29 @@ void orc_psums(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, co
   }
 }
 
-/* Alg. 5, second loop, with the plain estimateMaxFromNormPowerSequence:    */
+/* Sec. 2.1, multiset projection with r = 1.  Given the two evenly spaced   */
+/* power sums s1 = ||u||_{p'}^{p'} and s2 = ||u||_{2p'}^{2p'}, the 1 x 2     */
+/* Hankel matrix [s1 s2] has the null vector gamma = (s2, -s1); the         */
+/* projection polynomial gamma_0 + gamma_1 a has the single root a = -g0/g1 */
+/* and the projected value is alpha = a^(1/p').                              */
+static double project_r1(double s1, double s2, double p_prime) {
+  double g0 = s2, g1 = -s1;
+  if (g1 == 0.0) return 0.0;
+  double a = -g0 / g1;
+  return a > 0.0 ? pow(a, 1.0 / p_prime) : 0.0;
+}
+
+/* Alg. 5, second loop, with estimateMaxFromNormPowerSequence:              */
 /* p* = largest p in P with S^(p) >= tau (the stable set is a prefix of P   */
 /* because S^(p) is non-increasing in p once every term is <= 1).           */
-/* Chat = r_i * c_j * (S^(p*))^(1/p*).  p_sel = log2(p*) | 0x80 if unstable. */
-void orc_estimate(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
-                  const double* r, const double* c, double tau, double* Chat, uint8_t* psel,
-                  double* Ssel) {
+/* estimator 0 (plain): Chat = r_i * c_j * (S^(p*))^(1/p*).                  */
+/* estimator 1 (projection r = 1): Chat = r_i * c_j *                      */
+/*   project_r1(S^(p* / 2), S^(p*), p* / 2)                                  */
+/* when p* / 2 is in P and p* is stable, else the plain form.                */
+/* p_sel = log2(p*) | 0x80 if unstable; S_sel = S^(p*).                      */
+void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
+                     const double* r, const double* c, double tau, int estimator, double* Chat,
+                     uint8_t* psel, double* Ssel) {
   int64_t i;
 #pragma omp parallel for schedule(static)
   for (i = 0; i < M; ++i) {
@@ -264,19 +286,31 @@ void orc_estimate(int64_t M, int64_t N, int n_p, const int* p_log2, const double
       }
       double s = S[((int64_t)q_sel * M + i) * N + j];
       double p = ldexp(1.0, p_log2[q_sel]);
-      double root = s > 0.0 ? pow(s, 1.0 / p) : 0.0;
-      if (Chat) Chat[i * N + j] = r[i] * c[j] * root;
+      double est = s > 0.0 ? pow(s, 1.0 / p) : 0.0;
+      if (estimator == 1 && !unstable && q_sel > 0 && p_log2[q_sel - 1] == p_log2[q_sel] - 1) {
+        double s_half = S[((int64_t)(q_sel - 1) * M + i) * N + j];
+        est = project_r1(s_half, s, 0.5 * p);
+      }
+      if (Chat) Chat[i * N + j] = r[i] * c[j] * est;
       if (psel) psel[i * N + j] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
       if (Ssel) Ssel[i * N + j] = s;
     }
   }
 }
 
+/* The plain estimator (estimator 0 of orc_estimate_ex). */
+void orc_estimate(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
+                  const double* r, const double* c, double tau, double* Chat, uint8_t* psel,
+                  double* Ssel) {
+  orc_estimate_ex(M, N, n_p, p_log2, S, r, c, tau, 0, Chat, psel, Ssel);
+}
+
 /* Scales + p-sums + estimate.  S (n_p*M*N doubles) may be NULL, in which   */
 /* case a temporary is used.                                                 */
-int orc_pnorm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
-              int64_t ldb, int n_p, const int* p_log2, double tau, int scaling, double* Chat,
-              uint8_t* psel, double* Ssel, double* S_all, double* r_out, double* c_out) {
+int orc_pnorm_ex(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+                 int64_t ldb, int n_p, const int* p_log2, double tau, int scaling, int estimator,
+                 double* Chat, uint8_t* psel, double* Ssel, double* S_all, double* r_out,
+                 double* c_out) {
   double* r = (double*)malloc(sizeof(double) * (M > 0 ? M : 1));
   double* c = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
   double* S = S_all ? S_all : (double*)malloc(sizeof(double) * (size_t)n_p * (M * N > 0 ? M * N : 1));
@@ -284,13 +318,20 @@ int orc_pnorm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, con
   orc_row_scales(M, K, A, lda, scaling, r);
   orc_col_scales(K, N, B, ldb, scaling, c);
   orc_psums(M, N, K, A, lda, B, ldb, r, c, n_p, p_log2, S);
-  orc_estimate(M, N, n_p, p_log2, S, r, c, tau, Chat, psel, Ssel);
+  orc_estimate_ex(M, N, n_p, p_log2, S, r, c, tau, estimator, Chat, psel, Ssel);
   if (r_out) memcpy(r_out, r, sizeof(double) * M);
   if (c_out) memcpy(c_out, c, sizeof(double) * N);
   free(r);
   free(c);
   if (!S_all) free(S);
   return 0;
+}
+
+int orc_pnorm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B,
+              int64_t ldb, int n_p, const int* p_log2, double tau, int scaling, double* Chat,
+              uint8_t* psel, double* Ssel, double* S_all, double* r_out, double* c_out) {
+  return orc_pnorm_ex(M, N, K, A, lda, B, ldb, n_p, p_log2, tau, scaling, 0, Chat, psel, Ssel,
+                      S_all, r_out, c_out);
 }
 
 /* Selected entries only: for n_e pairs (ii[e], jj[e]) of the product A*B, */

@@ -383,3 +383,114 @@ def test_entries_match_full_psums(orc):
     ex, Se = orc.entries(A, B, ii, jj, pl, r, c)
     np.testing.assert_array_equal(ex, orc.maxprod(A, B)[ii, jj])
     np.testing.assert_allclose(Se, S[:, ii, jj].T, rtol=1e-14)
+
+
+# ------------------------------------------------------ r = 1 projection ---
+# Sec. 2.1 (multiset projection).  With v = (u / max u)^(p*/2) the r = 1
+# estimate is max u * (||v||_2^2 / ||v||_1)^(2/p*), which never exceeds max u
+# and is smallest, over v in [0,1]^n with v_1 = 1, at the two-valued
+# v = (1, lam, ..., lam) with lam = 1/(sqrt(n)+1), where the ratio is
+# 2/(sqrt(n)+1).
+def _row_product(orc, u, pl, estimator, tau=1e-300):
+    """The oracle on the 1 x n by n x 1 product whose only output entry has
+    u_k = u[k] (B = ones, so the column scale is 1)."""
+    u = np.asarray(u, dtype=np.float64)
+    out = orc.pnorm(u[None, :], np.ones((len(u), 1)), pl, tau=tau, estimator=estimator)
+    return out["C"][0, 0], out["p_sel"][0, 0]
+
+
+def test_projection_r1_exact_on_single_valued_rows(orc):
+    """All u_k equal: the multiset has one value, which r = 1 recovers exactly
+    while the plain norm is K^(1/p*) too large."""
+    for beta, K in ((0.3, 7), (0.71, 40), (1.0, 3)):
+        c1, ps = _row_product(orc, [beta] * K, [0, 1, 2, 3, 4], 1)
+        c0, _ = _row_product(orc, [beta] * K, [0, 1, 2, 3, 4], 0)
+        assert ps == 4
+        np.testing.assert_allclose(c1, beta, rtol=1e-14)
+        np.testing.assert_allclose(c0, beta * K ** (1 / 16), rtol=1e-14)
+
+
+@pytest.mark.parametrize("n,lp", [(2, 3), (5, 4), (33, 6), (1000, 2)])
+def test_projection_r1_two_valued_closed_form(orc, n, lp):
+    """u = (1, lam^(2/p*), ...): estimate = ((1+(n-1)lam^2)/(1+(n-1)lam))^(2/p*)."""
+    p = 2.0 ** lp
+    for lam in (0.0, 0.05, 1 / (math.sqrt(n) + 1), 0.5, 0.999):
+        u = [1.0] + [lam ** (2 / p)] * (n - 1)
+        est, ps = _row_product(orc, u, list(range(lp + 1)), 1)
+        assert ps == lp
+        want = ((1 + (n - 1) * lam * lam) / (1 + (n - 1) * lam)) ** (2 / p)
+        np.testing.assert_allclose(est, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 9])
+def test_projection_r1_worst_case_brute_force(orc, n):
+    """Brute force over v in [0,1]^n with v_1 = 1: (estimate / max)^(p*/2) =
+    ||v||_2^2/||v||_1 >= 2/(sqrt(n)+1), attained at lam = 1/(sqrt(n)+1)."""
+    lp = 3
+    p = 2.0 ** lp
+    bound = 2 / (math.sqrt(n) + 1)
+    g = workloads.rng(1601 + n)
+    worst = np.inf
+    for _ in range(400):
+        v = np.concatenate([[1.0], g.random(n - 1) ** g.choice([0.3, 1.0, 3.0])])
+        est, _ = _row_product(orc, v ** (2 / p), list(range(lp + 1)), 1)
+        worst = min(worst, est ** (p / 2))
+    assert worst >= bound * (1 - 1e-12)
+    grid = np.linspace(0.0, 1.0, 2001)
+    vals = []
+    for lam in grid:
+        est, _ = _row_product(orc, [1.0] + [lam ** (2 / p)] * (n - 1), list(range(lp + 1)), 1)
+        vals.append(est ** (p / 2))
+    vals = np.array(vals)
+    assert vals.min() >= bound * (1 - 1e-12)
+    np.testing.assert_allclose(vals.min(), bound, rtol=1e-5)
+    assert abs(grid[np.argmin(vals)] - 1 / (math.sqrt(n) + 1)) <= 1e-3
+
+
+def test_projection_general_r_matches_and_recovers_multisets(orc):
+    """The Hankel null-space construction (Sec. 2.1): r = 1 agrees with the
+    oracle's estimator; r = 2 recovers both values of a two-valued multiset and
+    r = 1 the value of a one-valued one."""
+    g = workloads.rng(1610)
+    for _ in range(20):
+        u = g.random(int(g.integers(2, 30)))
+        lp = int(g.integers(1, 6))
+        p = 2.0 ** lp
+        est, _ = _row_product(orc, u / u.max(), list(range(lp + 1)), 1)
+        half = p / 2
+        sums = [np.sum((u / u.max()) ** (m * half)) for m in (1, 2)]
+        np.testing.assert_allclose(orc.project(sums, half, 1)[-1], est, rtol=1e-12)
+    for b1, h1, b2, h2 in ((0.9, 1, 0.4, 5), (0.8, 3, 0.2, 2), (0.55, 2, 0.5, 7)):
+        u = np.array([b1] * h1 + [b2] * h2)
+        pp = 4.0
+        sums = [np.sum(u ** (m * pp)) for m in (1, 2, 3, 4)]
+        np.testing.assert_allclose(orc.project(sums, pp, 2), sorted([b1, b2]), rtol=1e-7)
+    sums = [5 * 0.6 ** (m * 8.0) for m in (1, 2)]
+    np.testing.assert_allclose(orc.project(sums, 8.0, 1), [0.6], rtol=1e-14)
+
+
+def test_projection_r1_envelope_on_products(orc):
+    """Every entry of a product: exact * (2/(sqrt(K)+1))^(2/p*) <= estimate <= exact."""
+    for seed, (M, N, K) in ((1620, (9, 11, 40)), (1621, (13, 7, 300))):
+        A, B = workloads.wide_range_pair(M, N, K, seed=seed)
+        A, B = A.astype(np.float64), B.astype(np.float64)
+        exact = orc.maxprod(A, B)
+        out = orc.pnorm(A, B, list(range(7)), tau=orc.default_tau(K, orc.F32_EXACT), estimator=1)
+        pstar = 2.0 ** (out["p_sel"] & 0x7F)
+        low = exact * (2 / (math.sqrt(K) + 1)) ** (2 / pstar)
+        assert np.all(out["C"] <= exact * (1 + 1e-12))
+        assert np.all(out["C"] >= low * (1 - 1e-12))
+
+
+def test_projection_r1_fallbacks_to_plain(orc):
+    """No p* / 2 in P (non-consecutive P, or p* = min P), or no stable p: the
+    plain estimate."""
+    A, B = workloads.uniform_pair(6, 5, 30, seed=1630, dtype=np.float64)
+    for pl in ([0, 2, 5], [3]):
+        a = orc.pnorm(A, B, pl, tau=1e-300, estimator=0)
+        b = orc.pnorm(A, B, pl, tau=1e-300, estimator=1)
+        np.testing.assert_array_equal(a["C"], b["C"])
+    a = orc.pnorm(A, B, [0, 1, 2], tau=1e300, estimator=0)
+    b = orc.pnorm(A, B, [0, 1, 2], tau=1e300, estimator=1)
+    assert np.all(b["p_sel"] == 0x80)
+    np.testing.assert_array_equal(a["C"], b["C"])
