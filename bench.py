@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--estimator", type=int, default=0, choices=[0, 1],
+                    help="0: plain largest-stable-p norm; 1: r = 1 multiset projection")
     ap.add_argument("--workload", default="pnorm",
                     choices=["pnorm", "apsp", "backward", "grouped"],
                     help="pnorm: the default product; the others measure the other paths")
@@ -61,8 +63,9 @@ P_LOG2 = list(range(7))
 LAUNCHES_PER_STEP = 1 + 3 * len(P_LOG2)  # maxima + (A images, B images, GEMM) per level
 
 
-def workload_name(n, compute):
-    return (f"maxprod_pnorm n={n} {compute} P={{1..64}} entries exp(-Exp(4)); "
+def workload_name(n, compute, estimator=0):
+    est = "" if estimator == 0 else " r=1 projection estimator;"
+    return (f"maxprod_pnorm n={n} {compute} P={{1..64}} entries exp(-Exp(4));{est} "
             f"exact CUDA-core (x,max) product as the comparison")
 
 
@@ -246,7 +249,8 @@ def run_ours(args):
 
     def step(ev0=None, ev1=None):
         return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n,
-                                out=C, want_ssel=False, check=False, ev_begin=ev0, ev_end=ev1)
+                                out=C, want_ssel=False, check=False, ev_begin=ev0, ev_end=ev1,
+                                estimator=args.estimator)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -295,8 +299,15 @@ def run_ours(args):
         ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
         Cs = C[ti, tj].double().cpu().numpy()
         ps = (psel[ti, tj].cpu().numpy() & 0x7F).astype(np.int64)
-        S_at = S[np.arange(len(ii)), ps]
-        pn_ref = r[ii] * c[jj] * np.power(S_at, 1.0 / 2.0 ** ps)
+        if args.estimator == 0:
+            S_at = S[np.arange(len(ii)), ps]
+            pn_ref = r[ii] * c[jj] * np.power(S_at, 1.0 / 2.0 ** ps)
+        else:
+            # the oracle's estimator on its own p-sums of the sampled entries
+            tau = oracle.default_tau(n, {"f32": 0, "tf32": 1, "bf16": 2, "f16": 3,
+                                         "e4m3": 4}[args.compute])
+            pn_ref = oracle.estimate(S.T[:, None, :], P_LOG2, np.ones(1), r[ii] * c[jj], tau,
+                                     estimator=1)[0][0]
         e_exact = np.abs(Cs - exact) / exact
         e_orc = np.abs(Cs - pn_ref) / pn_ref
         err = {"samples": int(len(ii)), "max_rel_vs_exact": float(e_exact.max()),
@@ -331,7 +342,8 @@ def run_ours(args):
     Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
     del C
     torch.cuda.empty_cache()
-    pipe = HostPipeline(n, n, n, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2)
+    pipe = HostPipeline(n, n, n, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2,
+                        estimator=args.estimator)
     KE = max(1, args.e2e_steps)
     pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -353,7 +365,8 @@ def run_ours(args):
         "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
-        "config": {"workload": workload_name(n, args.compute), "n": n, "p_log2": P_LOG2,
+        "config": {"workload": workload_name(n, args.compute, args.estimator), "n": n,
+                   "p_log2": P_LOG2,
                    "outputs": "C and p_sel", "l2": "inputs larger than L2 (1 GiB each), no flush",
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * n,

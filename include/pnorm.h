@@ -105,6 +105,20 @@ typedef struct pn_opts {
   /* Test hooks, 0 in normal use.  Bit 0: the copy producer skips one stage
    * so that the consumer's bounded wait runs out (PN_ETIMEOUT). */
   int32_t debug_flags;
+  /* Estimate of max_k u_k from the p-sums (Sec. 2.1):
+   *   0 (default) = plain, (S^(p*))^(1/p*), an overestimate by at most
+   *       K^(1/p*);
+   *   1 = multiset projection with r = 1 from the two evenly spaced sums at
+   *       p* / 2 and p*: (S^(p*) / S^(p* / 2))^(2/p*), an underestimate by at most
+   *       the factor (2/(sqrt(K)+1))^(2/p*).  Entries whose p* / 2 is not in P
+   *       (p* = min P, or a gap in P) and unstable entries keep the plain
+   *       estimate.  p_sel and S_sel still report p* and S^(p*).  The level
+   *       p* / 2 is then evaluated for every tile holding an entry resolved at
+   *       p*, about one more tensor-core pass in total.  maxprod_pnorm,
+   *       maxprod_pnorm_static and the grouped call accept it (the grouped
+   *       table is built for one value); apsp_pnorm and
+   *       maxprod_pnorm_backward return PN_EUNSUPPORTED for 1. */
+  int32_t estimator;
 } pn_opts;
 
 /* Human-readable name of a status code (static string). */

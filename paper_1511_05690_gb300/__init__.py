@@ -109,8 +109,9 @@ def _ld(x: torch.Tensor) -> int:
 def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), compute="bf16",
                   tau=None, scaling=2, tile_n=0, out=None, want_psel=True, want_ssel=True,
                   check=True, ev_begin=None, ev_end=None, stream=None, timeout_ns=0,
-                  debug_flags=0):
-    """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None)."""
+                  debug_flags=0, estimator=0):
+    """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None).
+    estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*)."""
     A, B = _mat(A, "A"), _mat(B, "B")
     M, K = A.shape
     K2, N = B.shape
@@ -122,7 +123,7 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
     ssel = torch.empty((M, N), dtype=torch.float32, device=dev) if want_ssel else None
     st = status_word(dev)
     o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(), _event(ev_begin),
-                  _event(ev_end), timeout_ns, debug_flags)
+                  _event(ev_end), timeout_ns, debug_flags, estimator)
     L = lib()
     need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
     if need == 0 and M * N > 0:
@@ -166,7 +167,7 @@ class GroupedProduct:
     alive for replays).  A_g: (M_g, K_g), B_g: (K_g, N_g), float32 CUDA."""
 
     def __init__(self, As, Bs, *, p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2,
-                 tile_n=0):
+                 tile_n=0, estimator=0):
         import numpy as np
         if len(As) != len(Bs):
             raise ValueError("As and Bs differ in length")
@@ -182,7 +183,8 @@ class GroupedProduct:
                 raise ValueError("inner dimensions differ")
             mnk += [a.shape[0], b.shape[1], a.shape[1]]
         self.status = status_word(dev)
-        self.opts = make_opts(p_log2, compute, tau, scaling, 2, tile_n, self.status.data_ptr())
+        self.opts = make_opts(p_log2, compute, tau, scaling, 2, tile_n, self.status.data_ptr(),
+                              estimator=estimator)
         L = lib()
         MNK = (ctypes.c_int64 * max(1, 3 * count))(*mnk)
         vp = ctypes.c_void_p
@@ -242,8 +244,9 @@ def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None,
 
 def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
                tau=None, scaling=2, diag_policy=2, tile_n=0, out=None, check=True,
-               stream=None, ev_begin=None, ev_end=None):
-    """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge)."""
+               stream=None, ev_begin=None, ev_end=None, estimator=0):
+    """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge).
+    Only the plain estimator (0) is supported; 1 raises PnError(PN_EUNSUPPORTED)."""
     W = _mat(W, "W")
     n = W.shape[0]
     if W.shape[1] != n:
@@ -252,7 +255,7 @@ def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), comput
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=dev)
     st = status_word(dev)
     o = make_opts(p_log2, compute, tau, scaling, diag_policy, tile_n, st.data_ptr(),
-                  _event(ev_begin), _event(ev_end))
+                  _event(ev_begin), _event(ev_end), estimator=estimator)
     L = lib()
     need = L.pn_apsp_workspace_size(n, ctypes.byref(o))
     if need == 0 and n > 0:

@@ -45,6 +45,7 @@ class PnOpts(ctypes.Structure):
         ("ev_gemm_end", ctypes.c_void_p),
         ("timeout_ns", ctypes.c_int64),
         ("debug_flags", ctypes.c_int32),
+        ("estimator", ctypes.c_int32),
     ]
 
 
@@ -129,7 +130,7 @@ def check(status: int, where: str = "") -> None:
 
 def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_policy=2,
               tile_n=0, dev_status=None, ev_begin=None, ev_end=None, timeout_ns=0,
-              debug_flags=0) -> PnOpts:
+              debug_flags=0, estimator=0) -> PnOpts:
     o = PnOpts()
     load().pn_default_opts(ctypes.byref(o))
     pl = [int(x) for x in p_log2]
@@ -148,4 +149,5 @@ def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_
     o.ev_gemm_end = ev_end
     o.timeout_ns = int(timeout_ns)
     o.debug_flags = int(debug_flags)
+    o.estimator = int(estimator)
     return o

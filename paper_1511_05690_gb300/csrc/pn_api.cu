@@ -56,6 +56,7 @@ bool opts_valid(const pn_opts* o) {
   if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256) return false;
   if (o->timeout_ns < 0) return false;
   if (std::isnan(o->tau)) return false;
+  if (o->estimator < 0 || o->estimator > 1) return false;
   return true;
 }
 
@@ -84,7 +85,8 @@ struct Layout {
   int state_ld = 0, n_p = 0, planes = 1;
   size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0, off_cflag = 0;
   size_t ctrl_bytes = 0;
-  size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_aimg = 0, off_bimg = 0;
+  size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_aimg = 0,
+         off_bimg = 0;
   size_t a_level_bytes = 0, b_level_bytes = 0, a_plane = 0, b_plane = 0;
   size_t total = 0;
 };
@@ -116,6 +118,9 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.off_c = off; off = align_up(off + sizeof(float) * N, WS_ALIGN);
   L.off_work = off; off = align_up(off + sizeof(int32_t) * L.n_p * (size_t)L.total_tiles, WS_ALIGN);
   L.off_state = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
+  if (o->estimator == 1) {
+    L.off_pend = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
+  }
   L.a_plane = static_cast<size_t>(L.RBA) * L.KB * IMG_BYTES;
   L.b_plane = static_cast<size_t>(L.RBB) * L.KB * IMG_BYTES;
   L.a_level_bytes = L.a_plane * L.planes;
@@ -202,6 +207,7 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.r = reinterpret_cast<float*>(ws + L.off_r);
   cm.c = reinterpret_cast<float*>(ws + L.off_c);
   cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
+  cm.pend = o->estimator == 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
   cm.status = o->dev_status;
   cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
   cm.debug_flags = o->debug_flags;
@@ -238,6 +244,7 @@ Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, int q) {
   lv.cflag = cflag + static_cast<size_t>(q) * L.tiles_n;
   lv.next_rflag = rflag + static_cast<size_t>(qn) * L.tiles_m;
   lv.next_cflag = cflag + static_cast<size_t>(qn) * L.tiles_n;
+  set_projection(lv, o, q);
   return lv;
 }
 
@@ -423,6 +430,7 @@ pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t l
                      int32_t n_squarings, const pn_opts* opts, void* ws, size_t ws_bytes,
                      void* stream) {
   if (!opts_valid(opts) || !dims_ok(n, n, n)) return PN_EINVAL;
+  if (opts->estimator != 0) return PN_EUNSUPPORTED;
   if (n == 0) return PN_OK;
   if (!W || !D || ldw < n || ldd < n) return PN_EINVAL;
   const size_t need = pn_apsp_workspace_size(n, opts);
@@ -468,7 +476,7 @@ pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A
                                  const uint8_t* p_sel, const float* dC, float* dA, float* dB,
                                  const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
   if (!opts_valid(opts) || !dims_ok(M, N, K)) return PN_EINVAL;
-  if (!bw_mode_ok(opts->compute)) return PN_EUNSUPPORTED;
+  if (!bw_mode_ok(opts->compute) || opts->estimator != 0) return PN_EUNSUPPORTED;
   if (K == 0) return PN_OK;  // dA and dB are empty
   if ((M > 0 && !dA) || (N > 0 && !dB)) return PN_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

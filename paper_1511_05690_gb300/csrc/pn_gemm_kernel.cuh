@@ -246,9 +246,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const bool use_rs = row_ok && (EPI == 0 || cm.grad_axis == 0);
       const float rs = use_rs ? cm.r[P.rc_r + i] : 0.0f;
       const int ch0 = half * HCH;
-      const uint32_t* st_row = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
+      const int64_t st_idx = P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
+      const uint32_t* st_row = cm.state + st_idx;
       const float inv_p = __uint_as_float((127u - (uint32_t)lv.plog) << 23);  // 2^-plog
-      uint32_t res_all[HCH];
+      uint32_t res_all[HCH], pend_all[HCH];
       bool any_left = false;
 #pragma unroll 1
       for (int hc = 0; hc < HCH; ++hc) {
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
+        pend_all[hc] = 0;
         if constexpr (EPI == 1) {
           if (row_ok && j0 < P.N) {
             const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
@@ -337,6 +339,64 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint32_t cand = lv.is_bottom ? open : (open & stable);
           any_left |= (open & ~cand) != 0u;
           near &= cand & (cm.fp64_near ? 0xffffffffu : 0u);
+          float* crow = P.C + (int64_t)i * P.ldc + j0;
+          // r = 1 projection (Sec. 2.1): entries resolved at 2p hold S^(2p) in C;
+          // with S^(p) from this level the estimate is (S^(2p) / S^(p))^(1/p).
+          // The ratio is clamped to <= 1 (S is non-increasing in p).
+          const uint32_t pend = lv.proj_here ? cm.pend[st_idx + hc] : 0u;
+          if (pend) {
+            // eight entries at a time (two float4 when the whole chunk is pending)
+            const float* cs = cm.c + P.rc_c + j0;
+            const bool pvec = pend == 0xffffffffu && P.vec_c;
+#pragma unroll
+            for (int e0 = 0; e0 < 32; e0 += 8) {
+              if (((pend >> e0) & 0xffu) == 0u) continue;
+              float y[8], cv[8];
+              if (pvec) {
+#pragma unroll
+                for (int h = 0; h < 8; h += 4) {
+                  const float4 s4 = *reinterpret_cast<const float4*>(crow + e0 + h);
+                  const float4 c4 = __ldg(reinterpret_cast<const float4*>(cs + e0 + h));
+                  y[h] = s4.x; y[h + 1] = s4.y; y[h + 2] = s4.z; y[h + 3] = s4.w;
+                  cv[h] = c4.x; cv[h + 1] = c4.y; cv[h + 2] = c4.z; cv[h + 3] = c4.w;
+                }
+              } else {
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                  const bool pe = (pend >> (e0 + h)) & 1u;
+                  y[h] = pe ? crow[e0 + h] : 1.0f;
+                  cv[h] = pe ? __ldg(cs + e0 + h) : 0.0f;
+                }
+              }
+#pragma unroll
+              for (int h = 0; h < 8; ++h) y[h] = y[h] / fmaxf(x[e0 + h], y[h]);
+              if constexpr (MODE == MODE_3XTF32) {
+                for (int s2i = 0; s2i < lv.plog; ++s2i) {
+#pragma unroll
+                  for (int h = 0; h < 8; ++h) y[h] = sqrtf(y[h]);
+                }
+              } else if (lv.plog > 0) {
+#pragma unroll
+                for (int h = 0; h < 8; ++h) y[h] = ex2_approx(lg2_approx(y[h]) * inv_p);
+              }
+#pragma unroll
+              for (int h = 0; h < 8; ++h) y[h] *= rs * cv[h];
+              if (pvec) {
+#pragma unroll
+                for (int h = 0; h < 8; h += 4)
+                  *reinterpret_cast<float4*>(crow + e0 + h) =
+                      make_float4(y[h], y[h + 1], y[h + 2], y[h + 3]);
+              } else {
+#pragma unroll
+                for (int h = 0; h < 8; ++h)
+                  if ((pend >> (e0 + h)) & 1u) crow[e0 + h] = y[h];
+              }
+            }
+          }
+          if (lv.proj_next) {
+            any_left |= cand != 0u;  // their S^(p/2) comes from the next level
+            pend_all[hc] = cand;
+          }
           if (cand) {
             const uint32_t pbits = lv.plog * 0x01010101u;
             uint32_t pw[8];
@@ -360,54 +420,56 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                   if ((cand >> e) & 1u) srow[e] = x[e];
               }
             }
-            if constexpr (MODE == MODE_3XTF32) {
-              // FP32-accurate mode: (S^(p))^(1/p) for p = 2^plog as plog correctly
-              // rounded square roots (about one ulp in total); repeated APSP
-              // squarings double any bias each step, so no approximation here
-              for (int s2 = 0; s2 < lv.plog; ++s2) {
+            // r = 1 projection with a level p/2 below: C keeps S^(p) until then
+            if (!lv.proj_next) {
+              if constexpr (MODE == MODE_3XTF32) {
+                // FP32-accurate mode: (S^(p))^(1/p) for p = 2^plog as plog correctly
+                // rounded square roots (about one ulp in total); repeated APSP
+                // squarings double any bias each step, so no approximation here
+                for (int s2 = 0; s2 < lv.plog; ++s2) {
 #pragma unroll
-                for (int e = 0; e < 32; ++e) x[e] = sqrtf(x[e]);
+                  for (int e = 0; e < 32; ++e) x[e] = sqrtf(x[e]);
+                }
+              } else if (lv.plog > 0) {
+                // (S^(p))^(1/p) = 2^(log2(S) / p): two MUFU operations, relative
+                // error ~2^-22, far below the operand rounding of these formats
+#pragma unroll
+                for (int e = 0; e < 32; ++e) x[e] = ex2_approx(lg2_approx(x[e]) * inv_p);
               }
-            } else if (lv.plog > 0) {
-              // (S^(p))^(1/p) = 2^(log2(S) / p): two MUFU operations, relative
-              // error ~2^-22, far below the operand rounding of these formats
+              if (near) {
+                // within a decade of tau, which for these formats sits near the
+                // FP32 underflow range: root in FP64
 #pragma unroll
-              for (int e = 0; e < 32; ++e) x[e] = ex2_approx(lg2_approx(x[e]) * inv_p);
-            }
-            if (near) {
-              // within a decade of tau, which for these formats sits near the
-              // FP32 underflow range: root in FP64
-#pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                if ((near >> e) & 1u) {
-                  double dr = static_cast<double>(__uint_as_float(v[e]) * cm.unscale);
-                  for (int s2 = 0; s2 < lv.plog; ++s2) dr = sqrt(dr);
-                  x[e] = static_cast<float>(dr);
+                for (int e = 0; e < 32; ++e) {
+                  if ((near >> e) & 1u) {
+                    double dr = static_cast<double>(__uint_as_float(v[e]) * cm.unscale);
+                    for (int s2 = 0; s2 < lv.plog; ++s2) dr = sqrt(dr);
+                    x[e] = static_cast<float>(dr);
+                  }
                 }
               }
-            }
-            const float* cs = cm.c + P.rc_c + j0;
-            if (jn == 32 && P.vec_c) {
+              const float* cs = cm.c + P.rc_c + j0;
+              if (jn == 32 && P.vec_c) {
 #pragma unroll
-              for (int e = 0; e < 32; e += 4) {
-                const float4 cv = __ldg(reinterpret_cast<const float4*>(cs + e));
-                x[e] *= rs * cv.x; x[e + 1] *= rs * cv.y; x[e + 2] *= rs * cv.z; x[e + 3] *= rs * cv.w;
+                for (int e = 0; e < 32; e += 4) {
+                  const float4 cv = __ldg(reinterpret_cast<const float4*>(cs + e));
+                  x[e] *= rs * cv.x; x[e + 1] *= rs * cv.y; x[e + 2] *= rs * cv.z; x[e + 3] *= rs * cv.w;
+                }
+              } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) x[e] *= rs * (e < jn ? __ldg(cs + e) : 0.0f);
               }
-            } else {
+              if (cm.post) {
+                // APSP squaring: distances are >= 0 (x <= 1) and d_ii = 0 (x_ii = 1)
+                if (cm.post == 2) {
 #pragma unroll
-              for (int e = 0; e < 32; ++e) x[e] *= rs * (e < jn ? __ldg(cs + e) : 0.0f);
-            }
-            if (cm.post) {
-              // APSP squaring: distances are >= 0 (x <= 1) and d_ii = 0 (x_ii = 1)
-              if (cm.post == 2) {
+                  for (int e = 0; e < 32; ++e) x[e] = fminf(x[e], 1.0f);
+                }
 #pragma unroll
-                for (int e = 0; e < 32; ++e) x[e] = fminf(x[e], 1.0f);
+                for (int e = 0; e < 32; ++e)
+                  if (j0 + e == i) x[e] = 1.0f;
               }
-#pragma unroll
-              for (int e = 0; e < 32; ++e)
-                if (j0 + e == i) x[e] = 1.0f;
             }
-            float* crow = P.C + (int64_t)i * P.ldc + j0;
             uint8_t* prow = P.psel ? P.psel + (int64_t)i * P.ldaux + j0 : nullptr;
             if (full_vec) {
 #pragma unroll
@@ -435,10 +497,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const bool tile_left = bar_red_or(any_left, 2, EPI_THREADS);
         if (tile_left) {
           if (row_ok) {
-            uint32_t* st_w = cm.state + P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
+            uint32_t* st_w = cm.state + st_idx;
 #pragma unroll
             for (int hc = 0; hc < HCH; ++hc)
               if (tn * BN + (ch0 + hc) * 32 < P.N) st_w[hc] = res_all[hc];
+            if (cm.pend) {
+#pragma unroll
+              for (int hc = 0; hc < HCH; ++hc)
+                if (tn * BN + (ch0 + hc) * 32 < P.N) cm.pend[st_idx + hc] = pend_all[hc];
+            }
           }
           if (et == 0) {
             const int slot = atomicAdd(lv.next_count, 1);

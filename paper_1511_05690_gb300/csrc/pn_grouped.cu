@@ -36,7 +36,7 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 struct GroupLayout {
   int32_t BN, total_tiles, total_xa, total_xb, total_tm, total_tn, total_ma, total_mb;
   uint64_t off_rmax, off_cmax, off_gmax, off_counts, off_rflag, off_cflag, ctrl_bytes;
-  uint64_t off_r, off_c, off_work, off_state, off_aimg, off_bimg, total;
+  uint64_t off_r, off_c, off_work, off_state, off_pend, off_aimg, off_bimg, total;
   uint64_t probs_offset;  // bytes from the table start to this layout's Prob[count]
   uint64_t lut_offset[7]; // bytes from the table start to each id -> problem table
 };
@@ -64,6 +64,7 @@ void id_counts(int32_t count, const int64_t* MNK, int mode, int BN, int64_t out[
 struct GroupHeader {
   uint64_t magic;
   int32_t count, n_p, mode, scaling;
+  int32_t estimator, pad;
   uint64_t signature;  // of the sizes, for the autotune cache
   int64_t sum_cube;    // sum of M*N*K over the problems
   GroupLayout layout[2];
@@ -162,6 +163,7 @@ pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float*
   H->n_p = opts->n_p;
   H->mode = mode;
   H->scaling = opts->scaling;
+  H->estimator = opts->estimator;
   H->signature = sig;
   H->sum_cube = sum_cube;
   size_t off_probs = align_up(sizeof(GroupHeader), 64);
@@ -266,6 +268,11 @@ pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float*
     L.off_c = off; off = align_up(off + sizeof(float) * cols, WS_ALIGN);
     L.off_work = off; off = align_up(off + sizeof(int32_t) * opts->n_p * static_cast<size_t>(tiles), WS_ALIGN);
     L.off_state = off; off = align_up(off + sizeof(uint32_t) * static_cast<size_t>(words), IMG_ALIGN);
+    L.off_pend = 0;
+    if (opts->estimator == 1) {
+      L.off_pend = off;
+      off = align_up(off + sizeof(uint32_t) * static_cast<size_t>(words), IMG_ALIGN);
+    }
     L.off_aimg = off; off += static_cast<size_t>(abytes);
     L.off_bimg = off; off += static_cast<size_t>(bbytes);
     L.total = align_up(off, WS_ALIGN);
@@ -303,6 +310,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   cm.r = reinterpret_cast<float*>(ws + L.off_r);
   cm.c = reinterpret_cast<float*>(ws + L.off_c);
   cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
+  cm.pend = H->estimator == 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
   cm.status = o->dev_status;
   cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
   cm.debug_flags = o->debug_flags;
@@ -334,6 +342,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     lv.cflag = cflag + static_cast<size_t>(q) * L.total_tn;
     lv.next_rflag = rflag + static_cast<size_t>(qn) * L.total_tm;
     lv.next_cflag = cflag + static_cast<size_t>(qn) * L.total_tn;
+    set_projection(lv, o, q);
     if (launch_power_a(cm, lv, stream)) return PN_ECUDA;
     if (launch_power_b(cm, lv, stream)) return PN_ECUDA;
     if (lv.is_top && o->ev_gemm_begin)
@@ -350,7 +359,7 @@ static pn_status check_group(const void* host_table, const void* dev_table, cons
   if (!host_table || !host_opts_valid(o)) return PN_EINVAL;
   const auto* H = static_cast<const GroupHeader*>(host_table);
   if (H->magic != GROUP_MAGIC || H->n_p != o->n_p || H->mode != o->compute ||
-      H->scaling != o->scaling)
+      H->scaling != o->scaling || H->estimator != o->estimator)
     return PN_EINVAL;
   if (H->count > 0 && (!dev_table || reinterpret_cast<uintptr_t>(dev_table) % 16)) return PN_EINVAL;
   const size_t need = H->layout[0].total > H->layout[1].total ? H->layout[0].total : H->layout[1].total;

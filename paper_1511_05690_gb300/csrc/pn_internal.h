@@ -77,6 +77,8 @@ struct Common {
   float* r;           // row scales
   float* c;           // column scales
   uint32_t* state;    // resolved-entry bits of tiles that go to a lower level
+  uint32_t* pend;     // r = 1 projection: bits of entries resolved at the level
+                      // above whose C holds S^(2p) (same layout as state), or null
   int32_t* status;
   uint64_t timeout_ns;
   int32_t debug_flags;
@@ -104,6 +106,8 @@ struct Level {
   uint8_t* next_rflag;
   uint8_t* next_cflag;
   const uint32_t* pmask;      // gradient launches: bit q set if some entry has p* = P[q]
+  int32_t proj_here;          // r = 1 projection: finish entries resolved at 2p (the level above)
+  int32_t proj_next;          // r = 1 projection: the next level is p/2; park S^(p) of new entries
 };
 
 // One operand image of the adjoint (maxprod_pnorm_backward).
@@ -152,6 +156,15 @@ __host__ __device__ inline void raster(int lt, int tiles_m, int tiles_n, int& tm
 }
 
 // --------------------------------------------------------- host helpers ---
+// r = 1 projection flags of level q (estimator 1, Sec. 2.1): level q finishes
+// the entries resolved at the level above when that level's p is 2p, and
+// parks S^(p) of the entries it resolves when the level below is p/2.
+inline void set_projection(Level& lv, const pn_opts* o, int q) {
+  const bool proj = o->estimator == 1;
+  lv.proj_next = (proj && q > 0 && o->p_log2[q - 1] == o->p_log2[q] - 1) ? 1 : 0;
+  lv.proj_here = (proj && q + 1 < o->n_p && o->p_log2[q + 1] == o->p_log2[q] + 1) ? 1 : 0;
+}
+
 int host_device_sms();                      // SMs of the current sm_103 device, else 0
 bool host_opts_valid(const pn_opts* o);
 double host_default_tau(int64_t K, int compute);

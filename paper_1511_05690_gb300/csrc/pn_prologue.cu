@@ -198,11 +198,40 @@ __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, 
   }
 }
 
-// Top level: one block per operand tile.  Lower levels: one block per tile
-// row, skipped unless a pushed output tile needs that row block.
+// Top level: one block per operand tile.  Lower levels: the same operand-tile
+// ids strided over a grid of a few blocks per SM; a tile is rebuilt only if a
+// pushed output tile needs its row block (few at most levels, every one when
+// the r = 1 projection sends every tile to the level p*/2).
 // Resident blocks per SM for the image kernels: as many as the registers of
 // the format's loads allow without heavy spilling -- more blocks keep more
 // loads in flight (the max pass, at HBM speed, keeps about 200 KB per SM).
+// Lower levels: block b owns the operand-tile ids b, b + gridDim.x, ...; the
+// threads test PRO_THREADS of them at once (one flag load each, in parallel)
+// and the block then builds the flagged ones in order.  `needed(id)` and
+// `body(id)` must be block-uniform in effect (body may synchronise the block).
+template <typename Need, typename Body>
+__device__ __forceinline__ void for_flagged_ids(int total, const Need& needed, const Body& body) {
+  __shared__ uint32_t mask[PRO_THREADS / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_ids = blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  for (int j0 = 0; j0 < n_ids; j0 += PRO_THREADS) {
+    const int j = j0 + threadIdx.x;
+    const bool need = j < n_ids && needed((int)blockIdx.x + j * (int)gridDim.x);
+    const uint32_t b = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) mask[warp] = b;
+    __syncthreads();
+    for (int w = 0; w < PRO_THREADS / 32; ++w) {
+      uint32_t m = mask[w];
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        m &= m - 1;
+        body((int)blockIdx.x + (j0 + w * 32 + bit) * (int)gridDim.x);
+      }
+    }
+    __syncthreads();  // mask is rewritten by the next round
+  }
+}
+
 template <int MODE>
 constexpr int img_min_blocks() {
   return MODE == MODE_E4M3 ? 3 : (MODE == MODE_BF16 || MODE == MODE_F16) ? 4 : 5;
@@ -219,12 +248,19 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int rb = local / P.KB;
     power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
   } else {
-    const int id = blockIdx.x;
-    if (!lv.rflag[id]) return;
-    const int g = find_prob(cm, id, 3);
-    const Prob& P = prob_at(cm, g);
-    const int rb = id - P.tm_base;
-    for (int kb = 0; kb < P.KB; ++kb) power_a_tile<MODE>(cm, lv, g, P, rb, kb);
+    for_flagged_ids(
+        cm.total_xa,
+        [&](int id) {
+          const Prob& P = prob_at(cm, find_prob(cm, id, 1));
+          return lv.rflag[P.tm_base + (id - P.xa_base) / P.KB] != 0;
+        },
+        [&](int id) {
+          const int g = find_prob(cm, id, 1);
+          const Prob& P = prob_at(cm, g);
+          const int local = id - P.xa_base;
+          const int rb = local / P.KB;
+          power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
+        });
   }
 }
 
@@ -296,8 +332,8 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
   }
 }
 
-// Top level: one block per operand tile.  Lower levels: one block per output
-// tile column, skipped unless a pushed output tile needs it.
+// Top level: one block per operand tile.  Lower levels: as for A, a tile is
+// rebuilt only if a pushed output tile needs its tile column.
 template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_b(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
@@ -310,15 +346,20 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int rb = local / P.KB;
     power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
   } else {
-    const int id = blockIdx.x;
-    if (!lv.cflag[id]) return;
-    const int g = find_prob(cm, id, 4);
-    const Prob& P = prob_at(cm, g);
     const int per_tile = cm.BN / TILE_M;
-    const int tn = id - P.tn_base;
-    for (int h = 0; h < per_tile; ++h)
-      for (int kb = 0; kb < P.KB; ++kb)
-        power_b_tile<MODE>(cm, lv, g, P, tn * per_tile + h, kb, stile);
+    for_flagged_ids(
+        cm.total_xb,
+        [&](int id) {
+          const Prob& P = prob_at(cm, find_prob(cm, id, 2));
+          return lv.cflag[P.tn_base + (id - P.xb_base) / P.KB / per_tile] != 0;
+        },
+        [&](int id) {
+          const int g = find_prob(cm, id, 2);
+          const Prob& P = prob_at(cm, g);
+          const int local = id - P.xb_base;
+          const int rb = local / P.KB;
+          power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
+        });
   }
 }
 
@@ -366,6 +407,16 @@ __global__ void k_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, i
   }
 }
 
+// Lower-level image grids: two waves of the resident blocks on every SM.
+int lower_grid(int total, int per_sm) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    sms = 152;
+  const int g = 2 * sms * per_sm;
+  return total < g ? total : g;
+}
+
 template <int MODE>
 int launch_power_b_t(const Common& cm, const Level& lv, void* stream) {
   const int smem = mode_bk(MODE) * 129 * 4;
@@ -376,7 +427,7 @@ int launch_power_b_t(const Common& cm, const Level& lv, void* stream) {
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const int grid = lv.is_top ? cm.total_xb : cm.total_tn;
+  const int grid = lv.is_top ? cm.total_xb : lower_grid(cm.total_xb, img_min_blocks<MODE>());
   k_power_b<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(cm, lv);
   return cudaGetLastError();
 }
@@ -399,13 +450,23 @@ int launch_maxes(const Common& cm, void* stream) {
 int launch_power_a(const Common& cm, const Level& lv, void* stream) {
   if (cm.total_xa <= 0) return 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int grid = lv.is_top ? cm.total_xa : cm.total_tm;
+  auto grid = [&](int per_sm) { return lv.is_top ? cm.total_xa : lower_grid(cm.total_xa, per_sm); };
   switch (cm.mode) {
-    case MODE_3XTF32: k_power_a<MODE_3XTF32><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
-    case MODE_TF32: k_power_a<MODE_TF32><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
-    case MODE_BF16: k_power_a<MODE_BF16><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
-    case MODE_F16: k_power_a<MODE_F16><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
-    case MODE_E4M3: k_power_a<MODE_E4M3><<<grid, PRO_THREADS, 0, s>>>(cm, lv); break;
+    case MODE_3XTF32:
+      k_power_a<MODE_3XTF32><<<grid(img_min_blocks<MODE_3XTF32>()), PRO_THREADS, 0, s>>>(cm, lv);
+      break;
+    case MODE_TF32:
+      k_power_a<MODE_TF32><<<grid(img_min_blocks<MODE_TF32>()), PRO_THREADS, 0, s>>>(cm, lv);
+      break;
+    case MODE_BF16:
+      k_power_a<MODE_BF16><<<grid(img_min_blocks<MODE_BF16>()), PRO_THREADS, 0, s>>>(cm, lv);
+      break;
+    case MODE_F16:
+      k_power_a<MODE_F16><<<grid(img_min_blocks<MODE_F16>()), PRO_THREADS, 0, s>>>(cm, lv);
+      break;
+    case MODE_E4M3:
+      k_power_a<MODE_E4M3><<<grid(img_min_blocks<MODE_E4M3>()), PRO_THREADS, 0, s>>>(cm, lv);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -79,6 +79,12 @@ def test_workspace_sizes(binding):
     assert lib.pn_workspace_size(-1, 10, 10, ctypes.byref(o)) == 0
     assert lib.pn_apsp_workspace_size(100, ctypes.byref(o)) > lib.pn_workspace_size(
         100, 100, 100, ctypes.byref(o))
+    # the r = 1 projection keeps a second word of state per 32 entries (M N / 8 bytes)
+    oproj = binding.make_opts(compute="bf16", estimator=1)
+    s1p = lib.pn_workspace_size(1000, 1000, 1000, ctypes.byref(oproj))
+    assert s1 + 1000 * 1024 // 8 <= s1p <= s1 + 1000 * 1024 // 8 + 4096
+    bad = binding.make_opts(estimator=2)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
 
 
 def test_argument_validation_before_any_device_call(binding):
@@ -95,6 +101,11 @@ def test_argument_validation_before_any_device_call(binding):
     assert lib.maxprod_exact(4, 4, 4, z, 4, z, 4, z, 4, 5, z) == 1
     assert lib.maxprod_exact(0, 4, 4, z, 4, z, 4, z, 4, 0, z) == 0
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, 3, z) == 1
+    # the projection estimator: APSP and the adjoint refuse it (PN_EUNSUPPORTED)
+    proj = binding.make_opts(compute="f32", estimator=1)
+    assert lib.apsp_pnorm(4, 16, 4, 16, 4, 0, ctypes.byref(proj), z, 0, z) == 7
+    assert lib.maxprod_pnorm_backward(4, 4, 4, 16, 16, 16, 16, 16, 16, 16, 16,
+                                      ctypes.byref(proj), z, 0, z) == 7
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
     assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1
