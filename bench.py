@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--count", type=int, default=4096,
+                    help="grouped workload: number of problems")
     ap.add_argument("--estimator", type=int, default=0, choices=[0, 1],
                     help="0: plain largest-stable-p norm; 1: r = 1 multiset projection")
     ap.add_argument("--workload", default="pnorm",
@@ -518,7 +520,7 @@ def run_other(args):
                     config={"workload": "maxprod_pnorm forward + backward n=2048 U(0,1], "
                             "loss sum log C, P={16} and P={1..64}", "n": n, "detail": out})
     else:
-        sizes = workloads.grouped_sizes(4096)
+        sizes = workloads.grouped_sizes(args.count)
         g = torch.Generator(device="cuda")
         g.manual_seed(workloads.SEED_BASE + 3)
         As = [1 - torch.rand((int(m), int(m)), generator=g, device="cuda") for m in sizes]
@@ -536,8 +538,8 @@ def run_other(args):
         ms = _timed(torch, graph.replay, K, args.warmup, stream)
         ops = float(np.sum(sizes.astype(np.float64) ** 3))
         line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="bf16",
-                    config={"workload": "4096 square products, n = round(16 * 64^U), BF16, "
-                            "P={1..64}, one launch per p level, CUDA graph replay",
+                    config={"workload": f"{args.count} square products, n = round(16 * 64^U), "
+                            "BF16, P={1..64}, one launch per p level, CUDA graph replay",
                             "sum_n3": ops, "tile_n": chosen})
     print(json.dumps(line), flush=True)
 

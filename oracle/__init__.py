@@ -83,6 +83,8 @@ def _load():
             lib.orc_pnorm_ex.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci, ci,
                                          vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm_ex.restype = ci
+            lib.orc_affine_fit.argtypes = [i64, vp, vp, vp, ci, vp]
+            lib.orc_apply_correction.argtypes = [i64, i64, i64, ci, vp, ci, vp, vp, vp, vp, vp]
             lib.orc_entries.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp,
                                         i64, vp, vp, vp, vp]
             lib.orc_floyd_warshall.argtypes = [i64, vp, i64]
@@ -210,12 +212,24 @@ def estimate(S, p_log2, r, c, tau: float, estimator: int = 0):
     return Chat, psel, Ssel
 
 
+def affine_fit(est, exact, cls, n_cls: int):
+    """Least-squares exact = a_q est + b_q per class q (Discussion); (n_cls, 2)."""
+    est, exact = _f64(est), _f64(exact)
+    cls = np.ascontiguousarray(cls, dtype=np.int32)
+    coef = np.empty((n_cls, 2), dtype=np.float64)
+    _load().orc_affine_fit(len(est), _p(est), _p(exact), _p(cls), int(n_cls), _p(coef))
+    return coef
+
+
 def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
-          estimator: int = 0):
+          estimator: int = 0, correction: int = 0, fit_ij=None):
     """Full p-norm estimate of the (x,max) product (Alg. 5 with H = Alg. 3).
     estimator 0 is the plain largest-stable-p norm, 1 the r = 1 projection.
+    correction 1 divides by K^(1/p*); correction 2 fits the affine model of
+    the Discussion on the sample entries fit_ij = (ii, jj) and applies it.
 
-    Returns a dict with Chat, p_sel, S_sel, r, c and (if want_S) S_all.
+    Returns a dict with Chat, p_sel, S_sel, r, c, coef (correction 2) and
+    (if want_S) S_all; Chat is the corrected estimate.
     """
     A, B = _f64(A), _f64(B)
     M, K = A.shape
@@ -233,7 +247,13 @@ def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
                               _p(S) if S is not None else None, _p(r), _p(c))
     if rc:
         raise MemoryError("oracle pnorm allocation failed")
-    out = dict(C=Chat, p_sel=psel, S_sel=Ssel, r=r, c=c)
+    coef = None
+    if correction == 2:
+        ii, jj = (np.asarray(x, dtype=np.int64) for x in fit_ij)
+        coef = fit_coefficients(A, B, ii, jj, pl, r, c, tau, estimator)
+    if correction:
+        apply_correction(Chat, psel, pl, K, r, c, correction, coef)
+    out = dict(C=Chat, p_sel=psel, S_sel=Ssel, r=r, c=c, coef=coef)
     if want_S:
         out["S"] = S
     return out
@@ -257,6 +277,29 @@ def project(sums, p_prime: float, r: int):
     roots = np.real(roots[np.abs(np.imag(roots)) <= 1e-9 * np.maximum(1.0, np.abs(roots))])
     roots = roots[roots > 0]
     return np.sort(roots ** (1.0 / p_prime))
+
+
+def fit_coefficients(A, B, ii, jj, p_log2, r, c, tau: float, estimator: int = 0):
+    """The affine model's (a_q, b_q) from the exact values at the sample
+    entries (ii, jj): scaled estimate and scaled exact value per sample, each
+    sample in the class of its own p*."""
+    pl = _plog(p_log2)
+    exact, S = entries(A, B, ii, jj, pl, r, c)
+    est, ps, _ = estimate(S.T[:, None, :], pl, np.ones(1), np.ones(len(ii)), tau, estimator)
+    idx = {int(v): q for q, v in enumerate(pl)}
+    cls = np.array([idx[int(b) & 0x7F] for b in ps[0]], dtype=np.int32)
+    return affine_fit(est[0], exact / (r[ii] * c[jj]), cls, len(pl))
+
+
+def apply_correction(Chat, psel, p_log2, K: int, r, c, correction: int, coef=None):
+    """Correction 1 or 2 applied to Chat in place (see oracle.c)."""
+    pl = _plog(p_log2)
+    M, N = Chat.shape
+    coef = np.zeros((len(pl), 2)) if coef is None else _f64(coef)
+    psel = np.ascontiguousarray(psel, dtype=np.uint8)
+    _load().orc_apply_correction(M, N, int(K), len(pl), _p(pl), int(correction), _p(coef),
+                                 _p(psel), _p(_f64(r)), _p(_f64(c)), _p(Chat))
+    return Chat
 
 
 def entries(A, B, ii, jj, p_log2, r, c):

@@ -26,6 +26,14 @@
  *     of the projection polynomial, (S^(2p') / S^(p'))^(1/p').  Entries
  *     whose p* / 2 is not in P (including p* = min P and unstable entries)
  *     keep the plain estimate.
+ *   - corrections (Sec. 2.1 bound remark; Discussion), in the scaled space
+ *     where the exact value lies in (0, 1]: correction 1 divides the estimate
+ *     by K^(1/p*), the upper end of its envelope; correction 2 fits
+ *     exact = a_q * est + b_q by least squares on sample entries whose exact
+ *     value is known, one (a_q, b_q) per p* class q, and applies it to every
+ *     entry of that class.  Degenerate classes: one sample, or a spread of the
+ *     estimates below 1e-12 of their second moment, fit the ratio
+ *     (b_q = 0); no sample leaves the class unchanged.
  *   - APSP (Sec. 2.2, Eq. for A^n): the diagonal is reset to 1 (distance 0)
  *     after each squaring when diag_policy >= 1; with diag_policy == 2 every
  *     entry is also clamped to <= 1 (distance >= 0).
@@ -294,6 +302,57 @@ void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const dou
       if (Chat) Chat[i * N + j] = r[i] * c[j] * est;
       if (psel) psel[i * N + j] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
       if (Ssel) Ssel[i * N + j] = s;
+    }
+  }
+}
+
+/* Discussion (affine model from a few exact sub-solutions): least squares  */
+/* exact_s = a_q * est_s + b_q over the samples s of class q = cls[s], from */
+/* the plain sums n, sum x, sum y, sum x^2, sum x y; coef[2q] = a_q,        */
+/* coef[2q + 1] = b_q.                                                       */
+void orc_affine_fit(int64_t n_s, const double* est, const double* exact, const int* cls, int n_cls,
+                    double* coef) {
+  for (int q = 0; q < n_cls; ++q) {
+    double n = 0.0, sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+    for (int64_t s = 0; s < n_s; ++s) {
+      if (cls[s] != q) continue;
+      n += 1.0;
+      sx += est[s];
+      sy += exact[s];
+      sxx += est[s] * est[s];
+      sxy += est[s] * exact[s];
+    }
+    double a = 1.0, b = 0.0;
+    if (n >= 2.0 && sxx - sx * sx / n > 1e-12 * sxx) {
+      a = (sxy - sx * sy / n) / (sxx - sx * sx / n);
+      b = (sy - a * sx) / n;
+    } else if (n >= 1.0 && sx > 0.0) {
+      a = sy / sx;
+    }
+    coef[2 * q] = a;
+    coef[2 * q + 1] = b;
+  }
+}
+
+/* Applies a correction to Chat in place, per entry, in the scaled space:   */
+/* est = Chat / (r_i c_j); correction 1: est / K^(1/p*); correction 2:      */
+/* a_q est + b_q with q the index of p* in P.                                */
+void orc_apply_correction(int64_t M, int64_t N, int64_t K, int n_p, const int* p_log2,
+                          int correction, const double* coef, const uint8_t* psel,
+                          const double* r, const double* c, double* Chat) {
+  int64_t i;
+#pragma omp parallel for schedule(static)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      int lp = psel[i * N + j] & 0x7F, q = 0;
+      for (int t = 0; t < n_p; ++t)
+        if (p_log2[t] == lp) q = t;
+      double rc = r[i] * c[j];
+      if (rc <= 0.0) continue;
+      double est = Chat[i * N + j] / rc;
+      if (correction == 1) est = est / pow((double)(K > 0 ? K : 1), 1.0 / ldexp(1.0, lp));
+      if (correction == 2) est = coef[2 * q] * est + coef[2 * q + 1];
+      Chat[i * N + j] = rc * est;
     }
   }
 }

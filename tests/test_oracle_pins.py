@@ -494,3 +494,90 @@ def test_projection_r1_fallbacks_to_plain(orc):
     b = orc.pnorm(A, B, [0, 1, 2], tau=1e300, estimator=1)
     assert np.all(b["p_sel"] == 0x80)
     np.testing.assert_array_equal(a["C"], b["C"])
+
+
+# ----------------------------------------------------------- corrections ---
+# Sec. 2.1 (dividing by the envelope's upper end K^(1/p*)) and the Discussion
+# (an affine model fitted to a few exact sub-solutions), both applied in the
+# scaled space where the exact value lies in (0, 1].
+def test_affine_fit_is_least_squares(orc):
+    """Per class: numpy's degree-1 polyfit; degenerate classes as documented."""
+    g = workloads.rng(1800)
+    x = g.random(300) + 0.5
+    y = 0.7 * x + 0.1 + 0.01 * g.standard_normal(300)
+    cls = g.integers(0, 3, 300).astype(np.int32)
+    cls[:5] = 4        # class 4: five samples with one x value -> ratio fit
+    x[:5] = 1.25
+    cls[5] = 5         # class 5: one sample -> ratio fit
+    coef = orc.affine_fit(x, y, cls, 7)
+    for q in range(3):
+        m = cls == q
+        a, b = np.polyfit(x[m], y[m], 1)
+        np.testing.assert_allclose(coef[q], [a, b], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(coef[4], [y[:5].sum() / x[:5].sum(), 0.0], rtol=1e-12)
+    np.testing.assert_allclose(coef[5], [y[5] / x[5], 0.0], rtol=1e-12)
+    assert list(coef[3]) == [1.0, 0.0] and list(coef[6]) == [1.0, 0.0]
+
+
+def test_divide_by_K_envelope(orc):
+    """Correction 1: K^(-1/p*) C <= Chat <= C, and all-ones becomes exact."""
+    A, B = workloads.uniform_pair(11, 13, 70, seed=1801, dtype=np.float64)
+    C = orc.maxprod(A, B)
+    out = orc.pnorm(A, B, [0, 1, 2, 3, 4], tau=1e-300, correction=1)
+    pstar = 2.0 ** (out["p_sel"] & 0x7F)
+    assert np.all(out["C"] <= C * (1 + 1e-13))
+    assert np.all(out["C"] >= C * 70 ** (-1 / pstar) * (1 - 1e-13))
+    ones = orc.pnorm(np.ones((3, 9)), np.ones((9, 4)), [0, 1, 2], tau=1e-300, correction=1)
+    np.testing.assert_allclose(ones["C"], 1.0, rtol=1e-14)
+
+
+def test_affine_correction_recovers_an_affine_relation(orc):
+    """Every u has m equal maxima v (and zeros): the plain estimate is
+    m^(1/p*) v, an exactly linear function of the exact value v, so a fit on a
+    few samples makes every entry exact."""
+    m, K = 6, 40
+    g = workloads.rng(1802)
+    A = np.zeros((10, K))
+    A[:, :m] = 1.0
+    B = np.zeros((K, 12))
+    B[:m, :] = 0.3 + 0.7 * g.random(12)  # column j: m copies of v_j
+    ii, jj = np.array([0, 3, 7]), np.array([1, 5, 11])
+    out = orc.pnorm(A, B, list(range(5)), tau=1e-300, correction=2, fit_ij=(ii, jj))
+    np.testing.assert_allclose(out["C"], orc.maxprod(A, B), rtol=1e-12)
+    np.testing.assert_allclose(out["coef"][4], [m ** (-1 / 16), 0.0], atol=1e-12)
+
+
+def test_affine_correction_normal_equations(orc):
+    """Samples = every entry: per class the residuals of the corrected scaled
+    estimate sum to zero and are orthogonal to the uncorrected estimate."""
+    A, B = workloads.wide_range_pair(24, 20, 300, seed=1803)
+    A, B = A.astype(np.float64), B.astype(np.float64)
+    pl = list(range(7))
+    tau = orc.default_tau(300, orc.BF16)
+    ii, jj = np.meshgrid(np.arange(24), np.arange(20), indexing="ij")
+    plain = orc.pnorm(A, B, pl, tau)
+    corr = orc.pnorm(A, B, pl, tau, correction=2, fit_ij=(ii.ravel(), jj.ravel()))
+    rc = plain["r"][:, None] * plain["c"][None, :]
+    x, z, e = plain["C"] / rc, corr["C"] / rc, orc.maxprod(A, B) / rc
+    for lp in np.unique(plain["p_sel"] & 0x7F):
+        msk = (plain["p_sel"] & 0x7F) == lp
+        res = e[msk] - z[msk]
+        assert abs(res.sum()) <= 1e-10 * msk.sum()
+        assert abs((res * x[msk]).sum()) <= 1e-10 * msk.sum()
+
+
+def test_affine_correction_reduces_error(orc):
+    """Wide-range entries (K = 2000, BF16 threshold): 256 exact samples bring
+    the median relative error of both estimators down by more than 5x."""
+    A, B = workloads.wide_range_pair(120, 110, 2000, seed=1804)
+    A, B = A.astype(np.float64), B.astype(np.float64)
+    g = workloads.rng(1805)
+    ii, jj = g.integers(0, 120, 256), g.integers(0, 110, 256)
+    tau = orc.default_tau(2000, orc.BF16)
+    exact = orc.maxprod(A, B)
+    for est in (0, 1):
+        e0 = np.median(np.abs(orc.pnorm(A, B, list(range(7)), tau, estimator=est)["C"] - exact)
+                       / exact)
+        c2 = orc.pnorm(A, B, list(range(7)), tau, estimator=est, correction=2, fit_ij=(ii, jj))
+        e2 = np.median(np.abs(c2["C"] - exact) / exact)
+        assert e2 < e0 / 5, (est, e0, e2)
