@@ -55,6 +55,9 @@ def parse_args():
                     help="grouped workload: number of problems")
     ap.add_argument("--estimator", type=int, default=0, choices=[0, 1],
                     help="0: plain largest-stable-p norm; 1: r = 1 multiset projection")
+    ap.add_argument("--correction", type=int, default=0, choices=[0, 1, 2],
+                    help="1: divide by K^(1/p*); 2: affine model fitted on --n-fit exact samples")
+    ap.add_argument("--n-fit", type=int, default=1024)
     ap.add_argument("--workload", default="pnorm",
                     choices=["pnorm", "apsp", "backward", "grouped"],
                     help="pnorm: the default product; the others measure the other paths")
@@ -65,8 +68,12 @@ P_LOG2 = list(range(7))
 LAUNCHES_PER_STEP = 1 + 3 * len(P_LOG2)  # maxima + (A images, B images, GEMM) per level
 
 
-def workload_name(n, compute, estimator=0):
+def workload_name(n, compute, estimator=0, correction=0, n_fit=0):
     est = "" if estimator == 0 else " r=1 projection estimator;"
+    if correction == 1:
+        est += " estimate / K^(1/p*);"
+    elif correction == 2:
+        est += f" affine correction from {n_fit} exact samples;"
     return (f"maxprod_pnorm n={n} {compute} P={{1..64}} entries exp(-Exp(4));{est} "
             f"exact CUDA-core (x,max) product as the comparison")
 
@@ -248,11 +255,18 @@ def run_ours(args):
     B = torch.from_numpy(B_h).cuda()
     C = torch.empty((n, n), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    corr = dict(estimator=args.estimator, correction=args.correction)
+    if args.correction == 2:
+        # sample entries of the affine model, drawn apart from the error samples
+        gfit = workloads.rng(None, 150)
+        fit_ii, fit_jj = gfit.integers(0, n, args.n_fit), gfit.integers(0, n, args.n_fit)
+        corr.update(fit_i=torch.from_numpy(fit_ii.astype(np.int32)).cuda(),
+                    fit_j=torch.from_numpy(fit_jj.astype(np.int32)).cuda())
 
     def step(ev0=None, ev1=None):
         return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n,
                                 out=C, want_ssel=False, check=False, ev_begin=ev0, ev_end=ev1,
-                                estimator=args.estimator)
+                                **corr)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -301,15 +315,30 @@ def run_ours(args):
         ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
         Cs = C[ti, tj].double().cpu().numpy()
         ps = (psel[ti, tj].cpu().numpy() & 0x7F).astype(np.int64)
-        if args.estimator == 0:
+        if args.estimator == 0 and args.correction == 0:
             S_at = S[np.arange(len(ii)), ps]
             pn_ref = r[ii] * c[jj] * np.power(S_at, 1.0 / 2.0 ** ps)
         else:
-            # the oracle's estimator on its own p-sums of the sampled entries
+            # the oracle's estimator (and correction) on its own p-sums of the
+            # sampled entries
             tau = oracle.default_tau(n, {"f32": 0, "tf32": 1, "bf16": 2, "f16": 3,
                                          "e4m3": 4}[args.compute])
-            pn_ref = oracle.estimate(S.T[:, None, :], P_LOG2, np.ones(1), r[ii] * c[jj], tau,
-                                     estimator=1)[0][0]
+            rc = r[ii] * c[jj]
+            pn_ref, ps_o, _ = oracle.estimate(S.T[:, None, :], P_LOG2, np.ones(1), rc, tau,
+                                              estimator=args.estimator)
+            coef = None
+            if args.correction == 2:
+                frows = np.unique(fit_ii)
+                rf = np.ones(n)
+                rf[frows] = oracle.row_scales(A_h[frows].astype(np.float64))
+                coef = oracle.fit_coefficients(A_h[frows].astype(np.float64),
+                                               B_h.astype(np.float64),
+                                               np.searchsorted(frows, fit_ii), fit_jj, P_LOG2,
+                                               rf[frows], c, tau, args.estimator)
+            if args.correction:
+                oracle.apply_correction(pn_ref, ps_o, P_LOG2, n, np.ones(1), rc,
+                                        args.correction, coef)
+            pn_ref = pn_ref[0]
         e_exact = np.abs(Cs - exact) / exact
         e_orc = np.abs(Cs - pn_ref) / pn_ref
         err = {"samples": int(len(ii)), "max_rel_vs_exact": float(e_exact.max()),
@@ -345,7 +374,7 @@ def run_ours(args):
     del C
     torch.cuda.empty_cache()
     pipe = HostPipeline(n, n, n, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2,
-                        estimator=args.estimator)
+                        **corr)
     KE = max(1, args.e2e_steps)
     pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -367,7 +396,8 @@ def run_ours(args):
         "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
-        "config": {"workload": workload_name(n, args.compute, args.estimator), "n": n,
+        "config": {"workload": workload_name(n, args.compute, args.estimator, args.correction,
+                                             args.n_fit), "n": n,
                    "p_log2": P_LOG2,
                    "outputs": "C and p_sel", "l2": "inputs larger than L2 (1 GiB each), no flush",
                    "parallelism": f"replicas x{world}"},

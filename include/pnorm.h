@@ -119,6 +119,29 @@ typedef struct pn_opts {
    *       table is built for one value); apsp_pnorm and
    *       maxprod_pnorm_backward return PN_EUNSUPPORTED for 1. */
   int32_t estimator;
+  /* Bias correction of the estimate, applied per entry in the scaled space
+   * (value / (r_i c_j), where the exact result lies in (0, 1]):
+   *   0 (default) = none;
+   *   1 = divide by K^(1/p*), the upper end of the plain estimate's envelope
+   *       (Sec. 2.1): the worst-case relative error becomes 1 - K^(-1/p*)
+   *       (plain estimator only; with estimator 1 PN_EINVAL);
+   *   2 = affine model fitted to a few exact sub-solutions (Discussion): at
+   *       the n_fit sample entries (fit_i[s], fit_j[s]) the library computes
+   *       the exact max and the estimate directly, fits exact = a_q est + b_q
+   *       by least squares per p* class q (one sample, or estimates spread by
+   *       less than 1e-12 of their second moment: the ratio fit, b_q = 0; no
+   *       sample: unchanged) and applies it to every entry of the class.
+   *       fit_i / fit_j are caller-owned device int32 arrays; an index outside
+   *       [0, M) x [0, N) is skipped and sets PN_EINVAL in dev_status.
+   *       fit_coef (optional, device, 2 * n_p floats) receives (a_q, b_q).
+   * maxprod_pnorm and maxprod_pnorm_static accept 1 and 2, the grouped call
+   * 1 (each problem's own K); apsp_pnorm and maxprod_pnorm_backward return
+   * PN_EUNSUPPORTED for a nonzero correction. */
+  int32_t correction;
+  int32_t n_fit;
+  const int32_t* fit_i;
+  const int32_t* fit_j;
+  float* fit_coef;
 } pn_opts;
 
 /* Human-readable name of a status code (static string). */

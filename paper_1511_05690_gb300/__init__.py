@@ -109,9 +109,13 @@ def _ld(x: torch.Tensor) -> int:
 def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), compute="bf16",
                   tau=None, scaling=2, tile_n=0, out=None, want_psel=True, want_ssel=True,
                   check=True, ev_begin=None, ev_end=None, stream=None, timeout_ns=0,
-                  debug_flags=0, estimator=0):
+                  debug_flags=0, estimator=0, correction=0, fit_i=None, fit_j=None,
+                  fit_coef=None):
     """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None).
-    estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*)."""
+    estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*).
+    correction 1: divide by K^(1/p*); 2: affine model per p* class fitted to the
+    exact values at the sample entries (fit_i, fit_j) (int32 CUDA tensors);
+    fit_coef (float32 CUDA tensor of 2 * len(p_log2)) receives (a_q, b_q)."""
     A, B = _mat(A, "A"), _mat(B, "B")
     M, K = A.shape
     K2, N = B.shape
@@ -122,8 +126,16 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
     psel = torch.empty((M, N), dtype=torch.uint8, device=dev) if want_psel else None
     ssel = torch.empty((M, N), dtype=torch.float32, device=dev) if want_ssel else None
     st = status_word(dev)
+    fit = dict(correction=correction)
+    if correction == 2:
+        fit_i = fit_i.to(device=dev, dtype=torch.int32).contiguous()
+        fit_j = fit_j.to(device=dev, dtype=torch.int32).contiguous()
+        if fit_i.numel() != fit_j.numel():
+            raise ValueError("fit_i and fit_j differ in length")
+        fit.update(n_fit=fit_i.numel(), fit_i=fit_i.data_ptr(), fit_j=fit_j.data_ptr(),
+                   fit_coef=fit_coef.data_ptr() if fit_coef is not None else None)
     o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(), _event(ev_begin),
-                  _event(ev_end), timeout_ns, debug_flags, estimator)
+                  _event(ev_end), timeout_ns, debug_flags, estimator, **fit)
     L = lib()
     need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
     if need == 0 and M * N > 0:
@@ -244,9 +256,10 @@ def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None,
 
 def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
                tau=None, scaling=2, diag_policy=2, tile_n=0, out=None, check=True,
-               stream=None, ev_begin=None, ev_end=None, estimator=0):
+               stream=None, ev_begin=None, ev_end=None, estimator=0, correction=0):
     """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge).
-    Only the plain estimator (0) is supported; 1 raises PnError(PN_EUNSUPPORTED)."""
+    Only the plain, uncorrected estimator is supported: a nonzero estimator or
+    correction raises PnError(PN_EUNSUPPORTED)."""
     W = _mat(W, "W")
     n = W.shape[0]
     if W.shape[1] != n:
@@ -255,7 +268,7 @@ def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), comput
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=dev)
     st = status_word(dev)
     o = make_opts(p_log2, compute, tau, scaling, diag_policy, tile_n, st.data_ptr(),
-                  _event(ev_begin), _event(ev_end), estimator=estimator)
+                  _event(ev_begin), _event(ev_end), estimator=estimator, correction=correction)
     L = lib()
     need = L.pn_apsp_workspace_size(n, ctypes.byref(o))
     if need == 0 and n > 0:

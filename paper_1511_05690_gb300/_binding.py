@@ -46,6 +46,11 @@ class PnOpts(ctypes.Structure):
         ("timeout_ns", ctypes.c_int64),
         ("debug_flags", ctypes.c_int32),
         ("estimator", ctypes.c_int32),
+        ("correction", ctypes.c_int32),
+        ("n_fit", ctypes.c_int32),
+        ("fit_i", ctypes.c_void_p),
+        ("fit_j", ctypes.c_void_p),
+        ("fit_coef", ctypes.c_void_p),
     ]
 
 
@@ -130,7 +135,8 @@ def check(status: int, where: str = "") -> None:
 
 def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_policy=2,
               tile_n=0, dev_status=None, ev_begin=None, ev_end=None, timeout_ns=0,
-              debug_flags=0, estimator=0) -> PnOpts:
+              debug_flags=0, estimator=0, correction=0, n_fit=0, fit_i=None, fit_j=None,
+              fit_coef=None) -> PnOpts:
     o = PnOpts()
     load().pn_default_opts(ctypes.byref(o))
     pl = [int(x) for x in p_log2]
@@ -150,4 +156,9 @@ def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_
     o.timeout_ns = int(timeout_ns)
     o.debug_flags = int(debug_flags)
     o.estimator = int(estimator)
+    o.correction = int(correction)
+    o.n_fit = int(n_fit)
+    o.fit_i = fit_i
+    o.fit_j = fit_j
+    o.fit_coef = fit_coef
     return o

@@ -57,6 +57,9 @@ bool opts_valid(const pn_opts* o) {
   if (o->timeout_ns < 0) return false;
   if (std::isnan(o->tau)) return false;
   if (o->estimator < 0 || o->estimator > 1) return false;
+  if (o->correction < 0 || o->correction > 2) return false;
+  if (o->correction == 1 && o->estimator != 0) return false;
+  if (o->correction == 2 && (o->n_fit < 1 || !o->fit_i || !o->fit_j)) return false;
   return true;
 }
 
@@ -83,8 +86,9 @@ float tau_up(double t) {
 struct Layout {
   int BN = 0, KB = 0, RBA = 0, RBB = 0, tiles_m = 0, tiles_n = 0, total_tiles = 0;
   int state_ld = 0, n_p = 0, planes = 1;
-  size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0, off_cflag = 0;
-  size_t ctrl_bytes = 0;
+  size_t off_fit = 0, off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0,
+         off_cflag = 0;
+  size_t ctrl_bytes = 0, off_coef = 0;
   size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_aimg = 0,
          off_bimg = 0;
   size_t a_level_bytes = 0, b_level_bytes = 0, a_plane = 0, b_plane = 0;
@@ -105,7 +109,9 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.total_tiles = L.tiles_m * L.tiles_n;
   L.state_ld = L.tiles_n * (L.BN / 32);
   size_t off = 0;
-  // control words, cleared at the start of every call
+  // control words, cleared at the start of every call (the FP64 class sums of
+  // the affine correction first, for their alignment)
+  L.off_fit = off; off += sizeof(double) * 5 * PN_MAX_P;
   L.off_rmax = off; off += sizeof(uint32_t) * M;
   L.off_cmax = off; off += sizeof(uint32_t) * N;
   L.off_gmax = off; off += sizeof(uint32_t) * 2;
@@ -114,6 +120,7 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.off_cflag = off; off += static_cast<size_t>(L.n_p) * L.tiles_n;
   L.ctrl_bytes = align_up(off, 16);
   off = align_up(off, WS_ALIGN);
+  L.off_coef = off; off = align_up(off + sizeof(float) * 2 * PN_MAX_P, WS_ALIGN);
   L.off_r = off; off = align_up(off + sizeof(float) * M, WS_ALIGN);
   L.off_c = off; off = align_up(off + sizeof(float) * N, WS_ALIGN);
   L.off_work = off; off = align_up(off + sizeof(int32_t) * L.n_p * (size_t)L.total_tiles, WS_ALIGN);
@@ -208,6 +215,8 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.c = reinterpret_cast<float*>(ws + L.off_c);
   cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
   cm.pend = o->estimator == 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
+  cm.corr = o->correction;
+  cm.coef = reinterpret_cast<const float*>(ws + L.off_coef);
   cm.status = o->dev_status;
   cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
   cm.debug_flags = o->debug_flags;
@@ -266,6 +275,21 @@ pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
     const Level lv = make_level(L, o, ws, q);
     if ((e = launch_power_a(cm, lv, stream))) return PN_ECUDA;
     if ((e = launch_power_b(cm, lv, stream))) return PN_ECUDA;
+    if (lv.is_top && o->correction == 2) {
+      // the affine model's coefficients, from the scales of the top level
+      FitArgs fa;
+      std::memset(&fa, 0, sizeof(fa));
+      fa.fi = o->fit_i;
+      fa.fj = o->fit_j;
+      fa.n_fit = o->n_fit;
+      fa.n_p = o->n_p;
+      for (int t = 0; t < o->n_p; ++t) fa.p_log2[t] = o->p_log2[t];
+      fa.estimator = o->estimator;
+      fa.sums = reinterpret_cast<double*>(ws + L.off_fit);
+      fa.coef = reinterpret_cast<float*>(ws + L.off_coef);
+      fa.user_coef = o->fit_coef;
+      if ((e = launch_fit(cm, fa, stream))) return PN_ECUDA;
+    }
     if (lv.is_top && o->ev_gemm_begin)
       if (cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_begin), s)) return PN_ECUDA;
     if ((e = launch_gemm_level(cm, lv, sms, stream))) return PN_ECUDA;
@@ -430,7 +454,7 @@ pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t l
                      int32_t n_squarings, const pn_opts* opts, void* ws, size_t ws_bytes,
                      void* stream) {
   if (!opts_valid(opts) || !dims_ok(n, n, n)) return PN_EINVAL;
-  if (opts->estimator != 0) return PN_EUNSUPPORTED;
+  if (opts->estimator != 0 || opts->correction != 0) return PN_EUNSUPPORTED;
   if (n == 0) return PN_OK;
   if (!W || !D || ldw < n || ldd < n) return PN_EINVAL;
   const size_t need = pn_apsp_workspace_size(n, opts);
@@ -476,7 +500,8 @@ pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A
                                  const uint8_t* p_sel, const float* dC, float* dA, float* dB,
                                  const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
   if (!opts_valid(opts) || !dims_ok(M, N, K)) return PN_EINVAL;
-  if (!bw_mode_ok(opts->compute) || opts->estimator != 0) return PN_EUNSUPPORTED;
+  if (!bw_mode_ok(opts->compute) || opts->estimator != 0 || opts->correction != 0)
+    return PN_EUNSUPPORTED;
   if (K == 0) return PN_OK;  // dA and dB are empty
   if ((M > 0 && !dA) || (N > 0 && !dB)) return PN_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -249,6 +249,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       const int64_t st_idx = P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
       const uint32_t* st_row = cm.state + st_idx;
       const float inv_p = __uint_as_float((127u - (uint32_t)lv.plog) << 23);  // 2^-plog
+      // bias correction of this level's estimates (scaled space): K^(-1/p),
+      // or the affine line of this level's class
+      float corr_a = 1.0f, corr_b = 0.0f;
+      if (EPI == 0 && cm.corr == 1) corr_a = exp2f(-log2f(static_cast<float>(P.K)) * inv_p);
+      if (EPI == 0 && cm.corr == 2) {
+        corr_a = cm.coef[2 * lv.q];
+        corr_b = cm.coef[2 * lv.q + 1];
+      }
       uint32_t res_all[HCH], pend_all[HCH];
       bool any_left = false;
 #pragma unroll 1
@@ -379,6 +387,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                 for (int h = 0; h < 8; ++h) y[h] = ex2_approx(lg2_approx(y[h]) * inv_p);
               }
+              if (cm.corr == 2) {  // the affine line of p*'s class (the level above)
+                const float pa = cm.coef[2 * (lv.q + 1)], pb = cm.coef[2 * (lv.q + 1) + 1];
+#pragma unroll
+                for (int h = 0; h < 8; ++h) y[h] = fmaf(pa, y[h], pb);
+              }
 #pragma unroll
               for (int h = 0; h < 8; ++h) y[h] *= rs * cv[h];
               if (pvec) {
@@ -447,6 +460,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                     x[e] = static_cast<float>(dr);
                   }
                 }
+              }
+              if (cm.corr) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) x[e] = fmaf(corr_a, x[e], corr_b);
               }
               const float* cs = cm.c + P.rc_c + j0;
               if (jn == 32 && P.vec_c) {

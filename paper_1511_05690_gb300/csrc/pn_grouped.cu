@@ -311,6 +311,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   cm.c = reinterpret_cast<float*>(ws + L.off_c);
   cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
   cm.pend = H->estimator == 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
+  cm.corr = o->correction;
   cm.status = o->dev_status;
   cm.timeout_ns = o->timeout_ns > 0 ? static_cast<uint64_t>(o->timeout_ns) : 2000000000ull;
   cm.debug_flags = o->debug_flags;
@@ -374,6 +375,7 @@ pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
   const GroupHeader* H = nullptr;
   const pn_status st = check_group(host_table, dev_table, opts, ws, ws_bytes, &H);
   if (st != PN_OK) return st;
+  if (opts->correction == 2) return PN_EUNSUPPORTED;  // sample entries index one product
   const int sms = host_device_sms();
   if (sms <= 0) return PN_EUNSUPPORTED;
   int l;
@@ -400,6 +402,7 @@ pn_status pn_grouped_autotune(const void* host_table, const void* dev_table, con
   const GroupHeader* H = nullptr;
   pn_status st = check_group(host_table, dev_table, opts, ws, ws_bytes, &H);
   if (st != PN_OK) return st;
+  if (opts->correction == 2) return PN_EUNSUPPORTED;
   const int sms = host_device_sms();
   if (sms <= 0) return PN_EUNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -86,7 +86,22 @@ struct Common {
   int32_t fp64_near;  // FP64 selection/root for entries with S < 10 tau (FP32-range formats)
   int32_t grad_axis;  // gradient epilogue: 0 = scale per output row (r), 1 = per column (c)
   int32_t post;       // APSP squaring: 1 = C_ii = 1, 2 = also C = min(C, 1)
-  int32_t pad3;
+  int32_t corr;       // bias correction: 0 none, 1 divide by K^(1/p*), 2 affine per p* class
+  const float* coef;  // correction 2: (a_q, b_q) per level q of P, device
+};
+
+// Sample entries and class sums of the affine correction (pn_correct.cu).
+struct FitArgs {
+  const int32_t* fi;
+  const int32_t* fj;
+  int32_t n_fit;
+  int32_t n_p;
+  int32_t p_log2[PN_MAX_P];
+  int32_t estimator;
+  int32_t pad;
+  double* sums;       // [PN_MAX_P][5]: n, sum est, sum exact, sum est^2, sum est * exact
+  float* coef;        // [PN_MAX_P][2]
+  float* user_coef;   // optional copy for the caller
 };
 
 // Control of one p level (one p of the family).
@@ -185,6 +200,7 @@ int launch_apsp_init(int64_t n, const float* W, int64_t ldw, float* X, int diag,
 int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd,
                       void* stream);
 int launch_gemm_grad(const Common& cm, const Level& lv, int num_sms, void* stream);
+int launch_fit(const Common& cm, const FitArgs& fa, void* stream);
 int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list, int n_p,
                    uint32_t* mask, void* stream);
 int launch_scales(const Common& cm, void* stream);

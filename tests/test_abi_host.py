@@ -85,6 +85,17 @@ def test_workspace_sizes(binding):
     assert s1 + 1000 * 1024 // 8 <= s1p <= s1 + 1000 * 1024 // 8 + 4096
     bad = binding.make_opts(estimator=2)
     assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    # corrections: division only with the plain estimator; the affine model
+    # needs its sample entries
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(binding.make_opts(correction=1))) > 0
+    bad = binding.make_opts(correction=1, estimator=1)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    bad = binding.make_opts(correction=2)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    good = binding.make_opts(correction=2, n_fit=4, fit_i=16, fit_j=16)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(good)) > 0
+    bad = binding.make_opts(correction=3)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
 
 
 def test_argument_validation_before_any_device_call(binding):
@@ -106,6 +117,8 @@ def test_argument_validation_before_any_device_call(binding):
     assert lib.apsp_pnorm(4, 16, 4, 16, 4, 0, ctypes.byref(proj), z, 0, z) == 7
     assert lib.maxprod_pnorm_backward(4, 4, 4, 16, 16, 16, 16, 16, 16, 16, 16,
                                       ctypes.byref(proj), z, 0, z) == 7
+    div = binding.make_opts(compute="f32", correction=1)
+    assert lib.apsp_pnorm(4, 16, 4, 16, 4, 0, ctypes.byref(div), z, 0, z) == 7
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
     assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1
