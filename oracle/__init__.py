@@ -83,6 +83,9 @@ def _load():
             lib.orc_pnorm_ex.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci, ci,
                                          vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm_ex.restype = ci
+            lib.orc_maxconv.argtypes = [i64, i64, vp, i64, vp, vp]
+            lib.orc_conv.argtypes = [i64, i64, vp, i64, vp, vp]
+            lib.orc_maxconv_pnorm.argtypes = [i64, i64, vp, i64, vp, ci, vp, dbl, vp, vp, vp]
             lib.orc_affine_fit.argtypes = [i64, vp, vp, vp, ci, vp]
             lib.orc_apply_correction.argtypes = [i64, i64, i64, ci, vp, ci, vp, vp, vp, vp, vp]
             lib.orc_entries.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp,
@@ -383,3 +386,49 @@ def col_logloss(A, bcol, plog_col):
     M, K = A.shape
     pl = np.ascontiguousarray(np.asarray(plog_col) & 0x7F, dtype=np.uint8)
     return float(_load().orc_col_logloss(M, K, _p(A), _p(bcol), _p(pl)))
+
+
+# ------------------------------------------------------- max-convolution ---
+def _batch(x):
+    x = _f64(x)
+    return x[None, :] if x.ndim == 1 else x
+
+
+def maxconv(x, y):
+    """Exact max-convolution z_m = max_i x_i y_(m-i) (Sec. 1), per batch row."""
+    x, y = _batch(x), _batch(y)
+    b, nx = x.shape
+    ny = y.shape[1]
+    z = np.empty((b, nx + ny - 1), dtype=np.float64)
+    _load().orc_maxconv(b, nx, _p(x), ny, _p(y), _p(z))
+    return z
+
+
+def conv(x, y):
+    """Naive ring convolution w_m = sum_i x_i y_(m-i), per batch row."""
+    x, y = _batch(x), _batch(y)
+    b, nx = x.shape
+    ny = y.shape[1]
+    w = np.empty((b, nx + ny - 1), dtype=np.float64)
+    _load().orc_conv(b, nx, _p(x), ny, _p(y), _p(w))
+    return w
+
+
+def maxconv_pnorm(x, y, p_log2, tau: float, want_S: bool = False):
+    """p-norm estimate of the max-convolution from naive-convolution p-sums of
+    the vectors scaled by their maxima (Sec. 1, Sec. 2.1).  Returns a dict with
+    z, p_sel and (if want_S) S of shape (batch, n_p, nz)."""
+    x, y = _batch(x), _batch(y)
+    b, nx = x.shape
+    ny = y.shape[1]
+    nz = nx + ny - 1
+    pl = _plog(p_log2)
+    z = np.empty((b, nz), dtype=np.float64)
+    psel = np.empty((b, nz), dtype=np.uint8)
+    S = np.empty((b, len(pl), nz), dtype=np.float64) if want_S else None
+    _load().orc_maxconv_pnorm(b, nx, _p(x), ny, _p(y), len(pl), _p(pl), float(tau), _p(z),
+                              _p(psel), _p(S) if S is not None else None)
+    out = dict(z=z, p_sel=psel)
+    if want_S:
+        out["S"] = S
+    return out

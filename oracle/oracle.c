@@ -616,3 +616,98 @@ double orc_col_logloss(int64_t M, int64_t K, const double* A, const double* bcol
   }
   return L;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Max-convolution (Sec. 1): z_m = max_i x_i y_(m-i) over the indices where */
+/* both factors exist, m = 0 .. nx + ny - 2.  One problem per batch row;    */
+/* x is batch x nx, y is batch x ny, z is batch x (nx + ny - 1), row-major.  */
+void orc_maxconv(int64_t batch, int64_t nx, const double* x, int64_t ny, const double* y,
+                 double* z) {
+  int64_t b;
+  int64_t nz = nx + ny - 1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (b = 0; b < batch; ++b) {
+    const double* xb = x + b * nx;
+    const double* yb = y + b * ny;
+    for (int64_t m = 0; m < nz; ++m) {
+      double mx = 0.0;
+      for (int64_t i = 0; i < nx; ++i) {
+        int64_t t = m - i;
+        if (t < 0 || t >= ny) continue;
+        double v = xb[i] * yb[t];
+        if (v > mx) mx = v;
+      }
+      z[b * nz + m] = mx;
+    }
+  }
+}
+
+/* The ring convolution G done naively (what an FFT convolution H computes */
+/* up to rounding): w_m = sum_i x_i y_(m-i).  Same layout as orc_maxconv.   */
+void orc_conv(int64_t batch, int64_t nx, const double* x, int64_t ny, const double* y, double* w) {
+  int64_t b;
+  int64_t nz = nx + ny - 1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (b = 0; b < batch; ++b) {
+    const double* xb = x + b * nx;
+    const double* yb = y + b * ny;
+    for (int64_t m = 0; m < nz; ++m) {
+      double s = 0.0;
+      for (int64_t i = 0; i < nx; ++i) {
+        int64_t t = m - i;
+        if (t < 0 || t >= ny) continue;
+        s += xb[i] * yb[t];
+      }
+      w[b * nz + m] = s;
+    }
+  }
+}
+
+/* p-norm estimate of the max-convolution (Sec. 1; the scaled H' of Sec.    */
+/* 2.1 with one scale per vector): x' = x / max x, y' = y / max y (a zero   */
+/* vector keeps scale 1); for each p in P the p-sums                        */
+/* S^(p)_m = sum_i x'_i^p y'_(m-i)^p by the naive convolution, with pow per */
+/* term; p* = the largest p with S^(p)_m >= tau (none: the smallest p,      */
+/* flagged 0x80 in p_sel); z_m = max x * max y * (S^(p*)_m)^(1/p*).          */
+/* S_all (optional) receives S as [batch][n_p][nz].                          */
+void orc_maxconv_pnorm(int64_t batch, int64_t nx, const double* x, int64_t ny, const double* y,
+                       int n_p, const int* p_log2, double tau, double* z, uint8_t* psel,
+                       double* S_all) {
+  int64_t b;
+  int64_t nz = nx + ny - 1;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (b = 0; b < batch; ++b) {
+    const double* xb = x + b * nx;
+    const double* yb = y + b * ny;
+    double mx = 0.0, my = 0.0;
+    for (int64_t i = 0; i < nx; ++i)
+      if (xb[i] > mx) mx = xb[i];
+    for (int64_t i = 0; i < ny; ++i)
+      if (yb[i] > my) my = yb[i];
+    double sx = mx > 0.0 ? mx : 1.0, sy = my > 0.0 ? my : 1.0;
+    for (int64_t m = 0; m < nz; ++m) {
+      int q_sel = -1;
+      double s_sel = 0.0;
+      for (int q = n_p - 1; q >= 0; --q) {
+        double p = ldexp(1.0, p_log2[q]);
+        double s = 0.0;
+        for (int64_t i = 0; i < nx; ++i) {
+          int64_t t = m - i;
+          if (t < 0 || t >= ny) continue;
+          s += pow(xb[i] / sx, p) * pow(yb[t] / sy, p);
+        }
+        if (S_all) S_all[(b * n_p + q) * nz + m] = s;
+        if (q_sel < 0 && s >= tau) {
+          q_sel = q;
+          s_sel = s;
+        }
+        if (q == 0 && q_sel < 0) s_sel = s;
+      }
+      int unstable = q_sel < 0;
+      if (unstable) q_sel = 0;
+      double p = ldexp(1.0, p_log2[q_sel]);
+      z[b * nz + m] = sx * sy * (s_sel > 0.0 ? pow(s_sel, 1.0 / p) : 0.0);
+      if (psel) psel[b * nz + m] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
+    }
+  }
+}

@@ -581,3 +581,99 @@ def test_affine_correction_reduces_error(orc):
         c2 = orc.pnorm(A, B, list(range(7)), tau, estimator=est, correction=2, fit_ij=(ii, jj))
         e2 = np.median(np.abs(c2["C"] - exact) / exact)
         assert e2 < e0 / 5, (est, e0, e2)
+
+
+# ------------------------------------------------------- max-convolution ---
+# Sec. 1: z_m = max_i x_i y_(m-i) and its p-norm estimate from ring
+# convolutions of the powered, max-scaled vectors.
+def test_maxconv_equals_maxprod_with_toeplitz(orc):
+    """max_i x_i y_(m-i) is the (x,max) product of the Toeplitz matrix of x
+    with y (Alg. 2 on a structured operand)."""
+    g = workloads.rng(2000)
+    for nx, ny in ((1, 1), (5, 3), (17, 29)):
+        x, y = g.random(nx), g.random(ny)
+        nz = nx + ny - 1
+        T = np.zeros((nz, ny))
+        for m in range(nz):
+            for t in range(ny):
+                if 0 <= m - t < nx:
+                    T[m, t] = x[m - t]
+        np.testing.assert_array_equal(orc.maxconv(x, y)[0], orc.maxprod(T, y[:, None])[:, 0])
+
+
+def test_conv_matches_numpy(orc):
+    g = workloads.rng(2001)
+    x, y = g.random((3, 40)), g.random((3, 25))
+    want = np.array([np.convolve(x[b], y[b]) for b in range(3)])
+    np.testing.assert_allclose(orc.conv(x, y), want, rtol=1e-13)
+
+
+def test_maxconv_pnorm_p1_is_convolution(orc):
+    g = workloads.rng(2002)
+    x, y = g.random((2, 30)) + 0.1, g.random((2, 20)) + 0.1
+    out = orc.maxconv_pnorm(x, y, [0], tau=1e-300)
+    want = np.array([np.convolve(x[b], y[b]) for b in range(2)])
+    np.testing.assert_allclose(out["z"], want, rtol=1e-13)
+
+
+def test_maxconv_pnorm_envelope_and_all_ones(orc):
+    """z <= zhat <= L_m^(1/p*) z with L_m the number of terms of index m, and
+    tight for all-ones vectors; zhat tends to z as p grows."""
+    g = workloads.rng(2003)
+    nx, ny = 50, 37
+    x, y = g.random(nx), g.random(ny)
+    z = orc.maxconv(x, y)[0]
+    L = np.array([min(m, nx - 1) - max(0, m - ny + 1) + 1 for m in range(nx + ny - 1)])
+    prev = None
+    for lp in range(0, 9):
+        zh = orc.maxconv_pnorm(x, y, [lp], tau=1e-300)["z"][0]
+        assert np.all(zh >= z * (1 - 1e-13))
+        assert np.all(zh <= z * L ** (1.0 / 2 ** lp) * (1 + 1e-13))
+        if prev is not None:
+            assert np.all(zh <= prev * (1 + 1e-13))
+        prev = zh
+    ones = orc.maxconv_pnorm(np.ones(nx), np.ones(ny), [0, 2, 4], tau=1e-12)
+    assert np.all(ones["p_sel"] == 4)
+    np.testing.assert_allclose(ones["z"][0], L ** (1 / 16), rtol=1e-14)
+
+
+def test_maxconv_pnorm_selection_with_tau(orc):
+    """The largest p with S >= tau is taken per index; a single-term index is
+    exact at any p.  x = y = (1, 1e-3): S^(p)_0 = 1, S^(p)_1 = 2 (1e-3)^p,
+    S^(p)_2 = (1e-6)^p; with tau = 0.9e-12 p* is 64, 4 and 2."""
+    x = np.array([1.0, 1e-3])
+    out = orc.maxconv_pnorm(x, x, [0, 1, 2, 3, 4, 5, 6], tau=0.9e-12, want_S=True)
+    assert list(out["p_sel"][0]) == [6, 2, 1]
+    np.testing.assert_allclose(out["z"][0], [1.0, 2 ** (1 / 4) * 1e-3, 1e-6], rtol=1e-12)
+    out = orc.maxconv_pnorm(x, x, [0, 1, 2], tau=1e-3)
+    assert out["p_sel"][0][2] == 0x80 | 0
+
+
+def test_maxconv_pnorm_sums_match_fft_convolution(orc):
+    """The p-sums are ring convolutions: numpy's FFT convolution of the
+    powered scaled vectors agrees to FFT rounding (a few 1e-16 of the largest)."""
+    g = workloads.rng(2004)
+    x, y = g.random(300) ** 0.25, g.random(200) ** 0.25
+    pl = [0, 2, 4, 6]
+    out = orc.maxconv_pnorm(x, y, pl, tau=1e-300, want_S=True)
+    nz = 499
+    for q, lp in enumerate(pl):
+        p = 2.0 ** lp
+        a, b = (x / x.max()) ** p, (y / y.max()) ** p
+        f = np.fft.irfft(np.fft.rfft(a, 512) * np.fft.rfft(b, 512), 512)[:nz]
+        scale = np.sqrt(np.sum(a * a) * np.sum(b * b))
+        assert np.max(np.abs(f - out["S"][0, q])) <= 1e-13 * scale
+
+
+def test_maxconv_limit_of_ring_convolutions(orc):
+    """log z_m = lim_p (1/p) log sum_i exp(p (log x_i + log y_(m-i))) by scipy's
+    logsumexp at p = 2^12 (Sec. 1), independent of the oracle's loops."""
+    from scipy.special import logsumexp
+    g = workloads.rng(2005)
+    x, y = g.random(23) + 0.05, g.random(31) + 0.05
+    z = orc.maxconv(x, y)[0]
+    p = 2.0 ** 12
+    for m in range(53):
+        terms = [p * (np.log(x[i]) + np.log(y[m - i])) for i in range(23) if 0 <= m - i < 31]
+        est = np.exp(logsumexp(terms) / p)
+        assert z[m] <= est * (1 + 1e-12) and est <= z[m] * len(terms) ** (1 / p) * (1 + 1e-12)
