@@ -59,7 +59,7 @@ def parse_args():
                     help="1: divide by K^(1/p*); 2: affine model fitted on --n-fit exact samples")
     ap.add_argument("--n-fit", type=int, default=1024)
     ap.add_argument("--workload", default="pnorm",
-                    choices=["pnorm", "apsp", "backward", "grouped"],
+                    choices=["pnorm", "apsp", "backward", "grouped", "maxconv"],
                     help="pnorm: the default product; the others measure the other paths")
     return ap.parse_args()
 
@@ -501,7 +501,61 @@ def run_other(args):
             "unit": "Gop/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic"}
-    if args.workload == "apsp":
+    if args.workload == "maxconv":
+        # batch of max-convolutions (Sec. 1), H = FP64 FFT, one CTA per problem
+        batch, n = args.count if args.count != 4096 else 1024, 4096
+        g = workloads.rng(None, 5)
+        xh = ((1.0 - g.random((batch, n))) ** 0.25).astype(np.float32)
+        yh = ((1.0 - g.random((batch, n))) ** 0.25).astype(np.float32)
+        x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+        nz = 2 * n - 1
+        z = torch.empty((batch, nz), dtype=torch.float32, device="cuda")
+        ze = torch.empty_like(z)
+        res = {}
+
+        def fwd():
+            res["psel"] = pn.maxconv_pnorm(x, y, out=z, check=False)[1]
+        ms = _timed(torch, fwd, K, args.warmup, stream)
+        pn.check_device_status(x.device, "maxconv_pnorm")
+        ems = _timed(torch, lambda: pn.maxconv_exact(x, y, out=ze), max(1, K // 5), 1, stream)
+        ops = float(batch) * n * n  # (x,max) terms of the exact max-convolution
+        psel = res["psel"].cpu().numpy()
+        zz, zex = z.cpu().numpy(), ze.cpu().numpy()
+        rel = np.abs(zz - zex) / zex
+        # FP64 work actually done: the FFT levels each problem ran (2 FFTs of
+        # N = 8192, 10 flops per butterfly), replaying the kernel's rule from
+        # p_sel -- after level q the open indices (p* below that level) either
+        # end the loop (none), go to the direct sums (few terms) or need the
+        # next FFT level
+        P = list(range(7))
+        N, logN = 8192, 13
+        mm = np.arange(nz)
+        L = np.minimum(mm, n - 1) - np.maximum(0, mm - n + 1) + 1
+        levels = np.zeros(batch, dtype=np.int64)
+        for b in range(batch):
+            lp = (psel[b] & 0x7F).astype(np.int64)
+            for q in range(len(P) - 1, -1, -1):
+                levels[b] += 1
+                W = int(L[lp < P[q]].sum())
+                if W == 0 or q == 0 or W * (8 + 2 * q) <= 10 * N * logN:
+                    break
+        flops = float(levels.sum()) * 2 * (N // 2) * logN * 10
+        line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f64 (FFT)",
+                    config={"workload": f"maxconv_pnorm batch={batch} n={n} (2n-1 outputs), "
+                            "entries exp(-Exp(4)), P={1..64}, tau=1e-12, FP64 FFT per problem "
+                            "in shared memory", "batch": batch, "n": n},
+                    exact_kernel={"ms": ems, "gops": ops / (ems / 1e3) / 1e9,
+                                  "speedup_of_pnorm": ems / ms},
+                    err={"outputs": int(rel.size), "max_rel_vs_exact": float(rel.max()),
+                         "median_rel_vs_exact": float(np.median(rel)),
+                         "p_sel_histogram": {str(2 ** int(k)): int(v) for k, v in
+                                             zip(*np.unique(psel & 0x7F, return_counts=True))}},
+                    roofline={"bound": "fp64", "achieved": flops / (ms / 1e3) / 1e12,
+                              "peak": 1.25, "unit": "TFLOP/s",
+                              "frac": flops / (ms / 1e3) / 1e12 / 1.25,
+                              "traffic": None, "levels_run_mean": float(levels.mean()),
+                              "peak_source": "nominal FP64 rate of the profiling recipe"})
+    elif args.workload == "apsp":
         n, T = 4096, 12
         W = torch.from_numpy(workloads.apsp_weights(n, density=0.1, index=1)).cuda()
         D = torch.empty_like(W)

@@ -229,6 +229,45 @@ PN_API pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const
                                    const float* B, int64_t ldb, float* C, int64_t ldc,
                                    int32_t semiring, int32_t variant, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Max-convolution (Sec. 1): for each of `batch` independent problems,
+ *   z_m = max_i x_i y_(m-i),  m = 0 .. nx + ny - 2,
+ * over the indices where both factors exist.  Layout: x is batch x nx
+ * (row stride ldx >= nx), y is batch x ny (ldy >= ny), z is batch x
+ * (nx + ny - 1) (ldz >= nx + ny - 1), all row-major FP32 device arrays owned
+ * by the caller; nx, ny >= 1 (else PN_EINVAL); batch 0 does nothing.
+ * ------------------------------------------------------------------------ */
+
+/* p-norm estimate with H = FFT convolution (Sec. 1; the scaled H' and the
+ * threshold tau of Sec. 2.1): x' = x / max x, y' = y / max y (a zero vector
+ * keeps scale 1); for each p of the family (largest first) the ring
+ * convolution S^(p) = x'^p * y'^p by a double-precision FFT; index m takes
+ * the largest p with S^(p)_m >= tau (none: the smallest p, flag 0x80 in
+ * p_sel) and z_m = max x * max y * (S^(p*)_m)^(1/p*).  One CTA per problem
+ * holds its transforms in shared memory: nx + ny - 1 <= 8192, else
+ * PN_EUNSUPPORTED.  opts: n_p / p_log2, tau (<= 0: pn_maxconv_default_tau()),
+ * dev_status (PN_EDOMAIN for an input outside [0, FLT_MAX]); compute,
+ * scaling and tile_n are not used; a nonzero estimator or correction returns
+ * PN_EUNSUPPORTED.  p_sel (optional; ldp >= nx + ny - 1) as in maxprod_pnorm.
+ * No workspace.  The first call on a device also fills a table of FFT
+ * twiddle factors (one kernel on `stream`): make it before capturing
+ * `stream` into a graph. */
+PN_API pn_status maxconv_pnorm(int64_t batch, int64_t nx, const float* x, int64_t ldx,
+                               int64_t ny, const float* y, int64_t ldy, float* z, int64_t ldz,
+                               uint8_t* p_sel, int64_t ldp, const pn_opts* opts, void* stream);
+
+/* The paper's threshold for a double-precision FFT convolution of vectors
+ * in [0, 1], 1e-12 (Sec. 2.1). */
+PN_API double pn_maxconv_default_tau(void);
+
+/* Exact max-convolution on the CUDA cores (the plain comparison): FP32
+ * products, each correctly rounded, and an exact max, so the result equals
+ * the FP64 max-convolution rounded to FP32.  nx + ny <= 50000 (shared
+ * memory), else PN_EUNSUPPORTED. */
+PN_API pn_status maxconv_exact(int64_t batch, int64_t nx, const float* x, int64_t ldx,
+                               int64_t ny, const float* y, int64_t ldy, float* z, int64_t ldz,
+                               void* stream);
+
 /* Workspace bytes for apsp_pnorm (0 on invalid options). */
 PN_API size_t pn_apsp_workspace_size(int64_t n, const pn_opts* opts);
 

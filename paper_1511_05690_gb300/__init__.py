@@ -254,6 +254,53 @@ def maxprod_exact(A: torch.Tensor, B: torch.Tensor, *, semiring=0, variant=None,
     return C
 
 
+def _rows(v, name):
+    """A (batch, n) float32 CUDA tensor with unit column stride (1-D -> one row)."""
+    if v.dim() == 1:
+        v = v.unsqueeze(0)
+    return _mat(v, name)
+
+
+def maxconv_pnorm(x: torch.Tensor, y: torch.Tensor, *, p_log2=tuple(range(7)), tau=None,
+                  out=None, want_psel=True, check=True, stream=None):
+    """p-norm estimate of the batched max-convolution z_m = max_i x_i y_(m-i)
+    with H = FP64 FFT convolution (Sec. 1).  x: (batch, nx), y: (batch, ny)
+    (or 1-D).  Returns (z, p_sel or None), z of shape (batch, nx + ny - 1)."""
+    x, y = _rows(x, "x"), _rows(y, "y")
+    if x.shape[0] != y.shape[0]:
+        raise ValueError("x and y differ in batch")
+    batch, nx = x.shape
+    ny = y.shape[1]
+    nz = nx + ny - 1
+    dev = x.device
+    z = out if out is not None else torch.empty((batch, nz), dtype=torch.float32, device=dev)
+    psel = torch.empty((batch, nz), dtype=torch.uint8, device=dev) if want_psel else None
+    st = status_word(dev)
+    o = make_opts(p_log2, "f32", tau, 2, 0, 0, st.data_ptr())
+    rc = lib().maxconv_pnorm(batch, nx, x.data_ptr(), _ld(x), ny, y.data_ptr(), _ld(y),
+                             z.data_ptr(), _ld(z), psel.data_ptr() if psel is not None else None,
+                             nz, ctypes.byref(o), _stream_ptr(stream))
+    _b.check(rc, "maxconv_pnorm")
+    if check:
+        check_device_status(dev, "maxconv_pnorm")
+    return z, psel
+
+
+def maxconv_exact(x: torch.Tensor, y: torch.Tensor, *, out=None, stream=None):
+    """Exact batched max-convolution on the CUDA cores (the comparison)."""
+    x, y = _rows(x, "x"), _rows(y, "y")
+    if x.shape[0] != y.shape[0]:
+        raise ValueError("x and y differ in batch")
+    batch, nx = x.shape
+    ny = y.shape[1]
+    z = out if out is not None else torch.empty((batch, nx + ny - 1), dtype=torch.float32,
+                                                device=x.device)
+    rc = lib().maxconv_exact(batch, nx, x.data_ptr(), _ld(x), ny, y.data_ptr(), _ld(y),
+                             z.data_ptr(), _ld(z), _stream_ptr(stream))
+    _b.check(rc, "maxconv_exact")
+    return z
+
+
 def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
                tau=None, scaling=2, diag_policy=2, tile_n=0, out=None, check=True,
                stream=None, ev_begin=None, ev_end=None, estimator=0, correction=0):

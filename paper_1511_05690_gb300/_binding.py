@@ -28,6 +28,7 @@ EXPORTS = (
     "pn_apsp_workspace_size", "apsp_pnorm", "pn_backward_workspace_size",
     "maxprod_pnorm_backward", "pn_grouped_table_bytes", "pn_grouped_build_table",
     "maxprod_pnorm_grouped", "maxprod_pnorm_static", "pn_autotune", "pn_grouped_autotune",
+    "maxconv_pnorm", "maxconv_exact", "pn_maxconv_default_tau",
 )
 
 
@@ -99,6 +100,12 @@ def load():
         lib.pn_maxprod_exact_variant.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32,
                                                  i32, vp]
         lib.pn_maxprod_exact_variant.restype = i32
+        lib.maxconv_pnorm.argtypes = [i64, i64, vp, i64, i64, vp, i64, vp, i64, vp, i64, optp, vp]
+        lib.maxconv_pnorm.restype = i32
+        lib.maxconv_exact.argtypes = [i64, i64, vp, i64, i64, vp, i64, vp, i64, vp]
+        lib.maxconv_exact.restype = i32
+        lib.pn_maxconv_default_tau.argtypes = []
+        lib.pn_maxconv_default_tau.restype = ctypes.c_double
         lib.pn_apsp_workspace_size.argtypes = [i64, optp]
         lib.pn_apsp_workspace_size.restype = sz
         lib.apsp_pnorm.argtypes = [i64, vp, i64, vp, i64, i32, optp, vp, sz, vp]

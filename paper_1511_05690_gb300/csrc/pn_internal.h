@@ -201,6 +201,27 @@ int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t 
                       void* stream);
 int launch_gemm_grad(const Common& cm, const Level& lv, int num_sms, void* stream);
 int launch_fit(const Common& cm, const FitArgs& fa, void* stream);
+
+// Batched max-convolution problems (pn_maxconv.cu).
+struct MaxconvArgs {
+  const float* x;
+  const float* y;
+  float* z;
+  uint8_t* psel;
+  int64_t ldx, ldy, ldz, ldp;
+  int64_t batch;
+  int32_t nx, ny, nz;
+  int32_t logN;        // FFT length 2^logN >= nz
+  int32_t n_p;
+  int32_t p_log2[PN_MAX_P];
+  double tau;
+  int32_t* status;
+};
+constexpr int MAXCONV_LOG_NMAX = 13;  // FFT length of the shared-memory kernel, at most
+int maxconv_fft_smem_bytes(int logN);
+int maxconv_exact_smem_bytes(int nx, int ny);
+int launch_maxconv_fft(const MaxconvArgs& ma, void* stream);
+int launch_maxconv_exact(const MaxconvArgs& ma, void* stream);
 int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list, int n_p,
                    uint32_t* mask, void* stream);
 int launch_scales(const Common& cm, void* stream);

@@ -119,6 +119,16 @@ def test_argument_validation_before_any_device_call(binding):
                                       ctypes.byref(proj), z, 0, z) == 7
     div = binding.make_opts(compute="f32", correction=1)
     assert lib.apsp_pnorm(4, 16, 4, 16, 4, 0, ctypes.byref(div), z, 0, z) == 7
+    # max-convolution: shapes and limits are checked on the host
+    assert lib.maxconv_pnorm(0, 4, z, 4, 4, z, 4, z, 7, z, 7, ctypes.byref(o), z) == 0
+    assert lib.maxconv_pnorm(2, 0, z, 4, 4, z, 4, z, 7, z, 7, ctypes.byref(o), z) == 1
+    assert lib.maxconv_pnorm(2, 5000, 16, 5000, 4000, 16, 4000, 16, 8999, z, 0,
+                             ctypes.byref(o), z) == 7
+    assert lib.maxconv_pnorm(2, 4, 16, 4, 4, 16, 4, 16, 7, z, 0, ctypes.byref(proj), z) == 7
+    assert lib.maxconv_pnorm(2, 4, 16, 3, 4, 16, 4, 16, 7, z, 0, ctypes.byref(o), z) == 1
+    assert lib.maxconv_exact(2, 4, 16, 4, 0, 16, 4, 16, 7, z) == 1
+    assert lib.maxconv_exact(1, 30000, 16, 30000, 30000, 16, 30000, 16, 59999, z) == 7
+    assert lib.pn_maxconv_default_tau() == 1e-12
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
     assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1
