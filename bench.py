@@ -522,8 +522,8 @@ def run_other(args):
         psel = res["psel"].cpu().numpy()
         zz, zex = z.cpu().numpy(), ze.cpu().numpy()
         rel = np.abs(zz - zex) / zex
-        # FP64 work actually done: the FFT levels each problem ran (2 FFTs of
-        # N = 8192, 10 flops per butterfly), replaying the kernel's rule from
+        # FP64 work actually done: the FFT levels each problem ran, replaying
+        # the kernel's rule from
         # p_sel -- after level q the open indices (p* below that level) either
         # end the loop (none), go to the direct sums (few terms) or need the
         # next FFT level
@@ -539,7 +539,12 @@ def run_other(args):
                 W = int(L[lp < P[q]].sum())
                 if W == 0 or q == 0 or W * (8 + 2 * q) <= 10 * N * logN:
                     break
-        flops = float(levels.sum()) * 2 * (N // 2) * logN * 10
+        # per level: forward FFT of length N (a multiply-free radix-4 first
+        # pass, 4N flops, then N/2 butterflies of 10 flops per stage), the
+        # spectrum (about 28 flops per output pair), inverse of length M = N/2
+        M = N // 2
+        per_level = 4 * N + 5 * N * (logN - 2) + 28 * M + 4 * M + 5 * M * (logN - 3)
+        flops = float(levels.sum()) * per_level
         line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f64 (FFT)",
                     config={"workload": f"maxconv_pnorm batch={batch} n={n} (2n-1 outputs), "
                             "entries exp(-Exp(4)), P={1..64}, tau=1e-12, FP64 FFT per problem "

@@ -262,8 +262,9 @@ PN_API double pn_maxconv_default_tau(void);
 
 /* Exact max-convolution on the CUDA cores (the plain comparison): FP32
  * products, each correctly rounded, and an exact max, so the result equals
- * the FP64 max-convolution rounded to FP32.  nx + ny <= 50000 (shared
- * memory), else PN_EUNSUPPORTED. */
+ * the FP64 max-convolution rounded to FP32.  nx + ny <= 2^30, else
+ * PN_EUNSUPPORTED.  When nx > 8192 the partial maxima of several blocks of
+ * terms meet in z by atomic max, after z is zeroed on `stream`. */
 PN_API pn_status maxconv_exact(int64_t batch, int64_t nx, const float* x, int64_t ldx,
                                int64_t ny, const float* y, int64_t ldy, float* z, int64_t ldz,
                                void* stream);

@@ -219,7 +219,7 @@ struct MaxconvArgs {
 };
 constexpr int MAXCONV_LOG_NMAX = 13;  // FFT length of the shared-memory kernel, at most
 int maxconv_fft_smem_bytes(int logN);
-int maxconv_exact_smem_bytes(int nx, int ny);
+int maxconv_exact_smem_bytes();
 int launch_maxconv_fft(const MaxconvArgs& ma, void* stream);
 int launch_maxconv_exact(const MaxconvArgs& ma, void* stream);
 int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list, int n_p,

@@ -20,10 +20,10 @@
 // ring convolution, which the FFT only reproduces) instead of running more
 // FFT levels.
 //
-// k_maxconv_exact: the exact comparison on the CUDA cores, one CTA per 2048
-// outputs of one problem, x and zero-padded y in shared memory, 8 consecutive
-// outputs per thread; each FP32 product is correctly rounded and the max is
-// exact, so the result is bit-identical to any sequential evaluation.
+// k_maxconv_exact: the exact comparison on the CUDA cores, one CTA per 1792
+// outputs and 8192 terms of one problem, 7 consecutive outputs per thread;
+// each FP32 product is correctly rounded and the max is exact, so the result
+// is bit-identical to any sequential evaluation.
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -54,20 +54,46 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 
-// In-place radix-2 decimation-in-time FFT of a[0..N) held in bit-reversed
-// order; natural order on return.  sign = -1 forward, +1 inverse (unscaled).
-__device__ void fft_dit(double2* a, const double2* tw, int logN, double sign) {
-  const int N = 1 << logN;
-  for (int s = 0; s < logN; ++s) {
-    const int h = 1 << s;                  // half span
-    const int step = (N >> 1) >> s;        // twiddle stride: N / (2h)
-    for (int b = threadIdx.x; b < (N >> 1); b += FFT_THREADS) {
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.x, b.y, -a.y * b.x));
+}
+
+// In-place radix-2 decimation-in-time FFT of a[0..L) (L = 2^logL) held in
+// bit-reversed order; natural order on return; unscaled.  INV selects the
+// inverse (conjugate twiddles).  tw[k * tws] = exp(-2 pi i k / L).  The first
+// two stages (twiddles 1 and -+i) run as one multiply-free radix-4 pass.
+template <bool INV>
+__device__ void fft_dit(double2* a, const double2* tw, int logL, int tws) {
+  const int L = 1 << logL;
+  int s0 = 0;
+  if (logL >= 2) {
+    for (int g = threadIdx.x; g < (L >> 2); g += FFT_THREADS) {
+      double2* q = a + 4 * g;
+      const double2 a0 = q[0], a1 = q[1], a2 = q[2], a3 = q[3];
+      const double2 b0 = make_double2(a0.x + a1.x, a0.y + a1.y);
+      const double2 b1 = make_double2(a0.x - a1.x, a0.y - a1.y);
+      const double2 b2 = make_double2(a2.x + a3.x, a2.y + a3.y);
+      const double2 b3 = make_double2(a2.x - a3.x, a2.y - a3.y);
+      // forward: t = -i b3; inverse: t = +i b3
+      const double2 t = INV ? make_double2(-b3.y, b3.x) : make_double2(b3.y, -b3.x);
+      q[0] = make_double2(b0.x + b2.x, b0.y + b2.y);
+      q[2] = make_double2(b0.x - b2.x, b0.y - b2.y);
+      q[1] = make_double2(b1.x + t.x, b1.y + t.y);
+      q[3] = make_double2(b1.x - t.x, b1.y - t.y);
+    }
+    __syncthreads();
+    s0 = 2;
+  }
+  for (int s = s0; s < logL; ++s) {
+    const int h = 1 << s;                     // half span
+    const int step = ((L >> 1) >> s) * tws;   // twiddle stride: L / (2h)
+    for (int b = threadIdx.x; b < (L >> 1); b += FFT_THREADS) {
       const int j = b & (h - 1);
       const int i0 = ((b >> s) << (s + 1)) + j;
       const int i1 = i0 + h;
-      double2 w = tw[j * step];
-      w.y *= -sign;                         // table holds the forward sign
-      const double2 t = cmul(w, a[i1]);
+      const double2 w = tw[j * step];
+      const double2 t = INV ? cmulc(w, a[i1]) : cmul(w, a[i1]);
       const double2 u = a[i0];
       a[i0] = make_double2(u.x + t.x, u.y + t.y);
       a[i1] = make_double2(u.x - t.x, u.y - t.y);
@@ -138,6 +164,21 @@ __device__ void direct_levels(const MaxconvArgs& ma, const float* x, const float
   res[m] = static_cast<uint8_t>(ma.p_log2[qs] | (stable ? 0 : 0x80));
 }
 
+// Z_k from A_k and A_(N-k) (the spectra of the packed real pair).
+__device__ __forceinline__ double2 spec_z(double2 ak, double2 an) {
+  const double2 X = make_double2(0.5 * (ak.x + an.x), 0.5 * (ak.y - an.y));
+  const double2 Y = make_double2(0.5 * (ak.y + an.y), -0.5 * (ak.x - an.x));
+  return cmul(X, Y);
+}
+
+// V_k = (Z_k + conj Z_(M-k)) / 2 + i conj(W^k) (Z_k - conj Z_(M-k)) / 2, w = W^k.
+__device__ __forceinline__ double2 spec_v(double2 zk, double2 zmk, double2 w) {
+  const double2 e = make_double2(0.5 * (zk.x + zmk.x), 0.5 * (zk.y - zmk.y));
+  const double2 d = make_double2(0.5 * (zk.x - zmk.x), 0.5 * (zk.y + zmk.y));
+  const double2 o = cmulc(w, d);  // O_k = conj(W^k) d
+  return make_double2(e.x - o.y, e.y + o.x);
+}
+
 __device__ __forceinline__ int bitrev(int k, int logN) {
   return logN == 0 ? 0 : static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - logN));
 }
@@ -191,7 +232,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
   }
   if (sx == 0.0) sx = 1.0;  // a zero vector keeps scale 1
   if (sy == 0.0) sy = 1.0;
-  const double invN = 1.0 / N;
+  const double invM = 2.0 / N;
   const float isx_f = static_cast<float>(1.0 / sx), isy_f = static_cast<float>(1.0 / sy);
   const double sxy = sx * sy;
   float* z = ma.z + (int64_t)b * ma.ldz;
@@ -214,37 +255,37 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
       a[bitrev(k, ma.logN)] = make_double2(xr, yr);
     }
     __syncthreads();
-    fft_dit(a, tw, ma.logN, -1.0);
-    // X_k = (A_k + conj A_(N-k)) / 2, Y_k = (A_k - conj A_(N-k)) / (2i),
-    // Z = X Y (Hermitian), written back in bit-reversed order
-    constexpr int PAIRS = FFT_NMAX / 2 / FFT_THREADS;
-    double2 zk[PAIRS];
-    for (int u = 0; u < PAIRS; ++u) {
+    fft_dit<false>(a, tw, ma.logN, 1);
+    // Spectrum of the ring convolution: X_k = (A_k + conj A_(N-k)) / 2,
+    // Y_k = (A_k - conj A_(N-k)) / (2i), Z = X Y (Hermitian: the convolution
+    // is real).  Its inverse runs at half length M = N / 2: with E, O the
+    // length-M DFTs of the even and odd samples of S, Z_k = E_k + W^k O_k and
+    // Z_(k+M) = conj Z_(M-k) = E_k - W^k O_k (W = exp(-2 pi i / N)), so
+    // V_k = E_k + i O_k = (Z_k + conj Z_(M-k)) / 2 + i W^-k (Z_k - conj Z_(M-k)) / 2
+    // is the DFT of v_j = S_2j + i S_(2j+1).  Thread work: k and M - k
+    // together (reads A at k, N - k, M - k, M + k).
+    const int M = N >> 1;
+    constexpr int QUADS = FFT_NMAX / 4 / FFT_THREADS + 1;
+    double2 vk[QUADS], vm[QUADS];
+    for (int u = 0; u < QUADS; ++u) {
       const int k = tid + u * FFT_THREADS;
-      if (k <= (N >> 1)) {
-        const double2 ak = a[k], an = a[(N - k) & (N - 1)];
-        const double2 X = make_double2(0.5 * (ak.x + an.x), 0.5 * (ak.y - an.y));
-        const double2 Y = make_double2(0.5 * (ak.y + an.y), -0.5 * (ak.x - an.x));
-        zk[u] = cmul(X, Y);
+      if (k <= (M >> 1)) {
+        const double2 zk = spec_z(a[k], a[(N - k) & (N - 1)]);
+        const double2 zm = spec_z(a[M - k], a[M + k]);
+        vk[u] = spec_v(zk, zm, tw[k]);
+        vm[u] = spec_v(zm, zk, (M - k) < M ? tw[M - k] : make_double2(1.0, 0.0));
       }
     }
-    double2 zmid = make_double2(0.0, 0.0);  // k = N/2 when it falls past the pairs
-    if (tid == 0 && (N >> 1) >= PAIRS * FFT_THREADS) {
-      const double2 ak = a[N >> 1];
-      zmid = make_double2(ak.x * ak.y, 0.0);
-    }
     __syncthreads();
-    for (int u = 0; u < PAIRS; ++u) {
+    for (int u = 0; u < QUADS; ++u) {
       const int k = tid + u * FFT_THREADS;
-      if (k <= (N >> 1)) {
-        a[bitrev(k, ma.logN)] = zk[u];
-        if (k != 0 && k != (N >> 1))
-          a[bitrev(N - k, ma.logN)] = make_double2(zk[u].x, -zk[u].y);
+      if (k <= (M >> 1)) {
+        a[bitrev(k, ma.logN - 1)] = vk[u];
+        if (k != 0 && (M - k) != k) a[bitrev(M - k, ma.logN - 1)] = vm[u];
       }
     }
-    if (tid == 0 && (N >> 1) >= PAIRS * FFT_THREADS) a[bitrev(N >> 1, ma.logN)] = zmid;
     __syncthreads();
-    fft_dit(a, tw, ma.logN, 1.0);
+    fft_dit<true>(a, tw, ma.logN - 1, 2);
     // selection: first (largest) p with S >= tau; the smallest p takes the rest
     if (tid == 0) {
       open_terms = 0ull;
@@ -254,7 +295,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
     unsigned long long my_terms = 0ull;
     for (int m = tid; m < ma.nz; m += FFT_THREADS) {
       if (res[m] != 0xFF) continue;
-      const double S = a[m].x * invN;
+      const double S = ((m & 1) ? a[m >> 1].y : a[m >> 1].x) * invM;
       const bool stable = S >= ma.tau;
       if (stable || q == 0) {
         z[m] = static_cast<float>(sxy * root_pow2(S, plog));
@@ -292,66 +333,87 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
 
 // ---------------------------------------------------------------- exact ---
 constexpr int MCX_THREADS = 256;
-constexpr int MCX_OUT = 8;                              // outputs per thread
+constexpr int MCX_OUT = 7;                              // outputs per thread
 constexpr int MCX_SPAN = MCX_THREADS * MCX_OUT;         // outputs per CTA
+constexpr int MCX_IB = 8192;                            // terms i per CTA
 
-// z_m for m in [m0, m0 + MCX_SPAN) of problems blockIdx.y, + gridDim.y, ...
-// Shared memory:
-// x[0..nx) and y padded with zeros so that y[t] for t in (-SPAN, ny + 8)
-// reads 0 outside [0, ny) (every product is >= 0, so zeros never change a
-// max over a nonempty set of valid terms).
+// z_m for m in [m0, m0 + MCX_SPAN), terms i in [i0, i0 + MCX_IB), problems
+// blockIdx.z, + gridDim.z, ...  Shared memory holds x[i0 .. i0 + IB + 8) and
+// the y values those terms reach, zero outside [0, ny), so invalid terms
+// contribute 0 (every product is >= 0, and the max over the nonempty set of
+// valid terms is unchanged; terms counted by two CTAs are harmless for a max).
+// Thread t owns outputs m0 + 7t .. m0 + 7t + 6: 7 is coprime with the 32
+// banks, so the threads of a warp read their y windows without conflicts,
+// and the warp walks one common range of i, so x is read by broadcast.
+// Several i-blocks combine by atomicMax on the float bits (non-negative
+// floats order like their bit patterns; z is zeroed first).
 __global__ void __launch_bounds__(MCX_THREADS)
     k_maxconv_exact(const __grid_constant__ MaxconvArgs ma) {
   extern __shared__ __align__(16) float sm[];
   const int m0 = blockIdx.x * MCX_SPAN;
-  const int ypad = MCX_SPAN + 8;
-  float* xs = sm;                        // nx (+8 slack)
-  float* ys = sm + ma.nx + 8 + ypad;     // ys[t] = y_t, valid for t in [-ypad, ny + ypad)
-  for (int64_t b = blockIdx.y; b < ma.batch; b += gridDim.y) {
+  const int i0 = blockIdx.y * MCX_IB;
+  const int warp = threadIdx.x >> 5;
+  float* xs = sm;                        // MCX_IB + 8 values: x[i0 + k]
+  float* ys = sm + MCX_IB + 8;           // MCX_SPAN + MCX_IB + 16 values: y[tb + u]
+  const int tb = m0 - i0 - MCX_IB - 8;   // y index of ys[0]
+  const bool atomic = gridDim.y > 1;
+  // terms of this CTA: i in [max(i0, m0 - ny + 1), min(i0 + IB, m0 + SPAN, nx))
+  const int c_lo = max(i0, m0 - ma.ny + 1);
+  const int c_hi = min(min(i0 + MCX_IB, m0 + MCX_SPAN), ma.nx);
+  if (c_lo >= c_hi || m0 >= ma.nz) return;
+  // the warp's outputs and terms
+  const int mw = m0 + warp * 32 * MCX_OUT;
+  const int w_lo = max(c_lo, mw - ma.ny + 1);
+  const int w_hi = min(c_hi, mw + 32 * MCX_OUT);
+  const int mt = m0 + threadIdx.x * MCX_OUT;
+  for (int64_t b = blockIdx.z; b < ma.batch; b += gridDim.z) {
     __syncthreads();  // the previous problem's reads are done
-    const float* x = ma.x + (int64_t)b * ma.ldx;
-    const float* y = ma.y + (int64_t)b * ma.ldy;
-    for (int k = threadIdx.x; k < ma.nx + 8; k += MCX_THREADS) xs[k] = k < ma.nx ? x[k] : 0.0f;
-    for (int t = threadIdx.x - ypad; t < ma.ny + ypad; t += MCX_THREADS)
-      ys[t] = (t >= 0 && t < ma.ny) ? y[t] : 0.0f;
+    const float* x = ma.x + b * ma.ldx;
+    const float* y = ma.y + b * ma.ldy;
+    for (int k = threadIdx.x; k < MCX_IB + 8; k += MCX_THREADS)
+      xs[k] = (i0 + k < ma.nx) ? x[i0 + k] : 0.0f;
+    for (int u = threadIdx.x; u < MCX_SPAN + MCX_IB + 16; u += MCX_THREADS) {
+      const int t = tb + u;
+      ys[u] = (t >= 0 && t < ma.ny) ? y[t] : 0.0f;
+    }
     __syncthreads();
-    const int mt = m0 + threadIdx.x * MCX_OUT;  // this thread's first output
     float acc[MCX_OUT];
 #pragma unroll
     for (int r = 0; r < MCX_OUT; ++r) acc[r] = 0.0f;
-    // valid i for some output of the thread: mt - ny + 1 <= i <= mt + 7, 0 <= i < nx
-    int ilo = mt - ma.ny + 1;
-    ilo = ilo < 0 ? 0 : ilo;
-    ilo &= ~1;
-    int ihi = mt + MCX_OUT - 1;
-    ihi = ihi > ma.nx - 1 ? ma.nx - 1 : ihi;
-    if (mt < ma.nz) {
 #pragma unroll 1
-      for (int i = ilo; i <= ihi; i += 8) {
-        float xv[8], yv[MCX_OUT + 8];
+    for (int i = w_lo; i < w_hi; i += 8) {
+      const int k = i - i0;
+      float xv[8], yv[MCX_OUT + 7];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) xv[e] = xs[i + e];  // zero past nx
-        // yv[u] = y_(mt - i - 7 + u), u in [0, 15)
+      for (int e = 0; e < 8; ++e) xv[e] = xs[k + e];
+      // yv[u] = y_(mt - i - 7 + u), i.e. ys[(mt - i - 7 + u) - tb]
+      const float* yp = ys + (mt - i - 7 - tb);
 #pragma unroll
-        for (int u = 0; u < MCX_OUT + 7; ++u) yv[u] = ys[mt - i - 7 + u];
+      for (int u = 0; u < MCX_OUT + 7; ++u) yv[u] = yp[u];
 #pragma unroll
-        for (int r = 0; r < MCX_OUT; ++r) {
+      for (int r = 0; r < MCX_OUT; ++r) {
 #pragma unroll
-          for (int e = 0; e < 8; e += 2) {
-            // terms i+e and i+e+1 of output mt + r: y index mt + r - i - e (- 1)
-            const float p0 = xv[e] * yv[r - e + 7];
-            const float p1 = xv[e + 1] * yv[r - e + 6];
-            float t;
-            asm("max.f32 %0, %1, %2, %3;" : "=f"(t) : "f"(acc[r]), "f"(p0), "f"(p1));
-            acc[r] = t;
-          }
+        for (int e = 0; e < 8; e += 2) {
+          // terms i+e and i+e+1 of output mt + r
+          const float p0 = xv[e] * yv[r - e + 7];
+          const float p1 = xv[e + 1] * yv[r - e + 6];
+          float t;
+          asm("max.f32 %0, %1, %2, %3;" : "=f"(t) : "f"(acc[r]), "f"(p0), "f"(p1));
+          acc[r] = t;
         }
       }
     }
-    float* z = ma.z + (int64_t)b * ma.ldz;
+    float* z = ma.z + b * ma.ldz;
 #pragma unroll
-    for (int r = 0; r < MCX_OUT; ++r)
-      if (mt + r < ma.nz) z[mt + r] = acc[r];
+    for (int r = 0; r < MCX_OUT; ++r) {
+      const int m = mt + r;
+      if (m >= ma.nz) continue;
+      if (atomic) {
+        if (acc[r] > 0.0f) atomicMax(reinterpret_cast<unsigned int*>(z + m), __float_as_uint(acc[r]));
+      } else {
+        z[m] = acc[r];
+      }
+    }
   }
 }
 
@@ -386,18 +448,26 @@ int launch_maxconv_fft(const MaxconvArgs& ma, void* stream) {
   return cudaGetLastError();
 }
 
-int maxconv_exact_smem_bytes(int nx, int ny) {
-  return static_cast<int>(sizeof(float)) * (nx + 8 + 2 * (MCX_SPAN + 8) + ny);
+int maxconv_exact_smem_bytes() {
+  return static_cast<int>(sizeof(float)) * (MCX_IB + 8 + MCX_SPAN + MCX_IB + 16);
 }
 
 int launch_maxconv_exact(const MaxconvArgs& ma, void* stream) {
-  const int smem = maxconv_exact_smem_bytes(ma.nx, ma.ny);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int smem = maxconv_exact_smem_bytes();
   const cudaError_t e = cudaFuncSetAttribute(k_maxconv_exact,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
+  const int iblocks = (ma.nx + MCX_IB - 1) / MCX_IB;
+  if (iblocks > 1) {  // partial maxima meet in z by atomicMax: start from 0
+    const cudaError_t me = cudaMemset2DAsync(ma.z, sizeof(float) * ma.ldz, 0,
+                                             sizeof(float) * ma.nz, ma.batch, s);
+    if (me != cudaSuccess) return me;
+  }
   const dim3 grid(static_cast<unsigned>((ma.nz + MCX_SPAN - 1) / MCX_SPAN),
+                  static_cast<unsigned>(iblocks),
                   static_cast<unsigned>(ma.batch < 65535 ? ma.batch : 65535));
-  k_maxconv_exact<<<grid, MCX_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(ma);
+  k_maxconv_exact<<<grid, MCX_THREADS, smem, s>>>(ma);
   return cudaGetLastError();
 }
 
@@ -442,7 +512,7 @@ pn_status maxconv_exact(int64_t batch, int64_t nx, const float* x, int64_t ldx, 
                         const float* y, int64_t ldy, float* z, int64_t ldz, void* stream) {
   if (batch < 0 || nx < 1 || ny < 1) return PN_EINVAL;
   if (batch == 0) return PN_OK;
-  if (nx + ny > 50000) return PN_EUNSUPPORTED;
+  if (nx + ny > (int64_t(1) << 30)) return PN_EUNSUPPORTED;
   const int64_t nz = nx + ny - 1;
   if (!x || !y || !z || ldx < nx || ldy < ny || ldz < nz) return PN_EINVAL;
   if (host_device_sms() <= 0) return PN_EUNSUPPORTED;

@@ -127,7 +127,7 @@ def test_argument_validation_before_any_device_call(binding):
     assert lib.maxconv_pnorm(2, 4, 16, 4, 4, 16, 4, 16, 7, z, 0, ctypes.byref(proj), z) == 7
     assert lib.maxconv_pnorm(2, 4, 16, 3, 4, 16, 4, 16, 7, z, 0, ctypes.byref(o), z) == 1
     assert lib.maxconv_exact(2, 4, 16, 4, 0, 16, 4, 16, 7, z) == 1
-    assert lib.maxconv_exact(1, 30000, 16, 30000, 30000, 16, 30000, 16, 59999, z) == 7
+    assert lib.maxconv_exact(1, 1 << 30, 16, 1 << 30, 1, 16, 1, 16, 1 << 30, z) == 7
     assert lib.pn_maxconv_default_tau() == 1e-12
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0

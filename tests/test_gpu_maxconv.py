@@ -50,7 +50,7 @@ def _pair(batch, nx, ny, seed, kind="wide"):
 
 
 EXACT_SHAPES = [(3, 1, 1), (2, 5, 3), (4, 300, 200), (2, 2500, 3000), (1, 1, 4000),
-                (3, 4096, 4096)]
+                (3, 4096, 4096), (2, 9000, 9000), (1, 20000, 300), (1, 300, 20000)]
 
 
 @pytest.mark.parametrize("shape", EXACT_SHAPES)
