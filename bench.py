@@ -59,7 +59,7 @@ def parse_args():
                     help="1: divide by K^(1/p*); 2: affine model fitted on --n-fit exact samples")
     ap.add_argument("--n-fit", type=int, default=1024)
     ap.add_argument("--workload", default="pnorm",
-                    choices=["pnorm", "apsp", "backward", "grouped", "maxconv"],
+                    choices=["pnorm", "apsp", "backward", "grouped", "maxconv", "maxconv-long"],
                     help="pnorm: the default product; the others measure the other paths")
     return ap.parse_args()
 
@@ -501,7 +501,58 @@ def run_other(args):
             "unit": "Gop/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic"}
-    if args.workload == "maxconv":
+    if args.workload == "maxconv-long":
+        # one long max-convolution (Sec. 1): n = 2^21 per vector, 2^22 - 1
+        # outputs, four-step FP64 FFT through a workspace
+        n = 1 << 21
+        g = workloads.rng(None, 6)
+        xh = ((1.0 - g.random(n)) ** 0.25).astype(np.float32)
+        yh = ((1.0 - g.random(n)) ** 0.25).astype(np.float32)
+        x, y = torch.from_numpy(xh).cuda(), torch.from_numpy(yh).cuda()
+        nz = 2 * n - 1
+        z = torch.empty((1, nz), dtype=torch.float32, device="cuda")
+        ze = torch.empty_like(z)
+        res = {}
+
+        def fwd():
+            res["psel"] = pn.maxconv_pnorm(x, y, out=z, check=False)[1]
+        ms = _timed(torch, fwd, K, args.warmup, stream)
+        pn.check_device_status(x.device, "maxconv_pnorm_long")
+        ems = _timed(torch, lambda: pn.maxconv_exact(x, y, out=ze), 1, 1, stream)
+        ops = float(n) * n
+        psel = res["psel"].cpu().numpy()[0]
+        zz, zex = z.cpu().numpy()[0], ze.cpu().numpy()[0]
+        rel = np.abs(zz - zex) / zex
+        # FP64 work: per FFT level two transforms of N = 2^22 (5 N log2 N
+        # flops each) plus the inter-step twiddles and the spectrum (~40 N)
+        N, logN = 1 << 22, 22
+        mm = np.arange(nz)
+        L = np.minimum(mm, n - 1) - np.maximum(0, mm - n + 1) + 1
+        lp = (psel & 0x7F).astype(np.int64)
+        P = list(range(7))
+        levels = 0
+        for q in range(len(P) - 1, -1, -1):
+            levels += 1
+            W = int(L[lp < P[q]].sum())
+            if W == 0 or q == 0 or W * (8 + 2 * q) <= 10 * N * logN:
+                break
+        flops = levels * (10.0 * N * logN + 40.0 * N)
+        line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f64 (FFT)",
+                    config={"workload": f"maxconv_pnorm (long) n={n} per vector ({nz} outputs), "
+                            "entries exp(-Exp(4)), P={1..64}, tau=1e-12, four-step FP64 FFT",
+                            "n": n},
+                    exact_kernel={"ms": ems, "gops": ops / (ems / 1e3) / 1e9,
+                                  "speedup_of_pnorm": ems / ms},
+                    err={"outputs": int(rel.size), "max_rel_vs_exact": float(rel.max()),
+                         "median_rel_vs_exact": float(np.median(rel)),
+                         "p_sel_histogram": {str(2 ** int(k)): int(v) for k, v in
+                                             zip(*np.unique(lp, return_counts=True))}},
+                    roofline={"bound": "fp64", "achieved": flops / (ms / 1e3) / 1e12,
+                              "peak": 1.25, "unit": "TFLOP/s",
+                              "frac": flops / (ms / 1e3) / 1e12 / 1.25, "traffic": None,
+                              "fft_levels": levels,
+                              "peak_source": "nominal FP64 rate of the profiling recipe"})
+    elif args.workload == "maxconv":
         # batch of max-convolutions (Sec. 1), H = FP64 FFT, one CTA per problem
         batch, n = args.count if args.count != 4096 else 1024, 4096
         g = workloads.rng(None, 5)

@@ -256,6 +256,24 @@ PN_API pn_status maxconv_pnorm(int64_t batch, int64_t nx, const float* x, int64_
                                int64_t ny, const float* y, int64_t ldy, float* z, int64_t ldz,
                                uint8_t* p_sel, int64_t ldp, const pn_opts* opts, void* stream);
 
+/* One long max-convolution (nx + ny - 1 up to 2^22), the same estimate with
+ * a four-step FFT through a caller-provided workspace: three kernels per p
+ * level (column FFTs with the powered inputs formed on the fly, row pairs with
+ * the spectrum product, inverse columns with the selection) and a fourth that
+ * ends the call when nothing is open or sums the few open terms of the
+ * remaining levels directly.  x, y, z (nx + ny - 1 floats) and p_sel
+ * (optional) are device arrays; ws is device memory of at least
+ * pn_maxconv_long_workspace_size(nx, ny, p_sel != NULL) bytes, 256-byte
+ * aligned, owned by the caller (PN_EWORKSPACE / PN_EALIGN otherwise); opts as
+ * for maxconv_pnorm.  nx + ny - 1 > 2^22: PN_EUNSUPPORTED. */
+PN_API pn_status maxconv_pnorm_long(int64_t nx, const float* x, int64_t ny, const float* y,
+                                    float* z, uint8_t* p_sel, const pn_opts* opts, void* ws,
+                                    size_t ws_bytes, void* stream);
+
+/* Workspace bytes of maxconv_pnorm_long (0 if the sizes are out of range);
+ * with_p_sel = 0 adds room for an internal p_sel. */
+PN_API size_t pn_maxconv_long_workspace_size(int64_t nx, int64_t ny, int32_t with_p_sel);
+
 /* The paper's threshold for a double-precision FFT convolution of vectors
  * in [0, 1], 1e-12 (Sec. 2.1). */
 PN_API double pn_maxconv_default_tau(void);

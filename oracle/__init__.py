@@ -84,6 +84,7 @@ def _load():
                                          vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm_ex.restype = ci
             lib.orc_maxconv.argtypes = [i64, i64, vp, i64, vp, vp]
+            lib.orc_maxconv_entries.argtypes = [i64, vp, i64, vp, ci, vp, i64, vp, vp, vp]
             lib.orc_conv.argtypes = [i64, i64, vp, i64, vp, vp]
             lib.orc_maxconv_pnorm.argtypes = [i64, i64, vp, i64, vp, ci, vp, dbl, vp, vp, vp]
             lib.orc_affine_fit.argtypes = [i64, vp, vp, vp, ci, vp]
@@ -432,3 +433,15 @@ def maxconv_pnorm(x, y, p_log2, tau: float, want_S: bool = False):
     if want_S:
         out["S"] = S
     return out
+
+
+def maxconv_entries(x, y, m, p_log2):
+    """Exact max and every p-sum at the outputs m of one max-convolution."""
+    x, y = _f64(x).ravel(), _f64(y).ravel()
+    m = np.ascontiguousarray(m, dtype=np.int64)
+    pl = _plog(p_log2)
+    ex = np.empty(len(m), dtype=np.float64)
+    S = np.empty((len(m), len(pl)), dtype=np.float64)
+    _load().orc_maxconv_entries(len(x), _p(x), len(y), _p(y), len(pl), _p(pl), len(m), _p(m),
+                                _p(ex), _p(S))
+    return ex, S

@@ -711,3 +711,40 @@ void orc_maxconv_pnorm(int64_t batch, int64_t nx, const double* x, int64_t ny, c
     }
   }
 }
+
+/* Selected outputs m[e] of one max-convolution: the exact max and every    */
+/* p-sum S^(p)_m of the max-scaled vectors (as in orc_maxconv_pnorm), with   */
+/* pow per term; S[e * n_p + q].  Cost O(n_e * min(nx, ny) * n_p).           */
+void orc_maxconv_entries(int64_t nx, const double* x, int64_t ny, const double* y, int n_p,
+                         const int* p_log2, int64_t n_e, const int64_t* m, double* exact,
+                         double* S) {
+  double mx = 0.0, my = 0.0;
+  for (int64_t i = 0; i < nx; ++i)
+    if (x[i] > mx) mx = x[i];
+  for (int64_t i = 0; i < ny; ++i)
+    if (y[i] > my) my = y[i];
+  double sx = mx > 0.0 ? mx : 1.0, sy = my > 0.0 ? my : 1.0;
+  int64_t e;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (e = 0; e < n_e; ++e) {
+    int64_t mm = m[e];
+    double best = 0.0;
+    for (int64_t i = 0; i < nx; ++i) {
+      int64_t t = mm - i;
+      if (t < 0 || t >= ny) continue;
+      double v = x[i] * y[t];
+      if (v > best) best = v;
+    }
+    if (exact) exact[e] = best;
+    for (int q = 0; q < n_p; ++q) {
+      double p = ldexp(1.0, p_log2[q]);
+      double s = 0.0;
+      for (int64_t i = 0; i < nx; ++i) {
+        int64_t t = mm - i;
+        if (t < 0 || t >= ny) continue;
+        s += pow(x[i] / sx, p) * pow(y[t] / sy, p);
+      }
+      S[e * n_p + q] = s;
+    }
+  }
+}

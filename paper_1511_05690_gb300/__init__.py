@@ -265,7 +265,9 @@ def maxconv_pnorm(x: torch.Tensor, y: torch.Tensor, *, p_log2=tuple(range(7)), t
                   out=None, want_psel=True, check=True, stream=None):
     """p-norm estimate of the batched max-convolution z_m = max_i x_i y_(m-i)
     with H = FP64 FFT convolution (Sec. 1).  x: (batch, nx), y: (batch, ny)
-    (or 1-D).  Returns (z, p_sel or None), z of shape (batch, nx + ny - 1)."""
+    (or 1-D).  Returns (z, p_sel or None), z of shape (batch, nx + ny - 1).
+    Up to nx + ny - 1 = 8192 one CTA per problem (maxconv_pnorm); longer
+    problems, up to 2^22, one call of maxconv_pnorm_long per row."""
     x, y = _rows(x, "x"), _rows(y, "y")
     if x.shape[0] != y.shape[0]:
         raise ValueError("x and y differ in batch")
@@ -277,10 +279,23 @@ def maxconv_pnorm(x: torch.Tensor, y: torch.Tensor, *, p_log2=tuple(range(7)), t
     psel = torch.empty((batch, nz), dtype=torch.uint8, device=dev) if want_psel else None
     st = status_word(dev)
     o = make_opts(p_log2, "f32", tau, 2, 0, 0, st.data_ptr())
-    rc = lib().maxconv_pnorm(batch, nx, x.data_ptr(), _ld(x), ny, y.data_ptr(), _ld(y),
+    L = lib()
+    if nz <= 8192:
+        rc = L.maxconv_pnorm(batch, nx, x.data_ptr(), _ld(x), ny, y.data_ptr(), _ld(y),
                              z.data_ptr(), _ld(z), psel.data_ptr() if psel is not None else None,
                              nz, ctypes.byref(o), _stream_ptr(stream))
-    _b.check(rc, "maxconv_pnorm")
+        _b.check(rc, "maxconv_pnorm")
+    else:
+        need = L.pn_maxconv_long_workspace_size(nx, ny, 1 if psel is not None else 0)
+        if need == 0:
+            raise PnError(_b.PN_EUNSUPPORTED, "maxconv_pnorm_long")
+        ws = workspace(need, dev)
+        for b in range(batch):
+            rc = L.maxconv_pnorm_long(nx, x[b].data_ptr(), ny, y[b].data_ptr(), z[b].data_ptr(),
+                                      psel[b].data_ptr() if psel is not None else None,
+                                      ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                      _stream_ptr(stream))
+            _b.check(rc, "maxconv_pnorm_long")
     if check:
         check_device_status(dev, "maxconv_pnorm")
     return z, psel

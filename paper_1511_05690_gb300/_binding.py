@@ -28,7 +28,8 @@ EXPORTS = (
     "pn_apsp_workspace_size", "apsp_pnorm", "pn_backward_workspace_size",
     "maxprod_pnorm_backward", "pn_grouped_table_bytes", "pn_grouped_build_table",
     "maxprod_pnorm_grouped", "maxprod_pnorm_static", "pn_autotune", "pn_grouped_autotune",
-    "maxconv_pnorm", "maxconv_exact", "pn_maxconv_default_tau",
+    "maxconv_pnorm", "maxconv_exact", "pn_maxconv_default_tau", "maxconv_pnorm_long",
+    "pn_maxconv_long_workspace_size",
 )
 
 
@@ -104,6 +105,10 @@ def load():
         lib.maxconv_pnorm.restype = i32
         lib.maxconv_exact.argtypes = [i64, i64, vp, i64, i64, vp, i64, vp, i64, vp]
         lib.maxconv_exact.restype = i32
+        lib.maxconv_pnorm_long.argtypes = [i64, vp, i64, vp, vp, vp, optp, vp, ctypes.c_size_t, vp]
+        lib.maxconv_pnorm_long.restype = i32
+        lib.pn_maxconv_long_workspace_size.argtypes = [i64, i64, i32]
+        lib.pn_maxconv_long_workspace_size.restype = ctypes.c_size_t
         lib.pn_maxconv_default_tau.argtypes = []
         lib.pn_maxconv_default_tau.restype = ctypes.c_double
         lib.pn_apsp_workspace_size.argtypes = [i64, optp]

@@ -164,6 +164,28 @@ __device__ void direct_levels(const MaxconvArgs& ma, const float* x, const float
   res[m] = static_cast<uint8_t>(ma.p_log2[qs] | (stable ? 0 : 0x80));
 }
 
+// In-place radix-2 decimation-in-frequency FFT of a[0..L) in natural order;
+// bit-reversed order on return; unscaled; INV: conjugate twiddles.
+template <bool INV>
+__device__ void fft_dif(double2* a, const double2* tw, int logL, int tws) {
+  const int L = 1 << logL;
+  for (int s = logL - 1; s >= 0; --s) {
+    const int h = 1 << s;
+    const int step = ((L >> 1) >> s) * tws;
+    for (int b = threadIdx.x; b < (L >> 1); b += FFT_THREADS) {
+      const int j = b & (h - 1);
+      const int i0 = ((b >> s) << (s + 1)) + j;
+      const int i1 = i0 + h;
+      const double2 u = a[i0], v = a[i1];
+      const double2 d = make_double2(u.x - v.x, u.y - v.y);
+      a[i0] = make_double2(u.x + v.x, u.y + v.y);
+      const double2 w = tw[j * step];
+      a[i1] = INV ? cmulc(w, d) : cmul(w, d);
+    }
+    __syncthreads();
+  }
+}
+
 // Z_k from A_k and A_(N-k) (the spectra of the packed real pair).
 __device__ __forceinline__ double2 spec_z(double2 ak, double2 an) {
   const double2 X = make_double2(0.5 * (ak.x + an.x), 0.5 * (ak.y - an.y));
@@ -417,6 +439,250 @@ __global__ void __launch_bounds__(MCX_THREADS)
   }
 }
 
+// ------------------------------------------------------- long problems ---
+// One max-convolution of any length up to N = 2^22 (nz = nx + ny - 1 <= N),
+// four-step FFT over the N1 x N2 view of the length-N buffer (index
+// n = N2 n1 + n2, N1 = 2^min(10, floor(log2 N / 2))):
+//   forward  A[k1 + N1 k2] = sum_n2 W_N2^(n2 k2) [W_N^(n2 k1) sum_n1 a[n] W_N1^(n1 k1)]
+//   inverse  s[n] = sum_k1 W_N1^-(n1 k1) [W_N^-(n2 k1) sum_k2 Z[k1 + N1 k2] W_N2^-(n2 k2)]
+// Three kernels per level: columns forward (the powered inputs are formed on
+// the fly), row pairs (forward rows, spectrum, inverse rows: row k1 holds the
+// partners N - k of row N1 - k1), columns inverse with the selection.  A
+// fourth kernel ends the level loop (nothing open) or sums the remaining
+// levels directly for few open terms.  All kernels of a finished call return
+// at once (device flag), so every launch is issued unconditionally.
+constexpr int LONG_CC = 8;   // columns per CTA of the column kernels
+
+struct LongArgs {
+  const float* x;
+  const float* y;
+  float* z;
+  uint8_t* res;            // p_sel, 0xFF while open
+  int32_t nx, ny, nz;
+  int32_t logN, l1, l2;    // N = 2^logN = N1 N2
+  int32_t n_p;
+  int32_t p_log2[PN_MAX_P];
+  double tau;
+  int32_t* status;
+  double2* buf;            // N complex
+  const double2* tlo;      // W_N^m, m < 2048
+  const double2* thi;      // W_N^(2048 m), m < N / 2048
+  unsigned long long* open_terms;  // per level
+  int32_t* done;
+  uint32_t* mxy;           // max x, max y (float bits)
+};
+
+__device__ __forceinline__ double2 w_n(const LongArgs& la, int m) {
+  return cmul(la.thi[m >> 11], la.tlo[m & 2047]);
+}
+
+__global__ void k_long_tables(double2* tlo, double2* thi, int logN) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double N = static_cast<double>(1 << logN);
+  double s, c;
+  if (k < 2048) {
+    sincospi(-2.0 * k / N, &s, &c);
+    tlo[k] = make_double2(c, s);
+  }
+  if (k < ((1 << logN) >> 11)) {
+    sincospi(-2.0 * (2048.0 * k) / N, &s, &c);
+    thi[k] = make_double2(c, s);
+  }
+}
+
+__global__ void k_long_max(const __grid_constant__ LongArgs la) {
+  float mx = 0.0f, my = 0.0f;
+  bool bad = false;
+  const int stride = gridDim.x * blockDim.x;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < la.nx; k += stride) {
+    const float v = la.x[k];
+    bad |= !(v >= 0.0f && v <= 3.4028235e38f);
+    mx = fmaxf(mx, v);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < la.ny; k += stride) {
+    const float v = la.y[k];
+    bad |= !(v >= 0.0f && v <= 3.4028235e38f);
+    my = fmaxf(my, v);
+  }
+  if (bad) {
+    set_status(la.status, PN_EDOMAIN);
+    *la.done = 1;  // nothing more runs
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(la.mxy, __float_as_uint(mx));
+    atomicMax(la.mxy + 1, __float_as_uint(my));
+  }
+}
+
+__device__ __forceinline__ void long_scales(const LongArgs& la, double& sx, double& sy) {
+  sx = __uint_as_float(la.mxy[0]);
+  sy = __uint_as_float(la.mxy[1]);
+  if (sx == 0.0) sx = 1.0;
+  if (sy == 0.0) sy = 1.0;
+}
+
+// columns [c0, c0 + CC): a[N2 n1 + n2] = x'^p + i y'^p, DFT over n1 (length
+// N1), times W_N^(n2 k1), stored row-major as buf[k1 N2 + n2].
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+    k_long_col_fwd(const __grid_constant__ LongArgs la, int q) {
+  if (*la.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N1 = 1 << la.l1, N2 = 1 << la.l2;
+  double2* col = reinterpret_cast<double2*>(smem);   // [CC][N1]
+  double2* tw = col + LONG_CC * N1;                   // N1 / 2
+  const int tid = threadIdx.x;
+  for (int k = tid; k < (N1 >> 1); k += FFT_THREADS) tw[k] = g_twiddle[k << (FFT_LOG_NMAX - la.l1)];
+  double sx, sy;
+  long_scales(la, sx, sy);
+  const float isx = static_cast<float>(1.0 / sx), isy = static_cast<float>(1.0 / sy);
+  const int plog = la.p_log2[q];
+  const int c0 = blockIdx.x * LONG_CC;
+  for (int e = tid; e < LONG_CC * N1; e += FFT_THREADS) {
+    const int n1 = e / LONG_CC, c = e % LONG_CC;
+    const int n = n1 * N2 + c0 + c;
+    float xr = 0.0f, yr = 0.0f;
+    if (n < la.nx) {
+      xr = la.x[n] * isx;
+      for (int s = 0; s < plog; ++s) xr *= xr;
+    }
+    if (n < la.ny) {
+      yr = la.y[n] * isy;
+      for (int s = 0; s < plog; ++s) yr *= yr;
+    }
+    col[c * N1 + bitrev(n1, la.l1)] = make_double2(xr, yr);
+  }
+  __syncthreads();
+  for (int c = 0; c < LONG_CC; ++c) fft_dit<false>(col + c * N1, tw, la.l1, 1);
+  for (int e = tid; e < LONG_CC * N1; e += FFT_THREADS) {
+    const int k1 = e / LONG_CC, c = e % LONG_CC;
+    const int n2 = c0 + c;
+    la.buf[(int64_t)k1 * N2 + n2] = cmul(w_n(la, n2 * k1), col[c * N1 + k1]);
+  }
+}
+
+// Z from a spectrum value and its partner (the packed real pair).
+__device__ __forceinline__ void pair_z(double2& a, double2& b) {
+  const double2 za = spec_z(a, b), zb = spec_z(b, a);
+  a = za;
+  b = zb;
+}
+
+// rows k1 and N1 - k1 (blockIdx.x = k1 in [0, N1/2]; rows 0 and N1/2 alone)
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+    k_long_rows(const __grid_constant__ LongArgs la) {
+  if (*la.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N1 = 1 << la.l1, N2 = 1 << la.l2;
+  double2* r0 = reinterpret_cast<double2*>(smem);  // row k1
+  double2* r1 = r0 + N2;                            // row N1 - k1
+  double2* tw = r1 + N2;                            // N2 / 2
+  const int tid = threadIdx.x;
+  const int k1 = blockIdx.x, k1b = N1 - k1;
+  const bool two = k1 != 0 && k1 != (N1 >> 1);
+  for (int k = tid; k < (N2 >> 1); k += FFT_THREADS) tw[k] = g_twiddle[k << (FFT_LOG_NMAX - la.l2)];
+  for (int k = tid; k < N2; k += FFT_THREADS) {
+    r0[bitrev(k, la.l2)] = la.buf[(int64_t)k1 * N2 + k];
+    if (two) r1[bitrev(k, la.l2)] = la.buf[(int64_t)k1b * N2 + k];
+  }
+  __syncthreads();
+  fft_dit<false>(r0, tw, la.l2, 1);
+  if (two) fft_dit<false>(r1, tw, la.l2, 1);
+  // spectrum in place: the partner of (k1, k2) is (N1 - k1, N2 - 1 - k2),
+  // of (0, k2) it is (0, (N2 - k2) mod N2)
+  if (two) {
+    for (int k2 = tid; k2 < N2; k2 += FFT_THREADS) pair_z(r0[k2], r1[N2 - 1 - k2]);
+  } else if (k1 == 0) {
+    for (int k2 = tid; k2 <= (N2 >> 1); k2 += FFT_THREADS) {
+      const int p2 = (N2 - k2) & (N2 - 1);
+      if (p2 == k2) r0[k2] = spec_z(r0[k2], r0[k2]);
+      else pair_z(r0[k2], r0[p2]);
+    }
+  } else {
+    for (int k2 = tid; k2 < (N2 >> 1); k2 += FFT_THREADS) pair_z(r0[k2], r0[N2 - 1 - k2]);
+  }
+  __syncthreads();
+  fft_dif<true>(r0, tw, la.l2, 1);
+  if (two) fft_dif<true>(r1, tw, la.l2, 1);
+  // bit-reversed rows; times conj W_N^(n2 k1)
+  for (int n2 = tid; n2 < N2; n2 += FFT_THREADS) {
+    la.buf[(int64_t)k1 * N2 + n2] = cmulc(w_n(la, n2 * k1), r0[bitrev(n2, la.l2)]);
+    if (two) la.buf[(int64_t)k1b * N2 + n2] = cmulc(w_n(la, n2 * k1b), r1[bitrev(n2, la.l2)]);
+  }
+}
+
+// columns [c0, c0 + CC): inverse DFT over k1 gives s[N2 n1 + n2]; the
+// selection of level q for every open index; open terms counted for the
+// direct-sum decision.
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+    k_long_col_inv(const __grid_constant__ LongArgs la, int q) {
+  if (*la.done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N1 = 1 << la.l1, N2 = 1 << la.l2;
+  double2* col = reinterpret_cast<double2*>(smem);
+  double2* tw = col + LONG_CC * N1;
+  const int tid = threadIdx.x;
+  for (int k = tid; k < (N1 >> 1); k += FFT_THREADS) tw[k] = g_twiddle[k << (FFT_LOG_NMAX - la.l1)];
+  const int c0 = blockIdx.x * LONG_CC;
+  for (int e = tid; e < LONG_CC * N1; e += FFT_THREADS) {
+    const int k1 = e / LONG_CC, c = e % LONG_CC;
+    col[c * N1 + bitrev(k1, la.l1)] = la.buf[(int64_t)k1 * N2 + c0 + c];
+  }
+  __syncthreads();
+  for (int c = 0; c < LONG_CC; ++c) fft_dit<true>(col + c * N1, tw, la.l1, 1);
+  double sx, sy;
+  long_scales(la, sx, sy);
+  const double sxy = sx * sy, invN = 1.0 / static_cast<double>(1 << la.logN);
+  const int plog = la.p_log2[q];
+  unsigned long long terms = 0ull;
+  for (int e = tid; e < LONG_CC * N1; e += FFT_THREADS) {
+    const int n1 = e / LONG_CC, c = e % LONG_CC;
+    const int m = n1 * N2 + c0 + c;
+    if (m >= la.nz || la.res[m] != 0xFF) continue;
+    const double S = col[c * N1 + n1].x * invN;
+    const bool stable = S >= la.tau;
+    if (stable || q == 0) {
+      la.z[m] = static_cast<float>(sxy * root_pow2(S, plog));
+      la.res[m] = static_cast<uint8_t>(plog | (stable ? 0 : 0x80));
+    } else {
+      terms += static_cast<unsigned long long>(terms_of(m, la.nx, la.ny));
+    }
+  }
+  if (terms) atomicAdd(la.open_terms + q, terms);
+}
+
+// After level q: nothing open ends the call; few open terms are summed
+// directly for every remaining level (then the call ends); otherwise the
+// next level runs.
+__global__ void k_long_direct(const __grid_constant__ LongArgs la, int q) {
+  if (*la.done) return;
+  const unsigned long long W = la.open_terms[q];
+  const int N = 1 << la.logN;
+  if (W == 0ull || q == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *la.done = 1;
+    return;
+  }
+  if (W * static_cast<unsigned long long>(8 + 2 * q) >
+      10ull * static_cast<unsigned long long>(N) * static_cast<unsigned long long>(la.logN))
+    return;
+  double sx, sy;
+  long_scales(la, sx, sy);
+  MaxconvArgs ma;
+  ma.nx = la.nx;
+  ma.ny = la.ny;
+  ma.tau = la.tau;
+  for (int t = 0; t < PN_MAX_P; ++t) ma.p_log2[t] = la.p_log2[t];
+  const double isx = static_cast<double>(static_cast<float>(1.0 / sx));
+  const double isy = static_cast<double>(static_cast<float>(1.0 / sy));
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < la.nz; m += gridDim.x * blockDim.x)
+    if (la.res[m] == 0xFF) direct_levels(ma, la.x, la.y, isx, isy, sx * sy, m, q, la.z, la.res);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *la.done = 1;  // read by the next launches only
+}
+
 std::mutex g_tw_mu;
 bool g_tw_ready[64];
 
@@ -427,19 +693,24 @@ int maxconv_fft_smem_bytes(int logN) {
   return N * 16 + (N / 2) * 16 + N;  // data, twiddles, p_sel of up to N indices
 }
 
-int launch_maxconv_fft(const MaxconvArgs& ma, void* stream) {
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+// The device's table of FFT twiddle factors, filled on the first use.
+int ensure_twiddles(cudaStream_t s) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  {
-    std::lock_guard<std::mutex> lk(g_tw_mu);
-    if (!g_tw_ready[dev]) {
-      k_twiddle_init<<<(FFT_NMAX / 2 + 255) / 256, 256, 0, s>>>();
-      const int e = cudaGetLastError();
-      if (e) return e;
-      g_tw_ready[dev] = true;
-    }
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  if (!g_tw_ready[dev]) {
+    k_twiddle_init<<<(FFT_NMAX / 2 + 255) / 256, 256, 0, s>>>();
+    const int e = cudaGetLastError();
+    if (e) return e;
+    g_tw_ready[dev] = true;
   }
+  return 0;
+}
+
+int launch_maxconv_fft(const MaxconvArgs& ma, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int te = ensure_twiddles(s);
+  if (te) return te;
   const int smem = maxconv_fft_smem_bytes(ma.logN);
   const cudaError_t e = cudaFuncSetAttribute(k_maxconv_fft,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -471,11 +742,109 @@ int launch_maxconv_exact(const MaxconvArgs& ma, void* stream) {
   return cudaGetLastError();
 }
 
+// Workspace of a long problem: control words, the W_N^m tables, the
+// complex buffer of N, and p_sel when the caller passes none.
+struct LongLayout {
+  size_t off_ctrl = 0, off_tlo = 0, off_thi = 0, off_buf = 0, off_res = 0, total = 0;
+};
+
+LongLayout long_layout(int64_t nz, int logN, bool own_res) {
+  LongLayout L;
+  size_t off = 0;
+  L.off_ctrl = off; off += 256;  // open_terms[16] (128 B), done, max x, max y
+  L.off_tlo = off; off += 2048 * sizeof(double2);
+  L.off_thi = off; off += 2048 * sizeof(double2);
+  L.off_buf = off; off += (size_t(1) << logN) * sizeof(double2);
+  if (own_res) { L.off_res = off; off += (static_cast<size_t>(nz) + 255) & ~size_t(255); }
+  L.total = off;
+  return L;
+}
+
+int long_logN(int64_t nz) {
+  int logN = 1;
+  while ((int64_t(1) << logN) < nz) ++logN;
+  return logN < 14 ? 14 : logN;
+}
+
+int launch_maxconv_long(const pn_opts* o, int64_t nx, const float* x, int64_t ny, const float* y,
+                        float* z, uint8_t* p_sel, uint8_t* ws, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int e = ensure_twiddles(s);
+  if (e) return e;
+  const int64_t nz = nx + ny - 1;
+  LongArgs la;
+  std::memset(&la, 0, sizeof(la));
+  la.logN = long_logN(nz);
+  la.l1 = la.logN / 2 < 10 ? la.logN / 2 : 10;
+  la.l2 = la.logN - la.l1;
+  const LongLayout L = long_layout(nz, la.logN, p_sel == nullptr);
+  la.x = x; la.y = y; la.z = z;
+  la.res = p_sel ? p_sel : ws + L.off_res;
+  la.nx = static_cast<int32_t>(nx);
+  la.ny = static_cast<int32_t>(ny);
+  la.nz = static_cast<int32_t>(nz);
+  la.n_p = o->n_p;
+  for (int q = 0; q < o->n_p; ++q) la.p_log2[q] = o->p_log2[q];
+  la.tau = o->tau > 0.0 ? o->tau : 1e-12;
+  la.status = o->dev_status;
+  la.buf = reinterpret_cast<double2*>(ws + L.off_buf);
+  la.tlo = reinterpret_cast<const double2*>(ws + L.off_tlo);
+  la.thi = reinterpret_cast<const double2*>(ws + L.off_thi);
+  la.open_terms = reinterpret_cast<unsigned long long*>(ws + L.off_ctrl);
+  la.done = reinterpret_cast<int32_t*>(ws + L.off_ctrl + 128);
+  la.mxy = reinterpret_cast<uint32_t*>(ws + L.off_ctrl + 136);
+  if ((e = cudaMemsetAsync(ws + L.off_ctrl, 0, 256, s))) return e;
+  if ((e = cudaMemsetAsync(la.res, 0xFF, static_cast<size_t>(nz), s))) return e;
+  k_long_tables<<<8, 256, 0, s>>>(reinterpret_cast<double2*>(ws + L.off_tlo),
+                                  reinterpret_cast<double2*>(ws + L.off_thi), la.logN);
+  k_long_max<<<152 * 4, 256, 0, s>>>(la);
+  const int N1 = 1 << la.l1, N2 = 1 << la.l2;
+  const int smem_col = (LONG_CC * N1 + N1 / 2) * static_cast<int>(sizeof(double2));
+  const int smem_row = (2 * N2 + N2 / 2) * static_cast<int>(sizeof(double2));
+  if ((e = cudaFuncSetAttribute(k_long_col_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_col)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_long_col_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_col)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_long_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_row)))
+    return e;
+  for (int q = o->n_p - 1; q >= 0; --q) {
+    k_long_col_fwd<<<N2 / LONG_CC, FFT_THREADS, smem_col, s>>>(la, q);
+    k_long_rows<<<N1 / 2 + 1, FFT_THREADS, smem_row, s>>>(la);
+    k_long_col_inv<<<N2 / LONG_CC, FFT_THREADS, smem_col, s>>>(la, q);
+    k_long_direct<<<152 * 4, 256, 0, s>>>(la, q);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace pn
 
 using namespace pn;
 
 extern "C" {
+
+size_t pn_maxconv_long_workspace_size(int64_t nx, int64_t ny, int32_t with_p_sel) {
+  if (nx < 1 || ny < 1 || nx + ny - 1 > (int64_t(1) << 22)) return 0;
+  const int64_t nz = nx + ny - 1;
+  return long_layout(nz, long_logN(nz), with_p_sel == 0).total;
+}
+
+pn_status maxconv_pnorm_long(int64_t nx, const float* x, int64_t ny, const float* y, float* z,
+                             uint8_t* p_sel, const pn_opts* opts, void* ws, size_t ws_bytes,
+                             void* stream) {
+  if (!host_opts_valid(opts)) return PN_EINVAL;
+  if (opts->estimator != 0 || opts->correction != 0) return PN_EUNSUPPORTED;
+  if (nx < 1 || ny < 1) return PN_EINVAL;
+  if (nx + ny - 1 > (int64_t(1) << 22)) return PN_EUNSUPPORTED;
+  if (!x || !y || !z) return PN_EINVAL;
+  const size_t need = pn_maxconv_long_workspace_size(nx, ny, p_sel != nullptr);
+  if (!ws || ws_bytes < need) return PN_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return PN_EALIGN;
+  if (host_device_sms() <= 0) return PN_EUNSUPPORTED;
+  return launch_maxconv_long(opts, nx, x, ny, y, z, p_sel, static_cast<uint8_t*>(ws), stream) == 0
+             ? PN_OK
+             : PN_ECUDA;
+}
+
 
 double pn_maxconv_default_tau(void) { return 1e-12; }
 

@@ -129,6 +129,14 @@ def test_argument_validation_before_any_device_call(binding):
     assert lib.maxconv_exact(2, 4, 16, 4, 0, 16, 4, 16, 7, z) == 1
     assert lib.maxconv_exact(1, 1 << 30, 16, 1 << 30, 1, 16, 1, 16, 1 << 30, z) == 7
     assert lib.pn_maxconv_default_tau() == 1e-12
+    # long max-convolution: workspace size and checks before any device call
+    w1 = lib.pn_maxconv_long_workspace_size(6000, 5000, 1)
+    w0 = lib.pn_maxconv_long_workspace_size(6000, 5000, 0)
+    assert w1 >= 16384 * 16 and w0 >= w1 + 10999
+    assert lib.pn_maxconv_long_workspace_size(1 << 22, 2, 1) == 0
+    assert lib.maxconv_pnorm_long(6000, 16, 5000, 16, 16, z, ctypes.byref(o), 256, 100, z) == 3
+    assert lib.maxconv_pnorm_long(6000, 16, 5000, 16, 16, 16, ctypes.byref(o), 264, w1, z) == 2
+    assert lib.maxconv_pnorm_long(1 << 22, 16, 2, 16, 16, 16, ctypes.byref(o), 256, w1, z) == 7
     assert lib.pn_maxprod_exact_variant(4, 4, 4, z, 4, z, 4, z, 4, 0, -1, z) == 1
     assert lib.apsp_pnorm(0, z, 0, z, 0, 0, ctypes.byref(o), z, 0, z) == 0
     assert lib.apsp_pnorm(4, z, 4, z, 4, 0, ctypes.byref(o), z, 0, z) == 1

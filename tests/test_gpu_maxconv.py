@@ -153,8 +153,8 @@ def test_maxconv_pnorm_edge_cases(pn, orc):
     z, psel = pn.maxconv_pnorm(torch.zeros((2, 10), device="cuda"),
                                torch.rand((2, 7), device="cuda"))
     assert torch.all(z == 0) and torch.all(psel == 0x80)
-    with pytest.raises(pn.PnError) as ei:
-        pn.maxconv_pnorm(torch.ones((1, 5000), device="cuda"), torch.ones((1, 4000), device="cuda"))
+    with pytest.raises(pn.PnError) as ei:  # longer than the long path's 2^22 outputs
+        pn.maxconv_pnorm(torch.ones((1, 1 << 22), device="cuda"), torch.ones((1, 2), device="cuda"))
     assert ei.value.status == 7
     bad = torch.rand((2, 30), device="cuda")
     bad[1, 3] = -1.0
@@ -164,3 +164,72 @@ def test_maxconv_pnorm_edge_cases(pn, orc):
     # the context stays usable after a device-detected domain error
     x, y = _pair(1, 20, 20, 2150)
     _check_pnorm(pn, orc, x, y, list(range(7)))
+
+
+# ---------------------------------------------------------- long problems ---
+def _check_long(pn, orc, x, y, pl, m, tau=1e-12):
+    """GPU long path against the oracle at the outputs m (plus the FFT bound)."""
+    nx, ny = len(x), len(y)
+    nz = nx + ny - 1
+    N = 1 << max(14, math.ceil(math.log2(nz)))
+    z, psel = pn.maxconv_pnorm(_dev(x), _dev(y), p_log2=pl, tau=tau)
+    z, psel = z.cpu().numpy()[0], psel.cpu().numpy()[0]
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    sx, sy = x64.max(), y64.max()
+    ex, S = orc.maxconv_entries(x64, y64, m, pl)
+    E = np.array([_fft_err((x64 / sx) ** 2.0 ** lp, (y64 / sy) ** 2.0 ** lp, N) for lp in pl])
+    rel = np.array([2 * (2.0 ** lp - 1) * 2.0 ** -24 for lp in pl])
+    est, ps, _ = orc.estimate(S.T[:, None, :], pl, np.ones(1), np.full(len(m), sx * sy), tau)
+    near = np.any(np.abs(S.T - tau) <= E[:, None] + rel[:, None] * S.T, axis=0)
+    agree = psel[m] == ps[0]
+    assert np.all(agree | near), m[~(agree | near)][:5]
+    idx = {lp: q for q, lp in enumerate(pl)}
+    q = np.array([idx[int(v) & 0x7F] for v in psel[m]])
+    S_at = S[np.arange(len(m)), q]
+    p = 2.0 ** (psel[m] & 0x7F)
+    want = sx * sy * np.power(np.maximum(S_at, 0.0), 1.0 / p)
+    tol = 1.5 * ((1 + E[q] / np.maximum(S_at, 1e-300) + rel[q]) ** (1.0 / p) - 1) + 8 * 2.0 ** -24
+    err = np.abs(z[m] - want) / np.maximum(want, 1e-300)
+    ok = ((psel[m] & 0x80) == 0) & (want > 0)
+    assert np.all(err[ok] <= tol[ok]), float(err[ok].max())
+    assert np.all(z[m][ok] >= ex[ok] * (1 - tol[ok]))
+    return z, psel
+
+
+def _sample_outputs(nz, count, seed):
+    g = workloads.rng(seed)
+    edge = np.concatenate([np.arange(40), np.arange(nz - 40, nz)])
+    return np.unique(np.concatenate([edge, g.integers(0, nz, count)]))
+
+
+@pytest.mark.parametrize("nx,ny", [(6000, 5000), (40000, 30000), (9000, 1)])
+def test_maxconv_long_matches_oracle(pn, orc, nx, ny):
+    x, y = _pair(1, nx, ny, 2300 + nx)
+    m = _sample_outputs(nx + ny - 1, 300, 2301)
+    _check_long(pn, orc, x[0], y[0], list(range(7)), m)
+
+
+def test_maxconv_long_several_levels(pn, orc):
+    """Small floor and a few spikes: most indices resolve at small p, so the
+    open terms stay many and the FFT levels run down the family."""
+    g = workloads.rng(2310)
+    x = (1e-3 * (0.5 + 0.5 * g.random(12000))).astype(np.float32)
+    y = (1e-3 * (0.5 + 0.5 * g.random(9000))).astype(np.float32)
+    x[[100, 7000]] = 1.0
+    y[4000] = 1.0
+    m = _sample_outputs(20999, 400, 2311)
+    z, psel = _check_long(pn, orc, x, y, list(range(7)), m)
+    assert len(np.unique(psel & 0x7F)) >= 4
+
+
+def test_maxconv_long_batch_rows_and_exact(pn, orc):
+    """Two rows through the long path equal two single calls; the exact
+    kernel at this length is bit-identical to the oracle."""
+    x, y = _pair(2, 7000, 6000, 2320)
+    z, psel = pn.maxconv_pnorm(_dev(x), _dev(y))
+    for b in range(2):
+        zb, pb = pn.maxconv_pnorm(_dev(x[b]), _dev(y[b]))
+        assert torch.equal(z[b], zb[0]) and torch.equal(psel[b], pb[0])
+    ze = pn.maxconv_exact(_dev(x), _dev(y)).cpu().numpy()
+    want = orc.maxconv(x.astype(np.float64), y.astype(np.float64)).astype(np.float32)
+    np.testing.assert_array_equal(ze, want)

@@ -677,3 +677,15 @@ def test_maxconv_limit_of_ring_convolutions(orc):
         terms = [p * (np.log(x[i]) + np.log(y[m - i])) for i in range(23) if 0 <= m - i < 31]
         est = np.exp(logsumexp(terms) / p)
         assert z[m] <= est * (1 + 1e-12) and est <= z[m] * len(terms) ** (1 / p) * (1 + 1e-12)
+
+
+def test_maxconv_entries_match_full(orc):
+    """Selected outputs equal the full oracle's (max and every p-sum)."""
+    g = workloads.rng(2200)
+    x, y = g.random(120) ** 0.25, g.random(90) ** 0.25
+    pl = [0, 2, 4, 6]
+    full = orc.maxconv_pnorm(x, y, pl, tau=1e-300, want_S=True)
+    m = np.array([0, 1, 50, 118, 119, 150, 208])
+    ex, S = orc.maxconv_entries(x, y, m, pl)
+    np.testing.assert_array_equal(ex, orc.maxconv(x, y)[0][m])
+    np.testing.assert_allclose(S, full["S"][0][:, m].T, rtol=1e-14)
