@@ -84,6 +84,7 @@ def _load():
                                          vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm_ex.restype = ci
             lib.orc_maxconv.argtypes = [i64, i64, vp, i64, vp, vp]
+            lib.orc_topk_xy.argtypes = [i64, vp, vp, ci, ci, vp, dbl, i64, vp, vp]
             lib.orc_maxconv_entries.argtypes = [i64, vp, i64, vp, ci, vp, i64, vp, vp, vp]
             lib.orc_conv.argtypes = [i64, i64, vp, i64, vp, vp]
             lib.orc_maxconv_pnorm.argtypes = [i64, i64, vp, i64, vp, ci, vp, dbl, vp, vp, vp]
@@ -445,3 +446,29 @@ def maxconv_entries(x, y, m, p_log2):
     _load().orc_maxconv_entries(len(x), _p(x), len(y), _p(y), len(pl), _p(pl), len(m), _p(m),
                                 _p(ex), _p(S))
     return ex, S
+
+
+def topk_xy(x, y, k, p_log2, tau: float = 1e-12, y_rev: bool = False):
+    """Approximate top-k of x_i y_j (Alg. 9 with the NormQueue, plain
+    estimator); returns (values, diagonals m = i + j, -1 when exhausted)."""
+    x, y = _f64(x).ravel(), _f64(y).ravel()
+    assert len(x) == len(y)
+    pl = _plog(p_log2)
+    vals = np.empty(k, dtype=np.float64)
+    diag = np.empty(k, dtype=np.int64)
+    _load().orc_topk_xy(len(x), _p(x), _p(y), int(bool(y_rev)), len(pl), _p(pl), float(tau),
+                        int(k), _p(vals), _p(diag))
+    return vals, diag
+
+
+def recover_indices(d1, d2, n):
+    """Index recovery of Alg. 9's discussion: the k-th result of the call on y
+    lies on diagonal m1 = i + j, of the call on reversed y on m2 = i + (n-1-j);
+    i = (m1 + m2 - n + 1) / 2, j = m1 - i.  Pairs whose parity or range is
+    impossible give (-1, -1)."""
+    d1, d2 = np.asarray(d1, dtype=np.int64), np.asarray(d2, dtype=np.int64)
+    t = d1 + d2 - n + 1
+    i = np.where((t % 2 == 0) & (d1 >= 0) & (d2 >= 0), t // 2, -1)
+    j = np.where(i >= 0, d1 - i, -1)
+    bad = (i < 0) | (i >= n) | (j < 0) | (j >= n)
+    return np.where(bad, -1, i), np.where(bad, -1, j)

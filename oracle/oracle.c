@@ -748,3 +748,88 @@ void orc_maxconv_entries(int64_t nx, const double* x, int64_t ny, const double* 
     }
   }
 }
+
+/* ---------------------------------------------------------------------- */
+/* Approximate top-k of the products x_i y_j (Alg. 9, E_(X' x Y'), with the  */
+/* NormQueue).  x' = x / max x, y' = y / max y; for every diagonal          */
+/* m = i + j the p-sums sigma^(p)_m = sum_i x'_i^p y'_(m-i)^p (naive ring    */
+/* convolution, FP64, pow per term); psi_m = estimateMaxFromNormPowerSequence */
+/* (the plain form: (sigma^(p*))^(1/p*) at the largest p with sigma >= tau,  */
+/* none: 0).  k times: take the diagonal m* with the largest psi (ties: the   */
+/* smallest m), emit (psi_m* max x max y, m*), subtract psi_m*^p from every  */
+/* sigma^(p)_m* (the NormQueue pop) and re-estimate psi_m* once; a diagonal  */
+/* is exhausted after as many pops as it has terms.  Readings of the printed */
+/* listing: the subtraction touches sigma_m* (not sigma_m), the re-estimate */
+/* follows the update of every p, and it is clamped to the value just       */
+/* popped from that diagonal (removing a multiset's max cannot raise its    */
+/* max; without the clamp, residuals of large p falling below tau hand the  */
+/* estimate to small p, whose norms are near the diagonal's whole sum).     */
+/* vals[k], diag[k] (-1 when every                                           */
+/* diagonal is exhausted).  y_rev != 0 uses y reversed (the second call of   */
+/* the index recovery).                                                     */
+void orc_topk_xy(int64_t n, const double* x, const double* y, int y_rev, int n_p,
+                 const int* p_log2, double tau, int64_t k, double* vals, int64_t* diag) {
+  int64_t nz = 2 * n - 1;
+  double mx = 0.0, my = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (x[i] > mx) mx = x[i];
+    if (y[i] > my) my = y[i];
+  }
+  double sx = mx > 0.0 ? mx : 1.0, sy = my > 0.0 ? my : 1.0;
+  double* sig = (double*)malloc(sizeof(double) * (size_t)nz * n_p);
+  double* psi = (double*)malloc(sizeof(double) * (size_t)nz);
+  int64_t* left = (int64_t*)malloc(sizeof(int64_t) * (size_t)nz);
+  if (!sig || !psi || !left) {
+    free(sig); free(psi); free(left);
+    return;
+  }
+  int64_t m;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (m = 0; m < nz; ++m) {
+    int64_t lo = m - n + 1 > 0 ? m - n + 1 : 0, hi = m < n - 1 ? m : n - 1;
+    left[m] = hi - lo + 1;
+    for (int q = 0; q < n_p; ++q) {
+      double p = ldexp(1.0, p_log2[q]), s = 0.0;
+      for (int64_t i = lo; i <= hi; ++i) {
+        double yv = y_rev ? y[n - 1 - (m - i)] : y[m - i];
+        s += pow(x[i] / sx, p) * pow(yv / sy, p);
+      }
+      sig[m * n_p + q] = s;
+    }
+  }
+  for (m = 0; m < nz; ++m) {
+    psi[m] = 0.0;
+    for (int q = n_p - 1; q >= 0; --q)
+      if (sig[m * n_p + q] >= tau) {
+        psi[m] = pow(sig[m * n_p + q], 1.0 / ldexp(1.0, p_log2[q]));
+        break;
+      }
+  }
+  for (int64_t t = 0; t < k; ++t) {
+    int64_t best = -1;
+    for (m = 0; m < nz; ++m)
+      if (left[m] > 0 && (best < 0 || psi[m] > psi[best])) best = m;
+    if (best < 0 || psi[best] <= 0.0) {
+      vals[t] = 0.0;
+      diag[t] = -1;
+      continue;
+    }
+    double a = psi[best];
+    vals[t] = a * sx * sy;
+    diag[t] = best;
+    left[best] -= 1;
+    for (int q = 0; q < n_p; ++q) sig[best * n_p + q] -= pow(a, ldexp(1.0, p_log2[q]));
+    psi[best] = 0.0;
+    if (left[best] > 0)
+      for (int q = n_p - 1; q >= 0; --q)
+        if (sig[best * n_p + q] >= tau) {
+          psi[best] = pow(sig[best * n_p + q], 1.0 / ldexp(1.0, p_log2[q]));
+          break;
+        }
+    /* the next max of a multiset never exceeds the one just removed */
+    if (psi[best] > a) psi[best] = a;
+  }
+  free(sig);
+  free(psi);
+  free(left);
+}

@@ -689,3 +689,61 @@ def test_maxconv_entries_match_full(orc):
     ex, S = orc.maxconv_entries(x, y, m, pl)
     np.testing.assert_array_equal(ex, orc.maxconv(x, y)[0][m])
     np.testing.assert_allclose(S, full["S"][0][:, m].T, rtol=1e-14)
+
+
+# ------------------------------------------------------------ top-k of xy ---
+def test_topk_recover_indices_brute_force(orc):
+    """Every (i, j): m1 = i + j and m2 = i + n - 1 - j give back (i, j)."""
+    n = 7
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    i, j = orc.recover_indices((ii + jj).ravel(), (ii + n - 1 - jj).ravel(), n)
+    np.testing.assert_array_equal(i, ii.ravel())
+    np.testing.assert_array_equal(j, jj.ravel())
+    i, j = orc.recover_indices([3, 12, -1], [4, 12, 2], n)  # parity / range / missing
+    assert list(i) == [-1, -1, -1] and list(j) == [-1, -1, -1]
+
+
+def test_topk_single_term_diagonals_are_exact(orc):
+    """Diagonals with one term are popped exactly, once, then exhausted; the
+    two-term diagonal of n = 2 (0.27 and 0.2) gives estimates within its
+    envelope (p* = 16: 0.3^16 >= 1e-12 > 0.3^32)."""
+    v, d = orc.topk_xy([0.5], [0.8], 3, list(range(13)))
+    np.testing.assert_allclose(v[0], 0.4, rtol=1e-14)
+    assert d[0] == 0 and list(d[1:]) == [-1, -1]
+    x, y = np.array([1.0, 0.3]), np.array([0.9, 0.2])
+    v, d = orc.topk_xy(x, y, 5, list(range(13)))
+    assert list(d) == [0, 1, 1, 2, -1]
+    np.testing.assert_allclose(v[[0, 3]], [0.9, 0.06], rtol=1e-12)
+    assert 0.27 <= v[1] <= 0.27 * 2 ** (1 / 16)
+    assert abs(v[2] - 0.2) <= 0.02 * 0.2
+
+
+def test_topk_monotone_and_close_to_exact(orc):
+    """Emitted values never increase; with P = {1..4096} they match the exact
+    top-k of x_i y_j within 0.5 %, and the first is within the
+    L^(1/4096) envelope of the exact max."""
+    g = workloads.rng(2400)
+    n = 300
+    x, y = g.random(n), g.random(n)
+    exact = np.sort(np.outer(x, y).ravel())[::-1]
+    v, d = orc.topk_xy(x, y, 150, list(range(13)))
+    assert np.all(np.diff(v) <= 1e-15 * v[:-1])
+    np.testing.assert_allclose(v, exact[:150], rtol=5e-3)
+    assert exact[0] <= v[0] <= exact[0] * n ** (1 / 4096) * (1 + 1e-12)
+
+
+def test_topk_recovered_indices_are_valid(orc):
+    """The two calls (y and reversed y) give index pairs; the consistent ones
+    (x_i y_j within 1 % of the estimate) are the top products themselves."""
+    g = workloads.rng(2401)
+    n = 400
+    x, y = g.random(n), g.random(n)
+    v, d1 = orc.topk_xy(x, y, 40, list(range(13)))
+    _, d2 = orc.topk_xy(x, y, 40, list(range(13)), y_rev=True)
+    i, j = orc.recover_indices(d1, d2, n)
+    ok = i >= 0
+    cons = ok.copy()
+    cons[ok] = np.abs(x[i[ok]] * y[j[ok]] - v[ok]) <= 1e-2 * v[ok]
+    assert cons.sum() >= 20
+    exact = np.sort(np.outer(x, y).ravel())[::-1][:60]
+    assert np.all(np.isin(np.round(x[i[cons]] * y[j[cons]], 14), np.round(exact, 14)))
