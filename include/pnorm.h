@@ -274,6 +274,30 @@ PN_API pn_status maxconv_pnorm_long(int64_t nx, const float* x, int64_t ny, cons
  * with_p_sel = 0 adds room for an internal p_sel. */
 PN_API size_t pn_maxconv_long_workspace_size(int64_t nx, int64_t ny, int32_t with_p_sel);
 
+/* Approximate top-k of the products x_i y_j (Alg. 9, E_(X' x Y'), with the
+ * NormQueue), for `batch` independent pairs x, y of length n (row strides
+ * ldx, ldy; 2n - 1 <= 8192, else PN_EUNSUPPORTED).  For every diagonal
+ * m = i + j the p-sums of the max-scaled powered vectors come from FP64 FFT
+ * convolutions (as in maxconv_pnorm, every p of opts' family; a family up to
+ * p = 4096, p_log2 0..12, makes the pops sharp); then k times the diagonal
+ * with the largest estimate is popped, psi^p is subtracted from each of its
+ * p-sums and it is re-estimated, clamped to the value just popped (removing
+ * a multiset's max cannot raise it); a diagonal is exhausted after as many
+ * pops as it has terms.  vals[b * ldk + t] receives the t-th value (0 once
+ * every diagonal is exhausted).  The same pops on y reversed give the
+ * diagonals i + (n - 1 - j); pairing the two calls' pops of equal rank,
+ * i = (m1 + m2 - n + 1) / 2 and j = m1 - i are written to idx_i / idx_j
+ * (optional) when x_i y_j agrees with the value within 1 %, else -1.
+ * ws: pn_topk_xy_workspace_size bytes, 256-byte aligned.  opts: family,
+ * tau (<= 0: 1e-12), dev_status; estimator / correction must be 0. */
+PN_API pn_status topk_xy(int64_t batch, int64_t n, const float* x, int64_t ldx, const float* y,
+                         int64_t ldy, int64_t k, float* vals, int32_t* idx_i, int32_t* idx_j,
+                         int64_t ldk, const pn_opts* opts, void* ws, size_t ws_bytes,
+                         void* stream);
+
+/* Workspace bytes of topk_xy (0 on invalid sizes or options). */
+PN_API size_t pn_topk_xy_workspace_size(int64_t batch, int64_t n, int64_t k, const pn_opts* opts);
+
 /* The paper's threshold for a double-precision FFT convolution of vectors
  * in [0, 1], 1e-12 (Sec. 2.1). */
 PN_API double pn_maxconv_default_tau(void);

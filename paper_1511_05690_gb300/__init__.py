@@ -301,6 +301,35 @@ def maxconv_pnorm(x: torch.Tensor, y: torch.Tensor, *, p_log2=tuple(range(7)), t
     return z, psel
 
 
+def topk_xy(x: torch.Tensor, y: torch.Tensor, k: int, *, p_log2=tuple(range(13)), tau=None,
+            check=True, stream=None):
+    """Approximate top-k of x_i y_j per batch row (Alg. 9 with the NormQueue)
+    and the recovered indices (-1 where the check fails).  Returns (vals, i, j),
+    each (batch, k)."""
+    x, y = _rows(x, "x"), _rows(y, "y")
+    if x.shape != y.shape:
+        raise ValueError("x and y must have the same shape")
+    batch, n = x.shape
+    dev = x.device
+    vals = torch.empty((batch, k), dtype=torch.float32, device=dev)
+    ii = torch.empty((batch, k), dtype=torch.int32, device=dev)
+    jj = torch.empty((batch, k), dtype=torch.int32, device=dev)
+    st = status_word(dev)
+    o = make_opts(p_log2, "f32", tau, 2, 0, 0, st.data_ptr())
+    L = lib()
+    need = L.pn_topk_xy_workspace_size(batch, n, k, ctypes.byref(o))
+    if need == 0:
+        raise PnError(_b.PN_EUNSUPPORTED, "topk_xy")
+    ws = workspace(need, dev)
+    rc = L.topk_xy(batch, n, x.data_ptr(), _ld(x), y.data_ptr(), _ld(y), k, vals.data_ptr(),
+                   ii.data_ptr(), jj.data_ptr(), k, ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                   _stream_ptr(stream))
+    _b.check(rc, "topk_xy")
+    if check:
+        check_device_status(dev, "topk_xy")
+    return vals, ii, jj
+
+
 def maxconv_exact(x: torch.Tensor, y: torch.Tensor, *, out=None, stream=None):
     """Exact batched max-convolution on the CUDA cores (the comparison)."""
     x, y = _rows(x, "x"), _rows(y, "y")

@@ -29,7 +29,7 @@ EXPORTS = (
     "maxprod_pnorm_backward", "pn_grouped_table_bytes", "pn_grouped_build_table",
     "maxprod_pnorm_grouped", "maxprod_pnorm_static", "pn_autotune", "pn_grouped_autotune",
     "maxconv_pnorm", "maxconv_exact", "pn_maxconv_default_tau", "maxconv_pnorm_long",
-    "pn_maxconv_long_workspace_size",
+    "pn_maxconv_long_workspace_size", "topk_xy", "pn_topk_xy_workspace_size",
 )
 
 
@@ -109,6 +109,11 @@ def load():
         lib.maxconv_pnorm_long.restype = i32
         lib.pn_maxconv_long_workspace_size.argtypes = [i64, i64, i32]
         lib.pn_maxconv_long_workspace_size.restype = ctypes.c_size_t
+        lib.topk_xy.argtypes = [i64, i64, vp, i64, vp, i64, i64, vp, vp, vp, i64, optp, vp,
+                                ctypes.c_size_t, vp]
+        lib.topk_xy.restype = i32
+        lib.pn_topk_xy_workspace_size.argtypes = [i64, i64, i64, optp]
+        lib.pn_topk_xy_workspace_size.restype = ctypes.c_size_t
         lib.pn_maxconv_default_tau.argtypes = []
         lib.pn_maxconv_default_tau.restype = ctypes.c_double
         lib.pn_apsp_workspace_size.argtypes = [i64, optp]

@@ -27,6 +27,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "pn_device.cuh"
 
@@ -205,6 +206,66 @@ __device__ __forceinline__ int bitrev(int k, int logN) {
   return logN == 0 ? 0 : static_cast<int>(__brev(static_cast<unsigned>(k)) >> (32 - logN));
 }
 
+// One level of the FFT convolution in shared memory: a = x'^p + i y'^p (zero
+// padded; powers in FP32, or in FP64 with POW64, which the NormQueue needs:
+// it subtracts the popped term's p-th power from the sums, so their error
+// must stay far below the next term's; y_rev reads y backwards), forward FFT
+// of length N,
+// the spectrum of the ring convolution, inverse at half length.  On return
+// S_m = (m odd ? a[m/2].y : a[m/2].x) * 2 / N.
+//
+// The spectrum: X_k = (A_k + conj A_(N-k)) / 2, Y_k = (A_k - conj A_(N-k)) /
+// (2i), Z = X Y (Hermitian: the convolution is real).  Its inverse runs at
+// half length M = N / 2: with E, O the length-M DFTs of the even and odd
+// samples of S, Z_k = E_k + W^k O_k and Z_(k+M) = conj Z_(M-k) = E_k - W^k O_k
+// (W = exp(-2 pi i / N)), so
+// V_k = E_k + i O_k = (Z_k + conj Z_(M-k)) / 2 + i W^-k (Z_k - conj Z_(M-k)) / 2
+// is the DFT of v_j = S_2j + i S_(2j+1).  Thread work: k and M - k together
+// (reads A at k, N - k, M - k, M + k).
+template <bool POW64>
+__device__ void conv_level(double2* a, const double2* tw, const MaxconvArgs& ma, const float* x,
+                           const float* y, double isx, double isy, int plog, bool y_rev) {
+  const int N = 1 << ma.logN;
+  const int tid = threadIdx.x;
+  using T = typename std::conditional<POW64, double, float>::type;
+  for (int k = tid; k < N; k += FFT_THREADS) {
+    T xr = 0, yr = 0;
+    if (k < ma.nx) {
+      xr = static_cast<T>(x[k]) * static_cast<T>(isx);
+      for (int s = 0; s < plog; ++s) xr *= xr;
+    }
+    if (k < ma.ny) {
+      yr = static_cast<T>(y[y_rev ? ma.ny - 1 - k : k]) * static_cast<T>(isy);
+      for (int s = 0; s < plog; ++s) yr *= yr;
+    }
+    a[bitrev(k, ma.logN)] = make_double2(static_cast<double>(xr), static_cast<double>(yr));
+  }
+  __syncthreads();
+  fft_dit<false>(a, tw, ma.logN, 1);
+  const int M = N >> 1;
+  constexpr int QUADS = FFT_NMAX / 4 / FFT_THREADS + 1;
+  double2 vk[QUADS], vm[QUADS];
+  for (int u = 0; u < QUADS; ++u) {
+    const int k = tid + u * FFT_THREADS;
+    if (k <= (M >> 1)) {
+      const double2 zk = spec_z(a[k], a[(N - k) & (N - 1)]);
+      const double2 zm = spec_z(a[M - k], a[M + k]);
+      vk[u] = spec_v(zk, zm, tw[k]);
+      vm[u] = spec_v(zm, zk, (M - k) < M ? tw[M - k] : make_double2(1.0, 0.0));
+    }
+  }
+  __syncthreads();
+  for (int u = 0; u < QUADS; ++u) {
+    const int k = tid + u * FFT_THREADS;
+    if (k <= (M >> 1)) {
+      a[bitrev(k, ma.logN - 1)] = vk[u];
+      if (k != 0 && (M - k) != k) a[bitrev(M - k, ma.logN - 1)] = vm[u];
+    }
+  }
+  __syncthreads();
+  fft_dit<true>(a, tw, ma.logN - 1, 2);
+}
+
 __global__ void __launch_bounds__(FFT_THREADS, 1)
     k_maxconv_fft(const __grid_constant__ MaxconvArgs ma) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -263,51 +324,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
 
   for (int q = ma.n_p - 1; q >= 0; --q) {
     const int plog = ma.p_log2[q];
-    // a = x'^p + i y'^p, zero padded, in bit-reversed order (powers in FP32)
-    for (int k = tid; k < N; k += FFT_THREADS) {
-      float xr = 0.0f, yr = 0.0f;
-      if (k < ma.nx) {
-        xr = x[k] * isx_f;
-        for (int s = 0; s < plog; ++s) xr *= xr;
-      }
-      if (k < ma.ny) {
-        yr = y[k] * isy_f;
-        for (int s = 0; s < plog; ++s) yr *= yr;
-      }
-      a[bitrev(k, ma.logN)] = make_double2(xr, yr);
-    }
-    __syncthreads();
-    fft_dit<false>(a, tw, ma.logN, 1);
-    // Spectrum of the ring convolution: X_k = (A_k + conj A_(N-k)) / 2,
-    // Y_k = (A_k - conj A_(N-k)) / (2i), Z = X Y (Hermitian: the convolution
-    // is real).  Its inverse runs at half length M = N / 2: with E, O the
-    // length-M DFTs of the even and odd samples of S, Z_k = E_k + W^k O_k and
-    // Z_(k+M) = conj Z_(M-k) = E_k - W^k O_k (W = exp(-2 pi i / N)), so
-    // V_k = E_k + i O_k = (Z_k + conj Z_(M-k)) / 2 + i W^-k (Z_k - conj Z_(M-k)) / 2
-    // is the DFT of v_j = S_2j + i S_(2j+1).  Thread work: k and M - k
-    // together (reads A at k, N - k, M - k, M + k).
-    const int M = N >> 1;
-    constexpr int QUADS = FFT_NMAX / 4 / FFT_THREADS + 1;
-    double2 vk[QUADS], vm[QUADS];
-    for (int u = 0; u < QUADS; ++u) {
-      const int k = tid + u * FFT_THREADS;
-      if (k <= (M >> 1)) {
-        const double2 zk = spec_z(a[k], a[(N - k) & (N - 1)]);
-        const double2 zm = spec_z(a[M - k], a[M + k]);
-        vk[u] = spec_v(zk, zm, tw[k]);
-        vm[u] = spec_v(zm, zk, (M - k) < M ? tw[M - k] : make_double2(1.0, 0.0));
-      }
-    }
-    __syncthreads();
-    for (int u = 0; u < QUADS; ++u) {
-      const int k = tid + u * FFT_THREADS;
-      if (k <= (M >> 1)) {
-        a[bitrev(k, ma.logN - 1)] = vk[u];
-        if (k != 0 && (M - k) != k) a[bitrev(M - k, ma.logN - 1)] = vm[u];
-      }
-    }
-    __syncthreads();
-    fft_dit<true>(a, tw, ma.logN - 1, 2);
+    conv_level<false>(a, tw, ma, x, y, isx_f, isy_f, plog, false);
     // selection: first (largest) p with S >= tau; the smallest p takes the rest
     if (tid == 0) {
       open_terms = 0ull;
@@ -683,6 +700,258 @@ __global__ void k_long_direct(const __grid_constant__ LongArgs la, int q) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *la.done = 1;  // read by the next launches only
 }
 
+// ------------------------------------------------------------ top-k x y ---
+// Approximate top-k of the products x_i y_j (Alg. 9 with the NormQueue), for
+// `batch` independent pairs of length n (2n - 1 <= 8192), each run twice (y,
+// and y reversed for the index recovery):
+//   k_topk_sums  one CTA per (problem, direction): the p-sums of every p of P
+//                for every diagonal m = i + j (the FFT level above), and the
+//                first estimate psi_m;
+//   k_topk_pop   one warp per (problem, direction): k NormQueue pops -- the
+//                diagonal with the largest psi (two-level argmax over blocks
+//                of 32 diagonals), its value, the subtraction of psi^p from
+//                every p-sum of that diagonal, the re-estimate clamped to the
+//                value just popped; a diagonal is exhausted after as many
+//                pops as it has terms;
+//   k_topk_index i = (m1 + m2 - n + 1) / 2, j = m1 - i from the diagonals of
+//                the two calls' pops of equal rank, kept when x_i y_j agrees
+//                with the popped value within TOPK_VERIFY.
+constexpr double TOPK_VERIFY = 1e-2;
+
+struct TopkArgs {
+  const float* x;
+  const float* y;
+  int64_t ldx, ldy;
+  int32_t batch, n, nz, logN, n_p, k;
+  int32_t p_log2[PN_MAX_P];
+  double tau;
+  double* sig;     // [batch][2][n_p][nz]
+  double* psi0;    // [batch][2][nz] first estimates
+  double* scale;   // [batch] max x * max y
+  int32_t* diag;   // [batch][2][k]
+  float* vals;     // [batch][ldk]
+  int32_t* out_i;
+  int32_t* out_j;
+  int64_t ldk;
+  int32_t* status;
+};
+
+// sigma^(1/2^plog) in FP64: FP32 square roots, then two Newton steps on
+// r^p = sigma (sigma >= tau > 0 is in the FP32 range for the default tau).
+__device__ double root_fp64(double sig, int plog) {
+  if (!(sig > 0.0)) return 0.0;
+  float rf = static_cast<float>(sig);
+  for (int s = 0; s < plog; ++s) rf = sqrtf(rf);
+  double r = rf;
+  if (!(r > 0.0)) {  // below the FP32 range: FP64 square roots
+    r = sig;
+    for (int s = 0; s < plog; ++s) r = sqrt(r);
+    return r;
+  }
+  const double p = ldexp(1.0, plog);
+  for (int it = 0; it < 2; ++it) {
+    double rp = r;
+    for (int s = 0; s < plog; ++s) rp *= rp;
+    r = r * (1.0 + (sig / rp - 1.0) / p);
+  }
+  return r;
+}
+
+__device__ __forceinline__ double pow_pow2(double a, int plog) {
+  for (int s = 0; s < plog; ++s) a *= a;
+  return a;
+}
+
+__global__ void __launch_bounds__(FFT_THREADS, 1)
+    k_topk_sums(const __grid_constant__ TopkArgs ta) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = 1 << ta.logN;
+  double2* a = reinterpret_cast<double2*>(smem);
+  double2* tw = a + N;
+  __shared__ float red[2][FFT_THREADS / 32];
+  const int b = blockIdx.x >> 1, dir = blockIdx.x & 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* x = ta.x + (int64_t)b * ta.ldx;
+  const float* y = ta.y + (int64_t)b * ta.ldy;
+  for (int k = tid; k < (N >> 1); k += FFT_THREADS) tw[k] = g_twiddle[k << (FFT_LOG_NMAX - ta.logN)];
+  float mx = 0.0f, my = 0.0f;
+  bool bad = false;
+  for (int k = tid; k < ta.n; k += FFT_THREADS) {
+    const float u = x[k], v = y[k];
+    bad |= !(u >= 0.0f && u <= 3.4028235e38f) || !(v >= 0.0f && v <= 3.4028235e38f);
+    mx = fmaxf(mx, u);
+    my = fmaxf(my, v);
+  }
+  if (__syncthreads_or(bad)) {
+    if (tid == 0) set_status(ta.status, PN_EDOMAIN);
+    return;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, off));
+  }
+  if (lane == 0) {
+    red[0][warp] = mx;
+    red[1][warp] = my;
+  }
+  __syncthreads();
+  double sx = 0.0, sy = 0.0;
+  for (int w = 0; w < FFT_THREADS / 32; ++w) {
+    sx = fmax(sx, static_cast<double>(red[0][w]));
+    sy = fmax(sy, static_cast<double>(red[1][w]));
+  }
+  if (sx == 0.0) sx = 1.0;
+  if (sy == 0.0) sy = 1.0;
+  if (tid == 0 && dir == 0) ta.scale[b] = sx * sy;
+  MaxconvArgs ma;
+  ma.nx = ta.n;
+  ma.ny = ta.n;
+  ma.logN = ta.logN;
+  const double invM = 2.0 / N;
+  double* sig = ta.sig + (int64_t)blockIdx.x * ta.n_p * ta.nz;
+  for (int q = 0; q < ta.n_p; ++q) {
+    conv_level<true>(a, tw, ma, x, y, 1.0 / sx, 1.0 / sy, ta.p_log2[q], dir == 1);
+    for (int m = tid; m < ta.nz; m += FFT_THREADS)
+      sig[(int64_t)q * ta.nz + m] = ((m & 1) ? a[m >> 1].y : a[m >> 1].x) * invM;
+    __syncthreads();
+  }
+  // first estimates: the largest p with sigma >= tau (none: 0)
+  double* psi = ta.psi0 + (int64_t)blockIdx.x * ta.nz;
+  for (int m = tid; m < ta.nz; m += FFT_THREADS) {
+    double e = 0.0;
+    for (int q = ta.n_p - 1; q >= 0; --q) {
+      const double v = sig[(int64_t)q * ta.nz + m];
+      if (v >= ta.tau) {
+        e = root_fp64(v, ta.p_log2[q]);
+        break;
+      }
+    }
+    psi[m] = e;
+  }
+}
+
+// (value, index) argmax across a warp: larger value, then smaller index.
+__device__ __forceinline__ void warp_argmax(double& v, int& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, off);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32) k_topk_pop(const __grid_constant__ TopkArgs ta) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nb = (ta.nz + 31) >> 5;
+  double* psi = reinterpret_cast<double*>(smem);       // nb * 32
+  double* bmax = psi + nb * 32;                        // nb
+  uint16_t* left = reinterpret_cast<uint16_t*>(bmax + nb);  // nb * 32
+  const int lane = threadIdx.x;
+  const int b = blockIdx.x >> 1, dir = blockIdx.x & 1;
+  double* sig = ta.sig + (int64_t)blockIdx.x * ta.n_p * ta.nz;
+  const double* psi0 = ta.psi0 + (int64_t)blockIdx.x * ta.nz;
+  int32_t* diag = ta.diag + (int64_t)blockIdx.x * ta.k;
+  for (int m = lane; m < nb * 32; m += 32) {
+    psi[m] = m < ta.nz ? psi0[m] : -1.0;
+    left[m] = m < ta.nz ? static_cast<uint16_t>(terms_of(m, ta.n, ta.n)) : 0;
+  }
+  __syncwarp();
+  for (int blk = 0; blk < nb; ++blk) {
+    double v = psi[blk * 32 + lane];
+    int i = lane;
+    warp_argmax(v, i);
+    if (lane == 0) bmax[blk] = v;
+  }
+  __syncwarp();
+  const double scale = dir == 0 ? ta.scale[b] : 0.0;
+  for (int t = 0; t < ta.k; ++t) {
+    // the block, then the diagonal, with the largest psi
+    double v = -2.0;
+    int bi = 0x7fffffff;
+    for (int blk = lane; blk < nb; blk += 32) {
+      const double w = bmax[blk];
+      if (w > v) {
+        v = w;
+        bi = blk;
+      }
+    }
+    warp_argmax(v, bi);
+    const int mcand = bi * 32 + lane;
+    double pv = psi[mcand];
+    int m = mcand;
+    warp_argmax(pv, m);
+    if (!(pv > 0.0)) {  // every diagonal exhausted or without a stable p
+      for (int r = t + lane; r < ta.k; r += 32) {
+        diag[r] = -1;
+        if (dir == 0) ta.vals[(int64_t)b * ta.ldk + r] = 0.0f;
+      }
+      break;
+    }
+    const double alpha = pv;
+    if (lane == 0) {
+      diag[t] = m;
+      if (dir == 0) ta.vals[(int64_t)b * ta.ldk + t] = static_cast<float>(alpha * scale);
+    }
+    const int rem = left[m] - 1;
+    // NormQueue pop: sigma^(p)_m -= alpha^p for every p (one lane per p)
+    double sq = 0.0;
+    if (lane < ta.n_p) {
+      const int64_t at = (int64_t)lane * ta.nz + m;
+      sq = sig[at] - pow_pow2(alpha, ta.p_log2[lane]);
+      sig[at] = sq;
+    }
+    // re-estimate: the largest p whose sigma is >= tau, clamped to alpha
+    const unsigned stable = __ballot_sync(0xffffffffu, lane < ta.n_p && sq >= ta.tau);
+    double e = 0.0;
+    if (rem > 0 && stable) {
+      const int qs = 31 - __clz(stable);
+      const double sv = __shfl_sync(0xffffffffu, sq, qs);
+      e = fmin(root_fp64(sv, ta.p_log2[qs]), alpha);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      psi[m] = e;
+      left[m] = static_cast<uint16_t>(rem);
+    }
+    __syncwarp();
+    double w = psi[bi * 32 + lane];
+    int wi = lane;
+    warp_argmax(w, wi);
+    if (lane == 0) bmax[bi] = w;
+    __syncwarp();
+  }
+}
+
+__global__ void k_topk_index(const __grid_constant__ TopkArgs ta) {
+  const int b = blockIdx.x;
+  const int32_t* d1 = ta.diag + (int64_t)(2 * b) * ta.k;
+  const int32_t* d2 = ta.diag + (int64_t)(2 * b + 1) * ta.k;
+  const float* x = ta.x + (int64_t)b * ta.ldx;
+  const float* y = ta.y + (int64_t)b * ta.ldy;
+  for (int t = threadIdx.x; t < ta.k; t += blockDim.x) {
+    int i = -1, j = -1;
+    const int m1 = d1[t], m2 = d2[t];
+    const int s = m1 + m2 - ta.n + 1;
+    if (m1 >= 0 && m2 >= 0 && (s & 1) == 0) {
+      const int ii = s >> 1, jj = m1 - ii;
+      if (ii >= 0 && ii < ta.n && jj >= 0 && jj < ta.n) {
+        const double v = ta.vals[(int64_t)b * ta.ldk + t];
+        const double prod = static_cast<double>(x[ii]) * static_cast<double>(y[jj]);
+        if (fabs(prod - v) <= TOPK_VERIFY * v) {
+          i = ii;
+          j = jj;
+        }
+      }
+    }
+    if (ta.out_i) ta.out_i[(int64_t)b * ta.ldk + t] = i;
+    if (ta.out_j) ta.out_j[(int64_t)b * ta.ldk + t] = j;
+  }
+}
+
 std::mutex g_tw_mu;
 bool g_tw_ready[64];
 
@@ -816,11 +1085,94 @@ int launch_maxconv_long(const pn_opts* o, int64_t nx, const float* x, int64_t ny
   return cudaGetLastError();
 }
 
+struct TopkLayout {
+  size_t off_sig = 0, off_psi = 0, off_scale = 0, off_diag = 0, total = 0;
+};
+
+TopkLayout topk_layout(int64_t batch, int64_t n, int64_t k, int n_p) {
+  TopkLayout L;
+  const int64_t nz = 2 * n - 1;
+  size_t off = 0;
+  L.off_sig = off; off += static_cast<size_t>(batch) * 2 * n_p * nz * sizeof(double);
+  off = (off + 255) & ~size_t(255);
+  L.off_psi = off; off += static_cast<size_t>(batch) * 2 * nz * sizeof(double);
+  off = (off + 255) & ~size_t(255);
+  L.off_scale = off; off += static_cast<size_t>(batch) * sizeof(double);
+  off = (off + 255) & ~size_t(255);
+  L.off_diag = off; off += static_cast<size_t>(batch) * 2 * k * sizeof(int32_t);
+  L.total = (off + 255) & ~size_t(255);
+  return L;
+}
+
+int launch_topk(const TopkArgs& ta0, uint8_t* ws, void* stream) {
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int e = ensure_twiddles(s);
+  if (e) return e;
+  TopkArgs ta = ta0;
+  const TopkLayout L = topk_layout(ta.batch, ta.n, ta.k, ta.n_p);
+  ta.sig = reinterpret_cast<double*>(ws + L.off_sig);
+  ta.psi0 = reinterpret_cast<double*>(ws + L.off_psi);
+  ta.scale = reinterpret_cast<double*>(ws + L.off_scale);
+  ta.diag = reinterpret_cast<int32_t*>(ws + L.off_diag);
+  const int N = 1 << ta.logN;
+  const int smem_sums = (N + N / 2) * static_cast<int>(sizeof(double2));
+  if ((e = cudaFuncSetAttribute(k_topk_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sums)))
+    return e;
+  const int nb = (ta.nz + 31) / 32;
+  const int smem_pop = nb * 32 * 8 + nb * 8 + nb * 32 * 2;
+  if ((e = cudaFuncSetAttribute(k_topk_pop, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pop)))
+    return e;
+  k_topk_sums<<<2 * ta.batch, FFT_THREADS, smem_sums, s>>>(ta);
+  k_topk_pop<<<2 * ta.batch, 32, smem_pop, s>>>(ta);
+  k_topk_index<<<ta.batch, 256, 0, s>>>(ta);
+  return cudaGetLastError();
+}
+
 }  // namespace pn
 
 using namespace pn;
 
 extern "C" {
+
+size_t pn_topk_xy_workspace_size(int64_t batch, int64_t n, int64_t k, const pn_opts* opts) {
+  if (!host_opts_valid(opts) || batch < 1 || n < 1 || 2 * n - 1 > (int64_t(1) << MAXCONV_LOG_NMAX) ||
+      k < 1 || batch > (1 << 20) || k > (int64_t(1) << 30))
+    return 0;
+  return topk_layout(batch, n, k, opts->n_p).total;
+}
+
+pn_status topk_xy(int64_t batch, int64_t n, const float* x, int64_t ldx, const float* y,
+                  int64_t ldy, int64_t k, float* vals, int32_t* idx_i, int32_t* idx_j,
+                  int64_t ldk, const pn_opts* opts, void* ws, size_t ws_bytes, void* stream) {
+  if (!host_opts_valid(opts)) return PN_EINVAL;
+  if (opts->estimator != 0 || opts->correction != 0) return PN_EUNSUPPORTED;
+  if (batch < 0 || n < 1 || k < 1) return PN_EINVAL;
+  if (batch == 0) return PN_OK;
+  if (2 * n - 1 > (int64_t(1) << MAXCONV_LOG_NMAX) || batch > (1 << 20) || k > (int64_t(1) << 30))
+    return PN_EUNSUPPORTED;
+  if (!x || !y || !vals || ldx < n || ldy < n || ldk < k) return PN_EINVAL;
+  const size_t need = pn_topk_xy_workspace_size(batch, n, k, opts);
+  if (!ws || ws_bytes < need) return PN_EWORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % 256) return PN_EALIGN;
+  if (host_device_sms() <= 0) return PN_EUNSUPPORTED;
+  TopkArgs ta;
+  std::memset(&ta, 0, sizeof(ta));
+  ta.x = x; ta.y = y; ta.ldx = ldx; ta.ldy = ldy;
+  ta.batch = static_cast<int32_t>(batch);
+  ta.n = static_cast<int32_t>(n);
+  ta.nz = static_cast<int32_t>(2 * n - 1);
+  int logN = 1;
+  while ((int64_t(1) << logN) < 2 * n - 1) ++logN;
+  ta.logN = logN;
+  ta.n_p = opts->n_p;
+  for (int q = 0; q < opts->n_p; ++q) ta.p_log2[q] = opts->p_log2[q];
+  ta.tau = opts->tau > 0.0 ? opts->tau : pn_maxconv_default_tau();
+  ta.k = static_cast<int32_t>(k);
+  ta.vals = vals; ta.out_i = idx_i; ta.out_j = idx_j; ta.ldk = ldk;
+  ta.status = opts->dev_status;
+  return launch_topk(ta, static_cast<uint8_t*>(ws), stream) == 0 ? PN_OK : PN_ECUDA;
+}
+
 
 size_t pn_maxconv_long_workspace_size(int64_t nx, int64_t ny, int32_t with_p_sel) {
   if (nx < 1 || ny < 1 || nx + ny - 1 > (int64_t(1) << 22)) return 0;
