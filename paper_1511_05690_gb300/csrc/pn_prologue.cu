@@ -248,6 +248,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int rb = local / P.KB;
     power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
   } else {
+    if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
     for_flagged_ids(
         cm.total_xa,
         [&](int id) {
@@ -346,6 +347,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int rb = local / P.KB;
     power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
   } else {
+    if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
     const int per_tile = cm.BN / TILE_M;
     for_flagged_ids(
         cm.total_xb,
