@@ -19,8 +19,10 @@ __host__ __device__ constexpr inline int stage_bytes(int mode, int BN) {
 __host__ __device__ constexpr int num_stages(int mode, int BN) {
   return SMEM_STAGE_BUDGET / stage_bytes(mode, BN) > 8 ? 8 : SMEM_STAGE_BUDGET / stage_bytes(mode, BN);
 }
+constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
 __host__ __device__ constexpr int smem_total(int mode, int BN) {
-  return num_stages(mode, BN) * stage_bytes(mode, BN) + 1024 /*align*/ + 256 /*barriers*/;
+  return num_stages(mode, BN) * stage_bytes(mode, BN) + 1024 /*align*/ + 256 /*barriers*/ +
+         EPI_WARPS * STG_BYTES;
 }
 __host__ __device__ constexpr int mma_kind(int mode) {
   return (mode == MODE_BF16 || mode == MODE_F16) ? KIND_F16 : mode == MODE_E4M3 ? KIND_F8 : KIND_TF32;
@@ -34,6 +36,71 @@ __host__ __device__ constexpr uint32_t ab_format(int mode) {
 __device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   int32_t never = 0;
   return mbar_wait(bar, parity, timeout_ns, &never);
+}
+
+// Stores a warp's 32 x 32 block of FP32 results through shared memory so that
+// the global writes are row-contiguous: lane l holds row l (v[c] for column
+// j0 + c) and mask bit c of lane l selects the entries of row l to write; row
+// r starts at base + r * ld.  stg is the warp's 4 KB buffer, float4 groups
+// XOR-swizzled by row (conflict-free both ways).  When every mask is full and
+// rows are 16-byte aligned, each instruction writes four whole 128-byte rows;
+// otherwise one row per instruction (rows with no entry are skipped).  The
+// call must be warp-uniform; base + r * ld is only formed for rows written.
+__device__ __forceinline__ void warp_store_f32(float* stg, const float (&v)[32], uint32_t mask,
+                                               float* base, int64_t ld, bool vec, int lane) {
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(stg + lane * 32 + ((g ^ (lane & 7)) << 2)) =
+        make_float4(v[4 * g], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+  __syncwarp();
+  if (__all_sync(0xffffffffu, mask == 0xffffffffu) && vec) {
+    const int g = lane & 7;
+#pragma unroll
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+      const int r = r0 + (lane >> 3);
+      const float4 t = *reinterpret_cast<const float4*>(stg + r * 32 + ((g ^ (r & 7)) << 2));
+      *reinterpret_cast<float4*>(base + r * ld + 4 * g) = t;
+    }
+  } else {
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t m = __shfl_sync(0xffffffffu, mask, r);
+      if (m == 0u) continue;
+      if ((m >> lane) & 1u)
+        base[r * ld + lane] = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+    }
+  }
+  __syncwarp();
+}
+
+// The same for a 32 x 32 block of bytes held as eight words per lane (w[q]
+// holds columns 4q..4q+3); the two 16-byte halves of row l are swapped when
+// bit 2 of l is set (conflict-free both ways).
+__device__ __forceinline__ void warp_store_u8(uint32_t* stg, const uint32_t (&w)[8], uint32_t mask,
+                                              uint8_t* base, int64_t ld, bool vec, int lane) {
+  const int sw = (lane >> 2) & 1;
+  *reinterpret_cast<uint4*>(stg + lane * 8 + (sw << 2)) = make_uint4(w[0], w[1], w[2], w[3]);
+  *reinterpret_cast<uint4*>(stg + lane * 8 + ((sw ^ 1) << 2)) = make_uint4(w[4], w[5], w[6], w[7]);
+  __syncwarp();
+  if (__all_sync(0xffffffffu, mask == 0xffffffffu) && vec) {
+    const int h = lane & 1;
+#pragma unroll
+    for (int r0 = 0; r0 < 32; r0 += 16) {
+      const int r = r0 + (lane >> 1);
+      const uint4 t = *reinterpret_cast<const uint4*>(stg + r * 8 + ((h ^ ((r >> 2) & 1)) << 2));
+      *reinterpret_cast<uint4*>(base + r * ld + 16 * h) = t;
+    }
+  } else {
+    const uint8_t* sb = reinterpret_cast<const uint8_t*>(stg);
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t m = __shfl_sync(0xffffffffu, mask, r);
+      if (m == 0u) continue;
+      if ((m >> lane) & 1u)
+        base[r * ld + lane] = sb[r * 32 + (((lane >> 4) ^ ((r >> 2) & 1)) << 4) + (lane & 15)];
+    }
+  }
+  __syncwarp();
 }
 
 // EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
@@ -220,6 +287,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int half = ew >> 2;
     const int et = threadIdx.x - 64;
     constexpr int HCH = CHUNKS / 2;  // 32-column chunks per warp
+    float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + ew * STG_BYTES);
     int it = 0;
     for (int idx = blockIdx.x; idx < count; idx += gridDim.x, ++it) {
       const int t = lv.is_top ? idx : lv.work[idx];
@@ -329,8 +397,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (e < jn) orow[e] = x[e];
             }
           }
-        } else if (row_ok && j0 < P.N) {
-          if (!lv.is_top) res = st_row[hc];
+        } else if (j0 < P.N) {  // warp-uniform: rows past M resolve nothing
+          if (!row_ok) res = 0xffffffffu;
+          else if (!lv.is_top) res = st_row[hc];
           const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
           const uint32_t inrange = jn == 32 ? 0xffffffffu : ((1u << jn) - 1u);
           // entries to resolve at this p: not yet resolved, in range, and stable
@@ -351,7 +420,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // r = 1 projection (Sec. 2.1): entries resolved at 2p hold S^(2p) in C;
           // with S^(p) from this level the estimate is (S^(2p) / S^(p))^(1/p).
           // The ratio is clamped to <= 1 (S is non-increasing in p).
-          const uint32_t pend = lv.proj_here ? cm.pend[st_idx + hc] : 0u;
+          const uint32_t pend = lv.proj_here && row_ok ? cm.pend[st_idx + hc] : 0u;
           if (pend) {
             // eight entries at a time (two float4 when the whole chunk is pending)
             const float* cs = cm.c + P.rc_c + j0;
@@ -410,7 +479,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             any_left |= cand != 0u;  // their S^(p/2) comes from the next level
             pend_all[hc] = cand;
           }
-          if (cand) {
+          if (__any_sync(0xffffffffu, cand != 0u)) {
             const uint32_t pbits = lv.plog * 0x01010101u;
             uint32_t pw[8];
 #pragma unroll
@@ -419,20 +488,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               const uint32_t flag = (nb & 1u) | ((nb & 2u) << 7) | ((nb & 4u) << 14) | ((nb & 8u) << 21);
               pw[q] = pbits | (flag << 7);
             }
+            // rows of this warp's block start at ibase
+            const int64_t ibase = (int64_t)tm * TILE_M + quarter * 32;
             // S_sel before x is overwritten by the root
-            float* srow = P.Ssel ? P.Ssel + (int64_t)i * P.ldaux + j0 : nullptr;
-            const bool full_vec = cand == 0xffffffffu && P.vec_c;
-            if (srow) {
-              if (full_vec) {
-#pragma unroll
-                for (int e = 0; e < 32; e += 4)
-                  *reinterpret_cast<float4*>(srow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
-              } else {
-#pragma unroll
-                for (int e = 0; e < 32; ++e)
-                  if ((cand >> e) & 1u) srow[e] = x[e];
-              }
-            }
+            if (P.Ssel)
+              warp_store_f32(stg, x, cand, P.Ssel + ibase * P.ldaux + j0, P.ldaux, P.vec_c, lane);
             // r = 1 projection with a level p/2 below: C keeps S^(p) until then
             if (!lv.proj_next) {
               if constexpr (MODE == MODE_3XTF32) {
@@ -487,24 +547,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                   if (j0 + e == i) x[e] = 1.0f;
               }
             }
-            uint8_t* prow = P.psel ? P.psel + (int64_t)i * P.ldaux + j0 : nullptr;
-            if (full_vec) {
-#pragma unroll
-              for (int e = 0; e < 32; e += 4)
-                *reinterpret_cast<float4*>(crow + e) = make_float4(x[e], x[e + 1], x[e + 2], x[e + 3]);
-              if (prow) {
-                *reinterpret_cast<uint4*>(prow) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
-                *reinterpret_cast<uint4*>(prow + 16) = make_uint4(pw[4], pw[5], pw[6], pw[7]);
-              }
-            } else {
-#pragma unroll
-              for (int e = 0; e < 32; ++e) {
-                if ((cand >> e) & 1u) {
-                  crow[e] = x[e];
-                  if (prow) prow[e] = static_cast<uint8_t>(pw[e >> 2] >> (8 * (e & 3)));
-                }
-              }
-            }
+            warp_store_f32(stg, x, cand, P.C + ibase * P.ldc + j0, P.ldc, P.vec_c, lane);
+            if (P.psel)
+              warp_store_u8(reinterpret_cast<uint32_t*>(stg), pw, cand,
+                            P.psel + ibase * P.ldaux + j0, P.ldaux, P.vec_c, lane);
             res |= cand;
           }
         }
