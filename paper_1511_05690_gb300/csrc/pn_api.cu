@@ -271,10 +271,12 @@ pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
   int e = cudaMemsetAsync(ws, 0, L.ctrl_bytes, s);
   if (e) return PN_ECUDA;
   if ((e = launch_maxes(cm, stream))) return PN_ECUDA;
+  OperandMaps maps;
+  make_operand_maps(cm, maps);
   for (int q = o->n_p - 1; q >= 0; --q) {
     const Level lv = make_level(L, o, ws, q);
-    if ((e = launch_power_a(cm, lv, stream))) return PN_ECUDA;
-    if ((e = launch_power_b(cm, lv, stream))) return PN_ECUDA;
+    if ((e = launch_power_a(cm, lv, stream, &maps))) return PN_ECUDA;
+    if ((e = launch_power_b(cm, lv, stream, &maps))) return PN_ECUDA;
     if (lv.is_top && o->correction == 2) {
       // the affine model's coefficients, from the scales of the top level
       FitArgs fa;

@@ -188,9 +188,24 @@ int host_tuned_bn(int mode, int64_t M, int64_t N, int64_t K);  // autotune cache
 
 // ------------------------------------------------------------ launchers ---
 // All return a cudaError_t value as int (0 = success).
+// Tensor maps (CUtensorMap, 128 opaque bytes) of the FP32 operands of a
+// single product, for the top-level image kernels; has_a / has_b are 0 when
+// the operand's rows are not 16-byte aligned or the driver's encoder is not
+// available (the per-tile kernels are used then).
+struct alignas(64) TensorMapBytes {
+  uint64_t w[16];
+};
+struct OperandMaps {
+  TensorMapBytes a, b;
+  int32_t has_a, has_b;
+};
+void make_operand_maps(const Common& cm, OperandMaps& maps);
+
 int launch_maxes(const Common& cm, void* stream);
-int launch_power_a(const Common& cm, const Level& lv, void* stream);
-int launch_power_b(const Common& cm, const Level& lv, void* stream);
+int launch_power_a(const Common& cm, const Level& lv, void* stream,
+                   const OperandMaps* maps = nullptr);
+int launch_power_b(const Common& cm, const Level& lv, void* stream,
+                   const OperandMaps* maps = nullptr);
 int launch_gemm_level(const Common& cm, const Level& lv, int num_sms, void* stream);
 int launch_exact(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
                  int64_t ldb, float* C, int64_t ldc, int semiring, int variant, void* stream);

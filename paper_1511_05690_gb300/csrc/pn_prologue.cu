@@ -8,6 +8,9 @@
 // exactly the shared-memory image the tensor cores read (K-major, 128-byte
 // swizzle).  The GEMM then moves each tile with one 1-D bulk copy.  Rows past
 // M (N) and K past K are zero in the image, so the GEMM needs no tail logic.
+#include <cstring>
+
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -140,22 +143,104 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
   }
 }
 
+// The maximum behind a row / column scale (its bits; 0 gives the scale 1),
+// and the power-of-two scale from it.
+__device__ __forceinline__ uint32_t scale_bits(const Common& cm, const uint32_t* mx, int64_t idx,
+                                               int g, int which) {
+  if (cm.scaling == 0) return 0u;
+  return cm.scaling == 1 ? cm.gmax[2 * g + which] : mx[idx];
+}
+__device__ __forceinline__ float scale_from_bits(const Common& cm, uint32_t bits) {
+  return cm.scaling == 0 ? 1.0f : pow2_ceil_f(__uint_as_float(bits));
+}
 __device__ __forceinline__ float scale_of(const Common& cm, const uint32_t* mx, int64_t idx,
                                           int g, int which) {
-  if (cm.scaling == 0) return 1.0f;
-  const uint32_t bits = cm.scaling == 1 ? cm.gmax[2 * g + which] : mx[idx];
-  return pow2_ceil_f(__uint_as_float(bits));
+  return scale_from_bits(cm, scale_bits(cm, mx, idx, g, which));
+}
+
+// v[u][e] <- v[u][e] / s[u] for power-of-two scales s[u]; a multiply by the
+// exact reciprocal whenever every scale of the warp has a normal one (called
+// by whole warps).
+template <int U, int EPC>
+__device__ __forceinline__ void div_scales(float (&v)[U][EPC], const float (&s)[U]) {
+  float inv[U];
+  bool ok = true;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    inv[u] = 1.0f / s[u];
+    ok = ok && recip_exact(s[u]);
+  }
+  if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[u][e] *= inv[u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[u][e] = div_pow2(v[u][e], s[u], inv[u], recip_exact(s[u]));
+  }
+}
+
+// v <- v^(2^plog) * opscale, the squarings of all U x EPC values interleaved
+// (independent chains; the same products as pow2k value by value).
+template <int U, int EPC>
+__device__ __forceinline__ void power_all(float (&v)[U][EPC], int plog, float opscale) {
+#pragma unroll 1
+  for (int t = 0; t < plog; ++t) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[u][e] *= v[u][e];
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) v[u][e] *= opscale;
 }
 
 // ----------------------------------------------------------- A images ---
+// Second half of an A image tile built by 1024 / U threads: thread t holds
+// the source values of image chunks (row (t >> 3) + (128 / U) u, 16-byte slot
+// t & 7), u < U (zero past M), and their row scales rs[u] (1 past M);
+// scales, powers, packs and stores them (a warp writes four whole 128-byte
+// image rows).
+template <int MODE, int U>
+__device__ __forceinline__ void power_a_store(const Common& cm, const Level& lv, const Prob& P,
+                                              int rb, int kb, float (&v)[U][Packer<MODE>::EPC],
+                                              const float (&rs)[U]) {
+  using PK = Packer<MODE>;
+  constexpr int RSTEP = TILE_M / U;
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
+  const int cc = threadIdx.x & 7;
+  if (lv.is_top && kb == 0 && cc == 0) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int row = rb * TILE_M + (threadIdx.x >> 3) + RSTEP * u;
+      if (row < P.M) cm.r[P.rc_r + row] = rs[u];
+    }
+  }
+  div_scales(v, rs);
+  power_all(v, lv.plog, opscale);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int rr = (threadIdx.x >> 3) + RSTEP * u;
+    uint4 hi, lo;
+    PK::pack(v[u], hi, lo);
+    const uint32_t off = sw128_offset(rr, cc * 16);
+    *reinterpret_cast<uint4*>(dst + off) = hi;
+    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, int g,
                                              const Prob& P, int rb, int kb) {
   using PK = Packer<MODE>;
   constexpr int EPC = PK::EPC;
   constexpr int BK = mode_bk(MODE);
-  const float opscale = ldexpf(1.0f, cm.s_op);
-  uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
   const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
   // 1024 16-byte output chunks per tile, 4 per thread: chunk = tid + 256 u,
   // row = chunk / 8 (8 threads cover one 128-byte image row), 16-byte slot
@@ -178,30 +263,20 @@ __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, 
       for (int e = 0; e < EPC; ++e) v[u][e] = (row < P.M && k0 + e < P.K) ? __ldg(src + e) : 0.0f;
     }
   }
+  float rs[4];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
-    const int rr = (threadIdx.x >> 3) + 32 * u;
-    const int row = rb * TILE_M + rr;
-    if (row < P.M) {
-      const float rs = scale_of(cm, cm.rmax, P.rc_r + row, g, 0);
-      if (lv.is_top && kb == 0 && cc == 0) cm.r[P.rc_r + row] = rs;
-      const float inv = 1.0f / rs;
-      const bool inv_ok = rs >= 1.1754944e-38f && rs <= 8.507059e37f;
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] = pow2k(div_pow2(v[u][e], rs, inv, inv_ok), lv.plog) * opscale;
-    }
-    uint4 hi, lo;
-    PK::pack(v[u], hi, lo);
-    const uint32_t off = sw128_offset(rr, cc * 16);
-    *reinterpret_cast<uint4*>(dst + off) = hi;
-    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
+    const int row = rb * TILE_M + (threadIdx.x >> 3) + 32 * u;
+    rs[u] = row < P.M ? scale_of(cm, cm.rmax, P.rc_r + row, g, 0) : 1.0f;
   }
+  power_a_store<MODE, 4>(cm, lv, P, rb, kb, v, rs);
 }
 
-// Top level: one block per operand tile.  Lower levels: the same operand-tile
-// ids strided over a grid of a few blocks per SM; a tile is rebuilt only if a
-// pushed output tile needs its row block (few at most levels, every one when
-// the r = 1 projection sends every tile to the level p*/2).
+// Top level without a tensor map (k_image_tma below): one block per operand
+// tile.  Lower levels: the same operand-tile ids strided over a grid of a few
+// blocks per SM; a tile is rebuilt only if a pushed output tile needs its row
+// block (few at most levels, every one when the r = 1 projection sends every
+// tile to the level p*/2).
 // Resident blocks per SM for the image kernels: as many as the registers of
 // the format's loads allow without heavy spilling -- more blocks keep more
 // loads in flight (the max pass, at HBM speed, keeps about 200 KB per SM).
@@ -247,22 +322,22 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int local = id - P.xa_base;
     const int rb = local / P.KB;
     power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
-  } else {
-    if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
-    for_flagged_ids(
-        cm.total_xa,
-        [&](int id) {
-          const Prob& P = prob_at(cm, find_prob(cm, id, 1));
-          return lv.rflag[P.tm_base + (id - P.xa_base) / P.KB] != 0;
-        },
-        [&](int id) {
-          const int g = find_prob(cm, id, 1);
-          const Prob& P = prob_at(cm, g);
-          const int local = id - P.xa_base;
-          const int rb = local / P.KB;
-          power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
-        });
+    return;
   }
+  if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
+  for_flagged_ids(
+      cm.total_xa,
+      [&](int id) {
+        const Prob& P = prob_at(cm, find_prob(cm, id, 1));
+        return lv.rflag[P.tm_base + (id - P.xa_base) / P.KB] != 0;
+      },
+      [&](int id) {
+        const int g = find_prob(cm, id, 1);
+        const Prob& P = prob_at(cm, g);
+        const int local = id - P.xa_base;
+        const int rb = local / P.KB;
+        power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
+      });
 }
 
 // ----------------------------------------------------------- B images ---
@@ -318,23 +393,30 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
   }
   __syncthreads();
   uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
+  float v[4][EPC];
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int ch = threadIdx.x + PRO_THREADS * u;
     const int nr = ch >> 3, cc = ch & 7;
-    float v[EPC];
 #pragma unroll
-    for (int e = 0; e < EPC; ++e) v[e] = pow2k(stile[(cc * EPC + e) * 129 + nr], lv.plog) * opscale;
+    for (int e = 0; e < EPC; ++e) v[u][e] = stile[(cc * EPC + e) * 129 + nr];
+  }
+  power_all(v, lv.plog, opscale);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int ch = threadIdx.x + PRO_THREADS * u;
+    const int nr = ch >> 3, cc = ch & 7;
     uint4 hi, lo;
-    PK::pack(v, hi, lo);
+    PK::pack(v[u], hi, lo);
     const uint32_t off = sw128_offset(nr, cc * 16);
     *reinterpret_cast<uint4*>(dst + off) = hi;
     if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.b_plane + off) = lo;
   }
 }
 
-// Top level: one block per operand tile.  Lower levels: as for A, a tile is
-// rebuilt only if a pushed output tile needs its tile column.
+// Top level without a tensor map: one block per operand tile.  Lower levels:
+// as for A, a tile is rebuilt only if a pushed output tile needs its tile
+// column.
 template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_b(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
@@ -346,22 +428,211 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const int local = id - P.xb_base;
     const int rb = local / P.KB;
     power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
-  } else {
-    if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
-    const int per_tile = cm.BN / TILE_M;
-    for_flagged_ids(
-        cm.total_xb,
-        [&](int id) {
-          const Prob& P = prob_at(cm, find_prob(cm, id, 2));
-          return lv.cflag[P.tn_base + (id - P.xb_base) / P.KB / per_tile] != 0;
-        },
-        [&](int id) {
-          const int g = find_prob(cm, id, 2);
-          const Prob& P = prob_at(cm, g);
-          const int local = id - P.xb_base;
-          const int rb = local / P.KB;
-          power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
-        });
+    return;
+  }
+  if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
+  const int per_tile = cm.BN / TILE_M;
+  for_flagged_ids(
+      cm.total_xb,
+      [&](int id) {
+        const Prob& P = prob_at(cm, find_prob(cm, id, 2));
+        return lv.cflag[P.tn_base + (id - P.xb_base) / P.KB / per_tile] != 0;
+      },
+      [&](int id) {
+        const int g = find_prob(cm, id, 2);
+        const Prob& P = prob_at(cm, g);
+        const int local = id - P.xb_base;
+        const int rb = local / P.KB;
+        power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
+      });
+}
+
+// ------------------------------------------------ TMA top-level images ---
+// The top level of a single product builds every operand tile once.  One
+// persistent CTA per SM walks the tile ids blockIdx.x, blockIdx.x + gridDim.x,
+// ... and keeps the FP32 source tiles of its next NST tiles in flight in a
+// shared-memory ring: one thread issues a 2-D tensor copy per tile (an A tile
+// is 128 rows x BK values, a B tile BK rows x 128 values; the copy fills
+// zeros past M, N and K), completion counted in bytes on the stage's mbarrier,
+// while all warps power and pack the current tile.  A images leave with
+// coalesced 16-byte stores; B^T images are transposed into a double-buffered
+// shared 16 KB image and written with one bulk copy per tile.
+constexpr int TMA_THREADS = 512;
+
+template <int MODE, bool IS_B>
+struct TmaCfg {
+  static constexpr int BK = mode_bk(MODE);
+  static constexpr int ROWS = IS_B ? BK : TILE_M;  // source rows per tile
+  static constexpr int COLS = IS_B ? TILE_M : BK;  // source values per row
+  static constexpr int STAGE_BYTES = ROWS * COLS * 4;
+  static constexpr int PLANES = MODE == MODE_3XTF32 ? 2 : 1;
+  static constexpr int OUT_BYTES = IS_B ? 2 * PLANES * IMG_BYTES : 0;
+  static constexpr int RING_BUDGET = 200 * 1024 - OUT_BYTES;
+  static constexpr int NST = RING_BUDGET / STAGE_BYTES > 8 ? 8 : RING_BUDGET / STAGE_BYTES;
+  static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OUT_BYTES + 8 * NST + 16;
+  static_assert(NST >= 2, "ring too small");
+};
+
+// Q float4 chunks of a staged row starting at src, read in the rotated order
+// (q + rot) mod Q (so that the 8 threads of a quarter warp, rot = cc Q / 8,
+// hit distinct banks) and returned in natural order.
+template <int Q>
+__device__ __forceinline__ void lds_rotated(const float* src, int rot, float* v) {
+  float4 t[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) t[q] = *reinterpret_cast<const float4*>(src + 4 * ((q + rot) & (Q - 1)));
+#pragma unroll
+  for (int c = 0; c < Q; ++c) {
+    float4 x = t[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+      if (((q + rot) & (Q - 1)) == c) x = t[q];
+    v[4 * c] = x.x; v[4 * c + 1] = x.y; v[4 * c + 2] = x.z; v[4 * c + 3] = x.w;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst_smem, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst_smem),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int MODE, bool IS_B>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+    k_image_tma(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
+                const __grid_constant__ CUtensorMap map) {
+  using CF = TmaCfg<MODE, IS_B>;
+  using PK = Packer<MODE>;
+  constexpr int EPC = PK::EPC;
+  constexpr int BK = CF::BK, NST = CF::NST;
+  constexpr int U = 1024 / TMA_THREADS;  // 16-byte image chunks per thread and tile
+  extern __shared__ uint8_t smem_dyn[];
+  const uint32_t raw = smem_u32(smem_dyn);
+  uint8_t* smem = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
+  float* ring = reinterpret_cast<float*>(smem);
+  uint8_t* outimg = smem + NST * CF::STAGE_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(outimg + CF::OUT_BYTES);
+  volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(full + NST);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const Prob& P = cm.single;
+  const int total = IS_B ? cm.total_xb : cm.total_xa;
+  const int mine = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (mine == 0) return;  // uniform
+  if (tid == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // thread 0: the tensor copy of this CTA's j-th tile into stage j % NST
+  auto issue = [&](int j) {
+    const int id = (int)blockIdx.x + j * (int)gridDim.x;
+    const int rb = id / P.KB, kb = id - rb * P.KB;
+    uint64_t* bar = &full[j % NST];
+    mbar_arrive_expect_tx(bar, CF::STAGE_BYTES);
+    const uint32_t dst = smem_u32(ring) + (j % NST) * CF::STAGE_BYTES;
+    if constexpr (!IS_B)
+      tma_load_2d(dst, &map, kb * BK, rb * TILE_M, bar);
+    else
+      tma_load_2d(dst, &map, rb * TILE_M, kb * BK, bar);
+  };
+
+  // A: thread = image chunks (row (tid >> 3) + (128 / U) u, slot tid & 7).
+  // B: warp w = slot w & 7 of image rows nr = lane + 32 (U (w >> 3) + u),
+  // i.e. contraction indices (w & 7) EPC + e of column rb 128 + nr.
+  const int cc = IS_B ? (warp & 7) : (tid & 7);
+  auto line = [&](int u) {  // this thread's image row of chunk u
+    return IS_B ? lane + 32 * (U * (warp >> 3) + u) : (tid >> 3) + (TILE_M / U) * u;
+  };
+  // the maxima behind this thread's U row (A) or column (B) scales of tile
+  // j, loaded one tile ahead of their use
+  uint32_t pre[U];
+  auto prefetch = [&](int jj) {
+    const int rbj = ((int)blockIdx.x + jj * (int)gridDim.x) / P.KB;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = rbj * TILE_M + line(u);
+      pre[u] = idx < (IS_B ? P.N : P.M)
+                   ? scale_bits(cm, IS_B ? cm.cmax : cm.rmax, (IS_B ? P.rc_c : P.rc_r) + idx, 0,
+                                IS_B ? 1 : 0)
+                   : 0u;
+    }
+  };
+
+  const uint64_t tmo = cm.timeout_ns;
+  if (tid == 0)
+    for (int j = 0; j < NST && j < mine; ++j) issue(j);
+  prefetch(0);
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  int j = 0;
+  for (; j < mine; ++j) {
+    const int s = j % NST;
+    if (tid == 0 && !mbar_wait(&full[s], (j / NST) & 1, tmo, abort_flag)) {
+      *abort_flag = 1;
+      set_status(cm.status, PN_ETIMEOUT);
+    }
+    __syncthreads();  // also: the shared B image (j & 1) is free again
+    if (*abort_flag) break;
+    const int id = (int)blockIdx.x + j * (int)gridDim.x;
+    const int rb = id / P.KB, kb = id - rb * P.KB;
+    const float* st = ring + s * (CF::STAGE_BYTES / 4);
+    float sc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) sc[u] = scale_from_bits(cm, pre[u]);
+    if (j + 1 < mine) prefetch(j + 1);
+    float v[U][EPC];  // the copy filled zeros past M, N and K
+    if constexpr (!IS_B) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        lds_rotated<EPC / 4>(st + line(u) * BK + cc * EPC, (cc * (EPC / 4) / 8) & (EPC / 4 - 1),
+                             v[u]);
+      power_a_store<MODE, U>(cm, lv, P, rb, kb, v, sc);
+    } else {
+      uint8_t* ob = outimg + (j & 1) * CF::PLANES * IMG_BYTES;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int nr = line(u);
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) v[u][e] = st[(cc * EPC + e) * TILE_M + nr];
+        if (kb == 0 && cc == 0 && rb * TILE_M + nr < P.N) cm.c[P.rc_c + rb * TILE_M + nr] = sc[u];
+      }
+      div_scales(v, sc);
+      power_all(v, lv.plog, opscale);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int nr = line(u);
+        uint4 hi, lo;
+        PK::pack(v[u], hi, lo);
+        const uint32_t off = sw128_offset(nr, cc * 16);
+        *reinterpret_cast<uint4*>(ob + off) = hi;
+        if constexpr (CF::PLANES == 2) *reinterpret_cast<uint4*>(ob + IMG_BYTES + off) = lo;
+      }
+      fence_proxy_async_smem();
+    }
+    __syncthreads();  // stage s is consumed; the shared B image is complete
+    if (tid == 0) {
+      if constexpr (IS_B) {
+        uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
+        const uint32_t src = smem_u32(outimg + (j & 1) * CF::PLANES * IMG_BYTES);
+        bulk_s2g(dst, src, IMG_BYTES);
+        if constexpr (CF::PLANES == 2) bulk_s2g(dst + P.b_plane, src + IMG_BYTES, IMG_BYTES);
+        bulk_commit();
+        bulk_wait_read<1>();  // the image of tile j - 1 has been read out
+      }
+      if (j + NST < mine) issue(j + NST);
+    }
+  }
+  if (tid == 0) {
+    if (j < mine) {  // gave up: let the copies in flight land before exiting
+      int32_t never = 0;
+      const int last = mine < j + NST ? mine : j + NST;
+      for (int t = j; t < last; ++t) mbar_wait(&full[t % NST], (t / NST) & 1, tmo, &never);
+    }
+    if constexpr (IS_B) bulk_wait_all();
   }
 }
 
@@ -409,14 +680,93 @@ __global__ void k_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, i
   }
 }
 
+int sm_count();
+
 // Lower-level image grids: two waves of the resident blocks on every SM.
 int lower_grid(int total, int per_sm) {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-    sms = 152;
-  const int g = 2 * sms * per_sm;
+  const int g = 2 * sm_count() * per_sm;
   return total < g ? total : g;
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      return 152;
+  }
+  return sms;
+}
+
+template <int MODE, bool IS_B>
+int launch_tma_t(const Common& cm, const Level& lv, void* stream, const TensorMapBytes& map) {
+  using CF = TmaCfg<MODE, IS_B>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_image_tma<MODE, IS_B>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int total = IS_B ? cm.total_xb : cm.total_xa;
+  const int grid = total < sm_count() ? total : sm_count();
+  k_image_tma<MODE, IS_B><<<grid, TMA_THREADS, CF::SMEM, static_cast<cudaStream_t>(stream)>>>(
+      cm, lv, *reinterpret_cast<const CUtensorMap*>(&map));
+  return cudaGetLastError();
+}
+
+template <bool IS_B>
+int launch_tma(const Common& cm, const Level& lv, void* stream, const TensorMapBytes& map) {
+  switch (cm.mode) {
+    case MODE_3XTF32: return launch_tma_t<MODE_3XTF32, IS_B>(cm, lv, stream, map);
+    case MODE_TF32: return launch_tma_t<MODE_TF32, IS_B>(cm, lv, stream, map);
+    case MODE_BF16: return launch_tma_t<MODE_BF16, IS_B>(cm, lv, stream, map);
+    case MODE_F16: return launch_tma_t<MODE_F16, IS_B>(cm, lv, stream, map);
+    case MODE_E4M3: return launch_tma_t<MODE_E4M3, IS_B>(cm, lv, stream, map);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Row-major FP32 matrix of rows x cols with row pitch ld (elements) as a 2-D
+// tensor map with box box_rows x box_cols, zeros outside the matrix.
+bool encode_fp32_2d(TensorMapBytes& out, const float* base, int64_t rows, int64_t cols, int64_t ld,
+                    int box_rows, int box_cols) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base || rows < 1 || cols < 1 || ld < cols) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld & 3) != 0) return false;
+  if (rows > (int64_t(1) << 31) || cols > (int64_t(1) << 31) || ld * 4 >= (int64_t(1) << 40))
+    return false;
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 4};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(box_cols), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(reinterpret_cast<CUtensorMap*>(&out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+            const_cast<float*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int MODE>
@@ -449,8 +799,18 @@ int launch_maxes(const Common& cm, void* stream) {
   return cudaGetLastError();
 }
 
-int launch_power_a(const Common& cm, const Level& lv, void* stream) {
+void make_operand_maps(const Common& cm, OperandMaps& maps) {
+  std::memset(&maps, 0, sizeof(maps));
+  if (cm.nprob != 1) return;
+  const Prob& P = cm.single;
+  const int bk = mode_bk(cm.mode);
+  maps.has_a = encode_fp32_2d(maps.a, P.A, P.M, P.K, P.lda, TILE_M, bk) ? 1 : 0;
+  maps.has_b = encode_fp32_2d(maps.b, P.B, P.K, P.N, P.ldb, bk, TILE_M) ? 1 : 0;
+}
+
+int launch_power_a(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
   if (cm.total_xa <= 0) return 0;
+  if (lv.is_top && maps && maps->has_a) return launch_tma<false>(cm, lv, stream, maps->a);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto grid = [&](int per_sm) { return lv.is_top ? cm.total_xa : lower_grid(cm.total_xa, per_sm); };
   switch (cm.mode) {
@@ -474,8 +834,9 @@ int launch_power_a(const Common& cm, const Level& lv, void* stream) {
   return cudaGetLastError();
 }
 
-int launch_power_b(const Common& cm, const Level& lv, void* stream) {
+int launch_power_b(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
   if (cm.total_xb <= 0) return 0;
+  if (lv.is_top && maps && maps->has_b) return launch_tma<true>(cm, lv, stream, maps->b);
   switch (cm.mode) {
     case MODE_3XTF32: return launch_power_b_t<MODE_3XTF32>(cm, lv, stream);
     case MODE_TF32: return launch_power_b_t<MODE_TF32>(cm, lv, stream);
