@@ -8,7 +8,7 @@
 namespace pn {
 namespace gemm {
 
-constexpr int EPI_WARPS = 8;                       // two per TMEM lane quarter
+constexpr int EPI_WARPS = 8;                       // two groups, one warp per TMEM lane quarter each
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int GEMM_THREADS = 64 + EPI_THREADS;     // producer, MMA, epilogue
 constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
@@ -126,6 +126,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
   const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
   if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
+  // epilogue split (below): tile per warp group where the epilogue, not the
+  // MMA, bounds a tile (grouped problems, or short contractions)
+  const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) &&
+                       (cm.nprob > 1 || cm.single.KB * mode_planes(MODE) <= 32);
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(tmem_slot + 1);
-  volatile int32_t* ok_flag = abort_flag + 1;  // [2], epilogue item hand-off
+  volatile int32_t* ok_flag = abort_flag + 1;  // [4], epilogue item hand-off (2 per group)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -147,11 +151,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], EPI_THREADS);
+      mbar_init(&acc_empty[b], by_tile ? EPI_THREADS / 2 : EPI_THREADS);
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
-    ok_flag[0] = ok_flag[1] = 0;
+    ok_flag[0] = ok_flag[1] = ok_flag[2] = ok_flag[3] = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -280,32 +284,41 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------- epilogue ---
-    // Warp w may only read TMEM lanes 32*(w%4)..+31 (one output row each);
-    // the two warps of a lane quarter split the tile's columns in halves.
+    // Warp w may only read TMEM lanes 32*(w%4)..+31 (one output row each).
+    // With several tiles per CTA (by_tile) the epilogue warps form two groups
+    // of four, one warp per lane quarter each; group g finishes the tiles
+    // that use accumulator buffer g (every other tile), so two tiles'
+    // epilogues overlap their latencies.  With few tiles all eight warps
+    // finish every tile, the two warps of a lane quarter taking one half of
+    // the columns each, which shortens the last tile's epilogue.
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int half = ew >> 2;
-    const int et = threadIdx.x - 64;
-    constexpr int HCH = CHUNKS / 2;  // 32-column chunks per warp
+    const int grp = by_tile ? ew >> 2 : 0;
+    const int nch = by_tile ? CHUNKS : CHUNKS / 2;  // 32-column chunks per warp
+    const int ch0 = by_tile ? 0 : (ew >> 2) * nch;
+    const int gthreads = by_tile ? EPI_THREADS / 2 : EPI_THREADS;
+    const int et = (threadIdx.x - 64) & (gthreads - 1);  // thread of the group
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + ew * STG_BYTES);
-    int it = 0;
-    for (int idx = blockIdx.x; idx < count; idx += gridDim.x, ++it) {
+    const int step = by_tile ? 2 : 1;
+    int it = grp;
+    for (int idx = blockIdx.x + grp * gridDim.x; idx < count; idx += step * gridDim.x, it += step) {
       const int t = lv.is_top ? idx : lv.work[idx];
       const int g = find_prob(cm, t, 0);
       const Prob& P = prob_at(cm, g);
       int tm, tn;
       raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
       const int buf = it & 1;
+      const int okslot = 2 * grp + ((it >> 1) & 1);
       if (et == 0) {
         const bool ok = mbar_wait(&acc_full[buf], (it >> 1) & 1, tmo, abort_flag);
         if (!ok) {
           *abort_flag = 1;
           set_status(cm.status, PN_ETIMEOUT);
         }
-        ok_flag[buf] = ok ? 1 : 0;
+        ok_flag[okslot] = ok ? 1 : 0;
       }
-      bar_sync_named(1, EPI_THREADS);
-      if (!ok_flag[buf]) break;
+      bar_sync_named(1 + grp, gthreads);
+      if (!ok_flag[okslot]) break;
       tc_fence_after();
 
       const int i = tm * TILE_M + quarter * 32 + lane;
@@ -313,7 +326,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       // row scale: the p-norm epilogue, or the dA gradient (grad_axis 0)
       const bool use_rs = row_ok && (EPI == 0 || cm.grad_axis == 0);
       const float rs = use_rs ? cm.r[P.rc_r + i] : 0.0f;
-      const int ch0 = half * HCH;
       const int64_t st_idx = P.state_off + (int64_t)i * P.state_ld + tn * CHUNKS + ch0;
       const uint32_t* st_row = cm.state + st_idx;
       const float inv_p = __uint_as_float((127u - (uint32_t)lv.plog) << 23);  // 2^-plog
@@ -325,15 +337,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         corr_a = cm.coef[2 * lv.q];
         corr_b = cm.coef[2 * lv.q + 1];
       }
-      uint32_t res_all[HCH], pend_all[HCH];
+      uint32_t res_all[CHUNKS], pend_all[CHUNKS];
       bool any_left = false;
 #pragma unroll 1
-      for (int hc = 0; hc < HCH; ++hc) {
+      for (int hc = 0; hc < nch; ++hc) {
         const int ch = ch0 + hc;
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + ch * 32, v);
         tmem_ld_wait();
-        if (hc == HCH - 1) {
+        if (hc == nch - 1) {
           tc_fence_before();
           mbar_arrive(&acc_empty[buf]);
         }
@@ -557,17 +569,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         res_all[hc] = res;
       }
       if (EPI == 0 && !lv.is_bottom) {
-        const bool tile_left = bar_red_or(any_left, 2, EPI_THREADS);
+        const bool tile_left = bar_red_or(any_left, 3 + grp, gthreads);
         if (tile_left) {
           if (row_ok) {
             uint32_t* st_w = cm.state + st_idx;
 #pragma unroll
-            for (int hc = 0; hc < HCH; ++hc)
-              if (tn * BN + (ch0 + hc) * 32 < P.N) st_w[hc] = res_all[hc];
+            for (int hc = 0; hc < CHUNKS; ++hc)
+              if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) st_w[hc] = res_all[hc];
             if (cm.pend) {
 #pragma unroll
-              for (int hc = 0; hc < HCH; ++hc)
-                if (tn * BN + (ch0 + hc) * 32 < P.N) cm.pend[st_idx + hc] = pend_all[hc];
+              for (int hc = 0; hc < CHUNKS; ++hc)
+                if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) cm.pend[st_idx + hc] = pend_all[hc];
             }
           }
           if (et == 0) {
