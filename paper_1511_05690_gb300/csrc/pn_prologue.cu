@@ -53,37 +53,34 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
     const int rb = local / P.KMA, seg = local - rb * P.KMA;
     const int k0 = seg * MAXSEG_A;
     const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
+    const int seg_len = P.K - k0 < MAXSEG_A ? P.K - k0 : MAXSEG_A;  // values in this segment
     for (int rr = 0; rr < 16; ++rr) {
       const int row = rb * TILE_M + warp * 16 + rr;
+      if (row >= P.M) break;  // warp-uniform; later rows are past M too
       float m = 0.0f;
-      if (row < P.M) {
-        const float* src = P.A + (int64_t)row * P.lda;
-        if (vec && k0 + MAXSEG_A <= P.K) {
-          float4 t[MAXSEG_A / 128];
+      const float* src = P.A + (int64_t)row * P.lda;
+      if (vec && seg_len == MAXSEG_A) {
+        float4 t[MAXSEG_A / 128];
 #pragma unroll
-          for (int it = 0; it < MAXSEG_A / 128; ++it)
-            t[it] = __ldg(reinterpret_cast<const float4*>(src + k0 + it * 128 + lane * 4));
+        for (int it = 0; it < MAXSEG_A / 128; ++it)
+          t[it] = __ldg(reinterpret_cast<const float4*>(src + k0 + it * 128 + lane * 4));
 #pragma unroll
-          for (int it = 0; it < MAXSEG_A / 128; ++it) {
-            bad |= !in_domain(t[it].x) | !in_domain(t[it].y) | !in_domain(t[it].z) |
-                   !in_domain(t[it].w);
-            m = fmaxf(m, fmaxf(fmaxf(t[it].x, t[it].y), fmaxf(t[it].z, t[it].w)));
-          }
-        } else {
-          for (int kk = lane; kk < MAXSEG_A; kk += 32) {
-            const int k = k0 + kk;
-            if (k < P.K) {
-              const float x = __ldg(src + k);
-              bad |= !in_domain(x);
-              m = fmaxf(m, x);
-            }
-          }
+        for (int it = 0; it < MAXSEG_A / 128; ++it) {
+          bad |= !in_domain(t[it].x) | !in_domain(t[it].y) | !in_domain(t[it].z) |
+                 !in_domain(t[it].w);
+          m = fmaxf(m, fmaxf(fmaxf(t[it].x, t[it].y), fmaxf(t[it].z, t[it].w)));
+        }
+      } else {
+        for (int kk = lane; kk < seg_len; kk += 32) {
+          const float x = __ldg(src + k0 + kk);
+          bad |= !in_domain(x);
+          m = fmaxf(m, x);
         }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
       m = nonneg_bits_max(m);
-      if (lane == 0 && row < P.M && m > 0.0f)
+      if (lane == 0 && m > 0.0f)
         atomicMax(cm.rmax + P.rc_r + row, __float_as_uint(m));
       bmax = fmaxf(bmax, m);
     }

@@ -279,3 +279,42 @@ def test_pnorm_large_sampled_entries(pn, orc):
         assert np.all(Cs >= exact * (1 - tol))
         assert np.all(Cs <= exact * n ** (1.0 / 2.0 ** q) * (1 + tol))
         del C, psel
+
+
+# ------------------------------------------------- top-level image paths ---
+@pytest.mark.parametrize("mode", ["f32", "tf32", "bf16", "e4m3"])
+@pytest.mark.parametrize("shape", [(203, 261, 517), (128, 256, 64), (5, 1000, 33)])
+def test_tensor_copy_images_match_per_tile_images(pn, mode, shape):
+    """Operands whose rows are 16-byte aligned get their top-level images from
+    one 2-D tensor copy per tile (zeros past M, N, K); unaligned rows from the
+    per-tile kernels.  Both build the same bytes, so the same values stored with
+    a padded row pitch (aligned) and contiguously (odd pitch) give bit-identical
+    C, p_sel and S_sel -- across ragged M, N, K tails and several p levels."""
+    M, N, K = shape
+    g = workloads.rng(2700 + M)
+    # entries 0.025..0.05 with one 1 per row of A and per column of B: the
+    # products through a matching pair are 1, all others at most 0.05, so
+    # p* spreads over several levels
+    A = (0.05 * (0.5 + 0.5 * g.random((M, K)))).astype(np.float32)
+    B = (0.05 * (0.5 + 0.5 * g.random((K, N)))).astype(np.float32)
+    A[np.arange(M), np.arange(M) % K] = 1.0
+    B[(np.arange(N) + 1) % K, np.arange(N)] = 1.0
+    Ap = torch.zeros((M, K + (4 - K % 4) % 4 + 4), dtype=torch.float32, device="cuda")
+    Bp = torch.zeros((K, N + (4 - N % 4) % 4 + 4), dtype=torch.float32, device="cuda")
+    Ap[:, :K] = _dev(A)
+    Bp[:, :N] = _dev(B)
+    Av, Bv = Ap[:, :K], Bp[:, :N]
+    assert Av.stride(0) % 4 == 0 and Bv.stride(0) % 4 == 0
+    # odd pitch: every row but the first misaligned
+    Ao = torch.zeros((M, K + 1 + K % 2), dtype=torch.float32, device="cuda")[:, :K]
+    Bo = torch.zeros((K, N + 1 + N % 2), dtype=torch.float32, device="cuda")[:, :N]
+    Ao.copy_(Av)
+    Bo.copy_(Bv)
+    if M > 1:
+        assert Ao.stride(0) % 2 == 1
+    C1, p1, s1 = pn.maxprod_pnorm(Av, Bv, compute=mode)
+    C2, p2, s2 = pn.maxprod_pnorm(Ao, Bo, compute=mode)
+    assert torch.equal(p1, p2)
+    assert torch.equal(C1, C2)
+    assert torch.equal(s1, s2)
+    assert len(torch.unique(p1 & 0x7F)) >= 2  # several levels took part
