@@ -77,6 +77,14 @@ def _load():
             lib.orc_psums.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
             lib.orc_estimate.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, vp, vp, vp]
             lib.orc_estimate_ex.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, ci, vp, vp, vp]
+            lib.orc_estimate_ex2.argtypes = [i64, i64, ci, vp, vp, vp, vp, vp, dbl, ci, vp, vp,
+                                             vp]
+            lib.orc_psums_real.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
+            lib.orc_entries_real.argtypes = [i64, vp, i64, vp, i64, vp, vp, ci, vp, i64, vp, vp,
+                                             vp]
+            lib.orc_project_r2.argtypes = [dbl, dbl, dbl, dbl, dbl]
+            lib.orc_project_r2.restype = dbl
+            lib.orc_project_r2_batch.argtypes = [i64, vp, vp, vp, vp, dbl, vp]
             lib.orc_pnorm.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci,
                                       vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm.restype = ci
@@ -201,20 +209,63 @@ def psums(A, B, p_log2, r=None, c=None, scaling: int = 2):
     return S
 
 
-def estimate(S, p_log2, r, c, tau: float, estimator: int = 0):
+def estimate(S, p_log2, r, c, tau: float, estimator: int = 0, S34=None):
     """Largest stable p per entry; returns (Chat, p_sel, S_sel).  estimator 1
-    replaces the root by the r = 1 projection from S^(p*/2) and S^(p*)."""
+    replaces the root by the r = 1 projection from S^(p*/2) and S^(p*);
+    estimator 2 by the r = 2 projection, which also needs S34[q] = the sums
+    at 3 p_q / 4 (same shape as S)."""
     S = _f64(S)
     n_p, M, N = S.shape
     pl = _plog(p_log2)
     assert len(pl) == n_p
     r, c = _f64(r), _f64(c)
+    if estimator == 2:
+        S34 = _f64(S34)
+        assert S34.shape == S.shape
     Chat = np.empty((M, N), dtype=np.float64)
     psel = np.empty((M, N), dtype=np.uint8)
     Ssel = np.empty((M, N), dtype=np.float64)
-    _load().orc_estimate_ex(M, N, n_p, _p(pl), _p(S), _p(r), _p(c), float(tau), int(estimator),
-                            _p(Chat), _p(psel), _p(Ssel))
+    _load().orc_estimate_ex2(M, N, n_p, _p(pl), _p(S), _p(S34) if S34 is not None else None,
+                             _p(r), _p(c), float(tau), int(estimator), _p(Chat), _p(psel),
+                             _p(Ssel))
     return Chat, psel, Ssel
+
+
+def project_r2(s1, s2, s3, s4, p_prime: float):
+    """The r = 2 multiset projection (Sec. 2.1) of the four evenly spaced
+    power sums s_m = sum_i u_i^(m p'), elementwise over arrays (see oracle.c)."""
+    s1, s2, s3, s4 = np.broadcast_arrays(*(np.asarray(x, dtype=np.float64) for x in (s1, s2, s3, s4)))
+    s1, s2, s3, s4 = (np.ascontiguousarray(x).ravel() for x in (s1, s2, s3, s4))
+    out = np.empty(len(s1), dtype=np.float64)
+    _load().orc_project_r2_batch(len(s1), _p(s1), _p(s2), _p(s3), _p(s4), float(p_prime), _p(out))
+    return out
+
+
+def psums_real(A, B, powers, r, c):
+    """S[q] = sum_k (a_ik/r_i * b_kj/c_j)^powers[q] for real powers; (n_p, M, N)."""
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    _, N = B.shape
+    pw = _f64(np.asarray(powers, dtype=np.float64))
+    r, c = _f64(r), _f64(c)
+    S = np.empty((len(pw), M, N), dtype=np.float64)
+    _load().orc_psums_real(M, N, K, _p(A), K, _p(B), N, _p(r), _p(c), len(pw), _p(pw), _p(S))
+    return S
+
+
+def entries_real(A, B, ii, jj, powers, r, c):
+    """p-sums at real powers at the entries (ii[e], jj[e]); shape (n_e, n_p)."""
+    A, B = _f64(A), _f64(B)
+    M, K = A.shape
+    _, N = B.shape
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    pw = _f64(np.asarray(powers, dtype=np.float64))
+    r, c = _f64(r), _f64(c)
+    S = np.empty((len(ii), len(pw)), dtype=np.float64)
+    _load().orc_entries_real(K, _p(A), K, _p(B), N, _p(r), _p(c), len(pw), _p(pw), len(ii),
+                             _p(ii), _p(jj), _p(S))
+    return S
 
 
 def affine_fit(est, exact, cls, n_cls: int):
@@ -229,7 +280,8 @@ def affine_fit(est, exact, cls, n_cls: int):
 def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
           estimator: int = 0, correction: int = 0, fit_ij=None):
     """Full p-norm estimate of the (x,max) product (Alg. 5 with H = Alg. 3).
-    estimator 0 is the plain largest-stable-p norm, 1 the r = 1 projection.
+    estimator 0 is the plain largest-stable-p norm, 1 the r = 1 projection,
+    2 the r = 2 projection (with the sums at 3p/4, computed here).
     correction 1 divides by K^(1/p*); correction 2 fits the affine model of
     the Discussion on the sample entries fit_ij = (ii, jj) and applies it.
 
@@ -240,6 +292,8 @@ def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
     M, K = A.shape
     K2, N = B.shape
     assert K == K2
+    if estimator == 2 and correction == 2:
+        raise ValueError("the affine correction is defined for estimators 0 and 1")
     pl = _plog(p_log2)
     Chat = np.empty((M, N), dtype=np.float64)
     psel = np.empty((M, N), dtype=np.uint8)

@@ -26,6 +26,14 @@
  *     of the projection polynomial, (S^(2p') / S^(p'))^(1/p').  Entries
  *     whose p* / 2 is not in P (including p* = min P and unstable entries)
  *     keep the plain estimate.
+ *   - projection estimator r = 2 (Sec. 2.1 with r = 2, the estimator of the
+ *     paper's experiments): the four evenly spaced sums are taken at
+ *     p' = p* / 4, 2p', 3p', 4p' = p* (the 3p' sums form the extra family
+ *     1.5 * 2^k); the 2 x 3 Hankel matrix's null vector is the cross product
+ *     of its rows and the estimate the larger root of its quadratic, to the
+ *     power 1/p'.  Entries whose p* / 2 and p* / 4 are not the two p below
+ *     p* in P keep the plain estimate; nearly single-valued sums
+ *     (s1 s3 - s2^2 <= 1e-6 s2^2) keep the r = 1 value.
  *   - corrections (Sec. 2.1 bound remark; Discussion), in the scaled space
  *     where the exact value lies in (0, 1]: correction 1 divides the estimate
  *     by K^(1/p*), the upper end of its envelope; correction 2 fits
@@ -253,6 +261,27 @@ void orc_psums(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, co
   }
 }
 
+/* The same sums at arbitrary real exponents pw[q] (the 3p/4 family of the */
+/* r = 2 projection): S[q][i][j] = sum_k pow(a_ik / r_i * b_kj / c_j, pw[q]). */
+void orc_psums_real(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
+                    const double* B, int64_t ldb, const double* r, const double* c, int n_p,
+                    const double* pw, double* S) {
+  int64_t i;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (i = 0; i < M; ++i) {
+    for (int64_t j = 0; j < N; ++j) {
+      for (int q = 0; q < n_p; ++q) {
+        double s = 0.0;
+        for (int64_t k = 0; k < K; ++k) {
+          double u = (A[i * lda + k] / r[i]) * (B[k * ldb + j] / c[j]);
+          s += pow(u, pw[q]);
+        }
+        S[((int64_t)q * M + i) * N + j] = s;
+      }
+    }
+  }
+}
+
 /* Sec. 2.1, multiset projection with r = 1.  Given the two evenly spaced   */
 /* power sums s1 = ||u||_{p'}^{p'} and s2 = ||u||_{2p'}^{2p'}, the 1 x 2     */
 /* Hankel matrix [s1 s2] has the null vector gamma = (s2, -s1); the         */
@@ -265,6 +294,33 @@ static double project_r1(double s1, double s2, double p_prime) {
   return a > 0.0 ? pow(a, 1.0 / p_prime) : 0.0;
 }
 
+/* Sec. 2.1, multiset projection with r = 2.  Given the four evenly spaced  */
+/* power sums s_m = ||u||_{m p'}^{m p'}, m = 1..4, the 2 x 3 Hankel matrix   */
+/* [s1 s2 s3; s2 s3 s4] has the null vector gamma = (s2 s4 - s3^2,          */
+/* s2 s3 - s1 s4, s1 s3 - s2^2), the cross product of its two rows; the     */
+/* roots a of gamma_0 + gamma_1 a + gamma_2 a^2 are the two projected        */
+/* values alpha^p' and the estimate is the larger alpha = a^(1/p').          */
+/* Readings: when gamma_2 <= 1e-6 s2^2 (the sums are those of nearly a      */
+/* single value: s1 s3 >= s2^2 always) the r = 1 projection from s1, s2 is  */
+/* returned; a negative discriminant (rounding) counts as zero; a root      */
+/* that is not positive also gives the r = 1 value.                          */
+double orc_project_r2(double s1, double s2, double s3, double s4, double p_prime) {
+  double g0 = s2 * s4 - s3 * s3;
+  double g1 = s2 * s3 - s1 * s4;
+  double g2 = s1 * s3 - s2 * s2;
+  if (!(g2 > 1e-6 * s2 * s2)) return project_r1(s1, s2, p_prime);
+  double disc = g1 * g1 - 4.0 * g0 * g2;
+  if (disc < 0.0) disc = 0.0;
+  double a = (-g1 + sqrt(disc)) / (2.0 * g2);
+  return a > 0.0 ? pow(a, 1.0 / p_prime) : project_r1(s1, s2, p_prime);
+}
+
+/* orc_project_r2 over n quadruples (s1[e], s2[e], s3[e], s4[e]).            */
+void orc_project_r2_batch(int64_t n, const double* s1, const double* s2, const double* s3,
+                          const double* s4, double p_prime, double* out) {
+  for (int64_t e = 0; e < n; ++e) out[e] = orc_project_r2(s1[e], s2[e], s3[e], s4[e], p_prime);
+}
+
 /* Alg. 5, second loop, with estimateMaxFromNormPowerSequence:              */
 /* p* = largest p in P with S^(p) >= tau (the stable set is a prefix of P   */
 /* because S^(p) is non-increasing in p once every term is <= 1).           */
@@ -272,10 +328,14 @@ static double project_r1(double s1, double s2, double p_prime) {
 /* estimator 1 (projection r = 1): Chat = r_i * c_j *                      */
 /*   project_r1(S^(p* / 2), S^(p*), p* / 2)                                  */
 /* when p* / 2 is in P and p* is stable, else the plain form.                */
+/* estimator 2 (projection r = 2): Chat = r_i * c_j *                      */
+/*   orc_project_r2(S^(p* / 4), S^(p* / 2), S^(3 p* / 4), S^(p*), p* / 4)     */
+/* when p* / 2 and p* / 4 are the two p below p* in P and p* is stable,     */
+/* else the plain form; S34[q] holds the sums at 3 p_q / 4.                  */
 /* p_sel = log2(p*) | 0x80 if unstable; S_sel = S^(p*).                      */
-void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
-                     const double* r, const double* c, double tau, int estimator, double* Chat,
-                     uint8_t* psel, double* Ssel) {
+void orc_estimate_ex2(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
+                      const double* S34, const double* r, const double* c, double tau,
+                      int estimator, double* Chat, uint8_t* psel, double* Ssel) {
   int64_t i;
 #pragma omp parallel for schedule(static)
   for (i = 0; i < M; ++i) {
@@ -299,11 +359,24 @@ void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const dou
         double s_half = S[((int64_t)(q_sel - 1) * M + i) * N + j];
         est = project_r1(s_half, s, 0.5 * p);
       }
+      if (estimator == 2 && S34 && !unstable && q_sel > 1 &&
+          p_log2[q_sel - 1] == p_log2[q_sel] - 1 && p_log2[q_sel - 2] == p_log2[q_sel] - 2) {
+        double s2 = S[((int64_t)(q_sel - 1) * M + i) * N + j];
+        double s1 = S[((int64_t)(q_sel - 2) * M + i) * N + j];
+        double s3 = S34[((int64_t)q_sel * M + i) * N + j];
+        est = orc_project_r2(s1, s2, s3, s, 0.25 * p);
+      }
       if (Chat) Chat[i * N + j] = r[i] * c[j] * est;
       if (psel) psel[i * N + j] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
       if (Ssel) Ssel[i * N + j] = s;
     }
   }
+}
+
+void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
+                     const double* r, const double* c, double tau, int estimator, double* Chat,
+                     uint8_t* psel, double* Ssel) {
+  orc_estimate_ex2(M, N, n_p, p_log2, S, NULL, r, c, tau, estimator, Chat, psel, Ssel);
 }
 
 /* Discussion (affine model from a few exact sub-solutions): least squares  */
@@ -377,7 +450,17 @@ int orc_pnorm_ex(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, 
   orc_row_scales(M, K, A, lda, scaling, r);
   orc_col_scales(K, N, B, ldb, scaling, c);
   orc_psums(M, N, K, A, lda, B, ldb, r, c, n_p, p_log2, S);
-  orc_estimate_ex(M, N, n_p, p_log2, S, r, c, tau, estimator, Chat, psel, Ssel);
+  double* S34 = NULL;
+  if (estimator == 2) {
+    double* pw = (double*)malloc(sizeof(double) * (n_p > 0 ? n_p : 1));
+    S34 = (double*)malloc(sizeof(double) * (size_t)n_p * (M * N > 0 ? M * N : 1));
+    if (!pw || !S34) return -1;
+    for (int q = 0; q < n_p; ++q) pw[q] = 0.75 * ldexp(1.0, p_log2[q]);
+    orc_psums_real(M, N, K, A, lda, B, ldb, r, c, n_p, pw, S34);
+    free(pw);
+  }
+  orc_estimate_ex2(M, N, n_p, p_log2, S, S34, r, c, tau, estimator, Chat, psel, Ssel);
+  free(S34);
   if (r_out) memcpy(r_out, r, sizeof(double) * M);
   if (c_out) memcpy(c_out, c, sizeof(double) * N);
   free(r);
@@ -421,6 +504,26 @@ void orc_entries(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, 
         }
         S[e * n_p + q] = s;
       }
+    }
+  }
+}
+
+/* The p-sums at the entries (ii[e], jj[e]) for real exponents pw[q]:      */
+/* S[e * n_p + q] = sum_k pow(a_ik / r_i * b_kj / c_j, pw[q]).               */
+void orc_entries_real(int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      const double* r, const double* c, int n_p, const double* pw, int64_t n_e,
+                      const int64_t* ii, const int64_t* jj, double* S) {
+  int64_t e;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (e = 0; e < n_e; ++e) {
+    int64_t i = ii[e], j = jj[e];
+    for (int q = 0; q < n_p; ++q) {
+      double s = 0.0;
+      for (int64_t k = 0; k < K; ++k) {
+        double u = (A[i * lda + k] / r[i]) * (B[k * ldb + j] / c[j]);
+        s += pow(u, pw[q]);
+      }
+      S[e * n_p + q] = s;
     }
   }
 }

@@ -496,6 +496,84 @@ def test_projection_r1_fallbacks_to_plain(orc):
     np.testing.assert_array_equal(a["C"], b["C"])
 
 
+# ------------------------------------------------------ r = 2 projection ---
+# Sec. 2.1 with r = 2: the four evenly spaced sums at p*/4, p*/2, 3p*/4, p*
+# are the moments m_0..m_3 of the measure with mass w_i x_i at each value
+# x_i = u_i^(p*/4); the projection's two values are that measure's 2-point
+# Gauss nodes.  Hence the projection recovers any two-valued multiset
+# exactly, and its larger node lies between the 1-point node (the r = 1
+# estimate) and max u.
+@pytest.mark.parametrize("lp", [2, 3, 6])
+def test_projection_r2_recovers_two_valued_rows(orc, lp):
+    """u with exactly two distinct values: the r = 2 estimate is max u (the
+    r = 1 estimate is not, while the low value still carries weight)."""
+    pl = list(range(lp + 1))
+    for hi, n_hi, lo, n_lo in ((1.0, 1, 0.5, 7), (0.8, 3, 0.79, 40), (0.9, 2, 0.05, 900),
+                               (0.37, 5, 0.2, 1)):
+        u = [hi] * n_hi + [lo] * n_lo
+        est2, ps = _row_product(orc, u, pl, 2)
+        est1, _ = _row_product(orc, u, pl, 1)
+        assert ps == lp
+        np.testing.assert_allclose(est2, hi, rtol=1e-9)
+        if n_lo * (lo / hi) ** (2.0 ** lp / 2) > 1e-3 * n_hi:  # the low value still counts
+            assert abs(est1 - hi) > 1e-6 * hi
+
+
+def test_projection_r2_single_valued_rows_keep_r1(orc):
+    """One value: s1 s3 = s2^2, the degenerate reading returns the r = 1
+    projection, which is exact here."""
+    for beta, K in ((0.3, 7), (0.71, 40), (1.0, 3)):
+        c2, ps = _row_product(orc, [beta] * K, [0, 1, 2, 3, 4], 2)
+        assert ps == 4
+        np.testing.assert_allclose(c2, beta, rtol=1e-13)
+
+
+def test_projection_r2_between_r1_and_exact(orc):
+    """Every stable entry of a product: r1 <= r2 <= exact (node interlacing and
+    the nodes' support)."""
+    for seed, (M, N, K) in ((1640, (9, 11, 40)), (1641, (13, 7, 300)), (1642, (5, 6, 2000))):
+        A, B = workloads.wide_range_pair(M, N, K, seed=seed)
+        A, B = A.astype(np.float64), B.astype(np.float64)
+        exact = orc.maxprod(A, B)
+        tau = orc.default_tau(K, orc.F32_EXACT)
+        o1 = orc.pnorm(A, B, list(range(7)), tau=tau, estimator=1)
+        o2 = orc.pnorm(A, B, list(range(7)), tau=tau, estimator=2)
+        assert np.array_equal(o1["p_sel"], o2["p_sel"])
+        assert np.all(o2["C"] <= exact * (1 + 1e-12))
+        assert np.all(o2["C"] >= o1["C"] * (1 - 1e-12))
+        assert np.mean(o2["C"] > o1["C"] * (1 + 1e-9)) > 0.5
+
+
+def test_projection_r2_matches_general_construction(orc):
+    """The closed-form r = 2 (cross product of the Hankel rows) against the
+    oracle's SVD null-space construction on random rows."""
+    g = workloads.rng(1650)
+    for _ in range(30):
+        u = g.random(int(g.integers(3, 60)))
+        u = u / u.max()
+        pp = float(2 ** int(g.integers(0, 4)))
+        sums = [np.sum(u ** (m * pp)) for m in (1, 2, 3, 4)]
+        np.testing.assert_allclose(orc.project_r2(*sums, pp)[0], orc.project(sums, pp, 2)[-1],
+                                   rtol=1e-6)
+
+
+def test_projection_r2_fallbacks(orc):
+    """p*/4 not in P (non-consecutive P, p* among the two smallest p), or no
+    stable p: the plain estimate; the 3p/4 sums are the real-power sums."""
+    A, B = workloads.uniform_pair(6, 5, 30, seed=1660, dtype=np.float64)
+    for pl in ([0, 2, 5], [3], [0, 1]):
+        a = orc.pnorm(A, B, pl, tau=1e-300, estimator=0)
+        b = orc.pnorm(A, B, pl, tau=1e-300, estimator=2)
+        np.testing.assert_array_equal(a["C"], b["C"])
+    a = orc.pnorm(A, B, [0, 1, 2], tau=1e300, estimator=0)
+    b = orc.pnorm(A, B, [0, 1, 2], tau=1e300, estimator=2)
+    assert np.all(b["p_sel"] == 0x80)
+    np.testing.assert_array_equal(a["C"], b["C"])
+    r, c = orc.row_scales(A), orc.col_scales(B)
+    np.testing.assert_allclose(orc.psums_real(A, B, [1.0, 4.0], r, c), orc.psums(A, B, [0, 2], r, c),
+                               rtol=1e-14)
+
+
 # ----------------------------------------------------------- corrections ---
 # Sec. 2.1 (dividing by the envelope's upper end K^(1/p*)) and the Discussion
 # (an affine model fitted to a few exact sub-solutions), both applied in the
