@@ -53,8 +53,9 @@ def parse_args():
     ap.add_argument("--no-exact", action="store_true")
     ap.add_argument("--count", type=int, default=4096,
                     help="grouped workload: number of problems")
-    ap.add_argument("--estimator", type=int, default=0, choices=[0, 1],
-                    help="0: plain largest-stable-p norm; 1: r = 1 multiset projection")
+    ap.add_argument("--estimator", type=int, default=0, choices=[0, 1, 2],
+                    help="0: plain largest-stable-p norm; 1 / 2: r = 1 / r = 2 multiset "
+                         "projection")
     ap.add_argument("--correction", type=int, default=0, choices=[0, 1, 2],
                     help="1: divide by K^(1/p*); 2: affine model fitted on --n-fit exact samples")
     ap.add_argument("--n-fit", type=int, default=1024)
@@ -66,11 +67,18 @@ def parse_args():
 
 
 P_LOG2 = list(range(7))
-LAUNCHES_PER_STEP = 1 + 3 * len(P_LOG2)  # maxima + (A images, B images, GEMM) per level
+
+
+def launches_per_step(args):
+    """maxima + (A images, B images, GEMM) per level; the r = 2 projection adds
+    a level at 3p/4 below every p whose p/2 and p/4 are in P; the affine
+    correction its two fit kernels."""
+    levels = len(P_LOG2) + (len(P_LOG2) - 2 if args.estimator == 2 else 0)
+    return 1 + 3 * levels + (2 if args.correction == 2 else 0)
 
 
 def workload_name(n, compute, estimator=0, correction=0, n_fit=0):
-    est = "" if estimator == 0 else " r=1 projection estimator;"
+    est = "" if estimator == 0 else f" r={estimator} projection estimator;"
     if correction == 1:
         est += " estimate / K^(1/p*);"
     elif correction == 2:
@@ -325,8 +333,16 @@ def run_ours(args):
             tau = oracle.default_tau(n, {"f32": 0, "tf32": 1, "bf16": 2, "f16": 3,
                                          "e4m3": 4}[args.compute])
             rc = r[ii] * c[jj]
+            S34 = None
+            if args.estimator == 2:
+                S34 = oracle.entries_real(A64, B_h.astype(np.float64), loc, jj,
+                                          [0.75 * 2.0 ** lp for lp in P_LOG2], r[rows], c)
+                S34 = S34.T[:, None, :]
+            # the r = 2 projection's resolution margin: 32 u of the operand format
+            r2_eta = 32 * {"f32": 2.0 ** -21, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8,
+                           "f16": 2.0 ** -11, "e4m3": 2.0 ** -4}[args.compute]
             pn_ref, ps_o, _ = oracle.estimate(S.T[:, None, :], P_LOG2, np.ones(1), rc, tau,
-                                              estimator=args.estimator)
+                                              estimator=args.estimator, S34=S34, r2_eta=r2_eta)
             coef = None
             if args.correction == 2:
                 frows = np.unique(fit_ii)
@@ -412,7 +428,7 @@ def run_ours(args):
                      "launch_ms": gemm_avg,
                      "peak_source": f"{peak_src} bf16_tflops_sustained x format ratio"},
         "clocks": clk,
-        "gpu_launches": LAUNCHES_PER_STEP * K,
+        "gpu_launches": launches_per_step(args) * K,
         "err": err,
         "exact_kernel": exact_info,
     }

@@ -117,14 +117,28 @@ typedef struct pn_opts {
    *       p*, about one more tensor-core pass in total.  maxprod_pnorm,
    *       maxprod_pnorm_static and the grouped call accept it (the grouped
    *       table is built for one value); apsp_pnorm and
-   *       maxprod_pnorm_backward return PN_EUNSUPPORTED for 1. */
+   *       maxprod_pnorm_backward return PN_EUNSUPPORTED for 1;
+   *   2 = multiset projection with r = 2 (the estimator of the paper's
+   *       experiments) from the four evenly spaced sums s_m at m p* / 4,
+   *       m = 1..4: the larger root a of gamma_0 + gamma_1 a + gamma_2 a^2,
+   *       gamma = (s2 s4 - s3^2, s2 s3 - s1 s4, s1 s3 - s2^2), to the power
+   *       4/p*; it never exceeds the exact max and never falls below the
+   *       r = 1 value.  The sums at 3p* / 4 come from extra levels
+   *       p = 1.5 * 2^k; entries whose p* / 2 and p* / 4 are not the two p
+   *       below p* in P (and unstable entries) keep the plain estimate, sums
+   *       of nearly one value (s1 s3 - s2^2 <= 1e-6 s2^2) the r = 1 value.
+   *       About three more tensor-core passes over every tile holding an
+   *       entry resolved at p*; the workspace grows by 2 M N floats.
+   *       maxprod_pnorm and maxprod_pnorm_static accept it; the grouped
+   *       call, apsp_pnorm and maxprod_pnorm_backward return PN_EUNSUPPORTED,
+   *       and it excludes correction 2 (PN_EINVAL). */
   int32_t estimator;
   /* Bias correction of the estimate, applied per entry in the scaled space
    * (value / (r_i c_j), where the exact result lies in (0, 1]):
    *   0 (default) = none;
    *   1 = divide by K^(1/p*), the upper end of the plain estimate's envelope
    *       (Sec. 2.1): the worst-case relative error becomes 1 - K^(-1/p*)
-   *       (plain estimator only; with estimator 1 PN_EINVAL);
+   *       (plain estimator only; with estimator 1 or 2 PN_EINVAL);
    *   2 = affine model fitted to a few exact sub-solutions (Discussion): at
    *       the n_fit sample entries (fit_i[s], fit_j[s]) the library computes
    *       the exact max and the estimate directly, fits exact = a_q est + b_q

@@ -112,7 +112,8 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
                   debug_flags=0, estimator=0, correction=0, fit_i=None, fit_j=None,
                   fit_coef=None):
     """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None).
-    estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*).
+    estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*);
+    2: r = 2 projection from the sums at p*/4, p*/2, 3p*/4 and p* (Sec. 2.1).
     correction 1: divide by K^(1/p*); 2: affine model per p* class fitted to the
     exact values at the sample entries (fit_i, fit_j) (int32 CUDA tensors);
     fit_coef (float32 CUDA tensor of 2 * len(p_log2)) receives (a_q, b_q)."""

@@ -56,9 +56,10 @@ bool opts_valid(const pn_opts* o) {
   if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256) return false;
   if (o->timeout_ns < 0) return false;
   if (std::isnan(o->tau)) return false;
-  if (o->estimator < 0 || o->estimator > 1) return false;
+  if (o->estimator < 0 || o->estimator > 2) return false;
   if (o->correction < 0 || o->correction > 2) return false;
   if (o->correction == 1 && o->estimator != 0) return false;
+  if (o->correction == 2 && o->estimator == 2) return false;
   if (o->correction == 2 && (o->n_fit < 1 || !o->fit_i || !o->fit_j)) return false;
   return true;
 }
@@ -85,12 +86,12 @@ float tau_up(double t) {
 // Workspace layout of one product (single problem).
 struct Layout {
   int BN = 0, KB = 0, RBA = 0, RBB = 0, tiles_m = 0, tiles_n = 0, total_tiles = 0;
-  int state_ld = 0, n_p = 0, planes = 1;
+  int state_ld = 0, n_p = 0, n_slots = 0, planes = 1;
   size_t off_fit = 0, off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0,
          off_cflag = 0;
   size_t ctrl_bytes = 0, off_coef = 0;
-  size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_aimg = 0,
-         off_bimg = 0;
+  size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_pend2 = 0,
+         off_park = 0, off_aimg = 0, off_bimg = 0;
   size_t a_level_bytes = 0, b_level_bytes = 0, a_plane = 0, b_plane = 0;
   size_t total = 0;
 };
@@ -100,6 +101,7 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   const int mode = o->compute;
   L.BN = choose_bn(o, M, N, K);
   L.n_p = o->n_p;
+  L.n_slots = make_schedule(o).n;
   L.planes = mode_planes(mode);
   L.KB = static_cast<int>(ceil_div(K, mode_bk(mode)));
   L.tiles_m = static_cast<int>(ceil_div(M, TILE_M));
@@ -115,18 +117,23 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.off_rmax = off; off += sizeof(uint32_t) * M;
   L.off_cmax = off; off += sizeof(uint32_t) * N;
   L.off_gmax = off; off += sizeof(uint32_t) * 2;
-  L.off_counts = off; off += sizeof(int32_t) * PN_MAX_P;
-  L.off_rflag = off; off += static_cast<size_t>(L.n_p) * L.tiles_m;
-  L.off_cflag = off; off += static_cast<size_t>(L.n_p) * L.tiles_n;
+  L.off_counts = off; off += sizeof(int32_t) * 2 * PN_MAX_P;
+  L.off_rflag = off; off += static_cast<size_t>(L.n_slots) * L.tiles_m;
+  L.off_cflag = off; off += static_cast<size_t>(L.n_slots) * L.tiles_n;
   L.ctrl_bytes = align_up(off, 16);
   off = align_up(off, WS_ALIGN);
   L.off_coef = off; off = align_up(off + sizeof(float) * 2 * PN_MAX_P, WS_ALIGN);
   L.off_r = off; off = align_up(off + sizeof(float) * M, WS_ALIGN);
   L.off_c = off; off = align_up(off + sizeof(float) * N, WS_ALIGN);
-  L.off_work = off; off = align_up(off + sizeof(int32_t) * L.n_p * (size_t)L.total_tiles, WS_ALIGN);
+  L.off_work = off;
+  off = align_up(off + sizeof(int32_t) * L.n_slots * (size_t)L.total_tiles, WS_ALIGN);
   L.off_state = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
-  if (o->estimator == 1) {
+  if (o->estimator >= 1) {
     L.off_pend = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
+  }
+  if (o->estimator == 2) {
+    L.off_pend2 = off; off = align_up(off + sizeof(uint32_t) * (size_t)M * L.state_ld, IMG_ALIGN);
+    L.off_park = off; off = align_up(off + sizeof(float) * 2 * (size_t)M * N, IMG_ALIGN);
   }
   L.a_plane = static_cast<size_t>(L.RBA) * L.KB * IMG_BYTES;
   L.b_plane = static_cast<size_t>(L.RBB) * L.KB * IMG_BYTES;
@@ -214,7 +221,15 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.r = reinterpret_cast<float*>(ws + L.off_r);
   cm.c = reinterpret_cast<float*>(ws + L.off_c);
   cm.state = reinterpret_cast<uint32_t*>(ws + L.off_state);
-  cm.pend = o->estimator == 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
+  cm.pend = o->estimator >= 1 ? reinterpret_cast<uint32_t*>(ws + L.off_pend) : nullptr;
+  cm.pend2 = o->estimator == 2 ? reinterpret_cast<uint32_t*>(ws + L.off_pend2) : nullptr;
+  cm.park = o->estimator == 2 ? reinterpret_cast<float*>(ws + L.off_park) : nullptr;
+  // r = 2 projection: its Hankel determinant must clear the p-sums' relative
+  // error (of order u, the powered operands' unit roundoff) by a margin
+  cm.r2_eta = std::ldexp(1.0f, 5 - (o->compute == PN_F32_EXACT ? 21
+                                    : o->compute == PN_BF16     ? 8
+                                    : o->compute == PN_E4M3     ? 4
+                                                                : 11));
   cm.corr = o->correction;
   cm.coef = reinterpret_cast<const float*>(ws + L.off_coef);
   cm.status = o->dev_status;
@@ -229,31 +244,44 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   cm.fp64_near = (o->compute == PN_F32_EXACT || o->compute == PN_TF32 || o->compute == PN_BF16);
 }
 
-// Level q of the p family (q = n_p-1 is the largest p).
-Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, int q) {
+// Slot t of the level schedule (slot 0 is the largest p).
+Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, const Schedule& sc, int t) {
   Level lv;
   std::memset(&lv, 0, sizeof(lv));
-  const int top = o->n_p - 1;
   int32_t* counts = reinterpret_cast<int32_t*>(ws + L.off_counts);
   int32_t* work = reinterpret_cast<int32_t*>(ws + L.off_work);
   uint8_t* rflag = ws + L.off_rflag;
   uint8_t* cflag = ws + L.off_cflag;
-  const int qn = q > 0 ? q - 1 : 0;
+  const int q = sc.q[t];
+  const int tn = t + 1 < sc.n ? t + 1 : t;
   lv.q = q;
-  lv.plog = o->p_log2[q];
-  lv.is_top = q == top;
-  lv.is_bottom = q == 0;
+  lv.half = sc.half[t];
+  lv.plog = o->p_log2[q] - lv.half;  // a half level's p is 1.5 * 2^(log2 p_q - 1)
+  lv.is_top = t == 0;
+  lv.is_bottom = t == sc.n - 1;
   lv.a_level = ws + L.off_aimg;
   lv.b_level = ws + L.off_bimg;
-  lv.work = work + static_cast<size_t>(q) * L.total_tiles;
-  lv.work_count = counts + q;
-  lv.next_work = work + static_cast<size_t>(qn) * L.total_tiles;
-  lv.next_count = counts + qn;
-  lv.rflag = rflag + static_cast<size_t>(q) * L.tiles_m;
-  lv.cflag = cflag + static_cast<size_t>(q) * L.tiles_n;
-  lv.next_rflag = rflag + static_cast<size_t>(qn) * L.tiles_m;
-  lv.next_cflag = cflag + static_cast<size_t>(qn) * L.tiles_n;
-  set_projection(lv, o, q);
+  lv.work = work + static_cast<size_t>(t) * L.total_tiles;
+  lv.work_count = counts + t;
+  lv.next_work = work + static_cast<size_t>(tn) * L.total_tiles;
+  lv.next_count = counts + tn;
+  lv.rflag = rflag + static_cast<size_t>(t) * L.tiles_m;
+  lv.cflag = cflag + static_cast<size_t>(t) * L.tiles_n;
+  lv.next_rflag = rflag + static_cast<size_t>(tn) * L.tiles_m;
+  lv.next_cflag = cflag + static_cast<size_t>(tn) * L.tiles_n;
+  if (o->estimator == 2) {
+    lv.r2_state = t > 0;
+    lv.r2_new = !lv.half && t + 1 < sc.n && sc.half[t + 1];
+    if (lv.r2_new && t + 2 < sc.n) {
+      const int ts = t + 2;
+      lv.skip_work = work + static_cast<size_t>(ts) * L.total_tiles;
+      lv.skip_count = counts + ts;
+      lv.skip_rflag = rflag + static_cast<size_t>(ts) * L.tiles_m;
+      lv.skip_cflag = cflag + static_cast<size_t>(ts) * L.tiles_n;
+    }
+  } else {
+    set_projection(lv, o, q);
+  }
   return lv;
 }
 
@@ -273,8 +301,9 @@ pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
   if ((e = launch_maxes(cm, stream))) return PN_ECUDA;
   OperandMaps maps;
   make_operand_maps(cm, maps);
-  for (int q = o->n_p - 1; q >= 0; --q) {
-    const Level lv = make_level(L, o, ws, q);
+  const Schedule sc = make_schedule(o);
+  for (int t = 0; t < sc.n; ++t) {
+    const Level lv = make_level(L, o, ws, sc, t);
     if ((e = launch_power_a(cm, lv, stream, &maps))) return PN_ECUDA;
     if ((e = launch_power_b(cm, lv, stream, &maps))) return PN_ECUDA;
     if (lv.is_top && o->correction == 2) {

@@ -103,6 +103,50 @@ __device__ __forceinline__ void warp_store_u8(uint32_t* stg, const uint32_t (&w)
   __syncwarp();
 }
 
+// r = 2 projection (Sec. 2.1) of the sums s_m = S^(m p'), m = 1..4, returned
+// as alpha^p': the larger root of gamma_0 + gamma_1 a + gamma_2 a^2 with
+// gamma = (s2 s4 - s3^2, s2 s3 - s1 s4, s1 s3 - s2^2), the cross product of
+// the Hankel rows [s1 s2 s3] and [s2 s3 s4].  Computed in FP32 on the sums
+// normalised by lam = s2 / s1 (t_m = s_m / (s1 lam^(m-1)), so t1 = t2 = 1
+// and every term is O(1)): a = lam * b with b the larger root of
+// (t4 - t3^2) + (t3 - t4) b + (t3 - 1) b^2.  The roots are the 2-point Gauss
+// nodes of the measure with moments s1..s4, so the larger lies between the
+// r = 1 value lam and the plain norm s4^(1/4); it is clamped there (never
+// binding for exact sums, bounding the effect of rounded ones).  Sums that
+// do not resolve a second value (gamma_2 <= eta s2^2, i.e. t3 - 1 <= eta) or
+// a root that is not positive give lam; a negative discriminant counts as 0.
+__device__ __forceinline__ float r2_project(float s1, float s2, float s3, float s4, float eta) {
+  const float lam = s2 / s1;
+  const float q = s1 / s2;
+  const float t3 = (s3 / s2) * q;
+  const float t4 = (s4 / s2) * q * q;
+  const float g2 = t3 - 1.0f;
+  if (!(g2 > eta)) return lam;
+  const float g1 = t3 - t4;
+  const float g0 = fmaf(-t3, t3, t4);
+  const float disc = fmaxf(fmaf(g1, g1, -4.0f * g0 * g2), 0.0f);
+  const float b = (sqrtf(disc) - g1) / (2.0f * g2);
+  if (!(b > 0.0f)) return lam;
+  return fminf(fmaxf(lam * b, lam), sqrtf(sqrtf(s4)));
+}
+
+// Stores x[e] at dst[e] for the entries e of mask (four at a time with one
+// 16-byte store when all four are set and vec).
+__device__ __forceinline__ void store_masked(float* dst, const float (&x)[32], uint32_t mask,
+                                             bool vec) {
+#pragma unroll
+  for (int e0 = 0; e0 < 32; e0 += 4) {
+    const uint32_t m4 = (mask >> e0) & 0xfu;
+    if (m4 == 0xfu && vec) {
+      *reinterpret_cast<float4*>(dst + e0) = make_float4(x[e0], x[e0 + 1], x[e0 + 2], x[e0 + 3]);
+    } else if (m4) {
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if ((m4 >> h) & 1u) dst[e0 + h] = x[e0 + h];
+    }
+  }
+}
+
 // EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
 // lists).  EPI 1: gradient epilogue of the adjoint, out (+)= acc * x'^(p-1) / s
 // with x the source element at the output position and s its row (grad_axis
@@ -337,8 +381,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         corr_a = cm.coef[2 * lv.q];
         corr_b = cm.coef[2 * lv.q + 1];
       }
-      uint32_t res_all[CHUNKS], pend_all[CHUNKS];
+      uint32_t res_all[CHUNKS], pend_all[CHUNKS], pend2_all[CHUNKS];
       bool any_left = false;
+      bool new_chain = false;  // r = 2: an entry of the tile resolved here
 #pragma unroll 1
       for (int hc = 0; hc < nch; ++hc) {
         const int ch = ch0 + hc;
@@ -352,6 +397,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
         pend_all[hc] = 0;
+        pend2_all[hc] = 0;
         if constexpr (EPI == 1) {
           if (row_ok && j0 < P.N) {
             const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
@@ -425,7 +471,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             near |= (x[e] < 10.0f * P.tau ? 1u : 0u) << e;
           }
           const uint32_t open = inrange & ~res;
-          const uint32_t cand = lv.is_bottom ? open : (open & stable);
+          // a half level (r = 2) resolves nothing: its p is not in P
+          const uint32_t cand = lv.half ? 0u : lv.is_bottom ? open : (open & stable);
           any_left |= (open & ~cand) != 0u;
           near &= cand & (cm.fp64_near ? 0xffffffffu : 0u);
           float* crow = P.C + (int64_t)i * P.ldc + j0;
@@ -491,6 +538,89 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             any_left |= cand != 0u;  // their S^(p/2) comes from the next level
             pend_all[hc] = cand;
           }
+          // r = 2 projection (Sec. 2.1): entries resolved at p* wait, in stages
+          // 1..3, for S^(3p*/4) (half level), S^(p*/2) and S^(p*/4); C keeps
+          // S^(p*), the two middle sums are parked in the workspace
+          if (lv.r2_state || lv.r2_new) {
+            uint32_t b0 = 0, b1 = 0;
+            if (lv.r2_state && row_ok) {
+              b0 = cm.pend[st_idx + hc];
+              b1 = cm.pend2[st_idx + hc];
+            }
+            if (b0 | b1) {
+              float* xs3 = cm.park + (int64_t)i * P.N + j0;  // S^(3p*/4)
+              float* xs2 = xs3 + (int64_t)P.M * P.N;         // S^(p*/2)
+              if (lv.half) {
+                const uint32_t w1 = b0 & ~b1;
+                store_masked(xs3, x, w1, P.vec_c);
+                b0 &= ~w1;
+                b1 |= w1;
+              } else {
+                const uint32_t w2 = b1 & ~b0, w3 = b0 & b1;
+                store_masked(xs2, x, w2, P.vec_c);
+                if (w3) {
+                  // this level's S is S^(p'), p' = p*/4: finish the projection
+                  const float* cs = cm.c + P.rc_c + j0;
+#pragma unroll
+                  for (int e0 = 0; e0 < 32; e0 += 4) {
+                    const uint32_t m4 = (w3 >> e0) & 0xfu;
+                    if (m4 == 0u) continue;
+                    float y2[4], y3[4], y4[4], cv[4];
+                    if (m4 == 0xfu && P.vec_c) {
+                      const float4 a2 = *reinterpret_cast<const float4*>(xs2 + e0);
+                      const float4 a3 = *reinterpret_cast<const float4*>(xs3 + e0);
+                      const float4 a4 = *reinterpret_cast<const float4*>(crow + e0);
+                      const float4 c4 = __ldg(reinterpret_cast<const float4*>(cs + e0));
+                      y2[0] = a2.x; y2[1] = a2.y; y2[2] = a2.z; y2[3] = a2.w;
+                      y3[0] = a3.x; y3[1] = a3.y; y3[2] = a3.z; y3[3] = a3.w;
+                      y4[0] = a4.x; y4[1] = a4.y; y4[2] = a4.z; y4[3] = a4.w;
+                      cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
+                    } else {
+#pragma unroll
+                      for (int h = 0; h < 4; ++h) {
+                        const bool on = (m4 >> h) & 1u;
+                        y2[h] = on ? xs2[e0 + h] : 1.0f;
+                        y3[h] = on ? xs3[e0 + h] : 1.0f;
+                        y4[h] = on ? crow[e0 + h] : 1.0f;
+                        cv[h] = on ? __ldg(cs + e0 + h) : 0.0f;
+                      }
+                    }
+                    float y[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                      y[h] = r2_project(x[e0 + h], y2[h], y3[h], y4[h], cm.r2_eta);
+                    if constexpr (MODE == MODE_3XTF32) {
+                      for (int s2i = 0; s2i < lv.plog; ++s2i) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) y[h] = sqrtf(y[h]);
+                      }
+                    } else if (lv.plog > 0) {
+#pragma unroll
+                      for (int h = 0; h < 4; ++h) y[h] = ex2_approx(lg2_approx(y[h]) * inv_p);
+                    }
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) y[h] *= rs * cv[h];
+                    if (m4 == 0xfu && P.vec_c) {
+                      *reinterpret_cast<float4*>(crow + e0) = make_float4(y[0], y[1], y[2], y[3]);
+                    } else {
+#pragma unroll
+                      for (int h = 0; h < 4; ++h)
+                        if ((m4 >> h) & 1u) crow[e0 + h] = y[h];
+                    }
+                  }
+                }
+                b0 = (b0 | w2) & ~w3;
+                b1 &= ~w3;
+              }
+            }
+            if (lv.r2_new) {
+              b0 |= cand;  // stage 1: their S^(3p*/4) comes next
+              new_chain |= cand != 0u;
+            }
+            pend_all[hc] = b0;
+            pend2_all[hc] = b1;
+            any_left |= (b0 | b1) != 0u;
+          }
           if (__any_sync(0xffffffffu, cand != 0u)) {
             const uint32_t pbits = lv.plog * 0x01010101u;
             uint32_t pw[8];
@@ -505,8 +635,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             // S_sel before x is overwritten by the root
             if (P.Ssel)
               warp_store_f32(stg, x, cand, P.Ssel + ibase * P.ldaux + j0, P.ldaux, P.vec_c, lane);
-            // r = 1 projection with a level p/2 below: C keeps S^(p) until then
-            if (!lv.proj_next) {
+            // a projection still to come (r = 1: level p/2 below; r = 2: the
+            // chain down to p/4): C keeps S^(p) until then
+            if (!lv.proj_next && !lv.r2_new) {
               if constexpr (MODE == MODE_3XTF32) {
                 // FP32-accurate mode: (S^(p))^(1/p) for p = 2^plog as plog correctly
                 // rounded square roots (about one ulp in total); repeated APSP
@@ -581,12 +712,20 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               for (int hc = 0; hc < CHUNKS; ++hc)
                 if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) cm.pend[st_idx + hc] = pend_all[hc];
             }
+            if (cm.pend2) {
+#pragma unroll
+              for (int hc = 0; hc < CHUNKS; ++hc)
+                if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) cm.pend2[st_idx + hc] = pend2_all[hc];
+            }
           }
+          // r = 2: a tile that starts no chain here skips the half level
+          const bool skip = lv.skip_work && !bar_red_or(new_chain, 3 + grp, gthreads);
           if (et == 0) {
-            const int slot = atomicAdd(lv.next_count, 1);
-            lv.next_work[slot] = t;
-            lv.next_rflag[P.tm_base + tm] = 1;
-            lv.next_cflag[P.tn_base + tn] = 1;
+            int32_t* cnt = skip ? lv.skip_count : lv.next_count;
+            const int slot = atomicAdd(cnt, 1);
+            (skip ? lv.skip_work : lv.next_work)[slot] = t;
+            (skip ? lv.skip_rflag : lv.next_rflag)[P.tm_base + tm] = 1;
+            (skip ? lv.skip_cflag : lv.next_cflag)[P.tn_base + tn] = 1;
           }
         }
       }

@@ -376,6 +376,7 @@ pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_table,
   const pn_status st = check_group(host_table, dev_table, opts, ws, ws_bytes, &H);
   if (st != PN_OK) return st;
   if (opts->correction == 2) return PN_EUNSUPPORTED;  // sample entries index one product
+  if (opts->estimator == 2) return PN_EUNSUPPORTED;
   const int sms = host_device_sms();
   if (sms <= 0) return PN_EUNSUPPORTED;
   int l;
@@ -402,7 +403,7 @@ pn_status pn_grouped_autotune(const void* host_table, const void* dev_table, con
   const GroupHeader* H = nullptr;
   pn_status st = check_group(host_table, dev_table, opts, ws, ws_bytes, &H);
   if (st != PN_OK) return st;
-  if (opts->correction == 2) return PN_EUNSUPPORTED;
+  if (opts->correction == 2 || opts->estimator == 2) return PN_EUNSUPPORTED;
   const int sms = host_device_sms();
   if (sms <= 0) return PN_EUNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

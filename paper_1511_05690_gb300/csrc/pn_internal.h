@@ -78,7 +78,11 @@ struct Common {
   float* c;           // column scales
   uint32_t* state;    // resolved-entry bits of tiles that go to a lower level
   uint32_t* pend;     // r = 1 projection: bits of entries resolved at the level
-                      // above whose C holds S^(2p) (same layout as state), or null
+                      // above whose C holds S^(2p) (same layout as state), or null;
+                      // r = 2 projection: bit 0 of each entry's pending stage
+  uint32_t* pend2;    // r = 2 projection: bit 1 of the pending stage, or null
+  float* park;        // r = 2 projection: S^(3p*/4) (M x N), then S^(p*/2) (M x N)
+  float r2_eta;       // r = 2 projection: resolution margin, 32 u of the operand format
   int32_t* status;
   uint64_t timeout_ns;
   int32_t debug_flags;
@@ -123,7 +127,44 @@ struct Level {
   const uint32_t* pmask;      // gradient launches: bit q set if some entry has p* = P[q]
   int32_t proj_here;          // r = 1 projection: finish entries resolved at 2p (the level above)
   int32_t proj_next;          // r = 1 projection: the next level is p/2; park S^(p) of new entries
+  // r = 2 projection.  A pending entry's 2-bit stage s (planes pend, pend2)
+  // names the sum it waits for: 1 = S^(3p*/4), 2 = S^(p*/2), 3 = S^(p*/4).
+  int32_t half;               // extra level p = 1.5 * 2^plog (= 3p/4 of the level above): no
+                              // entry resolves here, stage-1 entries park S^(p)
+  int32_t r2_new;             // entries resolving here start a chain (C keeps S^(p*), stage 1)
+  int32_t r2_state;           // pending stages are read and written at this level
+  // With r2_new the next slot is the half level 3p/4, which only entries
+  // resolved here need: tiles that start no chain skip it and go to the
+  // slot after it (the next p of P) through these lists.
+  int32_t* skip_work;
+  int32_t* skip_count;
+  uint8_t* skip_rflag;
+  uint8_t* skip_cflag;
 };
+
+// The level schedule: every p of P from the largest down, each followed --
+// for the r = 2 projection (estimator 2) -- by an extra "half" level at
+// 3p/4 when p/2 and p/4 are the two p below it in P.  Slot t runs level
+// (q[t], half[t]); its work list, counts and flags are slot t's.
+struct Schedule {
+  int n;
+  int8_t q[2 * PN_MAX_P];
+  int8_t half[2 * PN_MAX_P];
+};
+inline Schedule make_schedule(const pn_opts* o) {
+  Schedule s;
+  s.n = 0;
+  for (int q = o->n_p - 1; q >= 0; --q) {
+    s.q[s.n] = static_cast<int8_t>(q);
+    s.half[s.n++] = 0;
+    if (o->estimator == 2 && q >= 2 && o->p_log2[q - 1] == o->p_log2[q] - 1 &&
+        o->p_log2[q - 2] == o->p_log2[q] - 2) {
+      s.q[s.n] = static_cast<int8_t>(q);
+      s.half[s.n++] = 1;
+    }
+  }
+  return s;
+}
 
 // One operand image of the adjoint (maxprod_pnorm_backward).
 //   kind 0: (src / scale)^p with one scale per contraction index

@@ -180,16 +180,23 @@ __device__ __forceinline__ void div_scales(float (&v)[U][EPC], const float (&s)[
   }
 }
 
-// v <- v^(2^plog) * opscale, the squarings of all U x EPC values interleaved
-// (independent chains; the same products as pow2k value by value).
+// v <- v^p * opscale with p = 2^plog, or p = 1.5 * 2^plog for a half level
+// (y * sqrt(y), y = v^(2^plog)); the squarings of all U x EPC values
+// interleaved (independent chains; the same products as pow2k value by value).
 template <int U, int EPC>
-__device__ __forceinline__ void power_all(float (&v)[U][EPC], int plog, float opscale) {
+__device__ __forceinline__ void power_all(float (&v)[U][EPC], int plog, int half, float opscale) {
 #pragma unroll 1
   for (int t = 0; t < plog; ++t) {
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int e = 0; e < EPC; ++e) v[u][e] *= v[u][e];
+  }
+  if (half) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int e = 0; e < EPC; ++e) v[u][e] *= sqrtf(v[u][e]);
   }
 #pragma unroll
   for (int u = 0; u < U; ++u)
@@ -220,7 +227,7 @@ __device__ __forceinline__ void power_a_store(const Common& cm, const Level& lv,
     }
   }
   div_scales(v, rs);
-  power_all(v, lv.plog, opscale);
+  power_all(v, lv.plog, lv.half, opscale);
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int rr = (threadIdx.x >> 3) + RSTEP * u;
@@ -398,7 +405,7 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
 #pragma unroll
     for (int e = 0; e < EPC; ++e) v[u][e] = stile[(cc * EPC + e) * 129 + nr];
   }
-  power_all(v, lv.plog, opscale);
+  power_all(v, lv.plog, lv.half, opscale);
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int ch = threadIdx.x + PRO_THREADS * u;
@@ -598,7 +605,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         if (kb == 0 && cc == 0 && rb * TILE_M + nr < P.N) cm.c[P.rc_c + rb * TILE_M + nr] = sc[u];
       }
       div_scales(v, sc);
-      power_all(v, lv.plog, opscale);
+      power_all(v, lv.plog, lv.half, opscale);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int nr = line(u);

@@ -83,7 +83,16 @@ def test_workspace_sizes(binding):
     oproj = binding.make_opts(compute="bf16", estimator=1)
     s1p = lib.pn_workspace_size(1000, 1000, 1000, ctypes.byref(oproj))
     assert s1 + 1000 * 1024 // 8 <= s1p <= s1 + 1000 * 1024 // 8 + 4096
-    bad = binding.make_opts(estimator=2)
+    # the r = 2 projection: two words of stage per 32 entries, two parked sums
+    # per entry (2 M N floats) and the extra half levels' work lists
+    o2 = binding.make_opts(compute="bf16", estimator=2)
+    s2p = lib.pn_workspace_size(1000, 1000, 1000, ctypes.byref(o2))
+    assert s1p + 1000 * 1024 // 8 + 8 * 1000 * 1000 <= s2p <= s1p + 1000 * 1024 // 8 + 8 * 1000 * 1000 + 65536
+    bad = binding.make_opts(estimator=3)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    bad = binding.make_opts(estimator=2, correction=2, n_fit=4, fit_i=16, fit_j=16)
+    assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
+    bad = binding.make_opts(estimator=2, correction=1)
     assert lib.pn_workspace_size(10, 10, 10, ctypes.byref(bad)) == 0
     # corrections: division only with the plain estimator; the affine model
     # needs its sample entries

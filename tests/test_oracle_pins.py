@@ -557,6 +557,25 @@ def test_projection_r2_matches_general_construction(orc):
                                    rtol=1e-6)
 
 
+def test_projection_r2_guard_and_clamp(orc):
+    """A margin eta above s1 s3 / s2^2 - 1 gives the r = 1 value; perturbed sums
+    (up to 5 %, no longer a moment sequence) still give a value between the
+    r = 1 value and the plain norm, the interval of the larger Gauss node."""
+    g = workloads.rng(1670)
+    for _ in range(200):
+        u = g.random(int(g.integers(2, 40)))
+        u = u / u.max()
+        pp = 4.0
+        s = np.array([np.sum(u ** (m * pp)) for m in (1, 2, 3, 4)])
+        t = s[2] * s[0] / s[1] ** 2 - 1
+        r1 = (s[1] / s[0]) ** (1 / pp)
+        np.testing.assert_allclose(orc.project_r2(*s, pp, eta=t * 1.01)[0], r1, rtol=1e-14)
+        sp = s * (1 + 0.05 * g.uniform(-1, 1, 4))
+        v = orc.project_r2(*sp, pp)[0]
+        lo, hi = (sp[1] / sp[0]) ** (1 / pp), sp[3] ** (1 / (4 * pp))
+        assert min(lo, hi) * (1 - 1e-12) <= v <= max(hi, lo) * (1 + 1e-12)
+
+
 def test_projection_r2_fallbacks(orc):
     """p*/4 not in P (non-consecutive P, p* among the two smallest p), or no
     stable p: the plain estimate; the 3p/4 sums are the real-power sums."""
