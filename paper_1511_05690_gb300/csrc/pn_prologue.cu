@@ -462,6 +462,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
 // coalesced 16-byte stores; B^T images are transposed into a double-buffered
 // shared 16 KB image and written with one bulk copy per tile.
 constexpr int TMA_THREADS = 512;
+constexpr int TMA_MAX_OWNED = 4096;  // tiles per CTA the tensor-copy kernel takes
 
 template <int MODE, bool IS_B>
 struct TmaCfg {
@@ -523,18 +524,48 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const Prob& P = cm.single;
   const int total = IS_B ? cm.total_xb : cm.total_xa;
-  const int mine = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  if (mine == 0) return;  // uniform
+  const int owned = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (owned == 0) return;  // uniform
+  if (!lv.is_top && *lv.work_count == 0) return;  // no tile pushed to this level (uniform)
+  // This CTA's tiles: ids blockIdx.x + k * gridDim.x, k < owned; below the top
+  // level only those whose row block (A) or tile column (B) is flagged,
+  // compacted into tile_k[] (the launcher bounds owned by TMA_MAX_OWNED).
+  __shared__ int32_t tile_k[TMA_MAX_OWNED];
+  __shared__ int32_t n_tiles;
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
     *abort_flag = 0;
+    n_tiles = 0;
     fence_barrier_init();
   }
   __syncthreads();
+  if (lv.is_top) {
+    for (int k = tid; k < owned; k += TMA_THREADS) tile_k[k] = k;
+    if (tid == 0) n_tiles = owned;
+  } else {
+    const int per_tile = cm.BN / TILE_M;
+    for (int k0 = 0; k0 < owned; k0 += TMA_THREADS) {
+      const int k = k0 + tid;
+      bool need = false;
+      if (k < owned) {
+        const int rb = ((int)blockIdx.x + k * (int)gridDim.x) / P.KB;
+        need = IS_B ? lv.cflag[rb / per_tile] != 0 : lv.rflag[rb] != 0;
+      }
+      const uint32_t bal = __ballot_sync(0xffffffffu, need);
+      int base = 0;
+      if (lane == 0 && bal) base = atomicAdd(&n_tiles, __popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (need) tile_k[base + __popc(bal & ((1u << lane) - 1u))] = k;
+      __syncthreads();  // n_tiles complete before the next round's adds are read
+    }
+  }
+  __syncthreads();
+  const int mine = n_tiles;
+  if (mine == 0) return;  // uniform
 
   // thread 0: the tensor copy of this CTA's j-th tile into stage j % NST
   auto issue = [&](int j) {
-    const int id = (int)blockIdx.x + j * (int)gridDim.x;
+    const int id = (int)blockIdx.x + tile_k[j] * (int)gridDim.x;
     const int rb = id / P.KB, kb = id - rb * P.KB;
     uint64_t* bar = &full[j % NST];
     mbar_arrive_expect_tx(bar, CF::STAGE_BYTES);
@@ -556,7 +587,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
   // j, loaded one tile ahead of their use
   uint32_t pre[U];
   auto prefetch = [&](int jj) {
-    const int rbj = ((int)blockIdx.x + jj * (int)gridDim.x) / P.KB;
+    const int rbj = ((int)blockIdx.x + tile_k[jj] * (int)gridDim.x) / P.KB;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int idx = rbj * TILE_M + line(u);
@@ -581,7 +612,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     }
     __syncthreads();  // also: the shared B image (j & 1) is free again
     if (*abort_flag) break;
-    const int id = (int)blockIdx.x + j * (int)gridDim.x;
+    const int id = (int)blockIdx.x + tile_k[j] * (int)gridDim.x;
     const int rb = id / P.KB, kb = id - rb * P.KB;
     const float* st = ring + s * (CF::STAGE_BYTES / 4);
     float sc[U];
@@ -602,7 +633,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
         const int nr = line(u);
 #pragma unroll
         for (int e = 0; e < EPC; ++e) v[u][e] = st[(cc * EPC + e) * TILE_M + nr];
-        if (kb == 0 && cc == 0 && rb * TILE_M + nr < P.N) cm.c[P.rc_c + rb * TILE_M + nr] = sc[u];
+        if (lv.is_top && kb == 0 && cc == 0 && rb * TILE_M + nr < P.N)
+          cm.c[P.rc_c + rb * TILE_M + nr] = sc[u];
       }
       div_scales(v, sc);
       power_all(v, lv.plog, lv.half, opscale);
@@ -722,6 +754,9 @@ int launch_tma_t(const Common& cm, const Level& lv, void* stream, const TensorMa
   return cudaGetLastError();
 }
 
+// The tensor-copy kernel takes at most TMA_MAX_OWNED tiles per CTA.
+bool tma_fits(int total) { return total <= TMA_MAX_OWNED * sm_count(); }
+
 template <bool IS_B>
 int launch_tma(const Common& cm, const Level& lv, void* stream, const TensorMapBytes& map) {
   switch (cm.mode) {
@@ -814,7 +849,7 @@ void make_operand_maps(const Common& cm, OperandMaps& maps) {
 
 int launch_power_a(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
   if (cm.total_xa <= 0) return 0;
-  if (lv.is_top && maps && maps->has_a) return launch_tma<false>(cm, lv, stream, maps->a);
+  if (maps && maps->has_a && tma_fits(cm.total_xa)) return launch_tma<false>(cm, lv, stream, maps->a);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto grid = [&](int per_sm) { return lv.is_top ? cm.total_xa : lower_grid(cm.total_xa, per_sm); };
   switch (cm.mode) {
@@ -840,7 +875,7 @@ int launch_power_a(const Common& cm, const Level& lv, void* stream, const Operan
 
 int launch_power_b(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
   if (cm.total_xb <= 0) return 0;
-  if (lv.is_top && maps && maps->has_b) return launch_tma<true>(cm, lv, stream, maps->b);
+  if (maps && maps->has_b && tma_fits(cm.total_xb)) return launch_tma<true>(cm, lv, stream, maps->b);
   switch (cm.mode) {
     case MODE_3XTF32: return launch_power_b_t<MODE_3XTF32>(cm, lv, stream);
     case MODE_TF32: return launch_power_b_t<MODE_TF32>(cm, lv, stream);
