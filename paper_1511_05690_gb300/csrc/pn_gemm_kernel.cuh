@@ -103,6 +103,17 @@ __device__ __forceinline__ void warp_store_u8(uint32_t* stg, const uint32_t (&w)
   __syncwarp();
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // r = 2 projection (Sec. 2.1) of the sums s_m = S^(m p'), m = 1..4, returned
 // as alpha^p': the larger root of gamma_0 + gamma_1 a + gamma_2 a^2 with
 // gamma = (s2 s4 - s3^2, s2 s3 - s1 s4, s1 s3 - s2^2), the cross product of
@@ -115,36 +126,63 @@ __device__ __forceinline__ void warp_store_u8(uint32_t* stg, const uint32_t (&w)
 // binding for exact sums, bounding the effect of rounded ones).  Sums that
 // do not resolve a second value (gamma_2 <= eta s2^2, i.e. t3 - 1 <= eta) or
 // a root that is not positive give lam; a negative discriminant counts as 0.
+// Reciprocals and square roots are the hardware approximations (about one
+// ulp): the sums' own errors are orders of magnitude larger.
 __device__ __forceinline__ float r2_project(float s1, float s2, float s3, float s4, float eta) {
-  const float lam = s2 / s1;
-  const float q = s1 / s2;
-  const float t3 = (s3 / s2) * q;
-  const float t4 = (s4 / s2) * q * q;
+  const float i1 = rcp_approx(s1), i2 = rcp_approx(s2);
+  const float lam = s2 * i1;
+  const float q = s1 * i2;
+  const float t3 = (s3 * i2) * q;
+  const float t4 = (s4 * i2) * q * q;
   const float g2 = t3 - 1.0f;
   if (!(g2 > eta)) return lam;
   const float g1 = t3 - t4;
   const float g0 = fmaf(-t3, t3, t4);
   const float disc = fmaxf(fmaf(g1, g1, -4.0f * g0 * g2), 0.0f);
-  const float b = (sqrtf(disc) - g1) / (2.0f * g2);
+  const float b = (sqrt_approx(disc) - g1) * rcp_approx(2.0f * g2);
   if (!(b > 0.0f)) return lam;
-  return fminf(fmaxf(lam * b, lam), sqrtf(sqrtf(s4)));
+  return fminf(fmaxf(lam * b, lam), sqrt_approx(sqrt_approx(s4)));
 }
 
-// Stores x[e] at dst[e] for the entries e of mask (four at a time with one
-// 16-byte store when all four are set and vec).
-__device__ __forceinline__ void store_masked(float* dst, const float (&x)[32], uint32_t mask,
-                                             bool vec) {
+// Finishes the r = 2 projection for the entries w3 of a warp's 32 x 32 block
+// (lane l holds row l: x = this level's S^(p*/4), rs its row scale): the
+// block is staged in stg and walked row by row, lane l taking column l, so
+// that the three parked sums are read and C is written as whole 128-byte
+// rows.  Row r's sums: S^(p*/2) at s2row + r ldp, S^(3p*/4) at s3row + r ldp,
+// S^(p*) in C at crow + r ldc; cs_lane is column l's scale.  The root is
+// plog correctly rounded square roots (FP32-accurate mode) or 2^(log2(a) / p').
+// Called by the whole warp.
+template <bool SQRT_ROOT>
+__device__ __forceinline__ void r2_finish_block(float* stg, const float (&x)[32], uint32_t w3,
+                                                float rs, const float* s2row, const float* s3row,
+                                                int64_t ldp, float* crow, int64_t ldc,
+                                                float cs_lane, float eta, int plog, float inv_p,
+                                                int lane) {
 #pragma unroll
-  for (int e0 = 0; e0 < 32; e0 += 4) {
-    const uint32_t m4 = (mask >> e0) & 0xfu;
-    if (m4 == 0xfu && vec) {
-      *reinterpret_cast<float4*>(dst + e0) = make_float4(x[e0], x[e0 + 1], x[e0 + 2], x[e0 + 3]);
-    } else if (m4) {
-#pragma unroll
-      for (int h = 0; h < 4; ++h)
-        if ((m4 >> h) & 1u) dst[e0 + h] = x[e0 + h];
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(stg + lane * 32 + ((g ^ (lane & 7)) << 2)) =
+        make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
+  __syncwarp();
+#pragma unroll 4
+  for (int r = 0; r < 32; ++r) {
+    const uint32_t m = __shfl_sync(0xffffffffu, w3, r);
+    const float rsr = __shfl_sync(0xffffffffu, rs, r);
+    if (m == 0u) continue;
+    if ((m >> lane) & 1u) {
+      const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+      const float s2 = __ldg(s2row + r * ldp + lane);  // parked at earlier levels
+      const float s3 = __ldg(s3row + r * ldp + lane);
+      float* c = crow + r * ldc + lane;
+      float a = r2_project(s1, s2, s3, *c, eta);
+      if constexpr (SQRT_ROOT) {
+        for (int t = 0; t < plog; ++t) a = sqrtf(a);
+      } else if (plog > 0) {
+        a = ex2_approx(lg2_approx(a) * inv_p);
+      }
+      *c = a * rsr * cs_lane;
     }
   }
+  __syncwarp();
 }
 
 // EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
@@ -547,71 +585,29 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               b0 = cm.pend[st_idx + hc];
               b1 = cm.pend2[st_idx + hc];
             }
-            if (b0 | b1) {
-              float* xs3 = cm.park + (int64_t)i * P.N + j0;  // S^(3p*/4)
-              float* xs2 = xs3 + (int64_t)P.M * P.N;         // S^(p*/2)
-              if (lv.half) {
-                const uint32_t w1 = b0 & ~b1;
-                store_masked(xs3, x, w1, P.vec_c);
-                b0 &= ~w1;
-                b1 |= w1;
-              } else {
-                const uint32_t w2 = b1 & ~b0, w3 = b0 & b1;
-                store_masked(xs2, x, w2, P.vec_c);
-                if (w3) {
-                  // this level's S is S^(p'), p' = p*/4: finish the projection
-                  const float* cs = cm.c + P.rc_c + j0;
-#pragma unroll
-                  for (int e0 = 0; e0 < 32; e0 += 4) {
-                    const uint32_t m4 = (w3 >> e0) & 0xfu;
-                    if (m4 == 0u) continue;
-                    float y2[4], y3[4], y4[4], cv[4];
-                    if (m4 == 0xfu && P.vec_c) {
-                      const float4 a2 = *reinterpret_cast<const float4*>(xs2 + e0);
-                      const float4 a3 = *reinterpret_cast<const float4*>(xs3 + e0);
-                      const float4 a4 = *reinterpret_cast<const float4*>(crow + e0);
-                      const float4 c4 = __ldg(reinterpret_cast<const float4*>(cs + e0));
-                      y2[0] = a2.x; y2[1] = a2.y; y2[2] = a2.z; y2[3] = a2.w;
-                      y3[0] = a3.x; y3[1] = a3.y; y3[2] = a3.z; y3[3] = a3.w;
-                      y4[0] = a4.x; y4[1] = a4.y; y4[2] = a4.z; y4[3] = a4.w;
-                      cv[0] = c4.x; cv[1] = c4.y; cv[2] = c4.z; cv[3] = c4.w;
-                    } else {
-#pragma unroll
-                      for (int h = 0; h < 4; ++h) {
-                        const bool on = (m4 >> h) & 1u;
-                        y2[h] = on ? xs2[e0 + h] : 1.0f;
-                        y3[h] = on ? xs3[e0 + h] : 1.0f;
-                        y4[h] = on ? crow[e0 + h] : 1.0f;
-                        cv[h] = on ? __ldg(cs + e0 + h) : 0.0f;
-                      }
-                    }
-                    float y[4];
-#pragma unroll
-                    for (int h = 0; h < 4; ++h)
-                      y[h] = r2_project(x[e0 + h], y2[h], y3[h], y4[h], cm.r2_eta);
-                    if constexpr (MODE == MODE_3XTF32) {
-                      for (int s2i = 0; s2i < lv.plog; ++s2i) {
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) y[h] = sqrtf(y[h]);
-                      }
-                    } else if (lv.plog > 0) {
-#pragma unroll
-                      for (int h = 0; h < 4; ++h) y[h] = ex2_approx(lg2_approx(y[h]) * inv_p);
-                    }
-#pragma unroll
-                    for (int h = 0; h < 4; ++h) y[h] *= rs * cv[h];
-                    if (m4 == 0xfu && P.vec_c) {
-                      *reinterpret_cast<float4*>(crow + e0) = make_float4(y[0], y[1], y[2], y[3]);
-                    } else {
-#pragma unroll
-                      for (int h = 0; h < 4; ++h)
-                        if ((m4 >> h) & 1u) crow[e0 + h] = y[h];
-                    }
-                  }
-                }
-                b0 = (b0 | w2) & ~w3;
-                b1 &= ~w3;
+            // rows of this warp's block in the parked arrays and in C
+            const int64_t ibr = (int64_t)tm * TILE_M + quarter * 32;
+            float* park3 = cm.park + ibr * P.N + j0;        // S^(3p*/4)
+            float* park2 = park3 + (int64_t)P.M * P.N;      // S^(p*/2)
+            if (lv.half) {
+              const uint32_t w1 = b0 & ~b1;
+              if (__any_sync(0xffffffffu, w1 != 0u))
+                warp_store_f32(stg, x, w1, park3, P.N, P.vec_c, lane);
+              b0 &= ~w1;
+              b1 |= w1;
+            } else if (lv.r2_state) {
+              const uint32_t w2 = b1 & ~b0, w3 = b0 & b1;
+              if (__any_sync(0xffffffffu, w2 != 0u))
+                warp_store_f32(stg, x, w2, park2, P.N, P.vec_c, lane);
+              if (__any_sync(0xffffffffu, w3 != 0u)) {
+                // this level's S is S^(p'), p' = p*/4: finish the projection
+                const float cs_lane = lane < P.N - j0 ? __ldg(cm.c + P.rc_c + j0 + lane) : 0.0f;
+                r2_finish_block<MODE == MODE_3XTF32>(stg, x, w3, rs, park2, park3, P.N,
+                                                     P.C + ibr * P.ldc + j0, P.ldc, cs_lane,
+                                                     cm.r2_eta, lv.plog, inv_p, lane);
               }
+              b0 = (b0 | w2) & ~w3;
+              b1 &= ~w3;
             }
             if (lv.r2_new) {
               b0 |= cand;  // stage 1: their S^(3p*/4) comes next
