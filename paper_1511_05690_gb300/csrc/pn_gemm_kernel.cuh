@@ -185,6 +185,45 @@ __device__ __forceinline__ void r2_finish_block(float* stg, const float (&x)[32]
   __syncwarp();
 }
 
+// Finishes the r = 1 projection for the entries `pend` of a warp's 32 x 32
+// block (lane l holds row l: x = this level's S^(p), rs its row scale; C
+// holds S^(2p) of these entries): (S^(2p) / S^(p))^(1/p), the ratio clamped
+// to <= 1 (S is non-increasing in p), then the affine line (pa, pb) when
+// `affine`, the scales, and the write-back to C -- row by row, lane l on
+// column l, so that C is read and written as 128-byte rows.  Called by the
+// whole warp.
+template <bool SQRT_ROOT>
+__device__ __forceinline__ void r1_finish_block(float* stg, const float (&x)[32], uint32_t pend,
+                                                float rs, float* crow, int64_t ldc, float cs_lane,
+                                                int plog, float inv_p, bool affine, float pa,
+                                                float pb, int lane) {
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(stg + lane * 32 + ((g ^ (lane & 7)) << 2)) =
+        make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
+  __syncwarp();
+#pragma unroll 4
+  for (int r = 0; r < 32; ++r) {
+    const uint32_t m = __shfl_sync(0xffffffffu, pend, r);
+    const float rsr = __shfl_sync(0xffffffffu, rs, r);
+    if (m == 0u) continue;
+    if ((m >> lane) & 1u) {
+      const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+      float* c = crow + r * ldc + lane;
+      const float s2 = *c;
+      float y = s2 / fmaxf(s1, s2);
+      if constexpr (SQRT_ROOT) {
+        for (int t = 0; t < plog; ++t) y = sqrtf(y);
+      } else if (plog > 0) {
+        y = ex2_approx(lg2_approx(y) * inv_p);
+      }
+      if (affine) y = fmaf(pa, y, pb);
+      *c = y * (rsr * cs_lane);
+    }
+  }
+  __syncwarp();
+}
+
 // EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
 // lists).  EPI 1: gradient epilogue of the adjoint, out (+)= acc * x'^(p-1) / s
 // with x the source element at the output position and s its row (grad_axis
@@ -513,64 +552,19 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           const uint32_t cand = lv.half ? 0u : lv.is_bottom ? open : (open & stable);
           any_left |= (open & ~cand) != 0u;
           near &= cand & (cm.fp64_near ? 0xffffffffu : 0u);
-          float* crow = P.C + (int64_t)i * P.ldc + j0;
           // r = 1 projection (Sec. 2.1): entries resolved at 2p hold S^(2p) in C;
           // with S^(p) from this level the estimate is (S^(2p) / S^(p))^(1/p).
           // The ratio is clamped to <= 1 (S is non-increasing in p).
           const uint32_t pend = lv.proj_here && row_ok ? cm.pend[st_idx + hc] : 0u;
-          if (pend) {
-            // eight entries at a time (two float4 when the whole chunk is pending)
-            const float* cs = cm.c + P.rc_c + j0;
-            const bool pvec = pend == 0xffffffffu && P.vec_c;
-#pragma unroll
-            for (int e0 = 0; e0 < 32; e0 += 8) {
-              if (((pend >> e0) & 0xffu) == 0u) continue;
-              float y[8], cv[8];
-              if (pvec) {
-#pragma unroll
-                for (int h = 0; h < 8; h += 4) {
-                  const float4 s4 = *reinterpret_cast<const float4*>(crow + e0 + h);
-                  const float4 c4 = __ldg(reinterpret_cast<const float4*>(cs + e0 + h));
-                  y[h] = s4.x; y[h + 1] = s4.y; y[h + 2] = s4.z; y[h + 3] = s4.w;
-                  cv[h] = c4.x; cv[h + 1] = c4.y; cv[h + 2] = c4.z; cv[h + 3] = c4.w;
-                }
-              } else {
-#pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                  const bool pe = (pend >> (e0 + h)) & 1u;
-                  y[h] = pe ? crow[e0 + h] : 1.0f;
-                  cv[h] = pe ? __ldg(cs + e0 + h) : 0.0f;
-                }
-              }
-#pragma unroll
-              for (int h = 0; h < 8; ++h) y[h] = y[h] / fmaxf(x[e0 + h], y[h]);
-              if constexpr (MODE == MODE_3XTF32) {
-                for (int s2i = 0; s2i < lv.plog; ++s2i) {
-#pragma unroll
-                  for (int h = 0; h < 8; ++h) y[h] = sqrtf(y[h]);
-                }
-              } else if (lv.plog > 0) {
-#pragma unroll
-                for (int h = 0; h < 8; ++h) y[h] = ex2_approx(lg2_approx(y[h]) * inv_p);
-              }
-              if (cm.corr == 2) {  // the affine line of p*'s class (the level above)
-                const float pa = cm.coef[2 * (lv.q + 1)], pb = cm.coef[2 * (lv.q + 1) + 1];
-#pragma unroll
-                for (int h = 0; h < 8; ++h) y[h] = fmaf(pa, y[h], pb);
-              }
-#pragma unroll
-              for (int h = 0; h < 8; ++h) y[h] *= rs * cv[h];
-              if (pvec) {
-#pragma unroll
-                for (int h = 0; h < 8; h += 4)
-                  *reinterpret_cast<float4*>(crow + e0 + h) =
-                      make_float4(y[h], y[h + 1], y[h + 2], y[h + 3]);
-              } else {
-#pragma unroll
-                for (int h = 0; h < 8; ++h)
-                  if ((pend >> (e0 + h)) & 1u) crow[e0 + h] = y[h];
-              }
-            }
+          if (lv.proj_here && __any_sync(0xffffffffu, pend != 0u)) {
+            const float cs_lane = lane < P.N - j0 ? __ldg(cm.c + P.rc_c + j0 + lane) : 0.0f;
+            // the affine line of p*'s class (the level above)
+            const bool affine = cm.corr == 2;
+            const float pa = affine ? cm.coef[2 * (lv.q + 1)] : 1.0f;
+            const float pb = affine ? cm.coef[2 * (lv.q + 1) + 1] : 0.0f;
+            r1_finish_block<MODE == MODE_3XTF32>(
+                stg, x, pend, rs, P.C + ((int64_t)tm * TILE_M + quarter * 32) * P.ldc + j0, P.ldc,
+                cs_lane, lv.plog, inv_p, affine, pa, pb, lane);
           }
           if (lv.proj_next) {
             any_left |= cand != 0u;  // their S^(p/2) comes from the next level
