@@ -356,17 +356,20 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
   const float opscale = ldexpf(1.0f, cm.s_op);
   __syncthreads();  // stile reuse across consecutive tiles
   {
-    // BK rows of K x 128 columns: thread = (row group tid/32, 4 columns),
-    // float4 loads, all issued before the scaled values go to shared memory.
+    // BK rows of K x 128 columns, all loads issued before the scaled values go
+    // to shared memory.  16-byte aligned rows: thread = (row group tid/32,
+    // columns 4 lane .. 4 lane + 3), float4 loads.  Otherwise thread = (row
+    // group, columns lane + 32 c), so that each load instruction reads one
+    // contiguous 128-byte row segment.
     const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-    const int n4 = rb * TILE_M + lane * 4;
+    const int n0 = rb * TILE_M;
     const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0) &&
-                     n4 + 4 <= P.N;
+                     n0 + TILE_M <= P.N;
     float cs[4], inv[4];
     bool inv_ok[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int n = n4 + c;
+      const int n = vec ? n0 + lane * 4 + c : n0 + lane + 32 * c;
       cs[c] = n < P.N ? scale_of(cm, cm.cmax, P.rc_c + n, g, 1) : 1.0f;
       inv[c] = 1.0f / cs[c];
       inv_ok[c] = cs[c] >= 1.1754944e-38f && cs[c] <= 8.507059e37f;
@@ -376,23 +379,26 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
 #pragma unroll
     for (int it = 0; it < BK / 8; ++it) {
       const int k = kb * BK + rg + 8 * it;
-      if (vec && k < P.K) {
-        t[it] = __ldg(reinterpret_cast<const float4*>(P.B + (int64_t)k * P.ldb + n4));
+      const float* src = P.B + (int64_t)k * P.ldb + n0;
+      if (vec) {
+        t[it] = k < P.K ? __ldg(reinterpret_cast<const float4*>(src + lane * 4))
+                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       } else {
-        const float* src = P.B + (int64_t)k * P.ldb;
-        t[it].x = (k < P.K && n4 < P.N) ? __ldg(src + n4) : 0.0f;
-        t[it].y = (k < P.K && n4 + 1 < P.N) ? __ldg(src + n4 + 1) : 0.0f;
-        t[it].z = (k < P.K && n4 + 2 < P.N) ? __ldg(src + n4 + 2) : 0.0f;
-        t[it].w = (k < P.K && n4 + 3 < P.N) ? __ldg(src + n4 + 3) : 0.0f;
+        const bool kin = k < P.K;
+        t[it].x = (kin && n0 + lane < P.N) ? __ldg(src + lane) : 0.0f;
+        t[it].y = (kin && n0 + lane + 32 < P.N) ? __ldg(src + lane + 32) : 0.0f;
+        t[it].z = (kin && n0 + lane + 64 < P.N) ? __ldg(src + lane + 64) : 0.0f;
+        t[it].w = (kin && n0 + lane + 96 < P.N) ? __ldg(src + lane + 96) : 0.0f;
       }
     }
 #pragma unroll
     for (int it = 0; it < BK / 8; ++it) {
-      float* rowp = stile + (rg + 8 * it) * 129 + lane * 4;
-      rowp[0] = div_pow2(t[it].x, cs[0], inv[0], inv_ok[0]);
-      rowp[1] = div_pow2(t[it].y, cs[1], inv[1], inv_ok[1]);
-      rowp[2] = div_pow2(t[it].z, cs[2], inv[2], inv_ok[2]);
-      rowp[3] = div_pow2(t[it].w, cs[3], inv[3], inv_ok[3]);
+      float* rowp = stile + (rg + 8 * it) * 129;
+      const int c0 = vec ? lane * 4 : lane, cst = vec ? 1 : 32;
+      rowp[c0] = div_pow2(t[it].x, cs[0], inv[0], inv_ok[0]);
+      rowp[c0 + cst] = div_pow2(t[it].y, cs[1], inv[1], inv_ok[1]);
+      rowp[c0 + 2 * cst] = div_pow2(t[it].z, cs[2], inv[2], inv_ok[2]);
+      rowp[c0 + 3 * cst] = div_pow2(t[it].w, cs[3], inv[3], inv_ok[3]);
     }
   }
   __syncthreads();
