@@ -12,13 +12,22 @@
 // mask of its resolved entries, and only those tiles are recomputed at the
 // next p.  The smallest p resolves whatever is left (flagged unstable).
 //
-// Kernel structure (one persistent CTA per SM, 6 warps):
+// Kernel structure (one persistent CTA per SM, 10 warps):
 //   warp 0      one thread issues 1-D bulk copies of pre-swizzled 16 KB
-//               operand tile images into a STAGES-deep shared-memory ring;
+//               operand tile images into a STAGES-deep shared-memory ring
+//               (192 KB);
 //   warp 1      allocates TMEM (two accumulators of 128 x BN FP32) and one
 //               thread issues tcgen05.mma (M=128, N=BN, 32 bytes of K each);
-//   warps 2-5   epilogue: tcgen05.ld of the accumulator (lane = output row),
-//               tau test, root by a sqrt chain, un-scaling, stores.
+//   warps 2-9   epilogue: tcgen05.ld of the accumulator (lane = output row),
+//               tau test, root, un-scaling, and stores staged through a 4 KB
+//               shared buffer per warp so that global writes are whole
+//               128-byte rows.  Where the epilogue bounds a tile (grouped
+//               problems, short contractions) the eight warps form two
+//               groups that finish alternate tiles, one per accumulator;
+//               otherwise all eight finish every tile on half the columns
+//               each.  The projection estimators (Sec. 2.1) park sums in C
+//               and the workspace and finish them at a lower level, walking
+//               each warp's 32 x 32 block row by row.
 // The accumulator is double-buffered so the epilogue of one tile overlaps the
 // MMAs of the next.  Every wait is bounded (PN_ETIMEOUT on expiry).
 #include "pn_gemm_kernel.cuh"
