@@ -726,7 +726,9 @@ struct TopkArgs {
   int32_t p_log2[PN_MAX_P];
   double tau;
   double* sig;     // [batch][2][n_p][nz]
-  double* psi0;    // [batch][2][nz] first estimates
+  double* psi0;    // [batch][2][nz] estimates (the first, then kept by the pops)
+  double* bmax0;   // [batch][2][nb] the largest estimate of each block of 32 diagonals
+  uint16_t* left;  // [batch][2][nz] terms of each diagonal not yet popped
   double* scale;   // [batch] max x * max y
   int32_t* diag;   // [batch][2][k]
   float* vals;     // [batch][ldk]
@@ -818,6 +820,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
   }
   // first estimates: the largest p with sigma >= tau (none: 0)
   double* psi = ta.psi0 + (int64_t)blockIdx.x * ta.nz;
+  uint16_t* left = ta.left + (int64_t)blockIdx.x * ta.nz;
   for (int m = tid; m < ta.nz; m += FFT_THREADS) {
     double e = 0.0;
     for (int q = ta.n_p - 1; q >= 0; --q) {
@@ -828,6 +831,18 @@ __global__ void __launch_bounds__(FFT_THREADS, 1)
       }
     }
     psi[m] = e;
+    left[m] = static_cast<uint16_t>(terms_of(m, ta.n, ta.n));
+  }
+  __syncthreads();
+  // the largest estimate of each block of 32 diagonals (-1 past the last)
+  const int nb = (ta.nz + 31) >> 5;
+  double* bmax = ta.bmax0 + (int64_t)blockIdx.x * nb;
+  for (int blk = warp; blk < nb; blk += FFT_THREADS / 32) {
+    const int m = blk * 32 + lane;
+    double v = m < ta.nz ? psi[m] : -1.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0) bmax[blk] = v;
   }
 }
 
@@ -844,28 +859,23 @@ __device__ __forceinline__ void warp_argmax(double& v, int& i) {
   }
 }
 
+// One warp per (problem, direction).  The estimates psi and the counts of
+// terms left live in the workspace; shared memory holds only the largest
+// estimate of each block of 32 diagonals, so every warp of the launch is
+// resident at once.  A pop reads the chosen block's 32 estimates with one
+// coalesced load.
 __global__ void __launch_bounds__(32) k_topk_pop(const __grid_constant__ TopkArgs ta) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int nb = (ta.nz + 31) >> 5;
-  double* psi = reinterpret_cast<double*>(smem);       // nb * 32
-  double* bmax = psi + nb * 32;                        // nb
-  uint16_t* left = reinterpret_cast<uint16_t*>(bmax + nb);  // nb * 32
+  double* bmax = reinterpret_cast<double*>(smem);  // nb
   const int lane = threadIdx.x;
   const int b = blockIdx.x >> 1, dir = blockIdx.x & 1;
   double* sig = ta.sig + (int64_t)blockIdx.x * ta.n_p * ta.nz;
-  const double* psi0 = ta.psi0 + (int64_t)blockIdx.x * ta.nz;
+  double* psi = ta.psi0 + (int64_t)blockIdx.x * ta.nz;
+  uint16_t* left = ta.left + (int64_t)blockIdx.x * ta.nz;
   int32_t* diag = ta.diag + (int64_t)blockIdx.x * ta.k;
-  for (int m = lane; m < nb * 32; m += 32) {
-    psi[m] = m < ta.nz ? psi0[m] : -1.0;
-    left[m] = m < ta.nz ? static_cast<uint16_t>(terms_of(m, ta.n, ta.n)) : 0;
-  }
-  __syncwarp();
-  for (int blk = 0; blk < nb; ++blk) {
-    double v = psi[blk * 32 + lane];
-    int i = lane;
-    warp_argmax(v, i);
-    if (lane == 0) bmax[blk] = v;
-  }
+  const double* bmax0 = ta.bmax0 + (int64_t)blockIdx.x * nb;
+  for (int blk = lane; blk < nb; blk += 32) bmax[blk] = bmax0[blk];
   __syncwarp();
   const double scale = dir == 0 ? ta.scale[b] : 0.0;
   for (int t = 0; t < ta.k; ++t) {
@@ -881,22 +891,25 @@ __global__ void __launch_bounds__(32) k_topk_pop(const __grid_constant__ TopkArg
     }
     warp_argmax(v, bi);
     const int mcand = bi * 32 + lane;
-    double pv = psi[mcand];
+    double pv = mcand < ta.nz ? psi[mcand] : -1.0;
+    const int lf = mcand < ta.nz ? left[mcand] : 0;
+    double pm = pv;
     int m = mcand;
-    warp_argmax(pv, m);
-    if (!(pv > 0.0)) {  // every diagonal exhausted or without a stable p
+    warp_argmax(pm, m);
+    if (!(pm > 0.0)) {  // every diagonal exhausted or without a stable p
       for (int r = t + lane; r < ta.k; r += 32) {
         diag[r] = -1;
         if (dir == 0) ta.vals[(int64_t)b * ta.ldk + r] = 0.0f;
       }
       break;
     }
-    const double alpha = pv;
+    const double alpha = pm;
     if (lane == 0) {
       diag[t] = m;
       if (dir == 0) ta.vals[(int64_t)b * ta.ldk + t] = static_cast<float>(alpha * scale);
     }
-    const int rem = left[m] - 1;
+    const int mi = m - bi * 32;  // the popped diagonal's lane
+    const int rem = __shfl_sync(0xffffffffu, lf, mi) - 1;
     // NormQueue pop: sigma^(p)_m -= alpha^p for every p (one lane per p)
     double sq = 0.0;
     if (lane < ta.n_p) {
@@ -912,13 +925,12 @@ __global__ void __launch_bounds__(32) k_topk_pop(const __grid_constant__ TopkArg
       const double sv = __shfl_sync(0xffffffffu, sq, qs);
       e = fmin(root_fp64(sv, ta.p_log2[qs]), alpha);
     }
-    __syncwarp();
-    if (lane == 0) {
+    if (lane == mi) {
+      pv = e;
       psi[m] = e;
       left[m] = static_cast<uint16_t>(rem);
     }
-    __syncwarp();
-    double w = psi[bi * 32 + lane];
+    double w = pv;
     int wi = lane;
     warp_argmax(w, wi);
     if (lane == 0) bmax[bi] = w;
@@ -1086,7 +1098,8 @@ int launch_maxconv_long(const pn_opts* o, int64_t nx, const float* x, int64_t ny
 }
 
 struct TopkLayout {
-  size_t off_sig = 0, off_psi = 0, off_scale = 0, off_diag = 0, total = 0;
+  size_t off_sig = 0, off_psi = 0, off_bmax = 0, off_left = 0, off_scale = 0, off_diag = 0,
+         total = 0;
 };
 
 TopkLayout topk_layout(int64_t batch, int64_t n, int64_t k, int n_p) {
@@ -1096,6 +1109,10 @@ TopkLayout topk_layout(int64_t batch, int64_t n, int64_t k, int n_p) {
   L.off_sig = off; off += static_cast<size_t>(batch) * 2 * n_p * nz * sizeof(double);
   off = (off + 255) & ~size_t(255);
   L.off_psi = off; off += static_cast<size_t>(batch) * 2 * nz * sizeof(double);
+  off = (off + 255) & ~size_t(255);
+  L.off_bmax = off; off += static_cast<size_t>(batch) * 2 * ((nz + 31) / 32) * sizeof(double);
+  off = (off + 255) & ~size_t(255);
+  L.off_left = off; off += static_cast<size_t>(batch) * 2 * nz * sizeof(uint16_t);
   off = (off + 255) & ~size_t(255);
   L.off_scale = off; off += static_cast<size_t>(batch) * sizeof(double);
   off = (off + 255) & ~size_t(255);
@@ -1112,6 +1129,8 @@ int launch_topk(const TopkArgs& ta0, uint8_t* ws, void* stream) {
   const TopkLayout L = topk_layout(ta.batch, ta.n, ta.k, ta.n_p);
   ta.sig = reinterpret_cast<double*>(ws + L.off_sig);
   ta.psi0 = reinterpret_cast<double*>(ws + L.off_psi);
+  ta.bmax0 = reinterpret_cast<double*>(ws + L.off_bmax);
+  ta.left = reinterpret_cast<uint16_t*>(ws + L.off_left);
   ta.scale = reinterpret_cast<double*>(ws + L.off_scale);
   ta.diag = reinterpret_cast<int32_t*>(ws + L.off_diag);
   const int N = 1 << ta.logN;
@@ -1119,7 +1138,7 @@ int launch_topk(const TopkArgs& ta0, uint8_t* ws, void* stream) {
   if ((e = cudaFuncSetAttribute(k_topk_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_sums)))
     return e;
   const int nb = (ta.nz + 31) / 32;
-  const int smem_pop = nb * 32 * 8 + nb * 8 + nb * 32 * 2;
+  const int smem_pop = nb * 8;
   if ((e = cudaFuncSetAttribute(k_topk_pop, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_pop)))
     return e;
   k_topk_sums<<<2 * ta.batch, FFT_THREADS, smem_sums, s>>>(ta);
