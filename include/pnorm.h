@@ -102,8 +102,10 @@ typedef struct pn_opts {
   void* ev_gemm_end;
   /* Limit of every bounded device-side wait, in nanoseconds; 0 = 2e9. */
   int64_t timeout_ns;
-  /* Test hooks, 0 in normal use.  Bit 0: the copy producer skips one stage
-   * so that the consumer's bounded wait runs out (PN_ETIMEOUT). */
+  /* Test hooks, 0 in normal use.  Bit 0: the tensor-core kernel's copy
+   * producer skips one stage so that the consumer's bounded wait runs out
+   * (PN_ETIMEOUT).  Bit 1: the tensor-copy image kernel announces its first
+   * tile's bytes without copying them, with the same effect. */
   int32_t debug_flags;
   /* Estimate of max_k u_k from the p-sums (Sec. 2.1):
    *   0 (default) = plain, (S^(p*))^(1/p*), an overestimate by at most

@@ -575,6 +575,9 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
     const int rb = id / P.KB, kb = id - rb * P.KB;
     uint64_t* bar = &full[j % NST];
     mbar_arrive_expect_tx(bar, CF::STAGE_BYTES);
+    // test hook (debug_flags bit 1): the first tile's bytes are announced but
+    // never copied, so the bounded wait for them runs out
+    if ((cm.debug_flags & 2) && j == 0) return;
     const uint32_t dst = smem_u32(ring) + (j % NST) * CF::STAGE_BYTES;
     if constexpr (!IS_B)
       tma_load_2d(dst, &map, kb * BK, rb * TILE_M, bar);

@@ -37,3 +37,18 @@ def test_bounded_wait_reports_timeout_and_context_survives(pn):
     C2, _, _ = pn.maxprod_pnorm(dA, dB, compute="bf16")
     assert torch.equal(C1, C2)
     assert torch.isfinite(C1).all()
+
+
+def test_image_kernel_wait_reports_timeout_and_context_survives(pn):
+    """The tensor-copy image kernel (16-byte aligned rows) waits, bounded, for a
+    tile whose bytes are announced but never copied: PN_ETIMEOUT, the copies in
+    flight land, and the next call works."""
+    A, B = workloads.uniform_pair(512, 512, 512, seed=32)
+    dA, dB = torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda()
+    with pytest.raises(pn.PnError) as ei:
+        pn.maxprod_pnorm(dA, dB, compute="bf16", timeout_ns=200_000_000, debug_flags=2)
+    assert ei.value.status == 6  # PN_ETIMEOUT
+    C1, _, _ = pn.maxprod_pnorm(dA, dB, compute="bf16")
+    C2, _, _ = pn.maxprod_pnorm(dA, dB, compute="bf16")
+    assert torch.equal(C1, C2)
+    assert torch.isfinite(C1).all()
