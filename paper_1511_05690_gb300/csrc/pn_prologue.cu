@@ -91,7 +91,11 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
     const int n4 = rb * TILE_M + lane * 4;
     const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0);
     float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (vec && n4 + 4 <= P.N && k0 + MAXSEG_B <= P.K) {
+    // whole aligned segment: thread = columns 4 lane .. 4 lane + 3, float4
+    // loads; otherwise thread = columns lane + 32 c, so that each load
+    // instruction reads one contiguous 128-byte row segment
+    const bool full_vec = vec && rb * TILE_M + TILE_M <= P.N && k0 + MAXSEG_B <= P.K;
+    if (full_vec) {
 #pragma unroll 8
       for (int it = 0; it < MAXSEG_B / 8; ++it) {
         const int k = k0 + warp + 8 * it;
@@ -101,13 +105,14 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
         m4[2] = fmaxf(m4[2], t.z); m4[3] = fmaxf(m4[3], t.w);
       }
     } else {
+      const int nl = rb * TILE_M + lane;
       for (int it = 0; it < MAXSEG_B / 8; ++it) {
         const int k = k0 + warp + 8 * it;
         if (k >= P.K) break;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          if (n4 + c < P.N) {
-            const float x = __ldg(P.B + (int64_t)k * P.ldb + n4 + c);
+          if (nl + 32 * c < P.N) {
+            const float x = __ldg(P.B + (int64_t)k * P.ldb + nl + 32 * c);
             bad |= !in_domain(x);
             m4[c] = fmaxf(m4[c], x);
           }
@@ -115,7 +120,8 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
       }
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = nonneg_bits_max(m4[c]);
+    for (int c = 0; c < 4; ++c)
+      red[warp][full_vec ? lane * 4 + c : lane + 32 * c] = nonneg_bits_max(m4[c]);
     __syncthreads();
     if (tid < 128) {
       float m = red[0][tid];
