@@ -15,14 +15,32 @@ passages they follow:
 * ``row_scales`` / ``col_scales`` -- the scaled H' of Sec. 2.1 (power-of-two
   reading, see ``oracle.c``).
 * ``psums`` -- Alg. 5 first loop: S^(p) = (A'^p)(B'^p) for every p in P.
-* ``estimate`` -- Alg. 5 second loop with the plain
-  estimateMaxFromNormPowerSequence (largest stable p).
-* ``pnorm`` -- the two together.
+* ``psums_real`` / ``entries_real`` -- the same sums at real exponents (the
+  3p/4 family that the r = 2 projection of Sec. 2.1 needs), all entries /
+  selected entries.
+* ``estimate`` -- Alg. 5 second loop: estimateMaxFromNormPowerSequence in the
+  plain form (largest stable p), or the multiset projection of Sec. 2.1 with
+  r = 1 (estimator 1) or r = 2 (estimator 2).
+* ``project`` -- the projection of Sec. 2.1 for any r from its Hankel matrix
+  (a general construction the r = 1 and r = 2 paths are checked against).
+* ``project_r2`` -- the r = 2 projection from its four sums (Sec. 2.1).
+* ``pnorm`` -- scales, sums and estimate together.
 * ``entries`` -- exact max and p-sums at selected entries only.
+* ``affine_fit`` / ``fit_coefficients`` / ``apply_correction`` -- the bias
+  corrections (Sec. 2.1 bound remark; Discussion): division by K^(1/p*), and
+  a least-squares affine map per p* class from exactly solved samples.
 * ``floyd_warshall`` -- exact APSP (the comparison of Sec. 3.1).
 * ``apsp_pnorm`` -- Sec. 2.2: exp(-W), repeated p-norm squaring, -log.
 * ``pnorm_grad`` / ``pnorm_grad_entries`` -- gradient of the p-norm product at
-  fixed p per entry (all entries / selected entries).
+  fixed p per entry (all entries / selected entries); ``row_logloss`` /
+  ``col_logloss`` are the losses its finite-difference pins use.
+* ``maxconv`` / ``conv`` -- naive max-convolution (Sec. 1) and the naive ring
+  convolution an FFT computes.
+* ``maxconv_pnorm`` / ``maxconv_entries`` -- the p-norm estimate of the
+  max-convolution (Sec. 1 with the scaling of Sec. 2.1), all outputs /
+  selected outputs.
+* ``topk_xy`` / ``recover_indices`` -- approximate top-k of x_i y_j (Alg. 9
+  with the NormQueue) and the index recovery from two calls.
 * ``default_tau`` -- the stability threshold reading (Sec. 2.1, tau).
 """
 from __future__ import annotations
