@@ -23,7 +23,8 @@ from ._binding import (PN_BF16, PN_E4M3, PN_F16, PN_F32_EXACT, PN_TF32, PnError,
 
 __all__ = ["maxprod_pnorm", "maxprod_exact", "apsp_pnorm", "default_tau", "workspace",
            "PnError", "make_opts", "status_string", "sm_count", "PNormMaxProd",
-           "maxprod_pnorm_backward", "GroupedProduct", "autotune"]
+           "maxprod_pnorm_backward", "GroupedProduct", "autotune", "maxconv_pnorm",
+           "maxconv_exact", "topk_xy"]
 
 _ws = {}
 _status = {}
