@@ -31,14 +31,46 @@ __device__ __forceinline__ bool in_domain(float x) {
 __device__ __forceinline__ float nonneg_bits_max(float m) { return m > 0.0f ? m : 0.0f; }
 
 // ------------------------------------------------------------- maxima ---
-// A unit: 128 rows x 1024 columns of A; each warp reduces 16 rows (float4
-// loads, 8 in flight per lane per row).  B unit: 128 columns x 256 rows of B;
-// each thread keeps the maxima of 4 columns over 32 rows, then the 8 row
-// groups are combined in shared memory.  One atomicMax per row / column per
-// unit.  Non-negative floats order like their bit patterns, so maxima are
-// kept as uint32 bits.
+// A unit: 128 rows x 1024 columns of A; each warp reduces 16 rows.  B unit:
+// 128 columns x 256 rows of B; each thread keeps the maxima of 4 columns over
+// 32 rows, then the 8 row groups are combined in shared memory.  One
+// atomicMax per row / column per unit.
+//
+// Non-negative floats order like their bit patterns, and every value of the
+// domain [0, 2^127] has bits <= DOMAIN_MAX_BITS, so the maxima run on the raw
+// bits: one unsigned max per value gives both the maximum and the domain
+// test.  A thread whose running maximum is above DOMAIN_MAX_BITS (one of its
+// values is negative, -0, +inf, NaN or above 2^127) goes over its values again
+// with the exact test, which flags the error and yields the maximum of the
+// non-negative values.
+constexpr uint32_t DOMAIN_MAX_BITS = 0x7F000000u;  // bits of 2^127
+
+__device__ __forceinline__ uint32_t umax3(uint32_t a, uint32_t b, uint32_t c) {
+  return max(a, max(b, c));
+}
+
+// Exact pass over len values src[0], src[step], ...: the maximum of the
+// non-negative values as bits (at most those of +inf), with bit 31 set if any
+// value is outside the domain.
+__device__ __forceinline__ uint32_t exact_max_bits(const float* src, int64_t step, int len) {
+  float m = 0.0f;
+  bool bad = false;
+  for (int t = 0; t < len; ++t) {
+    const float x = __ldg(src + t * step);
+    bad |= !in_domain(x);
+    m = fmaxf(m, x);
+  }
+  return __float_as_uint(nonneg_bits_max(m)) | (bad ? 0x80000000u : 0u);
+}
+
+// Folds the error bit of exact_max_bits into bad and returns the maximum.
+__device__ __forceinline__ uint32_t take_exact(uint32_t e, bool& bad) {
+  bad |= (e >> 31) != 0u;
+  return e & 0x7FFFFFFFu;
+}
+
 __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ Common cm) {
-  __shared__ float red[8][128];
+  __shared__ uint32_t red[8][128];
   __shared__ float blk_max[PRO_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int id = blockIdx.x;
@@ -54,82 +86,126 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
     const int k0 = seg * MAXSEG_A;
     const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
     const int seg_len = P.K - k0 < MAXSEG_A ? P.K - k0 : MAXSEG_A;  // values in this segment
-    for (int rr = 0; rr < 16; ++rr) {
-      const int row = rb * TILE_M + warp * 16 + rr;
-      if (row >= P.M) break;  // warp-uniform; later rows are past M too
-      float m = 0.0f;
-      const float* src = P.A + (int64_t)row * P.lda;
-      if (vec && seg_len == MAXSEG_A) {
-        float4 t[MAXSEG_A / 128];
+    const float* base = P.A + k0;
+    // the row maximum from each lane's bits (all <= DOMAIN_MAX_BITS here)
+    auto commit_row = [&](int row, uint32_t u) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) u = max(u, __shfl_xor_sync(0xffffffffu, u, o));
+      if (lane == 0 && u > 0u) atomicMax(cm.rmax + P.rc_r + row, u);
+      bmax = fmaxf(bmax, __uint_as_float(u));
+    };
+    if (vec && seg_len == MAXSEG_A) {
+      // whole aligned segment: 16-byte loads, 8 in flight per lane per row
+      for (int rr = 0; rr < 16; ++rr) {
+        const int row = rb * TILE_M + warp * 16 + rr;
+        if (row >= P.M) break;  // warp-uniform; later rows are past M too
+        const float* src = base + (int64_t)row * P.lda;
+        uint4 t[MAXSEG_A / 128];
 #pragma unroll
         for (int it = 0; it < MAXSEG_A / 128; ++it)
-          t[it] = __ldg(reinterpret_cast<const float4*>(src + k0 + it * 128 + lane * 4));
+          t[it] = __ldg(reinterpret_cast<const uint4*>(src + it * 128 + lane * 4));
+        uint32_t u = 0u;
 #pragma unroll
-        for (int it = 0; it < MAXSEG_A / 128; ++it) {
-          bad |= !in_domain(t[it].x) | !in_domain(t[it].y) | !in_domain(t[it].z) |
-                 !in_domain(t[it].w);
-          m = fmaxf(m, fmaxf(fmaxf(t[it].x, t[it].y), fmaxf(t[it].z, t[it].w)));
+        for (int it = 0; it < MAXSEG_A / 128; ++it)
+          u = umax3(u, max(t[it].x, t[it].y), max(t[it].z, t[it].w));
+        if (u > DOMAIN_MAX_BITS) {
+          uint32_t e = 0u;
+          for (int q = 0; q < 4; ++q)
+            e = max(e, take_exact(exact_max_bits(src + lane * 4 + q, 128, MAXSEG_A / 128), bad));
+          u = e;
         }
-      } else {
-        for (int kk = lane; kk < seg_len; kk += 32) {
-          const float x = __ldg(src + k0 + kk);
-          bad |= !in_domain(x);
-          m = fmaxf(m, x);
+        commit_row(row, u);
+      }
+    } else {
+      // four rows at a time, lane reading columns lane + 32 t: 16 loads in
+      // flight per lane, each load instruction one contiguous row segment.
+      // The loads are unconditional: a column past the segment reads the
+      // segment's last value (already part of the row maximum) and a row past
+      // M reads row M - 1 (never committed).
+      for (int rr = 0; rr < 16; rr += 4) {
+        const int row0 = rb * TILE_M + warp * 16 + rr;
+        if (row0 >= P.M) break;  // warp-uniform
+        uint32_t u[4] = {0u, 0u, 0u, 0u};
+        for (int kk0 = lane; kk0 < seg_len; kk0 += 128) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float* src = base + (int64_t)min(row0 + r, P.M - 1) * P.lda;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              u[r] = max(u[r], __float_as_uint(__ldg(src + min(kk0 + 32 * q, seg_len - 1))));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = row0 + r;
+          if (row < P.M) {  // warp-uniform
+            if (u[r] > DOMAIN_MAX_BITS) {
+              const int cnt = lane < seg_len ? (seg_len - 1 - lane) / 32 + 1 : 0;
+              u[r] = take_exact(exact_max_bits(base + (int64_t)row * P.lda + lane, 32, cnt), bad);
+            }
+            commit_row(row, u[r]);
+          }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      m = nonneg_bits_max(m);
-      if (lane == 0 && m > 0.0f)
-        atomicMax(cm.rmax + P.rc_r + row, __float_as_uint(m));
-      bmax = fmaxf(bmax, m);
     }
   } else {
     const int local = id - P.mb_base;
     const int rb = local / P.KMB, seg = local - rb * P.KMB;
     const int k0 = seg * MAXSEG_B;
     const int n4 = rb * TILE_M + lane * 4;
+    const int nl = rb * TILE_M + lane;
     const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0);
-    float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    // whole aligned segment: thread = columns 4 lane .. 4 lane + 3, float4
+    uint32_t u4[4] = {0u, 0u, 0u, 0u};
+    // whole aligned segment: thread = columns 4 lane .. 4 lane + 3, 16-byte
     // loads; otherwise thread = columns lane + 32 c, so that each load
-    // instruction reads one contiguous 128-byte row segment
+    // instruction reads one contiguous 128-byte row segment, 16 in flight
     const bool full_vec = vec && rb * TILE_M + TILE_M <= P.N && k0 + MAXSEG_B <= P.K;
     if (full_vec) {
 #pragma unroll 8
       for (int it = 0; it < MAXSEG_B / 8; ++it) {
         const int k = k0 + warp + 8 * it;
-        const float4 t = __ldg(reinterpret_cast<const float4*>(P.B + (int64_t)k * P.ldb + n4));
-        bad |= !in_domain(t.x) | !in_domain(t.y) | !in_domain(t.z) | !in_domain(t.w);
-        m4[0] = fmaxf(m4[0], t.x); m4[1] = fmaxf(m4[1], t.y);
-        m4[2] = fmaxf(m4[2], t.z); m4[3] = fmaxf(m4[3], t.w);
+        const uint4 t = __ldg(reinterpret_cast<const uint4*>(P.B + (int64_t)k * P.ldb + n4));
+        u4[0] = max(u4[0], t.x); u4[1] = max(u4[1], t.y);
+        u4[2] = max(u4[2], t.z); u4[3] = max(u4[3], t.w);
       }
     } else {
-      const int nl = rb * TILE_M + lane;
-      for (int it = 0; it < MAXSEG_B / 8; ++it) {
-        const int k = k0 + warp + 8 * it;
-        if (k >= P.K) break;
+      // unconditional loads: a row past K reads row K - 1 of the same column
+      // (part of this segment), a column past N reads column N - 1 (its
+      // maximum is never committed)
+      int ncol[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          if (nl + 32 * c < P.N) {
-            const float x = __ldg(P.B + (int64_t)k * P.ldb + nl + 32 * c);
-            bad |= !in_domain(x);
-            m4[c] = fmaxf(m4[c], x);
-          }
+      for (int c = 0; c < 4; ++c) ncol[c] = min(nl + 32 * c, P.N - 1);
+      for (int it0 = 0; it0 < MAXSEG_B / 8; it0 += 4) {
+        if (k0 + warp + 8 * it0 >= P.K) break;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float* src = P.B + (int64_t)min(k0 + warp + 8 * (it0 + q), P.K - 1) * P.ldb;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) u4[c] = max(u4[c], __float_as_uint(__ldg(src + ncol[c])));
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-      red[warp][full_vec ? lane * 4 + c : lane + 32 * c] = nonneg_bits_max(m4[c]);
+    for (int c = 0; c < 4; ++c) {
+      const int n = full_vec ? n4 + c : nl + 32 * c;
+      if (n >= P.N) u4[c] = 0u;
+      if (u4[c] > DOMAIN_MAX_BITS) {
+        // rows k0 + warp + 8 t < K of column n (n < N: other columns stay 0)
+        const int rows = P.K - k0 < MAXSEG_B ? P.K - k0 : MAXSEG_B;
+        const int cnt = warp < rows ? (rows - 1 - warp) / 8 + 1 : 0;
+        u4[c] = take_exact(exact_max_bits(P.B + (int64_t)(k0 + warp) * P.ldb + n, 8 * P.ldb, cnt),
+                           bad);
+      }
+      red[warp][full_vec ? lane * 4 + c : lane + 32 * c] = u4[c];
+    }
     __syncthreads();
     if (tid < 128) {
-      float m = red[0][tid];
+      uint32_t m = red[0][tid];
 #pragma unroll
-      for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w][tid]);
+      for (int w = 1; w < 8; ++w) m = max(m, red[w][tid]);
       const int n = rb * TILE_M + tid;
-      if (n < P.N && m > 0.0f) atomicMax(cm.cmax + P.rc_c + n, __float_as_uint(m));
-      bmax = m;
+      if (n < P.N && m > 0u) atomicMax(cm.cmax + P.rc_c + n, m);
+      bmax = __uint_as_float(m);
     }
   }
   if (__syncthreads_or(bad) && tid == 0) set_status(cm.status, PN_EDOMAIN);

@@ -232,6 +232,33 @@ def test_pnorm_domain_error(pn):
     pn.maxprod_pnorm(_dev(A), _dev(B))
 
 
+@pytest.mark.parametrize("shape", [(20, 30, 40), (130, 260, 1024)])
+@pytest.mark.parametrize("where", ["A", "B"])
+def test_pnorm_domain_values(pn, shape, where):
+    """Inputs must lie in [0, 2^127]: a negative value, +-inf, NaN or a value
+    above 2^127 anywhere in either operand gives PN_EDOMAIN, in the maxima
+    pass's 16-byte path (full aligned segments: K = 1024 rows of A, 128 columns
+    x 256 rows of B) and in its scalar path (K = 40, N = 30); -0 acts as 0 and
+    2^127 itself is accepted."""
+    M, N, K = shape
+    A, B = workloads.uniform_pair(M, N, K, seed=12)
+    X = A if where == "A" else B
+    pos = (M // 2, K - 1) if where == "A" else (K - 1, N // 2)
+    for bad in (-1.0, np.nan, np.inf, -np.inf, 3.0e38):
+        X[pos] = bad
+        with pytest.raises(pn.PnError) as ei:
+            pn.maxprod_pnorm(_dev(A), _dev(B))
+        assert ei.value.status == 4, bad
+    X[pos] = 0.0
+    C0, p0, _ = pn.maxprod_pnorm(_dev(A), _dev(B))
+    X[pos] = -0.0
+    C1, p1, _ = pn.maxprod_pnorm(_dev(A), _dev(B))
+    assert torch.equal(C0, C1) and torch.equal(p0, p1)
+    X[pos] = 2.0 ** 127
+    C2, _, _ = pn.maxprod_pnorm(_dev(A), _dev(B))
+    assert torch.isfinite(C2).all()
+
+
 def test_pnorm_host_errors(pn):
     import ctypes
     L = pn.lib()
