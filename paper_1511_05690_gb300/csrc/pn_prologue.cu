@@ -330,24 +330,33 @@ __device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, 
   const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
   // 1024 16-byte output chunks per tile, 4 per thread: chunk = tid + 256 u,
   // row = chunk / 8 (8 threads cover one 128-byte image row), 16-byte slot
-  // = chunk % 8.  All loads are issued before any arithmetic.
+  // = chunk % 8.  All loads are issued, unconditionally, before any
+  // arithmetic: rows past M and columns past K read the clamped (in-bounds)
+  // index and are zeroed afterwards.
   float v[4][EPC];
   const int cc = threadIdx.x & 7;
   const int k0 = kb * BK + cc * EPC;
+  const bool vec_k = vec && k0 + EPC <= P.K;  // this thread's columns are whole 16-byte groups
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int row = rb * TILE_M + (threadIdx.x >> 3) + 32 * u;
-    const float* src = P.A + (int64_t)row * P.lda + k0;
-    if (row < P.M && vec && k0 + EPC <= P.K) {
+    const float* srow = P.A + (int64_t)min(row, P.M - 1) * P.lda;
+    if (vec_k) {
 #pragma unroll
       for (int e = 0; e < EPC; e += 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(src + e));
+        const float4 t = __ldg(reinterpret_cast<const float4*>(srow + k0 + e));
         v[u][e] = t.x; v[u][e + 1] = t.y; v[u][e + 2] = t.z; v[u][e + 3] = t.w;
       }
     } else {
 #pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] = (row < P.M && k0 + e < P.K) ? __ldg(src + e) : 0.0f;
+      for (int e = 0; e < EPC; ++e) v[u][e] = __ldg(srow + min(k0 + e, P.K - 1));
     }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool row_in = rb * TILE_M + (threadIdx.x >> 3) + 32 * u < P.M;
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) v[u][e] = (row_in && k0 + e < P.K) ? v[u][e] : 0.0f;
   }
   float rs[4];
 #pragma unroll
@@ -457,30 +466,45 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
       inv_ok[c] = cs[c] >= 1.1754944e-38f && cs[c] <= 8.507059e37f;
       if (lv.is_top && kb == 0 && rg == 0 && n < P.N) cm.c[P.rc_c + n] = cs[c];
     }
-    float4 t[BK / 8];
+    // Loads in chunks of up to 8 row groups (64 rows), all of a chunk
+    // issued, unconditionally, before its values are used: rows past K and
+    // columns past N read the clamped (in-bounds) index and are zeroed after.
+    constexpr int CH = BK / 8 < 8 ? BK / 8 : 8;
+    const int nlast = P.N - 1 - n0;  // last column of the tile block in bounds
 #pragma unroll
-    for (int it = 0; it < BK / 8; ++it) {
-      const int k = kb * BK + rg + 8 * it;
-      const float* src = P.B + (int64_t)k * P.ldb + n0;
-      if (vec) {
-        t[it] = k < P.K ? __ldg(reinterpret_cast<const float4*>(src + lane * 4))
-                        : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      } else {
-        const bool kin = k < P.K;
-        t[it].x = (kin && n0 + lane < P.N) ? __ldg(src + lane) : 0.0f;
-        t[it].y = (kin && n0 + lane + 32 < P.N) ? __ldg(src + lane + 32) : 0.0f;
-        t[it].z = (kin && n0 + lane + 64 < P.N) ? __ldg(src + lane + 64) : 0.0f;
-        t[it].w = (kin && n0 + lane + 96 < P.N) ? __ldg(src + lane + 96) : 0.0f;
+    for (int it0 = 0; it0 < BK / 8; it0 += CH) {
+      float4 t[CH];
+#pragma unroll
+      for (int i = 0; i < CH; ++i) {
+        const int k = kb * BK + rg + 8 * (it0 + i);
+        const float* srow = P.B + (int64_t)min(k, P.K - 1) * P.ldb + n0;
+        if (vec) {
+          t[i] = __ldg(reinterpret_cast<const float4*>(srow + lane * 4));
+        } else {
+          t[i].x = __ldg(srow + min(lane, nlast));
+          t[i].y = __ldg(srow + min(lane + 32, nlast));
+          t[i].z = __ldg(srow + min(lane + 64, nlast));
+          t[i].w = __ldg(srow + min(lane + 96, nlast));
+        }
       }
-    }
 #pragma unroll
-    for (int it = 0; it < BK / 8; ++it) {
-      float* rowp = stile + (rg + 8 * it) * 129;
-      const int c0 = vec ? lane * 4 : lane, cst = vec ? 1 : 32;
-      rowp[c0] = div_pow2(t[it].x, cs[0], inv[0], inv_ok[0]);
-      rowp[c0 + cst] = div_pow2(t[it].y, cs[1], inv[1], inv_ok[1]);
-      rowp[c0 + 2 * cst] = div_pow2(t[it].z, cs[2], inv[2], inv_ok[2]);
-      rowp[c0 + 3 * cst] = div_pow2(t[it].w, cs[3], inv[3], inv_ok[3]);
+      for (int i = 0; i < CH; ++i) {
+        const bool kin = kb * BK + rg + 8 * (it0 + i) < P.K;
+        if (vec) {
+          t[i] = kin ? t[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        } else {
+          t[i].x = (kin && lane <= nlast) ? t[i].x : 0.0f;
+          t[i].y = (kin && lane + 32 <= nlast) ? t[i].y : 0.0f;
+          t[i].z = (kin && lane + 64 <= nlast) ? t[i].z : 0.0f;
+          t[i].w = (kin && lane + 96 <= nlast) ? t[i].w : 0.0f;
+        }
+        float* rowp = stile + (rg + 8 * (it0 + i)) * 129;
+        const int c0 = vec ? lane * 4 : lane, cst = vec ? 1 : 32;
+        rowp[c0] = div_pow2(t[i].x, cs[0], inv[0], inv_ok[0]);
+        rowp[c0 + cst] = div_pow2(t[i].y, cs[1], inv[1], inv_ok[1]);
+        rowp[c0 + 2 * cst] = div_pow2(t[i].z, cs[2], inv[2], inv_ok[2]);
+        rowp[c0 + 3 * cst] = div_pow2(t[i].w, cs[3], inv[3], inv_ok[3]);
+      }
     }
   }
   __syncthreads();
