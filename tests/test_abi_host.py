@@ -156,3 +156,78 @@ def test_missing_library_fails_loudly(binding, monkeypatch):
     monkeypatch.setattr(binding, "LIB_PATH", "/nonexistent/libpnorm.so")
     with pytest.raises(RuntimeError, match="not built"):
         binding.load()
+
+
+def _group_args(sizes, ptr=0x10000):
+    """ctypes arguments of a group: MNK and distinct 256-byte-aligned placeholder
+    addresses (the table builder stores them and reads their alignment only)."""
+    vp = ctypes.c_void_p
+    n = len(sizes)
+    MNK = (ctypes.c_int64 * max(1, 3 * n))(*[v for s in sizes for v in s])
+    mk = lambda k: (vp * max(1, n))(*[None if 0 in s[:2] else ptr + 256 * (3 * g + k)  # noqa: E731
+                                       for g, s in enumerate(sizes)])
+    return n, MNK, mk(0), mk(1), mk(2)
+
+
+def _build(lib, binding, sizes, o, short=0):
+    import numpy as np
+    n, MNK, A, B, C = _group_args(sizes)
+    tb = lib.pn_grouped_table_bytes(n, MNK, ctypes.byref(o))
+    assert tb > 0
+    table = np.zeros(tb, dtype=np.uint8)
+    ws = ctypes.c_size_t(0)
+    rc = lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(o),
+                                    table.ctypes.data_as(ctypes.c_void_p), tb - short,
+                                    ctypes.byref(ws))
+    return rc, table, ws.value
+
+
+def test_grouped_table_builder_on_the_host(binding):
+    """pn_grouped_build_table runs on the host only: deterministic bytes, a
+    workspace that holds every problem's operand images, empty problems
+    without pointers or tiles, and PN_EINVAL for every invalid argument."""
+    import numpy as np
+    lib = binding.load()
+    o = binding.make_opts(compute="bf16")
+    sizes = [(16, 16, 16), (300, 200, 1000), (129, 1, 77), (1, 700, 5)]
+    rc, t1, ws = _build(lib, binding, sizes, o)
+    assert rc == 0 and ws > 0 and ws % 256 == 0
+    rc2, t2, ws2 = _build(lib, binding, sizes, o)
+    assert rc2 == 0 and ws2 == ws and np.array_equal(t1, t2)
+    # the 128-wide layout alone needs every A and B^T image tile: 16 KB per
+    # 128 rows (columns) x 64 values of K in BF16
+    img = sum((-(-m // 128) + -(-n // 128)) * -(-k // 64) for m, n, k in sizes) * 16384
+    assert ws >= img
+    # more work, larger table and workspace
+    rc3, t3, ws3 = _build(lib, binding, sizes + [(512, 512, 512)], o)
+    assert rc3 == 0 and len(t3) > len(t1) and ws3 > ws
+    # empty problems take no pointers and no tiles (only their scale words)
+    rc4, t4, ws4 = _build(lib, binding, sizes + [(0, 50, 50), (50, 0, 50), (0, 0, 0)], o)
+    assert rc4 == 0 and ws <= ws4 <= ws + 4096
+    # 3xTF32: two planes of 4-byte values, 32 per 128-byte image row
+    o32 = binding.make_opts(compute="f32")
+    rc5, _, ws5 = _build(lib, binding, sizes, o32)
+    img32 = 2 * sum((-(-m // 128) + -(-n // 128)) * -(-k // 32) for m, n, k in sizes) * 16384
+    assert rc5 == 0 and ws5 >= img32 > 3 * img
+    # invalid arguments
+    assert _build(lib, binding, sizes, o, short=1)[0] == 1            # table too small
+    n, MNK, A, B, C = _group_args([(4, 4, 0)])                       # empty contraction
+    assert lib.pn_grouped_table_bytes(n, MNK, ctypes.byref(o)) > 0
+    tab = np.zeros(1 << 16, dtype=np.uint8)
+    vpt = tab.ctypes.data_as(ctypes.c_void_p)
+    assert lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(o), vpt, tab.size, None) == 1
+    n, MNK, A, B, C = _group_args([(4, 4, 4)])
+    A[0] = None                                                       # missing operand
+    assert lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(o), vpt, tab.size, None) == 1
+    for bad in ([(-1, 4, 4)], [(4, 1 << 30, 4)]):                     # size out of range
+        n, MNK, A, B, C = _group_args(bad)
+        assert lib.pn_grouped_table_bytes(n, MNK, ctypes.byref(o)) == 0
+        assert lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(o), vpt, tab.size,
+                                          None) == 1
+    badopt = binding.make_opts(compute="bf16")
+    badopt.n_p = 0
+    n, MNK, A, B, C = _group_args(sizes)
+    assert lib.pn_grouped_table_bytes(n, MNK, ctypes.byref(badopt)) == 0
+    assert lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(badopt), vpt, tab.size,
+                                      None) == 1
+    assert lib.pn_grouped_build_table(-1, MNK, A, B, C, ctypes.byref(o), vpt, tab.size, None) == 1
