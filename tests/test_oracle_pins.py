@@ -683,19 +683,54 @@ def test_affine_correction_reduces_error(orc):
 # ------------------------------------------------------- max-convolution ---
 # Sec. 1: z_m = max_i x_i y_(m-i) and its p-norm estimate from ring
 # convolutions of the powered, max-scaled vectors.
+def _toeplitz(x, ny):
+    nz = len(x) + ny - 1
+    T = np.zeros((nz, ny))
+    for m in range(nz):
+        for t in range(ny):
+            if 0 <= m - t < len(x):
+                T[m, t] = x[m - t]
+    return T
+
+
 def test_maxconv_equals_maxprod_with_toeplitz(orc):
     """max_i x_i y_(m-i) is the (x,max) product of the Toeplitz matrix of x
     with y (Alg. 2 on a structured operand)."""
     g = workloads.rng(2000)
     for nx, ny in ((1, 1), (5, 3), (17, 29)):
         x, y = g.random(nx), g.random(ny)
-        nz = nx + ny - 1
-        T = np.zeros((nz, ny))
-        for m in range(nz):
-            for t in range(ny):
-                if 0 <= m - t < nx:
-                    T[m, t] = x[m - t]
+        T = _toeplitz(x, ny)
         np.testing.assert_array_equal(orc.maxconv(x, y)[0], orc.maxprod(T, y[:, None])[:, 0])
+
+
+def test_maxconv_pnorm_equals_pnorm_with_toeplitz(orc):
+    """The p-norm max-convolution is the p-norm product of the Toeplitz matrix of
+    x with the column y (Sec. 1 and Alg. 5 on a structured operand), computed by
+    independent code.  With max x = max y = 1 the vector scaling and the
+    product's global power-of-two scaling (scaling = 1) both leave the values
+    unchanged, so the sums, p* and the estimate agree at a binding tau; with
+    other maxima and every p stable the estimate, which does not depend on the
+    scales, still agrees."""
+    g = workloads.rng(2002)
+    pl = list(range(7))
+    seen = set()
+    for nx, ny in ((1, 1), (6, 4), (40, 33), (200, 170)):
+        x, y = g.random(nx), g.random(ny)
+        x[g.integers(nx)] = 1.0
+        y[g.integers(ny)] = 1.0
+        T = _toeplitz(x, ny)
+        mc = orc.maxconv_pnorm(x, y, pl, tau=1e-3, want_S=True)
+        pr = orc.pnorm(T, y[:, None], pl, tau=1e-3, scaling=1, want_S=True)
+        assert np.array_equal(mc["p_sel"][0], pr["p_sel"][:, 0])
+        np.testing.assert_allclose(mc["S"][0], pr["S"][:, :, 0], rtol=1e-13, atol=1e-300)
+        np.testing.assert_allclose(mc["z"][0], pr["C"][:, 0], rtol=1e-13)
+        seen |= set(np.unique(mc["p_sel"][0] & 0x7F).tolist())
+        x2, y2 = 3.7 * g.random(nx), 0.3 * g.random(ny)
+        mc2 = orc.maxconv_pnorm(x2, y2, pl, tau=1e-300)
+        pr2 = orc.pnorm(_toeplitz(x2, ny), y2[:, None], pl, tau=1e-300, scaling=1)
+        assert np.all(mc2["p_sel"][0] == 6) and np.all(pr2["p_sel"][:, 0] == 6)
+        np.testing.assert_allclose(mc2["z"][0], pr2["C"][:, 0], rtol=1e-13)
+    assert len(seen) >= 3  # tau = 1e-3 selects several p*
 
 
 def test_conv_matches_numpy(orc):
