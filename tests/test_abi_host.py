@@ -231,3 +231,22 @@ def test_grouped_table_builder_on_the_host(binding):
     assert lib.pn_grouped_build_table(n, MNK, A, B, C, ctypes.byref(badopt), vpt, tab.size,
                                       None) == 1
     assert lib.pn_grouped_build_table(-1, MNK, A, B, C, ctypes.byref(o), vpt, tab.size, None) == 1
+
+
+def test_python_layer_has_no_cpu_path(binding):
+    """Every entry point of the Python layer refuses host tensors (and other
+    dtypes or ranks) before any work: there is no CPU fallback."""
+    torch = pytest.importorskip("torch")
+    import paper_1511_05690_gb300 as pn
+    a = torch.rand(8, 8)
+    calls = [lambda: pn.maxprod_pnorm(a, a), lambda: pn.maxprod_exact(a, a),
+             lambda: pn.apsp_pnorm(a), lambda: pn.GroupedProduct([a], [a]),
+             lambda: pn.maxconv_pnorm(a, a), lambda: pn.maxconv_exact(a, a),
+             lambda: pn.topk_xy(a, a, 3)]
+    for call in calls:
+        with pytest.raises(ValueError, match="CUDA"):
+            call()
+    with pytest.raises(ValueError, match="float32"):
+        pn.maxprod_pnorm(a.double(), a.double())
+    with pytest.raises(ValueError, match="2-D"):
+        pn.maxprod_pnorm(torch.rand(8), a)
