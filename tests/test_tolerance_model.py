@@ -89,3 +89,53 @@ def test_the_bound_is_within_a_small_factor(orc, mode):
         ratio = max(float((np.abs(S_emu[q] - ref["S"][q]) / ref["S"][q]).max() / s_tol(mode, K, lp))
                     for q, lp in enumerate(pl))
         assert 0.3 <= ratio <= 1.0, (mode, K, ratio)
+
+
+def _emulated_power(x, lp, half):
+    """x^(2^lp) by FP32 squarings, times its FP32 square root for the half
+    levels 1.5 * 2^lp (as the operand images form them)."""
+    for _ in range(lp):
+        x = (x * x).astype(np.float32)
+    if half:
+        x = (x * np.sqrt(x, dtype=np.float32)).astype(np.float32)
+    return x
+
+
+def _emulated_sum(a, b, lp, half, mode):
+    x = _round_mantissa(_emulated_power(a, lp, half), _KEEP[mode])
+    y = _round_mantissa(_emulated_power(b, lp, half), _KEEP[mode])
+    terms = (x[:, :, None].astype(np.float64) * y[None, :, :]).astype(np.float32)
+    return np.add.accumulate(terms, axis=1, dtype=np.float32)[:, -1, :].astype(np.float64)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "tf32"])
+@pytest.mark.parametrize("K", [5, 40, 700])
+def test_r2_bounds_hold_the_emulated_projection(orc, mode, K):
+    """The r = 2 parity bounds: the projection of sums carrying the emulated
+    GPU arithmetic stays inside r2_bounds built from the exact sums, both in
+    the well-resolved band (strong) and in the r = 1 .. plain bracket."""
+    from test_gpu_projection_r2 import _ETA, r2_bounds
+    A, B = workloads.wide_range_pair(24, 20, K, seed=3200 + K)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    pl = list(range(7))
+    tau = orc.default_tau(K, {"bf16": orc.BF16, "tf32": orc.TF32}[mode])
+    ref = orc.pnorm(A64, B64, pl, tau, want_S=True, estimator=2, r2_eta=_ETA[mode])
+    r, c = ref["r"], ref["c"]
+    a = (A64 / r[:, None]).astype(np.float32)
+    b = (B64 / c[None, :]).astype(np.float32)
+    n_strong = 0
+    for ls in range(2, 7):
+        sel = ((ref["p_sel"] & 0x7F) == ls) & ((ref["p_sel"] & 0x80) == 0)
+        if not sel.any():
+            continue
+        ps = 2.0 ** ls
+        exact = [ref["S"][ls - 2], ref["S"][ls - 1],
+                 orc.psums_real(A64, B64, [0.75 * ps], r, c)[0], ref["S"][ls]]
+        emu = [_emulated_sum(a, b, ls - 2, 0, mode), _emulated_sum(a, b, ls - 1, 0, mode),
+               _emulated_sum(a, b, ls - 1, 1, mode), _emulated_sum(a, b, ls, 0, mode)]
+        s = np.stack([e[sel] for e in exact])
+        lo, hi, strong = r2_bounds(orc, s, ps, mode, K, tau)
+        v = orc.project_r2(*[e[sel] for e in emu], ps / 4, eta=_ETA[mode])
+        assert np.all((v >= lo) & (v <= hi)), (mode, K, ls)
+        n_strong += int(strong.sum())
+    assert n_strong > 0  # the corner band, not only the bracket, is exercised
