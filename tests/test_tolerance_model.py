@@ -139,3 +139,29 @@ def test_r2_bounds_hold_the_emulated_projection(orc, mode, K):
         assert np.all((v >= lo) & (v <= hi)), (mode, K, ls)
         n_strong += int(strong.sum())
     assert n_strong > 0  # the corner band, not only the bracket, is exercised
+
+
+@pytest.mark.parametrize("mode", ["bf16", "tf32"])
+@pytest.mark.parametrize("K", [1, 5, 40, 700])
+def test_r1_tolerance_holds_the_emulated_projection(orc, mode, K):
+    """The r = 1 parity tolerance: (S^(p*) / S^(p*/2))^(2/p*) from sums carrying
+    the emulated GPU arithmetic stays within proj_tol of the oracle's
+    projection at every projected entry."""
+    from test_gpu_projection import proj_tol
+    A, B = workloads.wide_range_pair(24, 20, K, seed=3300 + K)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    pl = list(range(7))
+    tau = orc.default_tau(K, {"bf16": orc.BF16, "tf32": orc.TF32}[mode])
+    ref = orc.pnorm(A64, B64, pl, tau, want_S=True, estimator=1)
+    S_emu = _emulated_sums(A64, B64, ref["r"], ref["c"], pl, mode)
+    rc = ref["r"][:, None] * ref["c"][None, :]
+    checked = 0
+    for ls in range(1, 7):
+        sel = ((ref["p_sel"] & 0x7F) == ls) & ((ref["p_sel"] & 0x80) == 0)
+        if not sel.any():
+            continue
+        v = rc[sel] * (S_emu[ls][sel] / S_emu[ls - 1][sel]) ** (2.0 / 2 ** ls)
+        err = np.abs(v - ref["C"][sel]) / ref["C"][sel]
+        assert np.all(err <= proj_tol(mode, K, ls)), (mode, K, ls, err.max())
+        checked += int(sel.sum())
+    assert checked > 0
