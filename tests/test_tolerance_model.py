@@ -185,3 +185,22 @@ def test_r1_tolerance_holds_the_emulated_projection(orc, mode, K):
         assert np.all(err <= proj_tol(mode, K, ls)), (mode, K, ls, err.max())
         checked += int(sel.sum())
     assert checked > 0
+
+
+def test_fft_bound_holds_for_a_standard_fft(orc):
+    """The max-convolution tests bound one FP64 FFT convolution output by
+    E = 4 log2(N) 2^-53 (|a|_1 |b|_2 + |b|_1 |a|_2); numpy's FP64 FFT of the
+    powered, max-scaled vectors stays inside it against the oracle's naive
+    convolution (the bound is loose for an accurate FFT: numpy uses under 5 %)."""
+    import math
+    from test_gpu_maxconv import _fft_err
+    g = workloads.rng(3400)
+    for nx, ny in ((37, 20), (1000, 1500), (6000, 5000), (3, 40000)):
+        x, y = 1.0 - g.random(nx), 1.0 - g.random(ny)
+        nz = nx + ny - 1
+        N = max(2, 1 << math.ceil(math.log2(nz)))
+        for p in (1, 8, 64):
+            a, b = (x / x.max()) ** p, (y / y.max()) ** p
+            w = orc.conv(a, b)[0]
+            f = np.fft.irfft(np.fft.rfft(a, N) * np.fft.rfft(b, N), N)[:nz]
+            assert np.abs(f - w).max() <= _fft_err(a, b, N), (nx, ny, p)
