@@ -447,11 +447,11 @@ __device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, 
   const float opscale = ldexpf(1.0f, cm.s_op);
   __syncthreads();  // stile reuse across consecutive tiles
   {
-    // BK rows of K x 128 columns, all loads issued before the scaled values go
-    // to shared memory.  16-byte aligned rows: thread = (row group tid/32,
-    // columns 4 lane .. 4 lane + 3), float4 loads.  Otherwise thread = (row
-    // group, columns lane + 32 c), so that each load instruction reads one
-    // contiguous 128-byte row segment.
+    // BK rows of K x 128 columns, staged in chunks of up to 64 rows (below).
+    // 16-byte aligned rows: thread = (row group tid/32, columns 4 lane ..
+    // 4 lane + 3), float4 loads.  Otherwise thread = (row group, columns
+    // lane + 32 c), so that each load instruction reads one contiguous
+    // 128-byte row segment.
     const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
     const int n0 = rb * TILE_M;
     const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0) &&
