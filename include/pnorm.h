@@ -192,7 +192,7 @@ PN_API size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* 
  *   C_ij = r_i c_j (S^(p*))^(1/p*).
  * If no p is stable, p* is the smallest p of P and p_sel carries 0x80.
  * A: M x K (lda >= K), B: K x N (ldb >= N), C: M x N (ldc >= N), all FP32,
- * all entries in [0, 2^127] (else PN_EDOMAIN on the device).
+ * all entries in [0, 2^127], -0 counting as 0 (else PN_EDOMAIN on the device).
  * p_sel (nullable): M x N bytes, row stride N, log2(p*) | 0x80 if unstable.
  * S_sel (nullable): M x N FP32, row stride N, the scaled p-sum at p*.
  * ws / ws_bytes: workspace of at least pn_workspace_size() bytes. */
