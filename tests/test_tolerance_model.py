@@ -204,3 +204,63 @@ def test_fft_bound_holds_for_a_standard_fft(orc):
             w = orc.conv(a, b)[0]
             f = np.fft.irfft(np.fft.rfft(a, N) * np.fft.rfft(b, N), N)[:nz]
             assert np.abs(f - w).max() <= _fft_err(a, b, N), (nx, ny, p)
+
+
+def _split_3xtf32(x):
+    hi = _round_mantissa(x, 10)
+    lo = _round_mantissa((x - hi).astype(np.float32), 10)
+    return hi, lo
+
+
+def _gemm_3xtf32(X, Y):
+    """X (m x l) @ Y (l x n) as three TF32 products (each exact in FP32),
+    accumulated sequentially in FP32 over l."""
+    xh, xl = _split_3xtf32(X)
+    yh, yl = _split_3xtf32(Y)
+    t = (xh[:, :, None].astype(np.float64) * yh[None] + xh[:, :, None].astype(np.float64) * yl[None]
+         + xl[:, :, None].astype(np.float64) * yh[None])
+    return np.add.accumulate(t.astype(np.float32), axis=1, dtype=np.float32)[:, -1, :]
+
+
+@pytest.mark.parametrize("shape,plog,underflows",
+                         [((64, 48, 80), 4, False), ((30, 20, 300), 2, False),
+                          ((40, 90, 33), 6, True)])
+def test_adjoint_tolerance_holds_the_emulated_gradient(orc, shape, plog, underflows):
+    """The adjoint's parity tolerance grad_tol: for L = sum log C at a fixed p,
+    W = G C / S = 1 / S, dA = (W B'^pT) a'^(p-1) / r and dB = (A'^pT W) b'^(p-1) / c,
+    emulated with FP32 sums, 3xTF32 products with FP32 accumulation and FP32
+    elementwise factors (a'^(p-1) as the product of the squarings, as the
+    gradient epilogue forms it), stay within grad_tol of the FP64 oracle
+    gradient (relative, with the GPU test's absolute floor of 1e-30 of the
+    largest entry).  Known limit: a'^(p-1) below the smallest normal FP32
+    2^-126 (a' < 2^(-126/(p-1)), about 0.25 at p = 64) keeps fewer bits, and
+    below 2^-149 it is 0, although W = 1/S can lift the exact entry above the
+    floor at short contractions (K = 33 here).  Entries whose factor is normal
+    meet the tolerance; those whose factor is 0 are 0."""
+    from test_gpu_backward import grad_tol, rel_err
+    M, N, K = shape
+    A, B = workloads.uniform_pair(M, N, K, seed=3500 + M)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    r, c = orc.row_scales(A64), orc.col_scales(B64)
+    a = (A64 / r[:, None]).astype(np.float32)
+    b = (B64 / c[None, :]).astype(np.float32)
+    ap, bp = a.copy(), b.copy()
+    am1, bm1 = np.ones_like(a), np.ones_like(b)
+    for _ in range(plog):  # x^(p-1) = x x^2 x^4 ... x^(p/2), x^p by squaring
+        am1, bm1 = (am1 * ap).astype(np.float32), (bm1 * bp).astype(np.float32)
+        ap, bp = (ap * ap).astype(np.float32), (bp * bp).astype(np.float32)
+    S = _gemm_3xtf32(ap, bp)
+    W = (np.float32(1.0) / S).astype(np.float32)
+    dA = (_gemm_3xtf32(W, bp.T) * am1 / r[:, None].astype(np.float32)).astype(np.float32)
+    dB = (_gemm_3xtf32(ap.T, W) * bm1 / c[None, :].astype(np.float32)).astype(np.float32)
+    plogs = np.full((M, N), plog, dtype=np.uint8)
+    Cref = orc.pnorm(A64, B64, [plog], 1e-300)["C"]
+    gA, gB = orc.pnorm_grad(A64, B64, plogs, 1.0 / Cref)
+    lost = 0
+    for d, g, f, L in ((dA, gA, am1, N), (dB, gB, bm1, M)):
+        assert np.all(d[f == 0] == 0)
+        under = f < 2.0 ** -126  # subnormal or zero factor
+        e = rel_err(d, g)
+        assert e[~under].max() <= grad_tol(plog, L), (e[~under].max(), grad_tol(plog, L))
+        lost += int((e[under] > grad_tol(plog, L)).sum())
+    assert (lost > 0) == underflows
