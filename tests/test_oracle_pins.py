@@ -385,6 +385,23 @@ def test_entries_match_full_psums(orc):
     np.testing.assert_allclose(Se, S[:, ii, jj].T, rtol=1e-14)
 
 
+
+def test_real_exponent_entries_match_full_sums(orc):
+    """The selected-entry loop at real exponents (the 3p/4 family) agrees with
+    the full real-exponent sums, and at integer powers of two with the
+    selected-entry loop of Alg. 5's sums."""
+    A, B = workloads.wide_range_pair(23, 17, 41, seed=27, dtype=np.float64)
+    r, c = orc.row_scales(A), orc.col_scales(B)
+    g = workloads.rng(28)
+    ii, jj = g.integers(0, 23, 50), g.integers(0, 17, 50)
+    pw = [0.75, 1.5, 3.0, 6.0, 12.0, 24.0, 48.0]
+    Sf = orc.psums_real(A, B, pw, r, c)
+    np.testing.assert_allclose(orc.entries_real(A, B, ii, jj, pw, r, c), Sf[:, ii, jj].T,
+                               rtol=1e-14)
+    _, Se = orc.entries(A, B, ii, jj, [0, 2, 4], r, c)
+    np.testing.assert_allclose(orc.entries_real(A, B, ii, jj, [1.0, 4.0, 16.0], r, c), Se,
+                               rtol=1e-14)
+
 # ------------------------------------------------------ r = 1 projection ---
 # Sec. 2.1 (multiset projection).  With v = (u / max u)^(p*/2) the r = 1
 # estimate is max u * (||v||_2^2 / ||v||_1)^(2/p*), which never exceeds max u
