@@ -338,11 +338,8 @@ def run_ours(args):
                 S34 = oracle.entries_real(A64, B_h.astype(np.float64), loc, jj,
                                           [0.75 * 2.0 ** lp for lp in P_LOG2], r[rows], c)
                 S34 = S34.T[:, None, :]
-            # the r = 2 projection's resolution margin: 32 u of the operand format
-            r2_eta = 32 * {"f32": 2.0 ** -21, "tf32": 2.0 ** -11, "bf16": 2.0 ** -8,
-                           "f16": 2.0 ** -11, "e4m3": 2.0 ** -4}[args.compute]
             pn_ref, ps_o, _ = oracle.estimate(S.T[:, None, :], P_LOG2, np.ones(1), rc, tau,
-                                              estimator=args.estimator, S34=S34, r2_eta=r2_eta)
+                                              estimator=args.estimator, S34=S34)
             coef = None
             if args.correction == 2:
                 frows = np.unique(fit_ii)

@@ -95,17 +95,17 @@ def _load():
             lib.orc_psums.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
             lib.orc_estimate.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, vp, vp, vp]
             lib.orc_estimate_ex.argtypes = [i64, i64, ci, vp, vp, vp, vp, dbl, ci, vp, vp, vp]
-            lib.orc_estimate_ex2.argtypes = [i64, i64, ci, vp, vp, vp, vp, vp, dbl, ci, dbl, vp,
+            lib.orc_estimate_ex2.argtypes = [i64, i64, ci, vp, vp, vp, vp, vp, dbl, ci, vp,
                                              vp, vp]
             lib.orc_pnorm_ex2.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci, ci,
-                                          dbl, vp, vp, vp, vp, vp, vp]
+                                          vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm_ex2.restype = ci
             lib.orc_psums_real.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, vp, ci, vp, vp]
             lib.orc_entries_real.argtypes = [i64, vp, i64, vp, i64, vp, vp, ci, vp, i64, vp, vp,
                                              vp]
-            lib.orc_project_r2.argtypes = [dbl, dbl, dbl, dbl, dbl, dbl]
+            lib.orc_project_r2.argtypes = [dbl, dbl, dbl, dbl, dbl]
             lib.orc_project_r2.restype = dbl
-            lib.orc_project_r2_batch.argtypes = [i64, vp, vp, vp, vp, dbl, dbl, vp]
+            lib.orc_project_r2_batch.argtypes = [i64, vp, vp, vp, vp, dbl, vp]
             lib.orc_pnorm.argtypes = [i64, i64, i64, vp, i64, vp, i64, ci, vp, dbl, ci,
                                       vp, vp, vp, vp, vp, vp]
             lib.orc_pnorm.restype = ci
@@ -230,11 +230,11 @@ def psums(A, B, p_log2, r=None, c=None, scaling: int = 2):
     return S
 
 
-def estimate(S, p_log2, r, c, tau: float, estimator: int = 0, S34=None, r2_eta: float = 1e-6):
+def estimate(S, p_log2, r, c, tau: float, estimator: int = 0, S34=None):
     """Largest stable p per entry; returns (Chat, p_sel, S_sel).  estimator 1
     replaces the root by the r = 1 projection from S^(p*/2) and S^(p*);
     estimator 2 by the r = 2 projection, which also needs S34[q] = the sums
-    at 3 p_q / 4 (same shape as S); r2_eta is its resolution margin."""
+    at 3 p_q / 4 (same shape as S)."""
     S = _f64(S)
     n_p, M, N = S.shape
     pl = _plog(p_log2)
@@ -247,19 +247,21 @@ def estimate(S, p_log2, r, c, tau: float, estimator: int = 0, S34=None, r2_eta: 
     psel = np.empty((M, N), dtype=np.uint8)
     Ssel = np.empty((M, N), dtype=np.float64)
     _load().orc_estimate_ex2(M, N, n_p, _p(pl), _p(S), _p(S34) if S34 is not None else None,
-                             _p(r), _p(c), float(tau), int(estimator), float(r2_eta), _p(Chat),
+                             _p(r), _p(c), float(tau), int(estimator), _p(Chat),
                              _p(psel), _p(Ssel))
     return Chat, psel, Ssel
 
 
-def project_r2(s1, s2, s3, s4, p_prime: float, eta: float = 1e-6):
+def project_r2(s1, s2, s3, s4, p_prime: float):
     """The r = 2 multiset projection (Sec. 2.1) of the four evenly spaced
-    power sums s_m = sum_i u_i^(m p'), elementwise over arrays (see oracle.c)."""
+    power sums s_m = sum_i u_i^(m p'), elementwise over arrays (see oracle.c):
+    sums with s1 s3 - s2^2 <= 1e-6 s2^2 (no second value resolved by exact
+    sums) give the r = 1 value."""
     s1, s2, s3, s4 = np.broadcast_arrays(*(np.asarray(x, dtype=np.float64) for x in (s1, s2, s3, s4)))
     s1, s2, s3, s4 = (np.ascontiguousarray(x).ravel() for x in (s1, s2, s3, s4))
     out = np.empty(len(s1), dtype=np.float64)
     _load().orc_project_r2_batch(len(s1), _p(s1), _p(s2), _p(s3), _p(s4), float(p_prime),
-                                 float(eta), _p(out))
+                                 _p(out))
     return out
 
 
@@ -300,11 +302,10 @@ def affine_fit(est, exact, cls, n_cls: int):
 
 
 def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
-          estimator: int = 0, correction: int = 0, fit_ij=None, r2_eta: float = 1e-6):
+          estimator: int = 0, correction: int = 0, fit_ij=None):
     """Full p-norm estimate of the (x,max) product (Alg. 5 with H = Alg. 3).
     estimator 0 is the plain largest-stable-p norm, 1 the r = 1 projection,
-    2 the r = 2 projection (with the sums at 3p/4, computed here; r2_eta is
-    its resolution margin, see oracle.c).
+    2 the r = 2 projection (with the sums at 3p/4, computed here).
     correction 1 divides by K^(1/p*); correction 2 fits the affine model of
     the Discussion on the sample entries fit_ij = (ii, jj) and applies it.
 
@@ -325,7 +326,7 @@ def pnorm(A, B, p_log2, tau: float, scaling: int = 2, want_S: bool = False,
     c = np.empty(N, dtype=np.float64)
     S = np.empty((len(pl), M, N), dtype=np.float64) if want_S else None
     rc = _load().orc_pnorm_ex2(M, N, K, _p(A), K, _p(B), N, len(pl), _p(pl), float(tau),
-                               int(scaling), int(estimator), float(r2_eta), _p(Chat), _p(psel),
+                               int(scaling), int(estimator), _p(Chat), _p(psel),
                                _p(Ssel), _p(S) if S is not None else None, _p(r), _p(c))
     if rc:
         raise MemoryError("oracle pnorm allocation failed")

@@ -33,10 +33,11 @@
  *     of its rows and the estimate the larger root of its quadratic, to the
  *     power 1/p'.  Entries whose p* / 2 and p* / 4 are not the two p below
  *     p* in P keep the plain estimate; sums that do not resolve a second
- *     value (s1 s3 - s2^2 <= eta s2^2, eta a margin over the sums' relative
- *     error: 1e-6 for exact sums, 32 u of the operand format on the GPU)
- *     keep the r = 1 value, and the root is clamped between the r = 1 value
- *     and the plain norm (the interval that holds the larger Gauss node).
+ *     value (s1 s3 - s2^2 <= 1e-6 s2^2: the oracle's sums are exact up to
+ *     FP64 rounding, so the margin only guards the rounding of that
+ *     difference, nothing of any operand format) keep the r = 1 value, and
+ *     the root is clamped between the r = 1 value and the plain norm (the
+ *     interval that holds the larger Gauss node).
  *   - corrections (Sec. 2.1 bound remark; Discussion), in the scaled space
  *     where the exact value lies in (0, 1]: correction 1 divides the estimate
  *     by K^(1/p*), the upper end of its envelope; correction 2 fits
@@ -306,18 +307,19 @@ static double project_r1(double s1, double s2, double p_prime) {
 /* The s_m are the moments of the measure with mass w x at each value x,   */
 /* so the roots are its 2-point Gauss nodes and the larger one lies between */
 /* the 1-point node s2 / s1 (the r = 1 value) and max x <= s4^(1/4) (the    */
-/* plain norm).  Readings: when gamma_2 <= eta s2^2 the sums do not resolve  */
-/* a second value (s1 s3 >= s2^2 always; eta is a margin over the sums'     */
-/* relative error, 1e-6 for exact sums) and the r = 1 value is returned;    */
+/* plain norm).  Readings: when gamma_2 <= R2_ETA s2^2 the sums do not      */
+/* resolve a second value (s1 s3 >= s2^2 always; R2_ETA = 1e-6 is a margin   */
+/* over the FP64 rounding of exact sums) and the r = 1 value is returned;   */
 /* a negative discriminant (rounding) counts as zero; a root that is not    */
 /* positive gives the r = 1 value; the root is clamped to [s2 / s1, s4^(1/4)] */
 /* (never binding for exact sums; with rounded sums it keeps the estimate   */
 /* between the r = 1 value and the plain norm).                              */
-double orc_project_r2(double s1, double s2, double s3, double s4, double p_prime, double eta) {
+#define R2_ETA 1e-6
+double orc_project_r2(double s1, double s2, double s3, double s4, double p_prime) {
   double g0 = s2 * s4 - s3 * s3;
   double g1 = s2 * s3 - s1 * s4;
   double g2 = s1 * s3 - s2 * s2;
-  if (!(g2 > eta * s2 * s2)) return project_r1(s1, s2, p_prime);
+  if (!(g2 > R2_ETA * s2 * s2)) return project_r1(s1, s2, p_prime);
   double disc = g1 * g1 - 4.0 * g0 * g2;
   if (disc < 0.0) disc = 0.0;
   double a = (-g1 + sqrt(disc)) / (2.0 * g2);
@@ -330,9 +332,9 @@ double orc_project_r2(double s1, double s2, double s3, double s4, double p_prime
 
 /* orc_project_r2 over n quadruples (s1[e], s2[e], s3[e], s4[e]).            */
 void orc_project_r2_batch(int64_t n, const double* s1, const double* s2, const double* s3,
-                          const double* s4, double p_prime, double eta, double* out) {
+                          const double* s4, double p_prime, double* out) {
   for (int64_t e = 0; e < n; ++e)
-    out[e] = orc_project_r2(s1[e], s2[e], s3[e], s4[e], p_prime, eta);
+    out[e] = orc_project_r2(s1[e], s2[e], s3[e], s4[e], p_prime);
 }
 
 /* Alg. 5, second loop, with estimateMaxFromNormPowerSequence:              */
@@ -349,7 +351,7 @@ void orc_project_r2_batch(int64_t n, const double* s1, const double* s2, const d
 /* p_sel = log2(p*) | 0x80 if unstable; S_sel = S^(p*).                      */
 void orc_estimate_ex2(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
                       const double* S34, const double* r, const double* c, double tau,
-                      int estimator, double r2_eta, double* Chat, uint8_t* psel, double* Ssel) {
+                      int estimator, double* Chat, uint8_t* psel, double* Ssel) {
   int64_t i;
 #pragma omp parallel for schedule(static)
   for (i = 0; i < M; ++i) {
@@ -378,7 +380,7 @@ void orc_estimate_ex2(int64_t M, int64_t N, int n_p, const int* p_log2, const do
         double s2 = S[((int64_t)(q_sel - 1) * M + i) * N + j];
         double s1 = S[((int64_t)(q_sel - 2) * M + i) * N + j];
         double s3 = S34[((int64_t)q_sel * M + i) * N + j];
-        est = orc_project_r2(s1, s2, s3, s, 0.25 * p, r2_eta);
+        est = orc_project_r2(s1, s2, s3, s, 0.25 * p);
       }
       if (Chat) Chat[i * N + j] = r[i] * c[j] * est;
       if (psel) psel[i * N + j] = (uint8_t)(p_log2[q_sel] | (unstable ? 0x80 : 0));
@@ -390,7 +392,7 @@ void orc_estimate_ex2(int64_t M, int64_t N, int n_p, const int* p_log2, const do
 void orc_estimate_ex(int64_t M, int64_t N, int n_p, const int* p_log2, const double* S,
                      const double* r, const double* c, double tau, int estimator, double* Chat,
                      uint8_t* psel, double* Ssel) {
-  orc_estimate_ex2(M, N, n_p, p_log2, S, NULL, r, c, tau, estimator, 1e-6, Chat, psel, Ssel);
+  orc_estimate_ex2(M, N, n_p, p_log2, S, NULL, r, c, tau, estimator, Chat, psel, Ssel);
 }
 
 /* Discussion (affine model from a few exact sub-solutions): least squares  */
@@ -455,7 +457,7 @@ void orc_estimate(int64_t M, int64_t N, int n_p, const int* p_log2, const double
 /* case a temporary is used.                                                 */
 int orc_pnorm_ex2(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
                   const double* B, int64_t ldb, int n_p, const int* p_log2, double tau,
-                  int scaling, int estimator, double r2_eta, double* Chat, uint8_t* psel,
+                  int scaling, int estimator, double* Chat, uint8_t* psel,
                   double* Ssel, double* S_all, double* r_out, double* c_out) {
   double* r = (double*)malloc(sizeof(double) * (M > 0 ? M : 1));
   double* c = (double*)malloc(sizeof(double) * (N > 0 ? N : 1));
@@ -473,7 +475,7 @@ int orc_pnorm_ex2(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda,
     orc_psums_real(M, N, K, A, lda, B, ldb, r, c, n_p, pw, S34);
     free(pw);
   }
-  orc_estimate_ex2(M, N, n_p, p_log2, S, S34, r, c, tau, estimator, r2_eta, Chat, psel, Ssel);
+  orc_estimate_ex2(M, N, n_p, p_log2, S, S34, r, c, tau, estimator, Chat, psel, Ssel);
   free(S34);
   if (r_out) memcpy(r_out, r, sizeof(double) * M);
   if (c_out) memcpy(c_out, c, sizeof(double) * N);
@@ -487,7 +489,7 @@ int orc_pnorm_ex(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, 
                  int64_t ldb, int n_p, const int* p_log2, double tau, int scaling, int estimator,
                  double* Chat, uint8_t* psel, double* Ssel, double* S_all, double* r_out,
                  double* c_out) {
-  return orc_pnorm_ex2(M, N, K, A, lda, B, ldb, n_p, p_log2, tau, scaling, estimator, 1e-6, Chat,
+  return orc_pnorm_ex2(M, N, K, A, lda, B, ldb, n_p, p_log2, tau, scaling, estimator, Chat,
                        psel, Ssel, S_all, r_out, c_out);
 }
 

@@ -575,18 +575,27 @@ def test_projection_r2_matches_general_construction(orc):
 
 
 def test_projection_r2_guard_and_clamp(orc):
-    """A margin eta above s1 s3 / s2^2 - 1 gives the r = 1 value; perturbed sums
-    (up to 5 %, no longer a moment sequence) still give a value between the
-    r = 1 value and the plain norm, the interval of the larger Gauss node."""
+    """Exact sums of n ones and one value y^(1/p'): t3 - 1 = s1 s3 / s2^2 - 1 is
+    about y / n.  Below the oracle's margin 1e-6 (no second value resolved by
+    FP64 sums) the result is the r = 1 value; above it the two values are
+    recovered and the estimate is the max, 1.  Perturbed sums (up to 5 %, no
+    longer a moment sequence) still give a value between the r = 1 value and
+    the plain norm, the interval of the larger Gauss node."""
     g = workloads.rng(1670)
+    pp = 4.0
+    for n in (1, 3, 17):
+        for y, resolved in ((1e-9, False), (1e-7, False), (1e-3, True), (0.3, True)):
+            u = np.concatenate([np.ones(n), [y ** (1 / pp)]])
+            s = np.array([np.sum(u ** (m * pp)) for m in (1, 2, 3, 4)])
+            t = s[2] * s[0] / s[1] ** 2 - 1
+            assert (t > 1e-6) == resolved, (n, y, t)
+            r1 = (s[1] / s[0]) ** (1 / pp)
+            want = 1.0 if resolved else r1
+            np.testing.assert_allclose(orc.project_r2(*s, pp)[0], want, rtol=1e-9)
     for _ in range(200):
         u = g.random(int(g.integers(2, 40)))
         u = u / u.max()
-        pp = 4.0
         s = np.array([np.sum(u ** (m * pp)) for m in (1, 2, 3, 4)])
-        t = s[2] * s[0] / s[1] ** 2 - 1
-        r1 = (s[1] / s[0]) ** (1 / pp)
-        np.testing.assert_allclose(orc.project_r2(*s, pp, eta=t * 1.01)[0], r1, rtol=1e-14)
         sp = s * (1 + 0.05 * g.uniform(-1, 1, 4))
         v = orc.project_r2(*sp, pp)[0]
         lo, hi = (sp[1] / sp[0]) ** (1 / pp), sp[3] ** (1 / (4 * pp))
