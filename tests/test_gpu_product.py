@@ -122,6 +122,9 @@ def _compare(pn, orc, A, B, mode, plog_list, tau=None, tile_n=0, scaling=2):
     bad = (err > tol) & (expect > 0)
     assert not np.any(bad), (f"{mode}: max rel err {err[expect > 0].max():.3e}, "
                              f"worst at {np.argwhere(bad)[:5]}")
+    if mode == "f32":
+        # the FP32 (3xTF32) bar: 1e-5 relative against the FP64 oracle everywhere
+        assert err[expect > 0].max(initial=0.0) <= 1e-5, float(err[expect > 0].max())
     assert np.all(C[expect == 0] == 0)
     # S_sel is the scaled p-sum at p*
     serr = np.abs(ssel - S_at) / np.maximum(S_at, 1e-300)

@@ -52,6 +52,64 @@ def test_hand_worked_3x3(orc):
     np.testing.assert_allclose(out["C"], expect, rtol=1e-15)
 
 
+def _golden_value(tok):
+    """A value of tests/golden/apsp_3node.txt: a rational, inf, ln<k>, or
+    sqrt(<rational>) optionally divided by an integer."""
+    import re
+    if tok == "inf":
+        return math.inf
+    if tok.startswith("ln"):
+        return math.log(int(tok[2:]))
+    m = re.fullmatch(r"sqrt\(([0-9/]+)\)(?:/([0-9]+))?", tok)
+    if m:
+        return math.sqrt(Fraction(m.group(1))) / (int(m.group(2)) if m.group(2) else 1)
+    return float(Fraction(tok))
+
+
+def _read_apsp_golden():
+    rows = {}
+    with open(os.path.join(GOLDEN, "apsp_3node.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            rows.setdefault(key, []).append(vals)
+    return rows
+
+
+@pytest.mark.parametrize("policy", [1, 2])
+def test_hand_worked_apsp_diag_policies(orc, policy):
+    """Hand-derived p-norm APSP (tests/golden/apsp_3node.txt): a zero-weight
+    edge makes one estimate exceed 1 after the first squaring.  Policy 1
+    (diagonal reset) and policy 2 (reset and clamp to x <= 1) give different
+    results, both fixed by hand; policy 2 never exceeds x = 1 and stays at or
+    above the exact x = exp(-d) (Floyd-Warshall, also in the file).  Dropping
+    the clamp gives policy 1's values; clamping only before a squaring leaves
+    entries above 1 after the last one; both fail here."""
+    g = _read_apsp_golden()
+    W = np.array([[_golden_value(t) for t in row] for row in g["W"]])
+    pl = [int(t) for t in g["p_log2"][0]]
+    tau = float(g["tau"][0][0])
+    T = int(g["squarings"][0][0])
+    exact = np.array([[_golden_value(t) for t in row] for row in g["exact"]])
+    np.testing.assert_allclose(orc.floyd_warshall(W), exact, rtol=1e-15, atol=0)
+    want = np.array([[_golden_value(t) for t in row] for row in g[f"X{policy}"]])
+    D, _ = orc.apsp_pnorm(W, pl, tau=tau, n_squarings=T, diag_policy=policy)
+    X = np.exp(-D)
+    np.testing.assert_allclose(X, want, rtol=1e-14)
+    assert np.all(np.diag(D) == 0.0)
+    x_exact = np.exp(-exact)
+    assert np.all(X >= x_exact * (1 - 1e-14))
+    if policy == 2:
+        assert np.all(X <= 1.0) and np.all(D >= 0.0)
+    else:
+        assert np.any(X > 1.0 + 1e-3)
+    # ceil(log2 n) squarings by default
+    D0, _ = orc.apsp_pnorm(W, pl, tau=tau, diag_policy=policy)
+    np.testing.assert_array_equal(D0, D)
+
+
 # ------------------------------------------------------ exact products ---
 def test_maxprod_rank_one_closed_form(orc):
     """A = u v^T, B = x y^T  =>  C_ij = u_i y_j max_k v_k x_k."""
