@@ -127,8 +127,11 @@ typedef struct pn_opts {
    *       4/p*; it never exceeds the exact max and never falls below the
    *       r = 1 value.  The sums at 3p* / 4 come from extra levels
    *       p = 1.5 * 2^k; entries whose p* / 2 and p* / 4 are not the two p
-   *       below p* in P (and unstable entries) keep the plain estimate, sums
-   *       of nearly one value (s1 s3 - s2^2 <= 1e-6 s2^2) the r = 1 value.
+   *       below p* in P (and unstable entries) keep the plain estimate; sums
+   *       that the operand format's rounding leaves unresolved
+   *       (s1 s3 - s2^2 <= eta s2^2, eta = 32 u of the powered-operand
+   *       format: 2^-16 PN_F32_EXACT, 2^-6 PN_TF32 / PN_F16, 2^-3 PN_BF16,
+   *       2 PN_E4M3, i.e. never resolved in E4M3) keep the r = 1 value.
    *       About three more tensor-core passes over every tile holding an
    *       entry resolved at p*; the workspace grows by 2 M N floats.
    *       maxprod_pnorm and maxprod_pnorm_static accept it; the grouped
@@ -202,8 +205,9 @@ PN_API pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, 
                         void* stream);
 
 /* Size of the scratch array behind maxprod_pnorm_static: 64 MiB of device
- * memory, reserved on every GPU that loads this library until the process
- * exits. */
+ * memory.  With CUDA's default lazy module loading it is reserved on a device
+ * once maxprod_pnorm_static is first used there, until the process exits or
+ * the device is reset. */
 #define PN_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 
 /* maxprod_pnorm for callers that cannot allocate device memory (no citation:
@@ -215,10 +219,13 @@ PN_API pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, 
  * allocates nothing.  Arguments and results are those of maxprod_pnorm.
  * Returns PN_EWORKSPACE when pn_workspace_size(M, N, K, opts) exceeds
  * PN_STATIC_SCRATCH_BYTES (with P = {1..64}, square products fit up to about
- * n = 3900 with BF16 operands and n = 2000 with PN_F32_EXACT).  The first call on a device looks up the array's device
- * address; make it before any stream capture.  Every call uses the same array,
- * so calls whose GPU work can overlap (other streams, other host threads) race
- * and must be serialised by the caller. */
+ * n = 3900 with BF16 operands and n = 2000 with PN_F32_EXACT).  A call made
+ * outside a stream capture looks up the array's device address (so a device
+ * reset, which moves the array, is picked up); a call made while `stream` is
+ * capturing uses the address of an earlier call on that device, so make one
+ * call on each device before capturing (PN_ECUDA otherwise).  Every call uses
+ * the same array, so calls whose GPU work can overlap (other streams, other
+ * host threads) race and must be serialised by the caller. */
 PN_API pn_status maxprod_pnorm_static(int64_t M, int64_t N, int64_t K, const float* A,
                                       int64_t lda, const float* B, int64_t ldb, float* C,
                                       int64_t ldc, uint8_t* p_sel, float* S_sel,

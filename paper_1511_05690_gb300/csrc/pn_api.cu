@@ -87,9 +87,9 @@ float tau_up(double t) {
 struct Layout {
   int BN = 0, KB = 0, RBA = 0, RBB = 0, tiles_m = 0, tiles_n = 0, total_tiles = 0;
   int state_ld = 0, n_p = 0, n_slots = 0, planes = 1;
-  size_t off_fit = 0, off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0,
+  size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0,
          off_cflag = 0;
-  size_t ctrl_bytes = 0, off_coef = 0;
+  size_t ctrl_bytes = 0, off_coef = 0, off_samp = 0, off_scls = 0;
   size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_pend2 = 0,
          off_park = 0, off_aimg = 0, off_bimg = 0;
   size_t a_level_bytes = 0, b_level_bytes = 0, a_plane = 0, b_plane = 0;
@@ -111,9 +111,7 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.total_tiles = L.tiles_m * L.tiles_n;
   L.state_ld = L.tiles_n * (L.BN / 32);
   size_t off = 0;
-  // control words, cleared at the start of every call (the FP64 class sums of
-  // the affine correction first, for their alignment)
-  L.off_fit = off; off += sizeof(double) * 5 * PN_MAX_P;
+  // control words, cleared at the start of every call
   L.off_rmax = off; off += sizeof(uint32_t) * M;
   L.off_cmax = off; off += sizeof(uint32_t) * N;
   L.off_gmax = off; off += sizeof(uint32_t) * 2;
@@ -123,6 +121,11 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.ctrl_bytes = align_up(off, 16);
   off = align_up(off, WS_ALIGN);
   L.off_coef = off; off = align_up(off + sizeof(float) * 2 * PN_MAX_P, WS_ALIGN);
+  if (o->correction == 2) {
+    // the affine correction's per-sample records (estimate, exact value, class)
+    L.off_samp = off; off = align_up(off + sizeof(double) * 2 * (size_t)o->n_fit, WS_ALIGN);
+    L.off_scls = off; off = align_up(off + sizeof(int32_t) * (size_t)o->n_fit, WS_ALIGN);
+  }
   L.off_r = off; off = align_up(off + sizeof(float) * M, WS_ALIGN);
   L.off_c = off; off = align_up(off + sizeof(float) * N, WS_ALIGN);
   L.off_work = off;
@@ -316,7 +319,8 @@ pn_status run_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
       fa.n_p = o->n_p;
       for (int t = 0; t < o->n_p; ++t) fa.p_log2[t] = o->p_log2[t];
       fa.estimator = o->estimator;
-      fa.sums = reinterpret_cast<double*>(ws + L.off_fit);
+      fa.samp = reinterpret_cast<double*>(ws + L.off_samp);
+      fa.scls = reinterpret_cast<int32_t*>(ws + L.off_scls);
       fa.coef = reinterpret_cast<float*>(ws + L.off_coef);
       fa.user_coef = o->fit_coef;
       if ((e = launch_fit(cm, fa, stream))) return PN_ECUDA;
@@ -478,7 +482,9 @@ pn_status pn_maxprod_exact_variant(int64_t M, int64_t N, int64_t K, const float*
 size_t pn_apsp_workspace_size(int64_t n, const pn_opts* opts) {
   if (!opts_valid(opts) || !dims_ok(n, n, n)) return 0;
   const size_t x_bytes = align_up(sizeof(float) * n * n, IMG_ALIGN);
-  return x_bytes + make_layout(n, n, n, opts).total;
+  // like pn_workspace_size: with tile_n = 0 large enough for either width the
+  // autotuner may pick later
+  return x_bytes + pn_workspace_size(n, n, n, opts);
 }
 
 pn_status apsp_pnorm(int64_t n, const float* W, int64_t ldw, float* D, int64_t ldd,

@@ -20,8 +20,9 @@ constexpr int FIT_THREADS = 256;  // one block per sample
 // One block per sample entry (i, j): u_k = (a_ik / r_i)(b_kj / c_j) in FP32,
 // the exact max over k and the p-sums S^(p) for every p of P (each thread a
 // strided part of k, then warp and block reductions), the sample's own p* and
-// estimate (the same rule as the epilogue), then FP64 class sums n, x, y,
-// x^2, x y with x = estimate and y = exact value.
+// estimate (the same rule as the epilogue); the sample's record (estimate,
+// exact value, class) goes to its own slot, so that the class sums can be
+// formed in a fixed order (deterministic results).
 __global__ void __launch_bounds__(FIT_THREADS)
     k_fit_samples(const __grid_constant__ Common cm, const __grid_constant__ FitArgs fa) {
   __shared__ float red[FIT_THREADS / 32][PN_MAX_P + 1];
@@ -30,7 +31,10 @@ __global__ void __launch_bounds__(FIT_THREADS)
   const Prob& P = cm.single;
   const int i = fa.fi[s], j = fa.fj[s];
   if (i < 0 || i >= P.M || j < 0 || j >= P.N) {
-    if (threadIdx.x == 0) set_status(cm.status, PN_EINVAL);
+    if (threadIdx.x == 0) {
+      set_status(cm.status, PN_EINVAL);
+      fa.scls[s] = -1;
+    }
     return;
   }
   const float ri = cm.r[P.rc_r + i], cj = cm.c[P.rc_c + j];
@@ -102,21 +106,34 @@ __global__ void __launch_bounds__(FIT_THREADS)
                                                            static_cast<double>(s_sel));
     est = pow(ratio, 2.0 / p);
   }
-  const double y = static_cast<double>(mx);
-  double* c5 = fa.sums + 5 * qs;
-  atomicAdd(c5 + 0, 1.0);
-  atomicAdd(c5 + 1, est);
-  atomicAdd(c5 + 2, y);
-  atomicAdd(c5 + 3, est * est);
-  atomicAdd(c5 + 4, est * y);
+  fa.samp[2 * s] = est;
+  fa.samp[2 * s + 1] = static_cast<double>(mx);
+  fa.scls[s] = qs;
 }
 
-// One thread per class: the least-squares line from the class sums (the
-// oracle's rule, including the degenerate cases).
+// One warp per class q: the FP64 sums n, x, y, x^2, x y over the samples of
+// the class (x = estimate, y = exact value), lane l taking samples l, l + 32,
+// ... in order and a fixed butterfly combining the lanes, so the sums and the
+// line are the same on every run; then the least-squares line (the oracle's
+// rule, including the degenerate cases).
 __global__ void k_fit_solve(const __grid_constant__ FitArgs fa) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= fa.n_p) return;
-  const double* c5 = fa.sums + 5 * q;
+  double c5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int s = lane; s < fa.n_fit; s += 32) {
+    if (fa.scls[s] != q) continue;
+    const double x = fa.samp[2 * s], y = fa.samp[2 * s + 1];
+    c5[0] += 1.0;
+    c5[1] += x;
+    c5[2] += y;
+    c5[3] += x * x;
+    c5[4] += x * y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int t = 0; t < 5; ++t) c5[t] += __shfl_xor_sync(0xffffffffu, c5[t], off);
+  if (lane != 0) return;
   const double n = c5[0], sx = c5[1], sy = c5[2], sxx = c5[3], sxy = c5[4];
   double a = 1.0, b = 0.0;
   if (n >= 2.0 && sxx - sx * sx / n > 1e-12 * sxx) {
@@ -142,7 +159,7 @@ int launch_fit(const Common& cm, const FitArgs& fa, void* stream) {
     const int e = cudaGetLastError();
     if (e) return e;
   }
-  k_fit_solve<<<1, 32, 0, s>>>(fa);
+  k_fit_solve<<<1, 32 * PN_MAX_P, 0, s>>>(fa);
   return cudaGetLastError();
 }
 

@@ -103,7 +103,8 @@ struct FitArgs {
   int32_t p_log2[PN_MAX_P];
   int32_t estimator;
   int32_t pad;
-  double* sums;       // [PN_MAX_P][5]: n, sum est, sum exact, sum est^2, sum est * exact
+  double* samp;       // [n_fit][2]: each sample's estimate and exact value
+  int32_t* scls;      // [n_fit]: each sample's p* class (-1: entry outside the product)
   float* coef;        // [PN_MAX_P][2]
   float* user_coef;   // optional copy for the caller
 };

@@ -1,9 +1,13 @@
 """The allocation-free entry point maxprod_pnorm_static, called through the C ABI.
 
 It serves callers that may not allocate device memory (they own only their
-inputs and outputs), so it runs in a scratch array inside the library.  This
-file is collected last so that a run stopping at the first failure has run
-every other test first; it also passes on its own in a fresh process.
+inputs and outputs), so it runs in a scratch array inside the library.  Both
+entry points run the same deterministic kernels on the same inputs, so the
+static call must give bit-identical C, p_sel and S_sel to maxprod_pnorm with
+a workspace of its own.  Every case follows a larger call, so scratch left
+over from that call would show.  This file is collected last so that a run
+stopping at the first failure has run every other test first; it also passes
+on its own in a fresh process.
 """
 import ctypes
 
@@ -27,23 +31,25 @@ def lib():
     return _binding
 
 
-def _rel_tol(K, plog):
-    # tolerance the parity tests use for BF16 operands (see test_gpu_product.s_tol)
-    p = 2.0 ** plog
-    s = 2 * (p - 1) * 2.0 ** -24 + 2 * 2.0 ** -8 + 2.0 ** -7 + K * 2.0 ** -23
-    return 1.5 * ((1 + s) ** (1.0 / p) - 1) + 2e-7
-
-
-def _run(b, fn_static, M, N, K, seed):
+def _run(b, M, N, K, seed, compute="bf16", estimator=0, correction=0):
+    """Calls maxprod_pnorm_static, then maxprod_pnorm with its own workspace,
+    on the same inputs; returns both (C, p_sel, S_sel) triples."""
     L = b.load()
     A_h, B_h = workloads.wide_range_pair(M, N, K, seed=seed)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
-    o = b.make_opts(compute="bf16", dev_status=status.data_ptr())
+    extra = {}
+    if correction == 2:
+        g = workloads.rng(seed + 1)
+        fi = torch.from_numpy(g.integers(0, M, 64).astype(np.int32)).cuda()
+        fj = torch.from_numpy(g.integers(0, N, 64).astype(np.int32)).cuda()
+        extra = dict(n_fit=64, fit_i=fi.data_ptr(), fit_j=fj.data_ptr())
+    o = b.make_opts(compute=compute, dev_status=status.data_ptr(), estimator=estimator,
+                    correction=correction, **extra)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     outs = []
-    for static in (fn_static, False):
+    for static in (True, False):
         C = torch.empty((M, N), dtype=torch.float32, device="cuda")
         psel = torch.empty((M, N), dtype=torch.uint8, device="cuda")
         ssel = torch.empty((M, N), dtype=torch.float32, device="cuda")
@@ -58,19 +64,31 @@ def _run(b, fn_static, M, N, K, seed):
         assert rc == 0, b.status_string(rc)
         torch.cuda.synchronize()
         assert int(status.item()) == 0
-        outs.append((C.cpu().numpy(), psel.cpu().numpy(), ssel.cpu().numpy()))
+        outs.append((C, psel, ssel))
     return outs
 
 
+def _assert_identical(outs):
+    (Cs, ps, ss), (Cw, pw, sw) = outs
+    assert torch.equal(ps, pw)
+    assert torch.equal(Cs, Cw)
+    assert torch.equal(ss, sw)
+
+
 def test_static_entry_matches_workspace_entry_twice(lib):
-    """Two calls in a row (different sizes, so stale scratch would show) agree
-    with maxprod_pnorm on the same inputs within the parity tolerance."""
+    """Two calls in a row, the second smaller than the first: bit-identical to
+    maxprod_pnorm on the same inputs."""
     for (M, N, K, seed) in [(700, 900, 1100, 11), (333, 257, 515, 12)]:
-        (Cs, ps, ss), (Cw, pw, sw) = _run(lib, True, M, N, K, seed)
-        np.testing.assert_array_equal(ps, pw)
-        tol = np.vectorize(lambda lp: _rel_tol(K, lp))(pw & 0x7F)
-        assert np.all(np.abs(Cs - Cw) <= tol * np.abs(Cw))
-        assert np.all(np.abs(ss - sw) <= tol * np.abs(sw))
+        _assert_identical(_run(lib, M, N, K, seed))
+
+
+@pytest.mark.parametrize("estimator,correction", [(2, 0), (0, 2), (1, 2)])
+def test_static_entry_projection_and_correction(lib, estimator, correction):
+    """The r = 2 projection (parked sums and pending stages in the scratch) and
+    the affine correction (sample records and coefficients in the scratch),
+    each right after a larger plain call: bit-identical to maxprod_pnorm."""
+    _assert_identical(_run(lib, 900, 800, 1000, 21))
+    _assert_identical(_run(lib, 300, 260, 400, 22, estimator=estimator, correction=correction))
 
 
 def test_static_entry_rejects_oversized_problems(lib):
