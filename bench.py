@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--k", type=int, default=0,
+                    help="contraction length of the default product (0: n); M = N = n")
     ap.add_argument("--compute", default="bf16")
     ap.add_argument("--tile-n", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=12)
@@ -51,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-exact", action="store_true")
+    ap.add_argument("--no-e4m3", action="store_true",
+                    help="skip the E4M3 run of the default product")
     ap.add_argument("--count", type=int, default=4096,
                     help="grouped workload: number of problems")
     ap.add_argument("--estimator", type=int, default=0, choices=[0, 1, 2],
@@ -61,7 +65,7 @@ def parse_args():
     ap.add_argument("--n-fit", type=int, default=1024)
     ap.add_argument("--workload", default="pnorm",
                     choices=["pnorm", "apsp", "backward", "grouped", "maxconv", "maxconv-long",
-                             "topk"],
+                             "topk", "peaks"],
                     help="pnorm: the default product; the others measure the other paths")
     return ap.parse_args()
 
@@ -170,11 +174,43 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def gemm_peak_tflops(compute, peaks):
-    """Dense tensor peak of the operand format: the measured BF16 figure (sustained:
-    the kernel runs inside a seconds-long loop) times the nominal format ratio."""
-    ratio = {"bf16": 1.0, "f16": 1.0, "tf32": 0.5, "f32": 0.5 / 3, "e4m3": 2.0}[compute]
-    return peaks["bf16_tflops_sustained"] * ratio
+TENSOR_PEAKS_PROFILE = "tensor_peaks_tf32_e4m3.md"
+
+
+def tensor_peaks():
+    """TF32 and E4M3 dense peaks measured on the GB300s with the library
+    GEMMs (``bench.py --workload peaks``), recorded in profiles/; {} if absent."""
+    out = {}
+    try:
+        text = open(os.path.join(ROOT, "profiles", TENSOR_PEAKS_PROFILE)).read()
+    except OSError:
+        return out
+    for key in ("tf32_tflops", "tf32_tflops_sustained", "e4m3_tflops", "e4m3_tflops_sustained"):
+        m = re.search(rf"^{key}:\s*([0-9.eE+]+)\s*$", text, re.M)
+        if m:
+            out[key] = float(m.group(1))
+    return out
+
+
+def gemm_peak_tflops(compute, peaks, burst=True, measured=None):
+    """Dense tensor peak of the operand format and where it comes from.  burst:
+    the figure for a kernel timed alone in a short region (else the sustained,
+    seconds-long one).  BF16 / FP16 take the measured BF16 figure; TF32 and
+    E4M3 their own measured figures when `measured` holds them, else the BF16
+    figure times the nominal format ratio; 3xTF32 issues three TF32 products."""
+    sfx = "" if burst else "_sustained"
+    measured = measured or {}
+    bf16 = peaks["bf16_tflops" + sfx]
+    if compute in ("bf16", "f16"):
+        return bf16, "measured bf16_tflops" + sfx
+    base = {"tf32": "tf32", "f32": "tf32", "e4m3": "e4m3"}[compute]
+    div = 3.0 if compute == "f32" else 1.0
+    key = f"{base}_tflops{sfx}"
+    if key in measured:
+        return measured[key] / div, f"measured {key}" + (" / 3 (3xTF32)" if div > 1 else "")
+    ratio = {"tf32": 0.5, "e4m3": 2.0}[base]
+    return bf16 * ratio / div, (f"bf16_tflops{sfx} x nominal {base} ratio {ratio}"
+                                + (" / 3 (3xTF32)" if div > 1 else ""))
 
 
 def gemm_source_sha():
@@ -211,6 +247,8 @@ def cpu_baseline(A_h, B_h, n, seconds, oracle):
     r = oracle.row_scales(A64)
     c = oracle.col_scales(B64)
 
+    Kc = A_h.shape[1]  # semiring ops per output entry
+
     def run(E):
         loc = g.integers(0, len(rows), E)
         jj = g.integers(0, n, E)
@@ -222,10 +260,62 @@ def cpu_baseline(A_h, B_h, n, seconds, oracle):
     t0 = run(E0)
     E = max(E0, int(E0 * seconds / max(t0, 1e-3)))
     t = run(E)
-    return {"value": E * n / t / 1e9, "unit": "Gop/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{E} random output entries of the n={n} product (exact max and "
-                      f"the {len(P_LOG2)} p-sums each, FP64); {t:.1f} s"}
+    cores = oracle.num_threads()
+    out = {"value": E * Kc / t / 1e9, "unit": "Gop/s", "cores": cores, "kind": "oracle",
+           "sample": f"{E} random output entries of the n={n} product (exact max and "
+                     f"the {len(P_LOG2)} p-sums each, FP64); {t:.1f} s"}
+    # the same oracle on one thread, on a quarter of the time budget
+    oracle.set_num_threads(1)
+    try:
+        t1 = run(16)
+        E1 = max(16, int(16 * 0.25 * seconds / max(t1, 1e-3)))
+        t1 = run(E1)
+    finally:
+        oracle.set_num_threads(cores)
+    out["single_thread"] = {"value": E1 * Kc / t1 / 1e9, "unit": "Gop/s", "cores": 1,
+                            "sample": f"{E1} random output entries, same work per entry; "
+                                      f"{t1:.1f} s"}
+    return out
+
+
+def link_probe(torch, host_in, host_out, dev_in, dev_out):
+    """Host link rates of the pinned buffers: one host->device copy alone, one
+    device->host copy alone, and both at once on two streams (GB/s, best of 3),
+    with the GPU's NUMA node and local CPUs and this process's CPU affinity."""
+    def timed(pairs):
+        best = None
+        streams = [torch.cuda.Stream() for _ in pairs]
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for st, (dst, src) in zip(streams, pairs):
+                with torch.cuda.stream(st):
+                    dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best
+    nb_in = host_in.numel() * host_in.element_size()
+    nb_out = dev_out.numel() * dev_out.element_size()
+    t_in = timed([(dev_in, host_in)])
+    t_out = timed([(host_out, dev_out)])
+    t_both = timed([(dev_in, host_in), (host_out, dev_out)])
+    out = {"h2d_alone_gbs": nb_in / t_in / 1e9, "d2h_alone_gbs": nb_out / t_out / 1e9,
+           "h2d_d2h_concurrent_gbs": (nb_in + nb_out) / t_both / 1e9}
+    try:
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        bus = f"{props.pci_domain_id:04x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+        base = f"/sys/bus/pci/devices/{bus}"
+        out["gpu_numa_node"] = open(base + "/numa_node").read().strip()
+        out["gpu_local_cpus"] = open(base + "/local_cpulist").read().strip()
+    except (OSError, AttributeError):
+        pass
+    try:
+        cpus = sorted(os.sched_getaffinity(0))
+        out["process_cpus"] = f"{cpus[0]}-{cpus[-1]} ({len(cpus)})" if cpus else ""
+    except (OSError, AttributeError):
+        pass
+    return out
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -259,7 +349,8 @@ def run_ours(args):
     import paper_1511_05690_gb300 as pn
 
     n = args.n
-    A_h, B_h = workloads.wide_range_pair(n, n, n)
+    Kc = args.k if args.k > 0 else n  # contraction length
+    A_h, B_h = workloads.wide_range_pair(n, n, Kc)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
     C = torch.empty((n, n), dtype=torch.float32, device="cuda")
@@ -304,7 +395,7 @@ def run_ours(args):
     ms = t_begin.elapsed_time(t_end)
     gemm_ms = [a.elapsed_time(b) for a, b in gev]
     ms_max = max_over_ranks(ms, world, device="cuda")
-    ops = float(n) ** 3
+    ops = float(n) * n * Kc
     value = job_value(world, ops, K, ms_max)
 
     # error of the estimate at sampled entries: vs exact and vs the FP64 p-norm
@@ -330,7 +421,7 @@ def run_ours(args):
         else:
             # the oracle's estimator (and correction) on its own p-sums of the
             # sampled entries
-            tau = oracle.default_tau(n, {"f32": 0, "tf32": 1, "bf16": 2, "f16": 3,
+            tau = oracle.default_tau(Kc, {"f32": 0, "tf32": 1, "bf16": 2, "f16": 3,
                                          "e4m3": 4}[args.compute])
             rc = r[ii] * c[jj]
             S34 = None
@@ -350,9 +441,10 @@ def run_ours(args):
                                                np.searchsorted(frows, fit_ii), fit_jj, P_LOG2,
                                                rf[frows], c, tau, args.estimator)
             if args.correction:
-                oracle.apply_correction(pn_ref, ps_o, P_LOG2, n, np.ones(1), rc,
+                oracle.apply_correction(pn_ref, ps_o, P_LOG2, Kc, np.ones(1), rc,
                                         args.correction, coef)
             pn_ref = pn_ref[0]
+        samples = dict(ii=ii, jj=jj, ti=ti, tj=tj, exact=exact, S=S, rc=r[ii] * c[jj])
         e_exact = np.abs(Cs - exact) / exact
         e_orc = np.abs(Cs - pn_ref) / pn_ref
         err = {"samples": int(len(ii)), "max_rel_vs_exact": float(e_exact.max()),
@@ -361,6 +453,57 @@ def run_ours(args):
                "median_rel_vs_fp64_pnorm": float(np.median(e_orc)),
                "p_sel_histogram": {str(2 ** int(k)): int(v) for k, v in
                                    zip(*np.unique(ps, return_counts=True))}}
+
+    # the same product with E4M3 operands (the n = 16384 configuration names
+    # both formats): its own short timed region, the top GEMM's events, and
+    # the error at the same sampled entries
+    e4m3_info = None
+    if (rank == 0 and args.compute == "bf16" and args.estimator == 0 and args.correction == 0
+            and not args.no_e4m3):
+        C8 = torch.empty_like(C)
+
+        def step8(ev0=None, ev1=None):
+            return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute="e4m3", tile_n=args.tile_n,
+                                    out=C8, want_ssel=False, check=False, ev_begin=ev0,
+                                    ev_end=ev1)
+        for _ in range(max(args.warmup, 3)):
+            step8()
+        K8 = max(1, min(K, 20))
+        ev8 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K8)]
+        a8, b8 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a8.record(stream)
+        for s8 in range(K8):
+            _, ps8, _ = step8(*ev8[s8])
+        b8.record(stream)
+        torch.cuda.synchronize()
+        pn.check_device_status(A.device, "e4m3 steps")
+        ms8 = a8.elapsed_time(b8) / K8
+        g8 = statistics.mean(x.elapsed_time(y) for x, y in ev8)
+        tp8 = tensor_peaks()
+        pk8, pk8_how = gemm_peak_tflops("e4m3", measured_peaks()[0], True, tp8)
+        ach8 = 2.0 * ops / (g8 / 1e3) / 1e12
+        e4m3_info = {"ms_per_step": ms8, "value": ops / (ms8 / 1e3) / 1e9, "unit": "Gop/s",
+                     "steps": K8,
+                     "roofline": {"bound": "tensor", "achieved": ach8, "peak": pk8,
+                                  "unit": "TFLOP/s", "frac": ach8 / pk8, "launch_ms": g8,
+                                  "peak_source": pk8_how}}
+        if err is not None:
+            sm = samples
+            C8s = C8[sm["ti"], sm["tj"]].double().cpu().numpy()
+            q8 = (ps8[sm["ti"], sm["tj"]].cpu().numpy() & 0x7F).astype(np.int64)
+            ref8 = sm["rc"] * np.power(sm["S"][np.arange(len(q8)), q8], 1.0 / 2.0 ** q8)
+            x8 = np.abs(C8s - sm["exact"]) / sm["exact"]
+            o8 = np.abs(C8s - ref8) / ref8
+            e4m3_info["err"] = {
+                "samples": int(len(q8)), "max_rel_vs_exact": float(x8.max()),
+                "median_rel_vs_exact": float(np.median(x8)),
+                "max_rel_vs_fp64_pnorm": float(o8.max()),
+                "median_rel_vs_fp64_pnorm": float(np.median(o8)),
+                "p_sel_histogram": {str(2 ** int(k)): int(v) for k, v in
+                                    zip(*np.unique(q8, return_counts=True))}}
+        del C8
 
     # exact CUDA-core product of the same inputs, for the comparison in the metric
     exact_info = None
@@ -387,7 +530,7 @@ def run_ours(args):
     Ch = torch.empty((n, n), dtype=torch.float32).pin_memory()
     del C
     torch.cuda.empty_cache()
-    pipe = HostPipeline(n, n, n, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2,
+    pipe = HostPipeline(n, n, Kc, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2,
                         **corr)
     KE = max(1, args.e2e_steps)
     pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up
@@ -395,40 +538,55 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    pipe.run([(Ah, Bh, Ch)] * KE, ev_start=x0, ev_end=x1)
+    stages = []
+    pipe.run([(Ah, Bh, Ch)] * KE, ev_start=x0, ev_end=x1, stages=stages)
     e2e_ms = max_over_ranks(x0.elapsed_time(x1) / KE, world, device="cuda")
     e2e_value = job_value(world, ops, 1, e2e_ms)
     pn.check_device_status(A.device, "e2e")
+    from paper_1511_05690_gb300.pipeline import stage_summary
+    e2e_stages = stage_summary(stages, pipe.h2d_bytes, pipe.d2h_bytes)
+    e2e_link = link_probe(torch, Ah, Ch, pipe.A[0], pipe.C[0])
     del pipe
 
     peaks, peak_src = measured_peaks()
     gemm_avg = statistics.mean(gemm_ms)
     achieved = 2.0 * ops / (gemm_avg / 1e3) / 1e12
-    peak = gemm_peak_tflops(args.compute, peaks)
+    # the GEMM is timed inside a short region (K steps, about 0.1 s): the burst
+    # figure; the sustained one is reported beside it
+    tp = tensor_peaks()
+    peak, peak_how = gemm_peak_tflops(args.compute, peaks, burst=True, measured=tp)
+    peak_s, _ = gemm_peak_tflops(args.compute, peaks, burst=False, measured=tp)
     line = {
         "metric": "Effective semiring Gop/s (n^3/s): p-norm TC vs exact GPU kernel at stated err",
         "value": value, "unit": "Gop/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
         "config": {"workload": workload_name(n, args.compute, args.estimator, args.correction,
-                                             args.n_fit), "n": n,
+                                             args.n_fit), "n": n, "k": Kc,
                    "p_log2": P_LOG2,
                    "outputs": "C and p_sel", "l2": "inputs larger than L2 (1 GiB each), no flush",
                    "parallelism": f"replicas x{world}"},
-        "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * n,
-                "d2h_bytes_per_step": 4 * n * n, "steps": KE,
+        "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * Kc,
+                "d2h_bytes_per_step": 4 * n * n, "steps": KE, "ms_per_step": e2e_ms,
                 "how": "pinned host A, B in / C out every step; steps overlap copy-in, "
-                       "compute and copy-out on three streams (one per copy direction)"},
+                       "compute and copy-out on three streams (one per copy direction)",
+                "stages": e2e_stages, "link": e2e_link},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(args.compute),
                      "kernel": "k_gemm_level (largest p), 2*n^3 FLOP per launch",
                      "launch_ms": gemm_avg,
-                     "peak_source": f"{peak_src} bf16_tflops_sustained x format ratio"},
+                     "peak_source": f"{peak_how} ({peak_src}; burst: the launch is timed "
+                                    f"inside a short region)",
+                     "peak_sustained": peak_s, "frac_of_sustained": achieved / peak_s},
         "clocks": clk,
         "gpu_launches": launches_per_step(args) * K,
         "err": err,
         "exact_kernel": exact_info,
     }
+    if e4m3_info is not None:
+        if exact_info is not None:
+            e4m3_info["speedup_over_exact_kernel"] = exact_info["ms"] / e4m3_info["ms_per_step"]
+        line["e4m3"] = e4m3_info
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         line["cpu_baseline"] = cpu_baseline(A_h, B_h, n, args.cpu_seconds, oracle)
@@ -503,6 +661,70 @@ def _timed(torch, fn, K, warmup, stream):
     return a.elapsed_time(b) / K
 
 
+def measure_tensor_peaks(torch, stream, n=8192, sustain_s=4.0):
+    """Dense tensor peaks of the library GEMMs, measured like the BF16 figure
+    of the measured-peaks file: 2 n^3 FLOP per product, n = 8192, best of 10
+    (burst) and back to back for a few seconds (sustained), CUDA events,
+    clocks sampled.  BF16: torch.matmul; TF32: torch.matmul on FP32 with TF32
+    allowed; E4M3: torch._scaled_mm (FP8 E4M3 operands, FP32 scales, BF16
+    out)."""
+    torch.manual_seed(0)
+    out = {"workload": "peaks", "n": n}
+
+    def run(name, fn):
+        try:
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            best = None
+            for _ in range(10):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+            clocks = ClockSampler(torch.cuda.current_device())
+            clocks.start()
+            time.sleep(0.3)
+            reps = max(1, int(sustain_s * 1e3 / best))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            clocks.mark_begin()
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            clocks.mark_end()
+            sus = a.elapsed_time(b) / reps
+            flop = 2.0 * n ** 3
+            out[f"{name}_tflops"] = flop / (best / 1e3) / 1e12
+            out[f"{name}_tflops_sustained"] = flop / (sus / 1e3) / 1e12
+            out[f"{name}_clocks"] = clocks.stop()
+        except Exception as e:  # a format the library GEMM does not offer here
+            out[f"{name}_error"] = f"{type(e).__name__}: {e}"[:300]
+
+    a16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    b16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    run("bf16", lambda: torch.matmul(a16, b16))
+    del a16, b16
+    a32 = torch.randn(n, n, device="cuda")
+    b32 = torch.randn(n, n, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    run("tf32", lambda: torch.matmul(a32, b32))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del a32, b32
+    a8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+    b8 = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()  # column-major
+    one = torch.ones((), device="cuda", dtype=torch.float32)
+    run("e4m3", lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one,
+                                         out_dtype=torch.bfloat16))
+    return out
+
+
 def run_other(args):
     """APSP n=4096 (12 squarings, 3xTF32), forward+backward n=2048 (3xTF32),
     or 4096 grouped products (BF16, CUDA-graph replay).  One JSON line."""
@@ -515,6 +737,10 @@ def run_other(args):
             "unit": "Gop/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "data": "synthetic"}
+    if args.workload == "peaks":
+        line = measure_tensor_peaks(torch, stream)
+        print(json.dumps(line), flush=True)
+        return
     if args.workload == "topk":
         # approximate top-k of x_i y_j (Alg. 9 with the NormQueue) for a batch
         # of pairs, with the index recovery (two calls: y and y reversed)

@@ -13,12 +13,34 @@ import bench
 
 
 def test_gemm_peak_ratios():
-    peaks = {"bf16_tflops_sustained": 1200.0}
-    assert bench.gemm_peak_tflops("bf16", peaks) == 1200.0
-    assert bench.gemm_peak_tflops("f16", peaks) == 1200.0
-    assert bench.gemm_peak_tflops("tf32", peaks) == 600.0
-    assert bench.gemm_peak_tflops("f32", peaks) == pytest.approx(200.0)  # 3 TF32 products
-    assert bench.gemm_peak_tflops("e4m3", peaks) == 2400.0
+    """Burst figure by default (the GEMM is timed in a short region), sustained
+    on request; TF32 / E4M3 take their own measured figures when recorded, else
+    the BF16 figure times the nominal ratio; 3xTF32 is a third of TF32."""
+    peaks = {"bf16_tflops": 1500.0, "bf16_tflops_sustained": 1200.0}
+    pk = lambda c, **kw: bench.gemm_peak_tflops(c, peaks, **kw)[0]  # noqa: E731
+    assert pk("bf16") == 1500.0 and pk("f16") == 1500.0
+    assert pk("bf16", burst=False) == 1200.0
+    assert pk("tf32") == 750.0 and pk("tf32", burst=False) == 600.0
+    assert pk("f32") == pytest.approx(250.0)  # 3 TF32 products
+    assert pk("e4m3") == 3000.0
+    meas = {"tf32_tflops": 900.0, "e4m3_tflops": 2800.0, "e4m3_tflops_sustained": 2500.0}
+    assert pk("tf32", measured=meas) == 900.0
+    assert pk("f32", measured=meas) == pytest.approx(300.0)
+    assert pk("e4m3", measured=meas) == 2800.0
+    assert pk("e4m3", burst=False, measured=meas) == 2500.0
+    assert pk("tf32", burst=False, measured=meas) == 600.0  # no sustained TF32 recorded
+    assert "measured e4m3_tflops" in bench.gemm_peak_tflops("e4m3", peaks, measured=meas)[1]
+
+
+def test_tensor_peaks_profile(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.tensor_peaks() == {}
+    (prof / bench.TENSOR_PEAKS_PROFILE).write_text(
+        "# notes\ntf32_tflops: 950.5\ne4m3_tflops: 3.1e3\ne4m3_tflops_sustained: 2700\n")
+    assert bench.tensor_peaks() == {"tf32_tflops": 950.5, "e4m3_tflops": 3100.0,
+                                    "e4m3_tflops_sustained": 2700.0}
 
 
 def test_measured_peaks_file_or_fallback(tmp_path, monkeypatch):
