@@ -286,6 +286,30 @@ __device__ __forceinline__ float pow_pm1(float x, int k) {
   return r;
 }
 
+// Gradient factor of the adjoint: acc * x'^(p-1) / s with x' = x / s, p = 2^k,
+// s a power of two.  x' = m 2^e is split by frexpf and the chain
+// x'^(2^k - 1) = x' x'^2 x'^4 ... x'^(2^(k-1)) runs on mantissas in
+// [0.5, 1) with the exponents summed exactly, each product renormalised, so
+// no intermediate under- or overflows however small x' is; the total
+// exponent is applied once at the end (ldexpf: one rounding, into the
+// subnormal range if the result lies there).  x = 0 gives 0 for k >= 1.
+__device__ __forceinline__ float grad_factor(float acc, float x, float s, int k) {
+  int ls, ex, d;
+  frexpf(s, &ls);
+  ls -= 1;                        // s = 2^ls
+  float xm = frexpf(x, &ex);      // x = xm 2^ex, so x' = xm 2^(ex - ls)
+  ex -= ls;
+  float rm = 1.0f;
+  int re = 0;
+  for (int t = 0; t < k; ++t) {
+    rm = frexpf(rm * xm, &d);     // product of two values in [0.5, 1]: normal
+    re += ex + d;
+    xm = frexpf(xm * xm, &d);
+    ex = 2 * ex + d;
+  }
+  return ldexpf(acc * rm, re - ls);
+}
+
 // Smallest power of two >= m (m > 0, finite); 1 for m == 0.  Returns +inf
 // when that power is beyond the float range.
 __device__ __forceinline__ float pow2_ceil_f(float m) {

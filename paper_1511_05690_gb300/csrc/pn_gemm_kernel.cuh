@@ -502,13 +502,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
               for (int e = 0; e < 32; ++e) sv[e] = e < jn ? __ldg(cs + e) : 1.0f;
             }
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float inv = 1.0f / sv[e];
-              const bool ok = recip_exact(sv[e]);
-              const float f = div_pow2(pow_pm1(div_pow2(x[e], sv[e], inv, ok), lv.plog), sv[e],
-                                       inv, ok);
-              x[e] = __uint_as_float(v[e]) * f;
-            }
+            for (int e = 0; e < 32; ++e) x[e] = grad_factor(__uint_as_float(v[e]), x[e], sv[e], lv.plog);
             if (!first) {
               if (vec) {
 #pragma unroll

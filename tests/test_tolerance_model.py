@@ -231,22 +231,36 @@ def _gemm_3xtf32(X, Y):
     return np.add.accumulate(t.astype(np.float32), axis=1, dtype=np.float32)[:, -1, :]
 
 
-@pytest.mark.parametrize("shape,plog,underflows",
-                         [((64, 48, 80), 4, False), ((30, 20, 300), 2, False),
-                          ((40, 90, 33), 6, True)])
-def test_adjoint_tolerance_holds_the_emulated_gradient(orc, shape, plog, underflows):
+def _grad_factor(acc, x, s, k):
+    """The gradient epilogue's acc * x'^(p-1) / s, x' = x / s, p = 2^k, in FP32:
+    x' split into mantissa and exponent (frexp), the chain x' x'^2 ... run on
+    mantissas in [0.5, 1) with every product renormalised and the exponents
+    summed exactly, the total exponent applied once (one rounding)."""
+    ls = np.frexp(s)[1] - 1
+    xm, ex = np.frexp(x)
+    ex = ex - ls
+    rm = np.ones_like(x)
+    re = np.zeros(x.shape, dtype=np.int64)
+    for _ in range(k):
+        rm, d = np.frexp((rm * xm).astype(np.float32))
+        re = re + ex + d
+        xm, d = np.frexp((xm * xm).astype(np.float32))
+        ex = 2 * ex + d
+    return np.ldexp((acc * rm).astype(np.float32).astype(np.float64), re - ls).astype(np.float32)
+
+
+@pytest.mark.parametrize("shape,plog",
+                         [((64, 48, 80), 4), ((30, 20, 300), 2), ((40, 90, 33), 6)])
+def test_adjoint_tolerance_holds_the_emulated_gradient(orc, shape, plog):
     """The adjoint's parity tolerance grad_tol: for L = sum log C at a fixed p,
     W = G C / S = 1 / S, dA = (W B'^pT) a'^(p-1) / r and dB = (A'^pT W) b'^(p-1) / c,
-    emulated with FP32 sums, 3xTF32 products with FP32 accumulation and FP32
-    elementwise factors (a'^(p-1) as the product of the squarings, as the
-    gradient epilogue forms it), stay within grad_tol of the FP64 oracle
-    gradient (relative, with the GPU test's absolute floor of 1e-30 of the
-    largest entry).  Known limit: a'^(p-1) below the smallest normal FP32
-    2^-126 (a' < 2^(-126/(p-1)), about 0.25 at p = 64) keeps fewer bits, and
-    below 2^-149 it is 0, although W = 1/S can lift the exact entry above the
-    floor at short contractions (K = 33 here).  Entries whose factor is normal
-    meet the tolerance; those whose factor is 0 are 0."""
-    from test_gpu_backward import grad_tol, rel_err
+    emulated with FP32 sums, 3xTF32 products with FP32 accumulation and the
+    gradient epilogue's factor (mantissa chain with separate exponents), stay
+    within grad_tol of the FP64 oracle gradient, plus FP32's subnormal spacing
+    2^-149 for exact entries below the FP32 range.  K = 33 at p = 64 is the case
+    where a'^(p-1) itself leaves the FP32 range (a' < 0.25) while W = 1/S lifts
+    many gradient entries back into it: every such entry is kept."""
+    from test_gpu_backward import grad_ok, grad_tol
     M, N, K = shape
     A, B = workloads.uniform_pair(M, N, K, seed=3500 + M)
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
@@ -254,22 +268,22 @@ def test_adjoint_tolerance_holds_the_emulated_gradient(orc, shape, plog, underfl
     a = (A64 / r[:, None]).astype(np.float32)
     b = (B64 / c[None, :]).astype(np.float32)
     ap, bp = a.copy(), b.copy()
-    am1, bm1 = np.ones_like(a), np.ones_like(b)
-    for _ in range(plog):  # x^(p-1) = x x^2 x^4 ... x^(p/2), x^p by squaring
-        am1, bm1 = (am1 * ap).astype(np.float32), (bm1 * bp).astype(np.float32)
+    for _ in range(plog):  # x^p by squaring
         ap, bp = (ap * ap).astype(np.float32), (bp * bp).astype(np.float32)
     S = _gemm_3xtf32(ap, bp)
     W = (np.float32(1.0) / S).astype(np.float32)
-    dA = (_gemm_3xtf32(W, bp.T) * am1 / r[:, None].astype(np.float32)).astype(np.float32)
-    dB = (_gemm_3xtf32(ap.T, W) * bm1 / c[None, :].astype(np.float32)).astype(np.float32)
+    r32, c32 = r.astype(np.float32), c.astype(np.float32)
+    dA = _grad_factor(_gemm_3xtf32(W, bp.T), A, np.broadcast_to(r32[:, None], A.shape), plog)
+    dB = _grad_factor(_gemm_3xtf32(ap.T, W), B, np.broadcast_to(c32[None, :], B.shape), plog)
     plogs = np.full((M, N), plog, dtype=np.uint8)
     Cref = orc.pnorm(A64, B64, [plog], 1e-300)["C"]
     gA, gB = orc.pnorm_grad(A64, B64, plogs, 1.0 / Cref)
-    lost = 0
-    for d, g, f, L in ((dA, gA, am1, N), (dB, gB, bm1, M)):
-        assert np.all(d[f == 0] == 0)
-        under = f < 2.0 ** -126  # subnormal or zero factor
-        e = rel_err(d, g)
-        assert e[~under].max() <= grad_tol(plog, L), (e[~under].max(), grad_tol(plog, L))
-        lost += int((e[under] > grad_tol(plog, L)).sum())
-    assert (lost > 0) == underflows
+    rescued = 0
+    for d, g, x, L in ((dA, gA, a, N), (dB, gB, b, M)):
+        assert grad_ok(d, g, grad_tol(plog, L)), (d, g)
+        # entries whose factor x'^(p-1) lies below FP32's normal range but whose
+        # gradient does not: lost by a plain FP32 product of the squarings
+        rescued += int(np.sum((x.astype(np.float64) ** (2 ** plog - 1) < 2.0 ** -126)
+                              & (g >= 2.0 ** -126)))
+    if plog == 6:
+        assert rescued > 0
