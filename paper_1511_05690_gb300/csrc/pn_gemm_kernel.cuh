@@ -535,11 +535,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           // (or the smallest p, which takes whatever is left)
           uint32_t stable = 0, near = 0;
           float x[32];
+          float mn = FLT_MAX;
 #pragma unroll
           for (int e = 0; e < 32; ++e) {
-            x[e] = __uint_as_float(v[e]) * cm.unscale;
-            stable |= (x[e] >= P.tau ? 1u : 0u) << e;
-            near |= (x[e] < 10.0f * P.tau ? 1u : 0u) << e;
+            x[e] = mode_op_shift(MODE) ? __uint_as_float(v[e]) * cm.unscale : __uint_as_float(v[e]);
+            mn = fminf(mn, x[e]);
+          }
+          if (jn == 32 && mn >= 10.0f * P.tau) {
+            // the common case: every entry of the lane's chunk is stable, none
+            // within a decade of tau (no per-entry masks to build)
+            stable = 0xffffffffu;
+          } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+              stable |= (x[e] >= P.tau ? 1u : 0u) << e;
+              near |= (x[e] < 10.0f * P.tau ? 1u : 0u) << e;
+            }
           }
           const uint32_t open = inrange & ~res;
           // a half level (r = 2) resolves nothing: its p is not in P
@@ -608,11 +619,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (__any_sync(0xffffffffu, cand != 0u)) {
             const uint32_t pbits = lv.plog * 0x01010101u;
             uint32_t pw[8];
+            if (P.psel) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const uint32_t nb = (~stable >> (4 * q)) & 0xfu;  // unstable bytes
-              const uint32_t flag = (nb & 1u) | ((nb & 2u) << 7) | ((nb & 4u) << 14) | ((nb & 8u) << 21);
-              pw[q] = pbits | (flag << 7);
+              for (int q = 0; q < 8; ++q) {
+                const uint32_t nb = (~stable >> (4 * q)) & 0xfu;  // unstable bytes
+                const uint32_t flag =
+                    (nb & 1u) | ((nb & 2u) << 7) | ((nb & 4u) << 14) | ((nb & 8u) << 21);
+                pw[q] = pbits | (flag << 7);
+              }
             }
             // rows of this warp's block start at ibase
             const int64_t ibase = (int64_t)tm * TILE_M + quarter * 32;
