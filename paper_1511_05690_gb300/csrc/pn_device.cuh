@@ -75,6 +75,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// ------------------------------------------------- flags across CTAs ---
+// Global flags written by one CTA and read by others in the same launch.
+__device__ __forceinline__ int32_t ld_acquire_gpu(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(int32_t* p, int32_t v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders this thread's generic-proxy global accesses with later async-proxy
+// (bulk copy) accesses: used by a writer after building data that other
+// CTAs' bulk copies read, and by a reader before issuing such copies.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Waits until *p >= need (acquire).  Gives up after timeout_ns nanoseconds or
+// once *abort is non-zero and returns false then.
+__device__ __forceinline__ bool wait_flag_geq(const int32_t* p, int32_t need, uint64_t timeout_ns,
+                                              volatile int32_t* abort) {
+  if (ld_acquire_gpu(p) >= need) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    __nanosleep(64);
+    if (ld_acquire_gpu(p) >= need) return true;
+    if (*abort) return false;
+    if (globaltimer_ns() - t0 > timeout_ns) return false;
+  }
+}
+
 // ----------------------------------------------------------- bulk copies ---
 // 1-D bulk copy global -> shared memory, completion counted in bytes on the
 // mbarrier.  Both addresses 16-byte aligned, size a multiple of 16.

@@ -61,6 +61,38 @@ __device__ __forceinline__ void warp_store_f32(float* stg, const float (&v)[32],
       const float4 t = *reinterpret_cast<const float4*>(stg + r * 32 + ((g ^ (r & 7)) << 2));
       *reinterpret_cast<float4*>(base + r * ld + 4 * g) = t;
     }
+  } else if (__all_sync(0xffffffffu, mask == 0u || mask == 0xffffffffu)) {
+    // whole rows, rows not 16-byte aligned: a row starting o floats past a
+    // 16-byte boundary is written as 7 aligned float4 (columns 4 - o + 4 q,
+    // q < 7) and its head (columns < 4 - o) and tail (columns >= 32 - o) as
+    // single floats; 8 lanes per row, four rows per instruction
+    const int q = lane & 7;
+    const uint32_t e0 = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(base) >> 2) & 3u;
+    const uint32_t l4 = static_cast<uint32_t>(ld) & 3u;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+      const int r = r0 + (lane >> 3);
+      if (__shfl_sync(0xffffffffu, mask, r) == 0u) continue;
+      const int o = static_cast<int>((e0 + static_cast<uint32_t>(r) * l4) & 3u);
+      float* rowp = base + r * ld;
+      const float* srow = stg + r * 32;
+      const int sw = r & 7;
+      if (o == 0) {
+        *reinterpret_cast<float4*>(rowp + 4 * q) =
+            *reinterpret_cast<const float4*>(srow + ((q ^ sw) << 2));
+      } else if (q < 7) {
+        const int c0 = 4 - o + 4 * q;
+        float4 t;
+        t.x = srow[((((c0 + 0) >> 2) ^ sw) << 2) + ((c0 + 0) & 3)];
+        t.y = srow[((((c0 + 1) >> 2) ^ sw) << 2) + ((c0 + 1) & 3)];
+        t.z = srow[((((c0 + 2) >> 2) ^ sw) << 2) + ((c0 + 2) & 3)];
+        t.w = srow[((((c0 + 3) >> 2) ^ sw) << 2) + ((c0 + 3) & 3)];
+        *reinterpret_cast<float4*>(rowp + c0) = t;
+      } else {
+        for (int c = 0; c < 4 - o; ++c) rowp[c] = srow[((c >> 2) ^ sw) * 4 + (c & 3)];
+        for (int c = 32 - o; c < 32; ++c) rowp[c] = srow[((c >> 2) ^ sw) * 4 + (c & 3)];
+      }
+    }
   } else {
 #pragma unroll 4
     for (int r = 0; r < 32; ++r) {
@@ -224,13 +256,110 @@ __device__ __forceinline__ void r1_finish_block(float* stg, const float (&x)[32]
   __syncwarp();
 }
 
-// EPI 0: p-norm epilogue (tau test, root, un-scaling, p_sel / S_sel, work
-// lists).  EPI 1: gradient epilogue of the adjoint, out (+)= acc * x'^(p-1) / s
-// with x the source element at the output position and s its row (grad_axis
-// 0) or column (1) scale; the first p present overwrites, later ones add.
-template <int MODE, int BN, int EPI>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
-    k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+// ------------------------------------------------------------ roles ---
+// The kernel's three roles as functions of a CTA context, so that the
+// single-level kernel runs them once and the persistent grouped kernel once
+// per level, with the ring positions and the tile count carried over.
+
+// Shared memory, barriers and TMEM of one CTA.
+struct Ctx {
+  uint8_t* smem;
+  uint64_t* full;
+  uint64_t* empty;
+  uint64_t* acc_full;
+  uint64_t* acc_empty;
+  uint64_t* drain;
+  uint32_t* tmem_slot;
+  volatile int32_t* abort_flag;
+  volatile int32_t* ok_flag;  // [4], epilogue item hand-off (2 per group)
+  uint32_t tmem_base;
+  uint64_t tmo;
+};
+
+// Operand blocks built earlier in the same launch: flags[tile row] (A) and
+// flags[b_off + tile column] (B) reach `need` once the level's images of the
+// block are written.  flags == nullptr: the images come from earlier launches.
+struct Ready {
+  const int32_t* flags;
+  int32_t need;
+  int32_t b_off;
+};
+
+// Copy producer state (ring position, copies in flight per stage).
+struct ProdState {
+  int stage;
+  uint32_t phase;
+  bool first;
+  bool aborted;
+  int8_t pend[8];
+};
+// MMA issuer state (ring position).
+struct MmaState {
+  int stage;
+  uint32_t phase;
+  bool aborted;
+};
+
+// Lays out shared memory, initialises the barriers, allocates TMEM (warp 1)
+// and synchronises the block.  Called by every thread.
+template <int MODE, int BN>
+__device__ __forceinline__ Ctx ctx_setup(bool by_tile) {
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
+  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  extern __shared__ uint8_t smem_raw[];
+  Ctx cx;
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  cx.smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+  cx.full = reinterpret_cast<uint64_t*>(cx.smem + STAGES * STAGE_BYTES);
+  cx.empty = cx.full + STAGES;
+  cx.acc_full = cx.empty + STAGES;
+  cx.acc_empty = cx.acc_full + 2;
+  cx.drain = cx.acc_empty + 2;
+  cx.tmem_slot = reinterpret_cast<uint32_t*>(cx.drain + 1);
+  cx.abort_flag = reinterpret_cast<volatile int32_t*>(cx.tmem_slot + 1);
+  cx.ok_flag = cx.abort_flag + 1;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&cx.full[s], 1);
+      mbar_init(&cx.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&cx.acc_full[b], 1);
+      mbar_init(&cx.acc_empty[b], by_tile ? EPI_THREADS / 2 : EPI_THREADS);
+    }
+    mbar_init(cx.drain, 1);
+    *cx.abort_flag = 0;
+    cx.ok_flag[0] = cx.ok_flag[1] = cx.ok_flag[2] = cx.ok_flag[3] = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(cx.tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  cx.tmem_base = *cx.tmem_slot;
+  return cx;
+}
+
+// Frees TMEM once every role is done.  Called by every thread.
+template <int BN>
+__device__ __forceinline__ void ctx_teardown(const Ctx& cx) {
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 1) {
+    tc_fence_after();
+    tmem_dealloc(cx.tmem_base, 2 * BN);
+  }
+}
+
+// Producer (one thread): bulk copies of the operand images of this CTA's
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... < count into the ring.
+template <int MODE, int BN>
+__device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, const Ctx& cx,
+                                             int count, ProdState& ps, const Ready& rd) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
   constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
@@ -238,72 +367,45 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   constexpr int STAGES = num_stages(MODE, BN);
   constexpr int KIND = mma_kind(MODE);
   constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
-  constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr int CHUNKS = BN / 32;
-  static_assert(STAGES >= 2, "operand ring too small");
-
-  if constexpr (EPI == 1) {
-    if (!((*lv.pmask >> lv.q) & 1u)) return;  // no entry selected this p
-  }
-  const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
-  if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
-  // epilogue split (below): tile per warp group where the epilogue, not the
-  // MMA, bounds a tile (grouped problems, or short contractions)
-  const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) &&
-                       (cm.nprob > 1 || cm.single.KB * mode_planes(MODE) <= 32);
-
-  extern __shared__ uint8_t smem_raw[];
-  const uint32_t raw_addr = smem_u32(smem_raw);
-  uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* drain = acc_empty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
-  volatile int32_t* abort_flag = reinterpret_cast<volatile int32_t*>(tmem_slot + 1);
-  volatile int32_t* ok_flag = abort_flag + 1;  // [4], epilogue item hand-off (2 per group)
-
+  (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
+  (void)IDESC; (void)CHUNKS;
+  uint8_t* smem = cx.smem;
+  uint64_t* full = cx.full;
+  uint64_t* empty = cx.empty;
+  uint64_t* acc_full = cx.acc_full;
+  uint64_t* acc_empty = cx.acc_empty;
+  uint64_t* drain = cx.drain;
+  volatile int32_t* abort_flag = cx.abort_flag;
+  volatile int32_t* ok_flag = cx.ok_flag;
+  const uint32_t tmem_base = cx.tmem_base;
+  const uint64_t tmo = cx.tmo;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], by_tile ? EPI_THREADS / 2 : EPI_THREADS);
-    }
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    ok_flag[0] = ok_flag[1] = ok_flag[2] = ok_flag[3] = 0;
-    fence_barrier_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
-  const uint64_t tmo = cm.timeout_ns;
-
-  if (warp == 0) {
-    // ------------------------------------------------------ producer ---
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      int8_t pend[STAGES];
-      for (int s = 0; s < STAGES; ++s) pend[s] = -1;
+  (void)smem; (void)full; (void)empty; (void)acc_full; (void)acc_empty; (void)drain;
+  (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
+  if (ps.aborted) return;
+    int stage = ps.stage;
+      uint32_t phase = ps.phase;
+      int8_t* pend = ps.pend;
       bool aborted = false;
-      bool first = true;
+      bool first = ps.first;
       const uint64_t pol = policy_evict_last();
       for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x) {
         const int t = lv.is_top ? idx : lv.work[idx];
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
         int tm, tn;
         raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+        if (rd.flags) {
+          // operand blocks built earlier in this launch (persistent grouped
+          // kernel): wait until both are ready for this level, then order
+          // their generic-proxy writes before the bulk copies read them
+          if (!wait_flag_geq(rd.flags + P.tm_base + tm, rd.need, tmo, abort_flag) ||
+              !wait_flag_geq(rd.flags + rd.b_off + P.tn_base + tn, rd.need, tmo, abort_flag)) {
+            aborted = true;
+            break;
+          }
+          fence_proxy_async_global();
+        }
         const uint8_t* a_src = lv.a_level + P.a_img + (int64_t)tm * P.KB * IMG_BYTES;
         const uint8_t* b_src = lv.b_level + P.b_img + (int64_t)tn * (BN / TILE_M) * P.KB * IMG_BYTES;
         for (int kb = 0; kb < P.KB; ++kb) {
@@ -336,22 +438,53 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
         first = false;
       }
+      ps.stage = stage;
+      ps.phase = phase;
+      ps.first = first;
       if (aborted) {
+        ps.aborted = true;
         *abort_flag = 1;
         set_status(cm.status, PN_ETIMEOUT);
         // let every copy still in flight land before the CTA exits
         for (int s = 0; s < STAGES; ++s)
           if (pend[s] >= 0) mbar_wait_drain(&full[s], static_cast<uint32_t>(pend[s]), tmo);
       }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    // ----------------------------------------------------- MMA issuer ---
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+}
+
+// MMA issuer (one thread): the tensor-core K loop of each tile into the
+// accumulator buffer it & 1, it = it0, it0 + 1, ... counting this CTA's
+// tiles over the whole launch.
+template <int MODE, int BN>
+__device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const Ctx& cx,
+                                        int count, int it0, MmaState& ms) {
+  constexpr int PLANES = mode_planes(MODE);
+  constexpr int A_BYTES = IMG_BYTES;
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
+  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int KIND = mma_kind(MODE);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr int CHUNKS = BN / 32;
+  (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
+  (void)IDESC; (void)CHUNKS;
+  uint8_t* smem = cx.smem;
+  uint64_t* full = cx.full;
+  uint64_t* empty = cx.empty;
+  uint64_t* acc_full = cx.acc_full;
+  uint64_t* acc_empty = cx.acc_empty;
+  uint64_t* drain = cx.drain;
+  volatile int32_t* abort_flag = cx.abort_flag;
+  volatile int32_t* ok_flag = cx.ok_flag;
+  const uint32_t tmem_base = cx.tmem_base;
+  const uint64_t tmo = cx.tmo;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  (void)smem; (void)full; (void)empty; (void)acc_full; (void)acc_empty; (void)drain;
+  (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
+  if (ms.aborted) return;
+    int stage = ms.stage;
+      uint32_t phase = ms.phase;
       bool aborted = false;
-      int it = 0;
+      int it = it0;
       for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x, ++it) {
         const int t = lv.is_top ? idx : lv.work[idx];
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
@@ -395,16 +528,48 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (aborted) break;
         mma_commit(&acc_full[buf]);
       }
+      ms.stage = stage;
+      ms.phase = phase;
       if (aborted) {
+        ms.aborted = true;
         *abort_flag = 1;
         set_status(cm.status, PN_ETIMEOUT);
         mma_commit(drain);  // completes once every issued MMA has finished
         mbar_wait_drain(drain, 0, tmo);
       }
-    }
-    __syncwarp();
-  } else {
-    // ------------------------------------------------------- epilogue ---
+}
+
+// Epilogue (warps 2-9).  EPI 0: p-norm epilogue (tau test, root, un-scaling,
+// p_sel / S_sel, work lists).  EPI 1: gradient epilogue of the adjoint,
+// out (+)= acc * x'^(p-1) / s with x the source element at the output position
+// and s its row (grad_axis 0) or column (1) scale; the first p present
+// overwrites, later ones add.
+template <int MODE, int BN, int EPI>
+__device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, const Ctx& cx,
+                                             int count, bool by_tile, int it0, const Ready& rd) {
+  constexpr int PLANES = mode_planes(MODE);
+  constexpr int A_BYTES = IMG_BYTES;
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
+  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int KIND = mma_kind(MODE);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr int CHUNKS = BN / 32;
+  (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
+  (void)IDESC; (void)CHUNKS;
+  uint8_t* smem = cx.smem;
+  uint64_t* full = cx.full;
+  uint64_t* empty = cx.empty;
+  uint64_t* acc_full = cx.acc_full;
+  uint64_t* acc_empty = cx.acc_empty;
+  uint64_t* drain = cx.drain;
+  volatile int32_t* abort_flag = cx.abort_flag;
+  volatile int32_t* ok_flag = cx.ok_flag;
+  const uint32_t tmem_base = cx.tmem_base;
+  const uint64_t tmo = cx.tmo;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  (void)smem; (void)full; (void)empty; (void)acc_full; (void)acc_empty; (void)drain;
+  (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
     // Warp w may only read TMEM lanes 32*(w%4)..+31 (one output row each).
     // With several tiles per CTA (by_tile) the epilogue warps form two groups
     // of four, one warp per lane quarter each; group g finishes the tiles
@@ -421,11 +586,24 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     const int et = (threadIdx.x - 64) & (gthreads - 1);  // thread of the group
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + ew * STG_BYTES);
     const int step = by_tile ? 2 : 1;
-    int it = grp;
-    for (int idx = blockIdx.x + grp * gridDim.x; idx < count; idx += step * gridDim.x, it += step) {
+    for (int j = by_tile ? ((grp - it0) & 1) : 0;; j += step) {
+      const int idx = blockIdx.x + j * gridDim.x;
+      if (idx >= count) break;
+      const int it = it0 + j;
       const int t = lv.is_top ? idx : lv.work[idx];
       const int g = find_prob(cm, t, 0);
       const Prob& P = prob_at(cm, g);
+      // the fields the chunk loop uses, held in registers: through the
+      // reference into the grouped table every store to C could alias them
+      const int PN = P.N;
+      const float Ptau = P.tau;
+      float* const PC = P.C;
+      const int64_t Pldc = P.ldc;
+      const bool Pvec = P.vec_c != 0;
+      uint8_t* const Ppsel = P.psel;
+      float* const PSsel = P.Ssel;
+      const int64_t Pldaux = P.ldaux;
+      const int64_t Prc_c = P.rc_c;
       int tm, tn;
       raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
       const int buf = it & 1;
@@ -435,6 +613,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         if (!ok) {
           *abort_flag = 1;
           set_status(cm.status, PN_ETIMEOUT);
+        }
+        // operand blocks built in this launch: acquire their flags, so that
+        // the scales written with them are visible to the whole group after
+        // the barrier below
+        if (ok && rd.flags) {
+          ld_acquire_gpu(rd.flags + P.tm_base + tm);
+          ld_acquire_gpu(rd.flags + rd.b_off + P.tn_base + tn);
         }
         ok_flag[okslot] = ok ? 1 : 0;
       }
@@ -476,11 +661,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         pend_all[hc] = 0;
         pend2_all[hc] = 0;
         if constexpr (EPI == 1) {
-          if (row_ok && j0 < P.N) {
-            const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
+          if (row_ok && j0 < PN) {
+            const int jn = PN - j0 < 32 ? PN - j0 : 32;
             const float* erow = P.A + (int64_t)i * P.lda + j0;
-            float* orow = P.C + (int64_t)i * P.ldc + j0;
-            const bool vec = jn == 32 && P.vec_c;
+            float* orow = PC + (int64_t)i * Pldc + j0;
+            const bool vec = jn == 32 && Pvec;
             const bool first = (*lv.pmask >> (lv.q + 1)) == 0u;
             float x[32], sv[32];
             if (vec) {
@@ -497,7 +682,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
               for (int e = 0; e < 32; ++e) sv[e] = rs;
             } else {
-              const float* cs = cm.c + P.rc_c + j0;
+              const float* cs = cm.c + Prc_c + j0;
 #pragma unroll
               for (int e = 0; e < 32; ++e) sv[e] = e < jn ? __ldg(cs + e) : 1.0f;
             }
@@ -526,10 +711,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 if (e < jn) orow[e] = x[e];
             }
           }
-        } else if (j0 < P.N) {  // warp-uniform: rows past M resolve nothing
+        } else if (j0 < PN) {  // warp-uniform: rows past M resolve nothing
           if (!row_ok) res = 0xffffffffu;
           else if (!lv.is_top) res = st_row[hc];
-          const int jn = P.N - j0 < 32 ? P.N - j0 : 32;
+          const int jn = PN - j0 < 32 ? PN - j0 : 32;
           const uint32_t inrange = jn == 32 ? 0xffffffffu : ((1u << jn) - 1u);
           // entries to resolve at this p: not yet resolved, in range, and stable
           // (or the smallest p, which takes whatever is left)
@@ -541,34 +726,36 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             x[e] = mode_op_shift(MODE) ? __uint_as_float(v[e]) * cm.unscale : __uint_as_float(v[e]);
             mn = fminf(mn, x[e]);
           }
-          if (jn == 32 && mn >= 10.0f * P.tau) {
+          if (jn == 32 && mn >= 10.0f * Ptau) {
             // the common case: every entry of the lane's chunk is stable, none
             // within a decade of tau (no per-entry masks to build)
             stable = 0xffffffffu;
           } else {
 #pragma unroll
             for (int e = 0; e < 32; ++e) {
-              stable |= (x[e] >= P.tau ? 1u : 0u) << e;
-              near |= (x[e] < 10.0f * P.tau ? 1u : 0u) << e;
+              stable |= (x[e] >= Ptau ? 1u : 0u) << e;
+              near |= (x[e] < 10.0f * Ptau ? 1u : 0u) << e;
             }
           }
           const uint32_t open = inrange & ~res;
           // a half level (r = 2) resolves nothing: its p is not in P
           const uint32_t cand = lv.half ? 0u : lv.is_bottom ? open : (open & stable);
           any_left |= (open & ~cand) != 0u;
-          near &= cand & (cm.fp64_near ? 0xffffffffu : 0u);
+          // FP64 near tau only for the FP32-range formats (the host's fp64_near rule)
+          constexpr bool FP64_NEAR = MODE == MODE_3XTF32 || MODE == MODE_TF32 || MODE == MODE_BF16;
+          near &= cand & (FP64_NEAR && cm.fp64_near ? 0xffffffffu : 0u);
           // r = 1 projection (Sec. 2.1): entries resolved at 2p hold S^(2p) in C;
           // with S^(p) from this level the estimate is (S^(2p) / S^(p))^(1/p).
           // The ratio is clamped to <= 1 (S is non-increasing in p).
           const uint32_t pend = lv.proj_here && row_ok ? cm.pend[st_idx + hc] : 0u;
           if (lv.proj_here && __any_sync(0xffffffffu, pend != 0u)) {
-            const float cs_lane = lane < P.N - j0 ? __ldg(cm.c + P.rc_c + j0 + lane) : 0.0f;
+            const float cs_lane = lane < PN - j0 ? __ldg(cm.c + Prc_c + j0 + lane) : 0.0f;
             // the affine line of p*'s class (the level above)
             const bool affine = cm.corr == 2;
             const float pa = affine ? cm.coef[2 * (lv.q + 1)] : 1.0f;
             const float pb = affine ? cm.coef[2 * (lv.q + 1) + 1] : 0.0f;
             r1_finish_block<MODE == MODE_3XTF32>(
-                stg, x, pend, rs, P.C + ((int64_t)tm * TILE_M + quarter * 32) * P.ldc + j0, P.ldc,
+                stg, x, pend, rs, PC + ((int64_t)tm * TILE_M + quarter * 32) * Pldc + j0, Pldc,
                 cs_lane, lv.plog, inv_p, affine, pa, pb, lane);
           }
           if (lv.proj_next) {
@@ -586,23 +773,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             }
             // rows of this warp's block in the parked arrays and in C
             const int64_t ibr = (int64_t)tm * TILE_M + quarter * 32;
-            float* park3 = cm.park + ibr * P.N + j0;        // S^(3p*/4)
-            float* park2 = park3 + (int64_t)P.M * P.N;      // S^(p*/2)
+            float* park3 = cm.park + ibr * PN + j0;        // S^(3p*/4)
+            float* park2 = park3 + (int64_t)P.M * PN;      // S^(p*/2)
             if (lv.half) {
               const uint32_t w1 = b0 & ~b1;
               if (__any_sync(0xffffffffu, w1 != 0u))
-                warp_store_f32(stg, x, w1, park3, P.N, P.vec_c, lane);
+                warp_store_f32(stg, x, w1, park3, PN, Pvec, lane);
               b0 &= ~w1;
               b1 |= w1;
             } else if (lv.r2_state) {
               const uint32_t w2 = b1 & ~b0, w3 = b0 & b1;
               if (__any_sync(0xffffffffu, w2 != 0u))
-                warp_store_f32(stg, x, w2, park2, P.N, P.vec_c, lane);
+                warp_store_f32(stg, x, w2, park2, PN, Pvec, lane);
               if (__any_sync(0xffffffffu, w3 != 0u)) {
                 // this level's S is S^(p'), p' = p*/4: finish the projection
-                const float cs_lane = lane < P.N - j0 ? __ldg(cm.c + P.rc_c + j0 + lane) : 0.0f;
-                r2_finish_block<MODE == MODE_3XTF32>(stg, x, w3, rs, park2, park3, P.N,
-                                                     P.C + ibr * P.ldc + j0, P.ldc, cs_lane,
+                const float cs_lane = lane < PN - j0 ? __ldg(cm.c + Prc_c + j0 + lane) : 0.0f;
+                r2_finish_block<MODE == MODE_3XTF32>(stg, x, w3, rs, park2, park3, PN,
+                                                     PC + ibr * Pldc + j0, Pldc, cs_lane,
                                                      cm.r2_eta, lv.plog, inv_p, lane);
               }
               b0 = (b0 | w2) & ~w3;
@@ -619,7 +806,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
           if (__any_sync(0xffffffffu, cand != 0u)) {
             const uint32_t pbits = lv.plog * 0x01010101u;
             uint32_t pw[8];
-            if (P.psel) {
+            if (Ppsel) {
 #pragma unroll
               for (int q = 0; q < 8; ++q) {
                 const uint32_t nb = (~stable >> (4 * q)) & 0xfu;  // unstable bytes
@@ -631,8 +818,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             // rows of this warp's block start at ibase
             const int64_t ibase = (int64_t)tm * TILE_M + quarter * 32;
             // S_sel before x is overwritten by the root
-            if (P.Ssel)
-              warp_store_f32(stg, x, cand, P.Ssel + ibase * P.ldaux + j0, P.ldaux, P.vec_c, lane);
+            if (PSsel)
+              warp_store_f32(stg, x, cand, PSsel + ibase * Pldaux + j0, Pldaux, Pvec, lane);
             // a projection still to come (r = 1: level p/2 below; r = 2: the
             // chain down to p/4): C keeps S^(p) until then
             if (!lv.proj_next && !lv.r2_new) {
@@ -650,7 +837,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 32; ++e) x[e] = ex2_approx(lg2_approx(x[e]) * inv_p);
               }
-              if (near) {
+              if (FP64_NEAR && near) {
                 // within a decade of tau, which for these formats sits near the
                 // FP32 underflow range: root in FP64
 #pragma unroll
@@ -666,8 +853,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
 #pragma unroll
                 for (int e = 0; e < 32; ++e) x[e] = fmaf(corr_a, x[e], corr_b);
               }
-              const float* cs = cm.c + P.rc_c + j0;
-              if (jn == 32 && P.vec_c) {
+              const float* cs = cm.c + Prc_c + j0;
+              if (jn == 32 && Pvec) {
 #pragma unroll
                 for (int e = 0; e < 32; e += 4) {
                   const float4 cv = __ldg(reinterpret_cast<const float4*>(cs + e));
@@ -688,10 +875,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                   if (j0 + e == i) x[e] = 1.0f;
               }
             }
-            warp_store_f32(stg, x, cand, P.C + ibase * P.ldc + j0, P.ldc, P.vec_c, lane);
-            if (P.psel)
+            warp_store_f32(stg, x, cand, PC + ibase * Pldc + j0, Pldc, Pvec, lane);
+            if (Ppsel)
               warp_store_u8(reinterpret_cast<uint32_t*>(stg), pw, cand,
-                            P.psel + ibase * P.ldaux + j0, P.ldaux, P.vec_c, lane);
+                            Ppsel + ibase * Pldaux + j0, Pldaux, Pvec, lane);
             res |= cand;
           }
         }
@@ -704,16 +891,16 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
             uint32_t* st_w = cm.state + st_idx;
 #pragma unroll
             for (int hc = 0; hc < CHUNKS; ++hc)
-              if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) st_w[hc] = res_all[hc];
+              if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) st_w[hc] = res_all[hc];
             if (cm.pend) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
-                if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) cm.pend[st_idx + hc] = pend_all[hc];
+                if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend[st_idx + hc] = pend_all[hc];
             }
             if (cm.pend2) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
-                if (hc < nch && tn * BN + (ch0 + hc) * 32 < P.N) cm.pend2[st_idx + hc] = pend2_all[hc];
+                if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend2[st_idx + hc] = pend2_all[hc];
             }
           }
           // r = 2: a tile that starts no chain here skips the half level
@@ -728,13 +915,44 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
         }
       }
     }
-  }
+}
 
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+// One p level: every CTA processes tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... of the level's tile list (the whole problem at the top level).
+template <int MODE, int BN, int EPI>
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
+    k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+  static_assert(num_stages(MODE, BN) >= 2, "operand ring too small");
+  if constexpr (EPI == 1) {
+    if (!((*lv.pmask >> lv.q) & 1u)) return;  // no entry selected this p
   }
+  const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
+  if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
+  // epilogue split: tile per warp group where the epilogue, not the MMA,
+  // bounds a tile (grouped problems, or short contractions)
+  const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) &&
+                       (cm.nprob > 1 || cm.single.KB * mode_planes(MODE) <= 32);
+  const Ctx cx = ctx_setup<MODE, BN>(by_tile);
+  const Ready none{nullptr, 0, 0};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (lane == 0) {
+      ProdState ps{};
+      for (int s = 0; s < 8; ++s) ps.pend[s] = -1;
+      ps.first = true;
+      run_producer<MODE, BN>(cm, lv, cx, count, ps, none);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      MmaState ms{};
+      run_mma<MODE, BN>(cm, lv, cx, count, 0, ms);
+    }
+    __syncwarp();
+  } else {
+    run_epilogue<MODE, BN, EPI>(cm, lv, cx, count, by_tile, 0, none);
+  }
+  ctx_teardown<BN>(cx);
 }
 
 template <int MODE, int BN, int EPI>

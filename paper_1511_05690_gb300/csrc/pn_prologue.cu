@@ -15,59 +15,11 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
-#include "pn_pack.cuh"
+#include "pn_image.cuh"
 
 namespace pn {
 
 namespace {
-
-constexpr int PRO_THREADS = 256;
-
-__device__ __forceinline__ bool in_domain(float x) {
-  // R+ with every power-of-two scale representable: 0 <= x <= 2^127.
-  return x >= 0.0f && x <= 1.7014118346046923e38f;
-}
-
-__device__ __forceinline__ float nonneg_bits_max(float m) { return m > 0.0f ? m : 0.0f; }
-
-// ------------------------------------------------------------- maxima ---
-// A unit: 128 rows x 1024 columns of A; each warp reduces 16 rows.  B unit:
-// 128 columns x 256 rows of B; each thread keeps the maxima of 4 columns over
-// 32 rows, then the 8 row groups are combined in shared memory.  One
-// atomicMax per row / column per unit.
-//
-// Non-negative floats order like their bit patterns, and every value of the
-// domain [0, 2^127] has bits <= DOMAIN_MAX_BITS, so the maxima run on the raw
-// bits: one unsigned max per value gives both the maximum and the domain
-// test.  A thread whose running maximum is above DOMAIN_MAX_BITS (one of its
-// values is negative, -0, +inf, NaN or above 2^127) goes over its values again
-// with the exact test, which flags the error and yields the maximum of the
-// non-negative values.
-constexpr uint32_t DOMAIN_MAX_BITS = 0x7F000000u;  // bits of 2^127
-
-__device__ __forceinline__ uint32_t umax3(uint32_t a, uint32_t b, uint32_t c) {
-  return max(a, max(b, c));
-}
-
-// Exact pass over len values src[0], src[step], ...: the maximum of the
-// non-negative values as bits (at most those of +inf), with bit 31 set if any
-// value is outside the domain.
-__device__ __forceinline__ uint32_t exact_max_bits(const float* src, int64_t step, int len) {
-  float m = 0.0f;
-  bool bad = false;
-  for (int t = 0; t < len; ++t) {
-    const float x = __ldg(src + t * step);
-    bad |= !in_domain(x);
-    m = fmaxf(m, x);
-  }
-  return __float_as_uint(nonneg_bits_max(m)) | (bad ? 0x80000000u : 0u);
-}
-
-// Folds the error bit of exact_max_bits into bad and returns the maximum.
-__device__ __forceinline__ uint32_t take_exact(uint32_t e, bool& bad) {
-  bad |= (e >> 31) != 0u;
-  return e & 0x7FFFFFFFu;
-}
 
 __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ Common cm) {
   __shared__ uint32_t red[8][128];
@@ -222,151 +174,6 @@ __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ C
   }
 }
 
-// The maximum behind a row / column scale (its bits; 0 gives the scale 1),
-// and the power-of-two scale from it.
-__device__ __forceinline__ uint32_t scale_bits(const Common& cm, const uint32_t* mx, int64_t idx,
-                                               int g, int which) {
-  if (cm.scaling == 0) return 0u;
-  return cm.scaling == 1 ? cm.gmax[2 * g + which] : mx[idx];
-}
-__device__ __forceinline__ float scale_from_bits(const Common& cm, uint32_t bits) {
-  return cm.scaling == 0 ? 1.0f : pow2_ceil_f(__uint_as_float(bits));
-}
-__device__ __forceinline__ float scale_of(const Common& cm, const uint32_t* mx, int64_t idx,
-                                          int g, int which) {
-  return scale_from_bits(cm, scale_bits(cm, mx, idx, g, which));
-}
-
-// v[u][e] <- v[u][e] / s[u] for power-of-two scales s[u]; a multiply by the
-// exact reciprocal whenever every scale of the warp has a normal one (called
-// by whole warps).
-template <int U, int EPC>
-__device__ __forceinline__ void div_scales(float (&v)[U][EPC], const float (&s)[U]) {
-  float inv[U];
-  bool ok = true;
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    inv[u] = 1.0f / s[u];
-    ok = ok && recip_exact(s[u]);
-  }
-  if (__all_sync(0xffffffffu, ok)) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] *= inv[u];
-  } else {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] = div_pow2(v[u][e], s[u], inv[u], recip_exact(s[u]));
-  }
-}
-
-// v <- v^p * opscale with p = 2^plog, or p = 1.5 * 2^plog for a half level
-// (y * sqrt(y), y = v^(2^plog)); the squarings of all U x EPC values
-// interleaved (independent chains; the same products as pow2k value by value).
-template <int U, int EPC>
-__device__ __forceinline__ void power_all(float (&v)[U][EPC], int plog, int half, float opscale) {
-#pragma unroll 1
-  for (int t = 0; t < plog; ++t) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] *= v[u][e];
-  }
-  if (half) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] *= sqrtf(v[u][e]);
-  }
-#pragma unroll
-  for (int u = 0; u < U; ++u)
-#pragma unroll
-    for (int e = 0; e < EPC; ++e) v[u][e] *= opscale;
-}
-
-// ----------------------------------------------------------- A images ---
-// Second half of an A image tile built by 1024 / U threads: thread t holds
-// the source values of image chunks (row (t >> 3) + (128 / U) u, 16-byte slot
-// t & 7), u < U (zero past M), and their row scales rs[u] (1 past M);
-// scales, powers, packs and stores them (a warp writes four whole 128-byte
-// image rows).
-template <int MODE, int U>
-__device__ __forceinline__ void power_a_store(const Common& cm, const Level& lv, const Prob& P,
-                                              int rb, int kb, float (&v)[U][Packer<MODE>::EPC],
-                                              const float (&rs)[U]) {
-  using PK = Packer<MODE>;
-  constexpr int RSTEP = TILE_M / U;
-  const float opscale = ldexpf(1.0f, cm.s_op);
-  uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
-  const int cc = threadIdx.x & 7;
-  if (lv.is_top && kb == 0 && cc == 0) {
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int row = rb * TILE_M + (threadIdx.x >> 3) + RSTEP * u;
-      if (row < P.M) cm.r[P.rc_r + row] = rs[u];
-    }
-  }
-  div_scales(v, rs);
-  power_all(v, lv.plog, lv.half, opscale);
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int rr = (threadIdx.x >> 3) + RSTEP * u;
-    uint4 hi, lo;
-    PK::pack(v[u], hi, lo);
-    const uint32_t off = sw128_offset(rr, cc * 16);
-    *reinterpret_cast<uint4*>(dst + off) = hi;
-    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
-  }
-}
-
-template <int MODE>
-__device__ __forceinline__ void power_a_tile(const Common& cm, const Level& lv, int g,
-                                             const Prob& P, int rb, int kb) {
-  using PK = Packer<MODE>;
-  constexpr int EPC = PK::EPC;
-  constexpr int BK = mode_bk(MODE);
-  const bool vec = ((P.lda & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.A) & 15) == 0);
-  // 1024 16-byte output chunks per tile, 4 per thread: chunk = tid + 256 u,
-  // row = chunk / 8 (8 threads cover one 128-byte image row), 16-byte slot
-  // = chunk % 8.  All loads are issued, unconditionally, before any
-  // arithmetic: rows past M and columns past K read the clamped (in-bounds)
-  // index and are zeroed afterwards.
-  float v[4][EPC];
-  const int cc = threadIdx.x & 7;
-  const int k0 = kb * BK + cc * EPC;
-  const bool vec_k = vec && k0 + EPC <= P.K;  // this thread's columns are whole 16-byte groups
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int row = rb * TILE_M + (threadIdx.x >> 3) + 32 * u;
-    const float* srow = P.A + (int64_t)min(row, P.M - 1) * P.lda;
-    if (vec_k) {
-#pragma unroll
-      for (int e = 0; e < EPC; e += 4) {
-        const float4 t = __ldg(reinterpret_cast<const float4*>(srow + k0 + e));
-        v[u][e] = t.x; v[u][e + 1] = t.y; v[u][e + 2] = t.z; v[u][e + 3] = t.w;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) v[u][e] = __ldg(srow + min(k0 + e, P.K - 1));
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const bool row_in = rb * TILE_M + (threadIdx.x >> 3) + 32 * u < P.M;
-#pragma unroll
-    for (int e = 0; e < EPC; ++e) v[u][e] = (row_in && k0 + e < P.K) ? v[u][e] : 0.0f;
-  }
-  float rs[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int row = rb * TILE_M + (threadIdx.x >> 3) + 32 * u;
-    rs[u] = row < P.M ? scale_of(cm, cm.rmax, P.rc_r + row, g, 0) : 1.0f;
-  }
-  power_a_store<MODE, 4>(cm, lv, P, rb, kb, v, rs);
-}
-
 // Top level without a tensor map (k_image_tma below): one block per operand
 // tile.  Lower levels: the same operand-tile ids strided over a grid of a few
 // blocks per SM; a tile is rebuilt only if a pushed output tile needs its row
@@ -416,7 +223,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const Prob& P = prob_at(cm, g);
     const int local = id - P.xa_base;
     const int rb = local / P.KB;
-    power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
+    power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, threadIdx.x);
     return;
   }
   if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
@@ -431,103 +238,8 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
         const Prob& P = prob_at(cm, g);
         const int local = id - P.xa_base;
         const int rb = local / P.KB;
-        power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB);
+        power_a_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, threadIdx.x);
       });
-}
-
-// ----------------------------------------------------------- B images ---
-// The B image holds B^T: image row n, K along the 128-byte row.  The tile of
-// B (BK rows of K x 128 columns) is staged in shared memory and transposed.
-template <int MODE>
-__device__ __forceinline__ void power_b_tile(const Common& cm, const Level& lv, int g,
-                                             const Prob& P, int rb, int kb, float* stile) {
-  using PK = Packer<MODE>;
-  constexpr int EPC = PK::EPC;
-  constexpr int BK = mode_bk(MODE);
-  const float opscale = ldexpf(1.0f, cm.s_op);
-  __syncthreads();  // stile reuse across consecutive tiles
-  {
-    // BK rows of K x 128 columns, staged in chunks of up to 64 rows (below).
-    // 16-byte aligned rows: thread = (row group tid/32, columns 4 lane ..
-    // 4 lane + 3), float4 loads.  Otherwise thread = (row group, columns
-    // lane + 32 c), so that each load instruction reads one contiguous
-    // 128-byte row segment.
-    const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
-    const int n0 = rb * TILE_M;
-    const bool vec = ((P.ldb & 3) == 0) && ((reinterpret_cast<uintptr_t>(P.B) & 15) == 0) &&
-                     n0 + TILE_M <= P.N;
-    float cs[4], inv[4];
-    bool inv_ok[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int n = vec ? n0 + lane * 4 + c : n0 + lane + 32 * c;
-      cs[c] = n < P.N ? scale_of(cm, cm.cmax, P.rc_c + n, g, 1) : 1.0f;
-      inv[c] = 1.0f / cs[c];
-      inv_ok[c] = cs[c] >= 1.1754944e-38f && cs[c] <= 8.507059e37f;
-      if (lv.is_top && kb == 0 && rg == 0 && n < P.N) cm.c[P.rc_c + n] = cs[c];
-    }
-    // Loads in chunks of up to 8 row groups (64 rows), all of a chunk
-    // issued, unconditionally, before its values are used: rows past K and
-    // columns past N read the clamped (in-bounds) index and are zeroed after.
-    constexpr int CH = BK / 8 < 8 ? BK / 8 : 8;
-    const int nlast = P.N - 1 - n0;  // last column of the tile block in bounds
-#pragma unroll
-    for (int it0 = 0; it0 < BK / 8; it0 += CH) {
-      float4 t[CH];
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const int k = kb * BK + rg + 8 * (it0 + i);
-        const float* srow = P.B + (int64_t)min(k, P.K - 1) * P.ldb + n0;
-        if (vec) {
-          t[i] = __ldg(reinterpret_cast<const float4*>(srow + lane * 4));
-        } else {
-          t[i].x = __ldg(srow + min(lane, nlast));
-          t[i].y = __ldg(srow + min(lane + 32, nlast));
-          t[i].z = __ldg(srow + min(lane + 64, nlast));
-          t[i].w = __ldg(srow + min(lane + 96, nlast));
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const bool kin = kb * BK + rg + 8 * (it0 + i) < P.K;
-        if (vec) {
-          t[i] = kin ? t[i] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        } else {
-          t[i].x = (kin && lane <= nlast) ? t[i].x : 0.0f;
-          t[i].y = (kin && lane + 32 <= nlast) ? t[i].y : 0.0f;
-          t[i].z = (kin && lane + 64 <= nlast) ? t[i].z : 0.0f;
-          t[i].w = (kin && lane + 96 <= nlast) ? t[i].w : 0.0f;
-        }
-        float* rowp = stile + (rg + 8 * (it0 + i)) * 129;
-        const int c0 = vec ? lane * 4 : lane, cst = vec ? 1 : 32;
-        rowp[c0] = div_pow2(t[i].x, cs[0], inv[0], inv_ok[0]);
-        rowp[c0 + cst] = div_pow2(t[i].y, cs[1], inv[1], inv_ok[1]);
-        rowp[c0 + 2 * cst] = div_pow2(t[i].z, cs[2], inv[2], inv_ok[2]);
-        rowp[c0 + 3 * cst] = div_pow2(t[i].w, cs[3], inv[3], inv_ok[3]);
-      }
-    }
-  }
-  __syncthreads();
-  uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
-  float v[4][EPC];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int ch = threadIdx.x + PRO_THREADS * u;
-    const int nr = ch >> 3, cc = ch & 7;
-#pragma unroll
-    for (int e = 0; e < EPC; ++e) v[u][e] = stile[(cc * EPC + e) * 129 + nr];
-  }
-  power_all(v, lv.plog, lv.half, opscale);
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int ch = threadIdx.x + PRO_THREADS * u;
-    const int nr = ch >> 3, cc = ch & 7;
-    uint4 hi, lo;
-    PK::pack(v[u], hi, lo);
-    const uint32_t off = sw128_offset(nr, cc * 16);
-    *reinterpret_cast<uint4*>(dst + off) = hi;
-    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.b_plane + off) = lo;
-  }
 }
 
 // Top level without a tensor map: one block per operand tile.  Lower levels:
@@ -543,7 +255,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     const Prob& P = prob_at(cm, g);
     const int local = id - P.xb_base;
     const int rb = local / P.KB;
-    power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
+    power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile, threadIdx.x, 0);
     return;
   }
   if (*lv.work_count == 0) return;  // no tile pushed to this level (uniform)
@@ -559,7 +271,7 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
         const Prob& P = prob_at(cm, g);
         const int local = id - P.xb_base;
         const int rb = local / P.KB;
-        power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile);
+        power_b_tile<MODE>(cm, lv, g, P, rb, local - rb * P.KB, stile, threadIdx.x, 0);
       });
 }
 
@@ -740,7 +452,7 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
       for (int u = 0; u < U; ++u)
         lds_rotated<EPC / 4>(st + line(u) * BK + cc * EPC, (cc * (EPC / 4) / 8) & (EPC / 4 - 1),
                              v[u]);
-      power_a_store<MODE, U>(cm, lv, P, rb, kb, v, sc);
+      power_a_store<MODE, U>(cm, lv, P, rb, kb, v, sc, threadIdx.x);
     } else {
       uint8_t* ob = outimg + (j & 1) * CF::PLANES * IMG_BYTES;
 #pragma unroll
