@@ -97,7 +97,8 @@ typedef struct pn_opts {
   /* Optional device int32 receiving device-side errors (see above). */
   int32_t* dev_status;
   /* Optional cudaEvent_t pair recorded on `stream` immediately before and
-   * after the first (largest-p) tensor-core launch, for timing it. */
+   * after the first (largest-p) tensor-core launch, for timing it (the
+   * persistent grouped launch: before and after that whole launch). */
   void* ev_gemm_begin;
   void* ev_gemm_end;
   /* Limit of every bounded device-side wait, in nanoseconds; 0 = 2e9. */
@@ -105,7 +106,9 @@ typedef struct pn_opts {
   /* Test hooks, 0 in normal use.  Bit 0: the tensor-core kernel's copy
    * producer skips one stage so that the consumer's bounded wait runs out
    * (PN_ETIMEOUT).  Bit 1: the tensor-copy image kernel announces its first
-   * tile's bytes without copying them, with the same effect. */
+   * tile's bytes without copying them, with the same effect.  Bit 2: the
+   * grouped call runs one launch sequence per p level instead of its single
+   * persistent launch (same results; for comparing the two). */
   int32_t debug_flags;
   /* Estimate of max_k u_k from the p-sums (Sec. 2.1):
    *   0 (default) = plain, (S^(p*))^(1/p*), an overestimate by at most
@@ -366,10 +369,16 @@ PN_API pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const f
                                  const uint8_t* p_sel, const float* dC, float* dA, float* dB,
                                  const pn_opts* opts, void* ws, size_t ws_bytes, void* stream);
 
-/* Grouped launch: many independent products C_g = A_g (x,max) B_g in one
- * persistent tensor-core launch per p level (Sec. 4: the p rings and the
- * problems parallelise coarsely).  Two steps, so that the run step never
- * copies host memory and can be captured in a CUDA graph:
+/* Grouped launch: many independent products C_g = A_g (x,max) B_g in ONE
+ * persistent launch over every problem, p level and output tile (Sec. 4: the
+ * p rings and the problems parallelise coarsely).  One CTA per SM (a
+ * cooperative launch) builds each operand block's maxima, scales and powered
+ * images, publishes it with a ready flag, runs the tensor-core tiles of the
+ * level as their blocks become ready, and meets the other CTAs at a bounded
+ * barrier before the next lower p; tiles with unresolved entries carry over
+ * through device work lists.  With scaling 1 (one global scale per operand)
+ * the call runs one launch sequence per p level instead.  Two steps, so that
+ * the run step never copies host memory and can be captured in a CUDA graph:
  *  1. pn_grouped_build_table() (host only, no CUDA calls) writes a table
  *     describing `count` problems (sizes MNK[3g..3g+2] = M_g, N_g, K_g, and
  *     DEVICE pointers A[g], B[g], C[g] of contiguous row-major FP32 matrices;

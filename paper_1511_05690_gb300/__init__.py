@@ -175,13 +175,14 @@ def autotune(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), comput
 
 class GroupedProduct:
     """Many independent p-norm (x,max) products C_g = A_g (x) B_g computed
-    together, one persistent launch per p level.  The problem table is built
+    together in one persistent launch over every problem, p level and tile
+    (scaling 1 uses one launch sequence per p level).  The problem table is built
     and copied to the device once here; run() only launches kernels, so it can
     be captured in a CUDA graph (the plan keeps its own workspace and outputs
     alive for replays).  A_g: (M_g, K_g), B_g: (K_g, N_g), float32 CUDA."""
 
     def __init__(self, As, Bs, *, p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2,
-                 tile_n=0, estimator=0):
+                 tile_n=0, estimator=0, correction=0, debug_flags=0):
         import numpy as np
         if len(As) != len(Bs):
             raise ValueError("As and Bs differ in length")
@@ -198,7 +199,8 @@ class GroupedProduct:
             mnk += [a.shape[0], b.shape[1], a.shape[1]]
         self.status = status_word(dev)
         self.opts = make_opts(p_log2, compute, tau, scaling, 2, tile_n, self.status.data_ptr(),
-                              estimator=estimator)
+                              estimator=estimator, correction=correction,
+                              debug_flags=debug_flags)
         L = lib()
         MNK = (ctypes.c_int64 * max(1, 3 * count))(*mnk)
         vp = ctypes.c_void_p

@@ -26,7 +26,7 @@ namespace pn {
 
 namespace {
 
-constexpr uint64_t GROUP_MAGIC = 0x3150524750504e50ull;  // "PNPPGRP1"
+constexpr uint64_t GROUP_MAGIC = 0x3250524750504e50ull;  // "PNPPGRP2"
 constexpr size_t WS_ALIGN = 256;
 constexpr size_t IMG_ALIGN = 1024;
 
@@ -35,7 +35,8 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 struct GroupLayout {
   int32_t BN, total_tiles, total_xa, total_xb, total_tm, total_tn, total_ma, total_mb;
-  uint64_t off_rmax, off_cmax, off_gmax, off_counts, off_rflag, off_cflag, ctrl_bytes;
+  uint64_t off_rmax, off_cmax, off_gmax, off_counts, off_rflag, off_cflag, off_ready, off_ldone,
+      ctrl_bytes;
   uint64_t off_r, off_c, off_work, off_state, off_pend, off_aimg, off_bimg, total;
   uint64_t probs_offset;  // bytes from the table start to this layout's Prob[count]
   uint64_t lut_offset[7]; // bytes from the table start to each id -> problem table
@@ -117,6 +118,21 @@ float time_ms(F fn, cudaStream_t s, int reps, pn_status* st) {
 }
 
 }  // namespace
+
+int grouped_persist_f16(const Common& cm, const GroupedRun& gr, int sms, void* stream);
+int grouped_persist_tf32(const Common& cm, const GroupedRun& gr, int sms, void* stream);
+int grouped_persist_f8(const Common& cm, const GroupedRun& gr, int sms, void* stream);
+
+int launch_grouped_persist(const Common& cm, const GroupedRun& gr, int num_sms, void* stream) {
+  switch (cm.mode) {
+    case MODE_BF16:
+    case MODE_F16: return grouped_persist_f16(cm, gr, num_sms, stream);
+    case MODE_TF32:
+    case MODE_3XTF32: return grouped_persist_tf32(cm, gr, num_sms, stream);
+    case MODE_E4M3: return grouped_persist_f8(cm, gr, num_sms, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 int host_tuned_bn(int mode, int64_t M, int64_t N, int64_t K) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -262,6 +278,10 @@ pn_status pn_grouped_build_table(int32_t count, const int64_t* MNK, const float*
     L.off_counts = off; off += sizeof(int32_t) * PN_MAX_P;
     L.off_rflag = off; off += static_cast<size_t>(opts->n_p) * tm;
     L.off_cflag = off; off += static_cast<size_t>(opts->n_p) * tn;
+    // persistent launch: a ready flag per operand block, a counter per level
+    off = align_up(off, 4);
+    L.off_ready = off; off += sizeof(int32_t) * static_cast<size_t>(tm + tn);
+    L.off_ldone = off; off += sizeof(int32_t) * PN_MAX_P;
     L.ctrl_bytes = align_up(off, 16);
     off = align_up(off, WS_ALIGN);
     L.off_r = off; off = align_up(off + sizeof(float) * rows, WS_ALIGN);
@@ -320,11 +340,24 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   if (L.total_tiles == 0) return PN_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(ws, 0, L.ctrl_bytes, s)) return PN_ECUDA;
-  if (launch_maxes(cm, stream)) return PN_ECUDA;
   int32_t* counts = reinterpret_cast<int32_t*>(ws + L.off_counts);
   int32_t* work = reinterpret_cast<int32_t*>(ws + L.off_work);
   uint8_t* rflag = ws + L.off_rflag;
   uint8_t* cflag = ws + L.off_cflag;
+  // One persistent launch for every level (scaling 2 and 0: the block
+  // builders find each block's maxima themselves); the global scale of
+  // scaling 1 needs every block of a problem first, so it keeps one launch
+  // per level.  debug_flags bit 2 forces the per-level launches (tests).
+  const bool persist = H->scaling != 1 && !(o->debug_flags & 4);
+  GroupedRun gr;
+  std::memset(&gr, 0, sizeof(gr));
+  gr.n_slots = o->n_p;
+  gr.n_a = L.total_tm;
+  gr.n_b = L.total_tn;
+  gr.maxima = 1;
+  gr.ready = reinterpret_cast<int32_t*>(ws + L.off_ready);
+  gr.level_done = reinterpret_cast<int32_t*>(ws + L.off_ldone);
+  if (!persist && launch_maxes(cm, stream)) return PN_ECUDA;
   for (int q = o->n_p - 1; q >= 0; --q) {
     const int qn = q > 0 ? q - 1 : 0;
     Level lv;
@@ -344,6 +377,10 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     lv.next_rflag = rflag + static_cast<size_t>(qn) * L.total_tm;
     lv.next_cflag = cflag + static_cast<size_t>(qn) * L.total_tn;
     set_projection(lv, o, q);
+    if (persist) {
+      gr.lv[o->n_p - 1 - q] = lv;
+      continue;
+    }
     if (launch_power_a(cm, lv, stream)) return PN_ECUDA;
     if (launch_power_b(cm, lv, stream)) return PN_ECUDA;
     if (lv.is_top && o->ev_gemm_begin)
@@ -352,6 +389,13 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     if (lv.is_top && o->ev_gemm_end)
       if (cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_end), s)) return PN_ECUDA;
   }
+  if (!persist) return PN_OK;
+  // the events bracket the whole persistent launch (every level)
+  if (o->ev_gemm_begin && cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_begin), s))
+    return PN_ECUDA;
+  if (launch_grouped_persist(cm, gr, sms, stream)) return PN_ECUDA;
+  if (o->ev_gemm_end && cudaEventRecord(static_cast<cudaEvent_t>(o->ev_gemm_end), s))
+    return PN_ECUDA;
   return PN_OK;
 }
 

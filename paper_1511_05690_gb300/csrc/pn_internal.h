@@ -143,6 +143,19 @@ struct Level {
   uint8_t* skip_cflag;
 };
 
+// One persistent grouped launch (k_grouped_persist): the levels of the
+// schedule in slot order (largest p first) and the cross-CTA control words.
+// Operand blocks: A row blocks are the tile rows (global ids 0 .. n_a - 1),
+// B column blocks the tile columns (ids n_a .. n_a + n_b - 1).
+struct GroupedRun {
+  Level lv[PN_MAX_P];
+  int32_t n_slots;
+  int32_t n_a, n_b;
+  int32_t maxima;        // top level: maxima and domain test in the block builders
+  int32_t* ready;        // [n_a + n_b]: slot + 1 once the block's images of that slot are written
+  int32_t* level_done;   // [n_slots]: CTAs that finished the slot
+};
+
 // The level schedule: every p of P from the largest down, each followed --
 // for the r = 2 projection (estimator 2) -- by an extra "half" level at
 // 3p/4 when p/2 and p/4 are the two p below it in P.  Slot t runs level
@@ -284,6 +297,9 @@ int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list,
 int launch_scales(const Common& cm, void* stream);
 int launch_bw_image(int mode, const BwImage& im, void* stream);
 int gemm_smem_bytes(int mode, int BN);
+// Persistent grouped launch: every level of a group in one cooperative launch
+// (returns a cudaError_t value).
+int launch_grouped_persist(const Common& cm, const GroupedRun& gr, int num_sms, void* stream);
 int gemm_stages(int mode, int BN);
 
 }  // namespace pn

@@ -1,5 +1,6 @@
-"""GPU parity of the grouped launch (many products, one launch per p level),
-its CUDA-graph capture and the tile-width autotuner."""
+"""GPU parity of the grouped call (many products in one persistent launch over
+every problem, p level and tile), its per-level launch sequence, its CUDA-graph
+capture and the tile-width autotuner."""
 import ctypes
 
 import numpy as np
@@ -142,3 +143,80 @@ def test_grouped_rejects_empty_contraction(pn):
         pn.GroupedProduct([torch.zeros((4, 0), device="cuda")],
                           [torch.zeros((0, 3), device="cuda")])
     assert ei.value.status == 1
+
+
+def _multilevel_problems(seed, count=12):
+    """Square problems whose entries spread p* over several levels: small
+    cross terms and one large product per row (as in the product tests)."""
+    g = workloads.rng(seed)
+    out = []
+    for n in [int(x) for x in g.integers(20, 300, count)] + [129, 257]:
+        A = (0.05 * (0.5 + 0.5 * g.random((n, n)))).astype(np.float32)
+        B = (0.05 * (0.5 + 0.5 * g.random((n, n)))).astype(np.float32)
+        A[np.arange(n), np.arange(n)] = 1.0
+        B[(np.arange(n) + 1) % n, np.arange(n)] = 1.0
+        out.append((A, B))
+    return out
+
+
+@pytest.mark.parametrize("mode,tile_n,estimator,correction",
+                         [("bf16", 128, 0, 0), ("bf16", 256, 0, 0), ("f32", 128, 0, 0),
+                          ("tf32", 256, 0, 0), ("f16", 128, 0, 0), ("e4m3", 256, 0, 0),
+                          ("bf16", 256, 1, 0), ("f32", 128, 0, 1)])
+def test_grouped_persistent_equals_level_launches(pn, mode, tile_n, estimator, correction):
+    """The single persistent launch and the per-level launch sequence run the
+    same arithmetic: bit-identical results, here with entries resolving at
+    several levels (work lists carried between levels inside the launch), the
+    r = 1 projection and the K^(1/p*) correction."""
+    probs = _multilevel_problems(830) + _problems(831, count=16)
+    As = [_dev(a) for a, _ in probs]
+    Bs = [_dev(b) for _, b in probs]
+    kw = dict(compute=mode, tile_n=tile_n, estimator=estimator, correction=correction)
+    tau = 1.0 if mode == "f16" else None  # FP16 operands: a tau the data clears at low p
+    persist = pn.GroupedProduct(As, Bs, tau=tau, **kw)
+    levels = pn.GroupedProduct(As, Bs, tau=tau, debug_flags=4, **kw)
+    C1 = persist.run(check=True)
+    C2 = levels.run(check=True)
+    for a, c1, c2 in zip(As, C1, C2):
+        assert torch.equal(c1, c2), (tuple(a.shape), mode)
+    # several levels took part
+    C, psel, _ = pn.maxprod_pnorm(As[0], Bs[0], compute=mode, tile_n=tile_n, tau=tau)
+    assert len(torch.unique(psel & 0x7F)) >= 2
+
+
+def test_grouped_persistent_multilevel_matches_oracle(pn, orc):
+    probs = _multilevel_problems(840, count=6)
+    plan = pn.GroupedProduct([_dev(a) for a, _ in probs], [_dev(b) for _, b in probs],
+                             compute="f32", tile_n=128)
+    Cs = [c.cpu().numpy() for c in plan.run(check=True)]
+    pl = list(range(7))
+    levels = set()
+    for (A, B), C in zip(probs, Cs):
+        K = A.shape[1]
+        tau = orc.default_tau(K, 0)
+        ref = orc.pnorm(A.astype(np.float64), B.astype(np.float64), pl, tau)
+        levels |= set(np.unique(ref["p_sel"] & 0x7F).tolist())
+        err = np.abs(C - ref["C"]) / ref["C"]
+        assert err.max() <= 1e-5, float(err.max())
+    assert len(levels) >= 3
+
+
+def test_grouped_persistent_domain_error(pn):
+    """A negative value in one problem of the group raises PN_EDOMAIN from the
+    block builders of the persistent launch, and the context stays usable."""
+    probs = _problems(850, count=10)
+    As = [_dev(a) for a, _ in probs]
+    Bs = [_dev(b) for _, b in probs]
+    As[3][2, 1] = -1.0
+    plan = pn.GroupedProduct(As, Bs, compute="bf16")
+    with pytest.raises(pn.PnError) as ei:
+        plan.run(check=True)
+    assert ei.value.status == 4
+    As[3][2, 1] = 0.5
+    Bs[5][0, 0] = float("nan")
+    plan = pn.GroupedProduct(As, Bs, compute="bf16")
+    with pytest.raises(pn.PnError) as ei:
+        plan.run(check=True)
+    assert ei.value.status == 4
+    Bs[5][0, 0] = 0.5
+    pn.GroupedProduct(As, Bs, compute="bf16").run(check=True)
