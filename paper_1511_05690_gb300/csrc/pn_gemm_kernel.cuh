@@ -301,9 +301,10 @@ struct MmaState {
 };
 
 // Lays out shared memory, initialises the barriers, allocates TMEM (warp 1)
-// and synchronises the block.  Called by every thread.
+// and synchronises the block.  timeout_ns limits every bounded wait of the
+// roles.  Called by every thread.
 template <int MODE, int BN>
-__device__ __forceinline__ Ctx ctx_setup(bool by_tile) {
+__device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
   constexpr int STAGES = num_stages(MODE, BN);
   constexpr uint32_t TMEM_COLS = 2 * BN;
@@ -319,6 +320,7 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile) {
   cx.tmem_slot = reinterpret_cast<uint32_t*>(cx.drain + 1);
   cx.abort_flag = reinterpret_cast<volatile int32_t*>(cx.tmem_slot + 1);
   cx.ok_flag = cx.abort_flag + 1;
+  cx.tmo = timeout_ns;
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -932,7 +934,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   // bounds a tile (grouped problems, or short contractions)
   const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) &&
                        (cm.nprob > 1 || cm.single.KB * mode_planes(MODE) <= 32);
-  const Ctx cx = ctx_setup<MODE, BN>(by_tile);
+  const Ctx cx = ctx_setup<MODE, BN>(by_tile, cm.timeout_ns);
   const Ready none{nullptr, 0, 0};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {

@@ -35,7 +35,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   static_assert(mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4 <= num_stages(MODE, BN) * stage_bytes(MODE, BN),
                 "block builders' staging does not fit the ring");
   __shared__ int32_t s_count;
-  const Ctx cx = ctx_setup<MODE, BN>(true);  // tiles alternate between the two epilogue groups
+  // tiles alternate between the two epilogue groups
+  const Ctx cx = ctx_setup<MODE, BN>(true, cm.timeout_ns);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ProdState ps{};
   for (int s = 0; s < 8; ++s) ps.pend[s] = -1;
