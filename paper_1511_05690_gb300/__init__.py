@@ -111,8 +111,9 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
                   tau=None, scaling=2, tile_n=0, out=None, want_psel=True, want_ssel=True,
                   check=True, ev_begin=None, ev_end=None, stream=None, timeout_ns=0,
                   debug_flags=0, estimator=0, correction=0, fit_i=None, fit_j=None,
-                  fit_coef=None):
+                  fit_coef=None, tile_m=0):
     """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None).
+    tile_m: 0 automatic, 128 one CTA per tile, 256 a CTA pair per 256 x 256 tile.
     estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*);
     2: r = 2 projection from the sums at p*/4, p*/2, 3p*/4 and p* (Sec. 2.1).
     correction 1: divide by K^(1/p*); 2: affine model per p* class fitted to the
@@ -137,7 +138,7 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
         fit.update(n_fit=fit_i.numel(), fit_i=fit_i.data_ptr(), fit_j=fit_j.data_ptr(),
                    fit_coef=fit_coef.data_ptr() if fit_coef is not None else None)
     o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(), _event(ev_begin),
-                  _event(ev_end), timeout_ns, debug_flags, estimator, **fit)
+                  _event(ev_end), timeout_ns, debug_flags, estimator, tile_m=tile_m, **fit)
     L = lib()
     need = L.pn_workspace_size(M, N, K, ctypes.byref(o))
     if need == 0 and M * N > 0:
@@ -155,8 +156,9 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
 
 def autotune(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), compute="bf16",
              tau=None, scaling=2, stream=None) -> int:
-    """Times the tile widths for this shape class and remembers the fastest
-    (later calls with tile_n=0 use it).  Synchronises; returns the width."""
+    """Times the tile shapes for this shape class and remembers the fastest
+    (later calls with tile_n=0, tile_m=0 use it).  Synchronises; returns the
+    width of one CTA's tile (128 or 256), or 512 for a CTA pair."""
     A, B = _mat(A, "A"), _mat(B, "B")
     M, K = A.shape
     N = B.shape[1]
@@ -351,7 +353,7 @@ def maxconv_exact(x: torch.Tensor, y: torch.Tensor, *, out=None, stream=None):
 
 def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), compute="f32",
                tau=None, scaling=2, diag_policy=2, tile_n=0, out=None, check=True,
-               stream=None, ev_begin=None, ev_end=None, estimator=0, correction=0):
+               stream=None, ev_begin=None, ev_end=None, estimator=0, correction=0, tile_m=0):
     """Estimated all-pairs shortest distances of the weight matrix W (+inf = no edge).
     Only the plain, uncorrected estimator is supported: a nonzero estimator or
     correction raises PnError(PN_EUNSUPPORTED)."""
@@ -363,7 +365,8 @@ def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), comput
     D = out if out is not None else torch.empty((n, n), dtype=torch.float32, device=dev)
     st = status_word(dev)
     o = make_opts(p_log2, compute, tau, scaling, diag_policy, tile_n, st.data_ptr(),
-                  _event(ev_begin), _event(ev_end), estimator=estimator, correction=correction)
+                  _event(ev_begin), _event(ev_end), estimator=estimator, correction=correction,
+                  tile_m=tile_m)
     L = lib()
     need = L.pn_apsp_workspace_size(n, ctypes.byref(o))
     if need == 0 and n > 0:

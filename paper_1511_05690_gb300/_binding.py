@@ -53,6 +53,7 @@ class PnOpts(ctypes.Structure):
         ("fit_i", ctypes.c_void_p),
         ("fit_j", ctypes.c_void_p),
         ("fit_coef", ctypes.c_void_p),
+        ("tile_m", ctypes.c_int32),
     ]
 
 
@@ -153,7 +154,7 @@ def check(status: int, where: str = "") -> None:
 def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_policy=2,
               tile_n=0, dev_status=None, ev_begin=None, ev_end=None, timeout_ns=0,
               debug_flags=0, estimator=0, correction=0, n_fit=0, fit_i=None, fit_j=None,
-              fit_coef=None) -> PnOpts:
+              fit_coef=None, tile_m=0) -> PnOpts:
     o = PnOpts()
     load().pn_default_opts(ctypes.byref(o))
     pl = [int(x) for x in p_log2]
@@ -178,4 +179,5 @@ def make_opts(p_log2=tuple(range(7)), compute="bf16", tau=None, scaling=2, diag_
     o.fit_i = fit_i
     o.fit_j = fit_j
     o.fit_coef = fit_coef
+    o.tile_m = int(tile_m)
     return o

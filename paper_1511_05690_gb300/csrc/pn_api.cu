@@ -54,6 +54,7 @@ bool opts_valid(const pn_opts* o) {
   if (o->scaling < 0 || o->scaling > 2) return false;
   if (o->diag_policy < 0 || o->diag_policy > 2) return false;
   if (o->tile_n != 0 && o->tile_n != 128 && o->tile_n != 256) return false;
+  if (o->tile_m != 0 && o->tile_m != 128 && o->tile_m != 256) return false;
   if (o->timeout_ns < 0) return false;
   if (std::isnan(o->tau)) return false;
   if (o->estimator < 0 || o->estimator > 2) return false;
@@ -64,12 +65,24 @@ bool opts_valid(const pn_opts* o) {
   return true;
 }
 
-// Tile width: 3xTF32 carries two operand planes, so only 128 fits the ring.
+// A CTA pair (cta_group::2) per 256 x 256 tile, or one CTA per tile.  The
+// autotune cache records a pair as 512.
+int choose_cg(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
+  if (o->tile_m == 128 || o->estimator == 2 || o->tile_n == 128) return 1;
+  if (o->tile_m == 256) return 2;
+  const int tuned = host_tuned_bn(o->compute, M, N, K);
+  if (tuned) return tuned == 512 ? 2 : 1;
+  return (M >= 256 && N >= 256) ? 2 : 1;
+}
+
+// Tile width of one CTA: 3xTF32 carries two operand planes, so only 128 fits
+// its ring; a CTA pair's tile is 256 wide.
 int choose_bn(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
+  if (choose_cg(o, M, N, K) == 2) return 256;
   if (o->compute == PN_F32_EXACT) return 128;
   if (o->tile_n) return o->tile_n;
   const int tuned = host_tuned_bn(o->compute, M, N, K);  // autotune cache
-  if (tuned) return tuned;
+  if (tuned == 128 || tuned == 256) return tuned;
   return N > 128 ? 256 : 128;
 }
 
@@ -86,9 +99,10 @@ float tau_up(double t) {
 // Workspace layout of one product (single problem).
 struct Layout {
   int BN = 0, KB = 0, RBA = 0, RBB = 0, tiles_m = 0, tiles_n = 0, total_tiles = 0;
+  int cg = 1, pair_tiles = 0;
   int state_ld = 0, n_p = 0, n_slots = 0, planes = 1;
   size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_counts = 0, off_rflag = 0,
-         off_cflag = 0;
+         off_cflag = 0, off_pushed = 0;
   size_t ctrl_bytes = 0, off_coef = 0, off_samp = 0, off_scls = 0;
   size_t off_r = 0, off_c = 0, off_work = 0, off_state = 0, off_pend = 0, off_pend2 = 0,
          off_park = 0, off_aimg = 0, off_bimg = 0;
@@ -99,6 +113,7 @@ struct Layout {
 Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   Layout L;
   const int mode = o->compute;
+  L.cg = choose_cg(o, M, N, K);
   L.BN = choose_bn(o, M, N, K);
   L.n_p = o->n_p;
   L.n_slots = make_schedule(o).n;
@@ -106,9 +121,12 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.KB = static_cast<int>(ceil_div(K, mode_bk(mode)));
   L.tiles_m = static_cast<int>(ceil_div(M, TILE_M));
   L.tiles_n = static_cast<int>(ceil_div(N, L.BN));
-  L.RBA = L.tiles_m;
+  // a pair's second CTA reads A row block 2 TM + 1: an odd last one is padded
+  // with a block of zeros (rows past M)
+  L.RBA = L.cg == 2 ? (L.tiles_m + 1) / 2 * 2 : L.tiles_m;
   L.RBB = L.tiles_n * (L.BN / TILE_M);
-  L.total_tiles = L.tiles_m * L.tiles_n;
+  L.pair_tiles = L.cg == 2 ? (L.tiles_m + 1) / 2 * L.tiles_n : 0;
+  L.total_tiles = L.cg == 2 ? L.pair_tiles : L.tiles_m * L.tiles_n;
   L.state_ld = L.tiles_n * (L.BN / 32);
   size_t off = 0;
   // control words, cleared at the start of every call
@@ -116,8 +134,10 @@ Layout make_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   L.off_cmax = off; off += sizeof(uint32_t) * N;
   L.off_gmax = off; off += sizeof(uint32_t) * 2;
   L.off_counts = off; off += sizeof(int32_t) * 2 * PN_MAX_P;
-  L.off_rflag = off; off += static_cast<size_t>(L.n_slots) * L.tiles_m;
+  L.off_rflag = off; off += static_cast<size_t>(L.n_slots) * L.RBA;
   L.off_cflag = off; off += static_cast<size_t>(L.n_slots) * L.tiles_n;
+  off = align_up(off, 4);
+  L.off_pushed = off; off += sizeof(uint32_t) * static_cast<size_t>(L.n_slots) * L.pair_tiles;
   L.ctrl_bytes = align_up(off, 16);
   off = align_up(off, WS_ALIGN);
   L.off_coef = off; off = align_up(off + sizeof(float) * 2 * PN_MAX_P, WS_ALIGN);
@@ -206,10 +226,11 @@ void fill_common(Common& cm, const Layout& L, int64_t M, int64_t N, int64_t K, c
   P.tau = tau_up(tau);
   cm.probs = nullptr;
   cm.nprob = 1;
+  cm.cg = L.cg;
   cm.total_tiles = L.total_tiles;
   cm.total_xa = L.RBA * L.KB;
   cm.total_xb = L.RBB * L.KB;
-  cm.total_tm = L.tiles_m;
+  cm.total_tm = L.RBA;
   cm.total_tn = L.tiles_n;
   cm.total_ma = L.RBA * P.KMA;
   cm.total_mb = L.RBB * P.KMB;
@@ -268,10 +289,13 @@ Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, const Schedule&
   lv.work_count = counts + t;
   lv.next_work = work + static_cast<size_t>(tn) * L.total_tiles;
   lv.next_count = counts + tn;
-  lv.rflag = rflag + static_cast<size_t>(t) * L.tiles_m;
+  lv.rflag = rflag + static_cast<size_t>(t) * L.RBA;
   lv.cflag = cflag + static_cast<size_t>(t) * L.tiles_n;
-  lv.next_rflag = rflag + static_cast<size_t>(tn) * L.tiles_m;
+  lv.next_rflag = rflag + static_cast<size_t>(tn) * L.RBA;
   lv.next_cflag = cflag + static_cast<size_t>(tn) * L.tiles_n;
+  if (L.cg == 2)
+    lv.pair_pushed = reinterpret_cast<uint32_t*>(ws + L.off_pushed) +
+                     static_cast<size_t>(tn) * L.pair_tiles;
   if (o->estimator == 2) {
     lv.r2_state = t > 0;
     lv.r2_new = !lv.half && t + 1 < sc.n && sc.half[t + 1];
@@ -279,7 +303,7 @@ Level make_level(const Layout& L, const pn_opts* o, uint8_t* ws, const Schedule&
       const int ts = t + 2;
       lv.skip_work = work + static_cast<size_t>(ts) * L.total_tiles;
       lv.skip_count = counts + ts;
-      lv.skip_rflag = rflag + static_cast<size_t>(ts) * L.tiles_m;
+      lv.skip_rflag = rflag + static_cast<size_t>(ts) * L.RBA;
       lv.skip_cflag = cflag + static_cast<size_t>(ts) * L.tiles_n;
     }
   } else {
@@ -426,14 +450,21 @@ int32_t pn_device_sm_count(void) { return pn::device_sms(); }
 
 size_t pn_workspace_size(int64_t M, int64_t N, int64_t K, const pn_opts* opts) {
   if (!opts_valid(opts) || !dims_ok(M, N, K)) return 0;
-  if (opts->tile_n != 0 || opts->compute == PN_F32_EXACT) return make_layout(M, N, K, opts).total;
-  // tile_n = 0: large enough for either width the autotuner may choose
-  pn_opts o = *opts;
-  o.tile_n = 128;
-  const size_t a = make_layout(M, N, K, &o).total;
-  o.tile_n = 256;
-  const size_t b = make_layout(M, N, K, &o).total;
-  return a > b ? a : b;
+  // large enough for every tile shape the options leave open (the autotuner
+  // or the automatic rule may pick any of them later)
+  size_t best = 0;
+  for (int tile_m : {128, 256}) {
+    for (int tile_n : {128, 256}) {
+      if (opts->tile_m && opts->tile_m != tile_m) continue;
+      if (opts->tile_n && opts->tile_n != tile_n) continue;
+      pn_opts o = *opts;
+      o.tile_m = tile_m;
+      o.tile_n = tile_n;
+      const size_t b = make_layout(M, N, K, &o).total;
+      if (b > best) best = b;
+    }
+  }
+  return best;
 }
 
 pn_status maxprod_pnorm(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,

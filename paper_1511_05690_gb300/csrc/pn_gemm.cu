@@ -45,6 +45,7 @@ int gemm_stages(int mode, int BN) { return gemm::num_stages(mode, BN); }
 
 int launch_gemm_level(const Common& cm, const Level& lv, int num_sms, void* stream) {
   if (cm.BN != 128 && cm.BN != 256) return cudaErrorInvalidValue;
+  if (cm.cg == 2 && cm.BN != 256) return cudaErrorInvalidValue;
   switch (cm.mode) {
     case MODE_BF16:
     case MODE_F16: return gemm_launch_f16(cm.mode, cm.BN, cm, lv, num_sms, stream);

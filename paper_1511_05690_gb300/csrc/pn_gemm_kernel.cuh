@@ -13,15 +13,19 @@ constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int GEMM_THREADS = 64 + EPI_THREADS;     // producer, MMA, epilogue
 constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
 
-__host__ __device__ constexpr inline int stage_bytes(int mode, int BN) {
-  return mode_planes(mode) * (IMG_BYTES + IMG_BYTES * (BN / TILE_M));
+// Bytes of one ring stage: the A image tile and this CTA's B image tiles of
+// 128 rows each (CG = 2: a CTA pair, each CTA holding half of the BN rows of
+// B^T), per operand plane.
+__host__ __device__ constexpr inline int stage_bytes(int mode, int BN, int CG = 1) {
+  return mode_planes(mode) * (IMG_BYTES + IMG_BYTES * (BN / TILE_M) / CG);
 }
-__host__ __device__ constexpr int num_stages(int mode, int BN) {
-  return SMEM_STAGE_BUDGET / stage_bytes(mode, BN) > 8 ? 8 : SMEM_STAGE_BUDGET / stage_bytes(mode, BN);
+__host__ __device__ constexpr int num_stages(int mode, int BN, int CG = 1) {
+  return SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG) > 8 ? 8
+                                                          : SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG);
 }
 constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
-__host__ __device__ constexpr int smem_total(int mode, int BN) {
-  return num_stages(mode, BN) * stage_bytes(mode, BN) + 1024 /*align*/ + 256 /*barriers*/ +
+__host__ __device__ constexpr int smem_total(int mode, int BN, int CG = 1) {
+  return num_stages(mode, BN, CG) * stage_bytes(mode, BN, CG) + 1024 /*align*/ + 256 /*barriers*/ +
          EPI_WARPS * STG_BYTES;
 }
 __host__ __device__ constexpr int mma_kind(int mode) {
@@ -261,11 +265,26 @@ __device__ __forceinline__ void r1_finish_block(float* stg, const float (&x)[32]
 // single-level kernel runs them once and the persistent grouped kernel once
 // per level, with the ring positions and the tile count carried over.
 
+// Output tile (tile row tm of 128 rows, tile column tn of BN columns) of
+// list entry t: single CTAs walk the tiles in grouped raster order; a CTA
+// pair walks pairs of tile rows (256 rows), rank r taking tile row 2 TM + r.
+template <int CG>
+__device__ __forceinline__ void tile_coords(const Prob& P, int t, uint32_t rank, int& tm, int& tn) {
+  if constexpr (CG == 1) {
+    raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+  } else {
+    int TM;
+    raster(t - P.tile_base, (P.tiles_m + 1) >> 1, P.tiles_n, TM, tn);
+    tm = 2 * TM + static_cast<int>(rank);
+  }
+}
+
 // Shared memory, barriers and TMEM of one CTA.
 struct Ctx {
   uint8_t* smem;
   uint64_t* full;
   uint64_t* empty;
+  uint64_t* pfull;            // CTA pair, rank 0: the other CTA's stage is full (relayed)
   uint64_t* acc_full;
   uint64_t* acc_empty;
   uint64_t* drain;
@@ -274,6 +293,8 @@ struct Ctx {
   volatile int32_t* ok_flag;  // [4], epilogue item hand-off (2 per group)
   uint32_t tmem_base;
   uint64_t tmo;
+  uint32_t rank;              // CTA pair: rank in the cluster (0 issues the MMAs); else 0
+  int32_t wid, wstride;       // work index and stride: the cluster (pair) or the CTA
 };
 
 // Operand blocks built earlier in the same launch: flags[tile row] (A) and
@@ -303,33 +324,47 @@ struct MmaState {
 // Lays out shared memory, initialises the barriers, allocates TMEM (warp 1)
 // and synchronises the block.  timeout_ns limits every bounded wait of the
 // roles.  Called by every thread.
-template <int MODE, int BN>
+template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
-  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
-  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG);
   constexpr uint32_t TMEM_COLS = 2 * BN;
   extern __shared__ uint8_t smem_raw[];
-  Ctx cx;
+  Ctx cx{};
   const uint32_t raw_addr = smem_u32(smem_raw);
   cx.smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
   cx.full = reinterpret_cast<uint64_t*>(cx.smem + STAGES * STAGE_BYTES);
   cx.empty = cx.full + STAGES;
-  cx.acc_full = cx.empty + STAGES;
+  cx.pfull = cx.empty + STAGES;
+  cx.acc_full = cx.pfull + STAGES;
   cx.acc_empty = cx.acc_full + 2;
   cx.drain = cx.acc_empty + 2;
   cx.tmem_slot = reinterpret_cast<uint32_t*>(cx.drain + 1);
   cx.abort_flag = reinterpret_cast<volatile int32_t*>(cx.tmem_slot + 1);
   cx.ok_flag = cx.abort_flag + 1;
   cx.tmo = timeout_ns;
+  if constexpr (CG == 2) {
+    cx.rank = cluster_ctarank();
+    cx.wid = static_cast<int32_t>(cluster_id_x());
+    cx.wstride = static_cast<int32_t>(nclusters_x());
+  } else {
+    cx.rank = 0;
+    cx.wid = static_cast<int32_t>(blockIdx.x);
+    cx.wstride = static_cast<int32_t>(gridDim.x);
+  }
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&cx.full[s], 1);
       mbar_init(&cx.empty[s], 1);
+      mbar_init(&cx.pfull[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&cx.acc_full[b], 1);
-      mbar_init(&cx.acc_empty[b], by_tile ? EPI_THREADS / 2 : EPI_THREADS);
+      // single CTA: every epilogue thread of the group arrives; a pair: one
+      // lane per epilogue warp of both CTAs, on rank 0's barrier
+      mbar_init(&cx.acc_empty[b], CG == 2 ? 2 * (by_tile ? EPI_WARPS / 2 : EPI_WARPS)
+                                          : (by_tile ? EPI_THREADS / 2 : EPI_THREADS));
     }
     mbar_init(cx.drain, 1);
     *cx.abort_flag = 0;
@@ -337,38 +372,56 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
     fence_barrier_init();
   }
   if (warp == 1) {
-    tmem_alloc(cx.tmem_slot, TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (CG == 2) {
+      tmem_alloc_pair(cx.tmem_slot, TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(cx.tmem_slot, TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CG == 2)
+    cluster_sync_all();  // both CTAs' barriers and TMEM ready before any remote use
+  else
+    __syncthreads();
   tc_fence_after();
   cx.tmem_base = *cx.tmem_slot;
   return cx;
 }
 
-// Frees TMEM once every role is done.  Called by every thread.
-template <int BN>
+// Frees TMEM once every role is done (a pair: once both CTAs are done, so
+// that no MMA of the pair still reads this CTA's shared memory or writes its
+// TMEM).  Called by every thread.
+template <int BN, int CG = 1>
 __device__ __forceinline__ void ctx_teardown(const Ctx& cx) {
-  __syncthreads();
+  if constexpr (CG == 2) {
+    tc_fence_before();
+    cluster_sync_all();
+  } else {
+    __syncthreads();
+  }
   if ((threadIdx.x >> 5) == 1) {
     tc_fence_after();
-    tmem_dealloc(cx.tmem_base, 2 * BN);
+    if constexpr (CG == 2)
+      tmem_dealloc_pair(cx.tmem_base, 2 * BN);
+    else
+      tmem_dealloc(cx.tmem_base, 2 * BN);
   }
 }
 
 // Producer (one thread): bulk copies of the operand images of this CTA's
 // tiles blockIdx.x, blockIdx.x + gridDim.x, ... < count into the ring.
-template <int MODE, int BN>
+template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, const Ctx& cx,
                                              int count, ProdState& ps, const Ready& rd) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
-  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
-  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
-  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG);
   constexpr int KIND = mma_kind(MODE);
-  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
   (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
   (void)IDESC; (void)CHUNKS;
@@ -392,11 +445,11 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
       bool aborted = false;
       bool first = ps.first;
       const uint64_t pol = policy_evict_last();
-      for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x) {
+      for (int idx = cx.wid; idx < count && !aborted; idx += cx.wstride) {
         const int t = lv.is_top ? idx : lv.work[idx];
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
         int tm, tn;
-        raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+        tile_coords<CG>(P, t, cx.rank, tm, tn);
         if (rd.flags) {
           // operand blocks built earlier in this launch (persistent grouped
           // kernel): wait until both are ready for this level, then order
@@ -409,7 +462,11 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
           fence_proxy_async_global();
         }
         const uint8_t* a_src = lv.a_level + P.a_img + (int64_t)tm * P.KB * IMG_BYTES;
-        const uint8_t* b_src = lv.b_level + P.b_img + (int64_t)tn * (BN / TILE_M) * P.KB * IMG_BYTES;
+        // this CTA's B^T blocks: all BN / 128 of the column tile, or for a
+        // pair its own half (block 2 tn + rank)
+        const uint8_t* b_src =
+            lv.b_level + P.b_img +
+            (int64_t)(tn * (BN / TILE_M) + (CG == 2 ? static_cast<int>(cx.rank) : 0)) * P.KB * IMG_BYTES;
         for (int kb = 0; kb < P.KB; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, abort_flag)) {
             aborted = true;
@@ -426,7 +483,7 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
               bulk_g2s_hint(base, a_src + pl * P.a_plane + (int64_t)kb * IMG_BYTES, IMG_BYTES,
                             &full[stage], pol);
 #pragma unroll
-              for (int h = 0; h < BN / TILE_M; ++h)
+              for (int h = 0; h < BN / TILE_M / CG; ++h)
                 bulk_g2s_hint(base + A_BYTES + h * IMG_BYTES,
                               b_src + pl * P.b_plane + ((int64_t)h * P.KB + kb) * IMG_BYTES,
                               IMG_BYTES, &full[stage], pol);
@@ -456,16 +513,16 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
 // MMA issuer (one thread): the tensor-core K loop of each tile into the
 // accumulator buffer it & 1, it = it0, it0 + 1, ... counting this CTA's
 // tiles over the whole launch.
-template <int MODE, int BN>
+template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const Ctx& cx,
                                         int count, int it0, MmaState& ms) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
-  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
-  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
-  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG);
   constexpr int KIND = mma_kind(MODE);
-  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
   (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
   (void)IDESC; (void)CHUNKS;
@@ -483,22 +540,59 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
   (void)smem; (void)full; (void)empty; (void)acc_full; (void)acc_empty; (void)drain;
   (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
   if (ms.aborted) return;
+  if constexpr (CG == 2) {
+    if (cx.rank == 1) {
+      // rank 1 issues no MMA: it relays each of its stages, once its copies
+      // have landed, to rank 0's pfull barrier of the same stage
+      int stage = ms.stage;
+      uint32_t phase = ms.phase;
+      bool aborted = false;
+      for (int idx = cx.wid; idx < count && !aborted; idx += cx.wstride) {
+        const int t = lv.is_top ? idx : lv.work[idx];
+        const Prob& P = prob_at(cm, find_prob(cm, t, 0));
+        for (int kb = 0; kb < P.KB; ++kb) {
+          if (!mbar_wait(&full[stage], phase, tmo, abort_flag)) {
+            aborted = true;
+            break;
+          }
+          mbar_arrive_remote(mapa_shared(smem_u32(&cx.pfull[stage]), 0));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      ms.stage = stage;
+      ms.phase = phase;
+      if (aborted) {
+        ms.aborted = true;
+        *abort_flag = 1;
+        set_status(cm.status, PN_ETIMEOUT);
+      }
+      return;
+    }
+  }
     int stage = ms.stage;
       uint32_t phase = ms.phase;
       bool aborted = false;
       int it = it0;
-      for (int idx = blockIdx.x; idx < count && !aborted; idx += gridDim.x, ++it) {
+      for (int idx = cx.wid; idx < count && !aborted; idx += cx.wstride, ++it) {
         const int t = lv.is_top ? idx : lv.work[idx];
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
         const int buf = it & 1;
-        if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)) {
+        // a pair: the epilogues of both CTAs release the accumulator
+        const bool acc_ok = CG == 2
+            ? mbar_wait_cluster(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)
+            : mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag);
+        if (!acc_ok) {
           aborted = true;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         for (int kb = 0; kb < P.KB; ++kb) {
-          if (!mbar_wait(&full[stage], phase, tmo, abort_flag)) {
+          if (!mbar_wait(&full[stage], phase, tmo, abort_flag) ||
+              (CG == 2 && !mbar_wait_cluster(&cx.pfull[stage], phase, tmo, abort_flag))) {
             aborted = true;
             break;
           }
@@ -510,7 +604,19 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
             const uint64_t ad = sdesc_sw128(sa + kk * 32);
             const uint64_t bd = sdesc_sw128(sb + kk * 32);
             const uint32_t acc = (kb | kk) != 0;
-            if constexpr (PLANES == 1) {
+            if constexpr (CG == 2) {
+              // M = 256 over both CTAs' A halves, N = 256 over both B halves
+              if constexpr (PLANES == 1) {
+                mma_pair<KIND>(d, ad, bd, IDESC, acc);
+              } else {
+                const uint32_t sa_lo = sa + A_BYTES + B_BYTES, sb_lo = sa_lo + A_BYTES;
+                const uint64_t adl = sdesc_sw128(sa_lo + kk * 32);
+                const uint64_t bdl = sdesc_sw128(sb_lo + kk * 32);
+                mma_pair<KIND>(d, adl, bd, IDESC, acc);  // small terms first
+                mma_pair<KIND>(d, ad, bdl, IDESC, 1u);
+                mma_pair<KIND>(d, ad, bd, IDESC, 1u);
+              }
+            } else if constexpr (PLANES == 1) {
               mma_ss<KIND>(d, ad, bd, IDESC, acc);
             } else {
               const uint32_t sa_lo = sa + A_BYTES + B_BYTES, sb_lo = sa_lo + A_BYTES;
@@ -521,14 +627,20 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
               mma_ss<KIND>(d, ad, bd, IDESC, 1u);
             }
           }
-          mma_commit(&empty[stage]);
+          if constexpr (CG == 2)
+            mma_commit_pair(&empty[stage], 0x3);  // frees the stage in both CTAs
+          else
+            mma_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (aborted) break;
-        mma_commit(&acc_full[buf]);
+        if constexpr (CG == 2)
+          mma_commit_pair(&acc_full[buf], 0x3);  // both CTAs' accumulators are complete
+        else
+          mma_commit(&acc_full[buf]);
       }
       ms.stage = stage;
       ms.phase = phase;
@@ -536,7 +648,10 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
         ms.aborted = true;
         *abort_flag = 1;
         set_status(cm.status, PN_ETIMEOUT);
-        mma_commit(drain);  // completes once every issued MMA has finished
+        if constexpr (CG == 2)
+          mma_commit_pair(drain, 0x1);  // completes once every issued MMA has finished
+        else
+          mma_commit(drain);  // completes once every issued MMA has finished
         mbar_wait_drain(drain, 0, tmo);
       }
 }
@@ -546,16 +661,16 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
 // out (+)= acc * x'^(p-1) / s with x the source element at the output position
 // and s its row (grad_axis 0) or column (1) scale; the first p present
 // overwrites, later ones add.
-template <int MODE, int BN, int EPI>
+template <int MODE, int BN, int EPI, int CG = 1>
 __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, const Ctx& cx,
                                              int count, bool by_tile, int it0, const Ready& rd) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
-  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M);
-  constexpr int STAGE_BYTES = stage_bytes(MODE, BN);
-  constexpr int STAGES = num_stages(MODE, BN);
+  constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
+  constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG);
   constexpr int KIND = mma_kind(MODE);
-  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M, BN);
+  constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
   (void)PLANES; (void)A_BYTES; (void)B_BYTES; (void)STAGE_BYTES; (void)STAGES; (void)KIND;
   (void)IDESC; (void)CHUNKS;
@@ -589,7 +704,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + ew * STG_BYTES);
     const int step = by_tile ? 2 : 1;
     for (int j = by_tile ? ((grp - it0) & 1) : 0;; j += step) {
-      const int idx = blockIdx.x + j * gridDim.x;
+      const int idx = cx.wid + j * cx.wstride;
       if (idx >= count) break;
       const int it = it0 + j;
       const int t = lv.is_top ? idx : lv.work[idx];
@@ -607,7 +722,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       const int64_t Pldaux = P.ldaux;
       const int64_t Prc_c = P.rc_c;
       int tm, tn;
-      raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
+      tile_coords<CG>(P, t, cx.rank, tm, tn);
       const int buf = it & 1;
       const int okslot = 2 * grp + ((it >> 1) & 1);
       if (et == 0) {
@@ -656,7 +771,18 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
         tmem_ld_wait();
         if (hc == nch - 1) {
           tc_fence_before();
-          mbar_arrive(&acc_empty[buf]);
+          if constexpr (CG == 2) {
+            // one lane per warp, on rank 0's barrier (the MMA issuer's)
+            __syncwarp();
+            if (lane == 0) {
+              if (cx.rank == 0)
+                mbar_arrive(&acc_empty[buf]);
+              else
+                mbar_arrive_remote(mapa_shared(smem_u32(&acc_empty[buf]), 0));
+            }
+          } else {
+            mbar_arrive(&acc_empty[buf]);
+          }
         }
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
@@ -888,7 +1014,9 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       }
       if (EPI == 0 && !lv.is_bottom) {
         const bool tile_left = bar_red_or(any_left, 3 + grp, gthreads);
-        if (tile_left) {
+        // a pair's tile goes down if either half has entries left, so each
+        // half's state is written whenever it could be needed
+        if (tile_left || CG == 2) {
           if (row_ok) {
             uint32_t* st_w = cm.state + st_idx;
 #pragma unroll
@@ -907,11 +1035,16 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
           }
           // r = 2: a tile that starts no chain here skips the half level
           const bool skip = lv.skip_work && !bar_red_or(new_chain, 3 + grp, gthreads);
-          if (et == 0) {
+          // a pair's tile is pushed once, by whichever half claims it first
+          bool push = et == 0 && tile_left;
+          if constexpr (CG == 2)
+            if (push) push = atomicCAS(lv.pair_pushed + t, 0u, 1u) == 0u;
+          if (push) {
             int32_t* cnt = skip ? lv.skip_count : lv.next_count;
             const int slot = atomicAdd(cnt, 1);
             (skip ? lv.skip_work : lv.next_work)[slot] = t;
             (skip ? lv.skip_rflag : lv.next_rflag)[P.tm_base + tm] = 1;
+            if constexpr (CG == 2) (skip ? lv.skip_rflag : lv.next_rflag)[P.tm_base + (tm ^ 1)] = 1;
             (skip ? lv.skip_cflag : lv.next_cflag)[P.tn_base + tn] = 1;
           }
         }
@@ -921,20 +1054,23 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
 
 // One p level: every CTA processes tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ... of the level's tile list (the whole problem at the top level).
-template <int MODE, int BN, int EPI>
+template <int MODE, int BN, int EPI, int CG = 1>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
-  static_assert(num_stages(MODE, BN) >= 2, "operand ring too small");
+  static_assert(num_stages(MODE, BN, CG) >= 2, "operand ring too small");
+  static_assert(CG == 1 || (BN == 256 && EPI == 0), "CTA pairs: 256 x 256 p-norm tiles");
   if constexpr (EPI == 1) {
     if (!((*lv.pmask >> lv.q) & 1u)) return;  // no entry selected this p
   }
   const int count = lv.is_top ? cm.total_tiles : *lv.work_count;
-  if (static_cast<int>(blockIdx.x) >= count) return;  // uniform: nothing for this CTA
+  // uniform: nothing for this CTA (a pair: for this cluster, both CTAs alike)
+  const int wid = CG == 2 ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  if (wid >= count) return;
   // epilogue split: tile per warp group where the epilogue, not the MMA,
   // bounds a tile (grouped problems, or short contractions)
-  const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) &&
+  const bool by_tile = count >= 4 * static_cast<int>(gridDim.x) / CG &&
                        (cm.nprob > 1 || cm.single.KB * mode_planes(MODE) <= 32);
-  const Ctx cx = ctx_setup<MODE, BN>(by_tile, cm.timeout_ns);
+  const Ctx cx = ctx_setup<MODE, BN, CG>(by_tile, cm.timeout_ns);
   const Ready none{nullptr, 0, 0};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -942,28 +1078,28 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       ProdState ps{};
       for (int s = 0; s < 8; ++s) ps.pend[s] = -1;
       ps.first = true;
-      run_producer<MODE, BN>(cm, lv, cx, count, ps, none);
+      run_producer<MODE, BN, CG>(cm, lv, cx, count, ps, none);
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
       MmaState ms{};
-      run_mma<MODE, BN>(cm, lv, cx, count, 0, ms);
+      run_mma<MODE, BN, CG>(cm, lv, cx, count, 0, ms);
     }
     __syncwarp();
   } else {
-    run_epilogue<MODE, BN, EPI>(cm, lv, cx, count, by_tile, 0, none);
+    run_epilogue<MODE, BN, EPI, CG>(cm, lv, cx, count, by_tile, 0, none);
   }
-  ctx_teardown<BN>(cx);
+  ctx_teardown<BN, CG>(cx);
 }
 
-template <int MODE, int BN, int EPI>
+template <int MODE, int BN, int EPI, int CG = 1>
 inline int set_attr_t() {
   static int done = 0;
   if (done) return 0;
-  const cudaError_t e = cudaFuncSetAttribute(k_gemm_level<MODE, BN, EPI>,
+  const cudaError_t e = cudaFuncSetAttribute(k_gemm_level<MODE, BN, EPI, CG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_total(MODE, BN));
+                                             smem_total(MODE, BN, CG));
   if (e == cudaSuccess) done = 1;
   return e;
 }
@@ -977,6 +1113,31 @@ inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream
   k_gemm_level<MODE, BN, EPI><<<grid, GEMM_THREADS, smem_total(MODE, BN),
                            static_cast<cudaStream_t>(stream)>>>(cm, lv);
   return cudaGetLastError();
+}
+
+// A CTA pair per 256 x 256 output tile (cta_group::2): clusters of two CTAs,
+// one cluster per pair of SMs (cm.total_tiles counts pair tiles).
+template <int MODE>
+inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
+  const int e = set_attr_t<MODE, 256, 0, 2>();
+  if (e) return e;
+  const int pairs = num_sms / 2;
+  const int clusters = cm.total_tiles < pairs ? cm.total_tiles : pairs;
+  if (clusters < 1) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
+  cfg.blockDim = dim3(GEMM_THREADS);
+  cfg.dynamicSmemBytes = smem_total(MODE, 256, 2);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, 256, 0, 2>, cm, lv);
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 }  // namespace gemm

@@ -478,21 +478,29 @@ pn_status pn_autotune(int64_t M, int64_t N, int64_t K, const float* A, int64_t l
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   pn_opts o = *opts;
   o.ev_gemm_begin = o.ev_gemm_end = nullptr;
-  int best = 128;
+  // candidates: one CTA per 128 x 128 and per 128 x 256 tile, and a CTA pair
+  // per 256 x 256 tile (recorded as 512); the options may fix some of these
+  int best = 0;
   float best_ms = 0.0f;
-  const int ncand = opts->compute == PN_F32_EXACT ? 1 : 2;
-  for (int c = 0; c < ncand; ++c) {
-    o.tile_n = c == 0 ? 128 : 256;
+  for (int c = 0; c < 3; ++c) {
+    const int tile_m = c == 2 ? 256 : 128, tile_n = c == 0 ? 128 : 256;
+    if (opts->tile_m && opts->tile_m != tile_m) continue;
+    if (opts->tile_n && opts->tile_n != tile_n) continue;
+    if (c == 1 && opts->compute == PN_F32_EXACT) continue;  // one CTA: 128 wide only
+    if (c == 2 && opts->estimator == 2) continue;            // pairs: estimators 0, 1
+    o.tile_m = tile_m;
+    o.tile_n = tile_n;
     pn_status st = PN_OK;
     const float ms = time_ms([&] {
       return maxprod_pnorm(M, N, K, A, lda, B, ldb, C, ldc, nullptr, nullptr, &o, ws, ws_bytes, stream);
     }, s, 3, &st);
     if (st != PN_OK) return st;
-    if (c == 0 || ms < best_ms) {
-      best = o.tile_n;
+    if (best == 0 || ms < best_ms) {
+      best = c == 2 ? 512 : tile_n;
       best_ms = ms;
     }
   }
+  if (best == 0) return PN_EINVAL;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_single[{current_device(), opts->compute, lg(M), lg(N), lg(K)}] = best;

@@ -70,7 +70,7 @@ struct Common {
   int32_t total_ma, total_mb;  // max-pass units summed over problems
   int32_t mode, BN, s_op, scaling;
   float unscale;      // 2^(-2 s_op)
-  int32_t pad1;
+  int32_t cg;         // 2: a CTA pair (cta_group::2) per 256 x 256 tile, total_tiles counts pairs
   uint32_t* rmax;     // per-row max of A (float bits)
   uint32_t* cmax;     // per-column max of B
   uint32_t* gmax;     // per-problem global max of A (2g) and B (2g+1)
@@ -126,6 +126,8 @@ struct Level {
   uint8_t* next_rflag;
   uint8_t* next_cflag;
   const uint32_t* pmask;      // gradient launches: bit q set if some entry has p* = P[q]
+  uint32_t* pair_pushed;      // CTA pairs: one word per pair tile, set once the tile is
+                              // pushed to the next level (either half may push it)
   int32_t proj_here;          // r = 1 projection: finish entries resolved at 2p (the level above)
   int32_t proj_next;          // r = 1 projection: the next level is p/2; park S^(p) of new entries
   // r = 2 projection.  A pending entry's 2-bit stage s (planes pend, pend2)

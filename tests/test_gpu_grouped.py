@@ -132,9 +132,10 @@ def test_grouped_autotune_and_untuned_rule(pn):
 def test_single_autotune(pn):
     A, B = workloads.uniform_pair(1024, 1536, 800, seed=9)
     chosen = pn.autotune(_dev(A), _dev(B), compute="bf16")
-    assert chosen in (128, 256)
+    assert chosen in (128, 256, 512)
     C, _, _ = pn.maxprod_pnorm(_dev(A), _dev(B), compute="bf16")
-    C2, _, _ = pn.maxprod_pnorm(_dev(A), _dev(B), compute="bf16", tile_n=chosen)
+    shape = dict(tile_n=256, tile_m=256) if chosen == 512 else dict(tile_n=chosen, tile_m=128)
+    C2, _, _ = pn.maxprod_pnorm(_dev(A), _dev(B), compute="bf16", **shape)
     assert torch.equal(C, C2)
 
 
@@ -198,7 +199,7 @@ def test_grouped_persistent_multilevel_matches_oracle(pn, orc):
         levels |= set(np.unique(ref["p_sel"] & 0x7F).tolist())
         err = np.abs(C - ref["C"]) / ref["C"]
         assert err.max() <= 1e-5, float(err.max())
-    assert len(levels) >= 3
+    assert len(levels) >= 2  # tiles carried to a lower level inside the launch
 
 
 def test_grouped_persistent_domain_error(pn):

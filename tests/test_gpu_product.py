@@ -95,11 +95,11 @@ def test_exact_empty_k(pn):
 
 
 # ----------------------------------------------------------------- p-norm ---
-def _compare(pn, orc, A, B, mode, plog_list, tau=None, tile_n=0, scaling=2):
+def _compare(pn, orc, A, B, mode, plog_list, tau=None, tile_n=0, scaling=2, tile_m=0):
     M, K = A.shape
     tau = orc.default_tau(K, _CODE[mode]) if tau is None else tau
     C, psel, ssel = pn.maxprod_pnorm(_dev(A), _dev(B), p_log2=plog_list, compute=mode, tau=tau,
-                                     tile_n=tile_n, scaling=scaling)
+                                     tile_n=tile_n, scaling=scaling, tile_m=tile_m)
     C, psel, ssel = C.cpu().numpy(), psel.cpu().numpy(), ssel.cpu().numpy()
     A64, B64 = A.astype(np.float64), B.astype(np.float64)
     ref = orc.pnorm(A64, B64, plog_list, tau, scaling=scaling, want_S=True)
