@@ -48,6 +48,8 @@ def parse_args():
                     help="contraction length of the default product (0: n); M = N = n")
     ap.add_argument("--compute", default="bf16")
     ap.add_argument("--tile-n", type=int, default=0)
+    ap.add_argument("--tile-m", type=int, default=0,
+                    help="0 automatic, 128 one CTA per tile, 256 a CTA pair per 256 x 256 tile")
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--err-samples", type=int, default=4096)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -411,8 +413,8 @@ def run_ours(args):
 
     def step(ev0=None, ev1=None):
         return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute=args.compute, tile_n=args.tile_n,
-                                out=C, want_ssel=False, check=False, ev_begin=ev0, ev_end=ev1,
-                                **corr)
+                                tile_m=args.tile_m, out=C, want_ssel=False, check=False,
+                                ev_begin=ev0, ev_end=ev1, **corr)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -510,8 +512,8 @@ def run_ours(args):
 
         def step8(ev0=None, ev1=None):
             return pn.maxprod_pnorm(A, B, p_log2=P_LOG2, compute="e4m3", tile_n=args.tile_n,
-                                    out=C8, want_ssel=False, check=False, ev_begin=ev0,
-                                    ev_end=ev1)
+                                    tile_m=args.tile_m, out=C8, want_ssel=False, check=False,
+                                    ev_begin=ev0, ev_end=ev1)
         for _ in range(max(args.warmup, 3)):
             step8()
         K8 = max(1, min(K, 20))
@@ -575,7 +577,8 @@ def run_ours(args):
         torch, [A_h, B_h, np.zeros((n, n), dtype=np.float32)])
     del C
     torch.cuda.empty_cache()
-    pipe = HostPipeline(n, n, Kc, compute=args.compute, tile_n=args.tile_n, p_log2=P_LOG2,
+    pipe = HostPipeline(n, n, Kc, compute=args.compute, tile_n=args.tile_n, tile_m=args.tile_m,
+                        p_log2=P_LOG2,
                         **corr)
     KE = max(1, args.e2e_steps)
     pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up

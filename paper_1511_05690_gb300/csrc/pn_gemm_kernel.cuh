@@ -274,7 +274,7 @@ __device__ __forceinline__ void tile_coords(const Prob& P, int t, uint32_t rank,
     raster(t - P.tile_base, P.tiles_m, P.tiles_n, tm, tn);
   } else {
     int TM;
-    raster(t - P.tile_base, (P.tiles_m + 1) >> 1, P.tiles_n, TM, tn);
+    raster(t - P.tile_base, (P.tiles_m + 1) >> 1, P.tiles_n, TM, tn, RASTER_GM / 2);
     tm = 2 * TM + static_cast<int>(rank);
   }
 }
@@ -1121,11 +1121,7 @@ template <int MODE>
 inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
   const int e = set_attr_t<MODE, 256, 0, 2>();
   if (e) return e;
-  const int pairs = num_sms / 2;
-  const int clusters = cm.total_tiles < pairs ? cm.total_tiles : pairs;
-  if (clusters < 1) return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
   cfg.blockDim = dim3(GEMM_THREADS);
   cfg.dynamicSmemBytes = smem_total(MODE, 256, 2);
   cfg.stream = static_cast<cudaStream_t>(stream);
@@ -1136,6 +1132,30 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  // A pair needs two SMs of one GPC; with an odd number of SMs in a GPC fewer
+  // than num_sms / 2 pairs fit at once.  The tile walk is persistent (each
+  // pair strides over the tiles), so a pair that is not resident would start
+  // its whole share after the others end: launch only resident pairs.
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static int resident[64] = {0};
+  int pairs = num_sms / 2;
+  if (dev >= 0 && dev < 64) {
+    if (resident[dev] == 0) {
+      cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs));
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_gemm_level<MODE, 256, 0, 2>, &cfg) != cudaSuccess ||
+          n < 1) {
+        cudaGetLastError();
+        n = pairs;
+      }
+      resident[dev] = n;
+    }
+    if (resident[dev] < pairs) pairs = resident[dev];
+  }
+  const int clusters = cm.total_tiles < pairs ? cm.total_tiles : pairs;
+  if (clusters < 1) return 0;
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
   const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, 256, 0, 2>, cm, lv);
   return le != cudaSuccess ? le : cudaGetLastError();
 }

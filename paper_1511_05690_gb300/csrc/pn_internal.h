@@ -216,12 +216,15 @@ __host__ __device__ inline int find_prob(const Common& cm, int id, int which) {
   return cm.lut[which][id];
 }
 
-// Local tile index -> (tile row, tile column), grouped raster order.
-__host__ __device__ inline void raster(int lt, int tiles_m, int tiles_n, int& tm, int& tn) {
-  const int group = RASTER_GM * tiles_n;
+// Local tile index -> (tile row, tile column), grouped raster order: groups
+// of `group_m` tile rows (RASTER_GM for 128-row tiles; a CTA pair's 256-row
+// tiles use half as many, so that a group covers the same rows of A).
+__host__ __device__ inline void raster(int lt, int tiles_m, int tiles_n, int& tm, int& tn,
+                                       int group_m = RASTER_GM) {
+  const int group = group_m * tiles_n;
   const int g = lt / group;
-  const int first_m = g * RASTER_GM;
-  const int gm = (tiles_m - first_m) < RASTER_GM ? (tiles_m - first_m) : RASTER_GM;
+  const int first_m = g * group_m;
+  const int gm = (tiles_m - first_m) < group_m ? (tiles_m - first_m) : group_m;
   const int local = lt - g * group;
   tm = first_m + local % gm;
   tn = local / gm;

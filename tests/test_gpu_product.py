@@ -265,7 +265,7 @@ def test_pnorm_domain_values(pn, shape, where):
 def test_pnorm_host_errors(pn):
     import ctypes
     L = pn.lib()
-    o = pn.make_opts(tile_n=256)  # a fixed width: the size query is then exact
+    o = pn.make_opts(tile_n=256, tile_m=128)  # a fixed tile shape: the size query is then exact
     A = torch.rand(64, 64, device="cuda")
     C = torch.empty(64, 64, device="cuda")
     need = L.pn_workspace_size(64, 64, 64, ctypes.byref(o))
