@@ -109,7 +109,10 @@ typedef struct pn_opts {
    * (PN_ETIMEOUT).  Bit 1: the tensor-copy image kernel announces its first
    * tile's bytes without copying them, with the same effect.  Bit 2: the
    * grouped call runs one launch sequence per p level instead of its single
-   * persistent launch (same results; for comparing the two). */
+   * persistent launch (same results; for comparing the two).  Bit 3: the
+   * persistent grouped launch also builds the top level's operand images
+   * itself instead of taking them from the image kernels launched before it
+   * (same results). */
   int32_t debug_flags;
   /* Estimate of max_k u_k from the p-sums (Sec. 2.1):
    *   0 (default) = plain, (S^(p*))^(1/p*), an overestimate by at most

@@ -1,7 +1,10 @@
 // Grouped products and the tile-width autotuner.
 //
-// Grouped: many independent (x,max) products in one launch per p level (the
-// problems and the p rings parallelise coarsely, Sec. 4).  Every kernel of the
+// Grouped: many independent (x,max) products evaluated together (the problems
+// and the p rings parallelise coarsely, Sec. 4): the maxima and the top
+// level's operand images in two image kernels, then every level of every
+// problem in one persistent tensor-core launch (pn_grouped_kernel.cuh); the
+// global scale of scaling 1 keeps one launch sequence per level.  Every kernel of the
 // product works on global ids (operand tile, output tile, tile row / column,
 // max-pass unit); a group is a table of Prob records with running offsets
 // into one shared workspace, plus id -> problem lookup tables so that a kernel
@@ -354,10 +357,17 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   gr.n_slots = o->n_p;
   gr.n_a = L.total_tm;
   gr.n_b = L.total_tn;
-  gr.maxima = 1;
   gr.ready = reinterpret_cast<int32_t*>(ws + L.off_ready);
   gr.level_done = reinterpret_cast<int32_t*>(ws + L.off_ldone);
-  if (!persist && launch_maxes(cm, stream)) return PN_ECUDA;
+  // The image kernels run at several CTAs per SM and keep far more loads in
+  // flight than the persistent kernel's eight builder warps per SM, so the
+  // maxima and the top level's images (every block) are written before the
+  // persistent launch; it builds only the pushed blocks of the lower levels.
+  // debug_flags bit 3 builds the top level inside the persistent kernel too.
+  const bool top_inside = persist && (o->debug_flags & 8);
+  gr.maxima = top_inside ? 1 : 0;
+  gr.top_built = top_inside ? 0 : 1;
+  if (!top_inside && launch_maxes(cm, stream)) return PN_ECUDA;
   for (int q = o->n_p - 1; q >= 0; --q) {
     const int qn = q > 0 ? q - 1 : 0;
     Level lv;
@@ -379,6 +389,10 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     set_projection(lv, o, q);
     if (persist) {
       gr.lv[o->n_p - 1 - q] = lv;
+      if (lv.is_top && !top_inside) {
+        if (launch_power_a(cm, lv, stream)) return PN_ECUDA;
+        if (launch_power_b(cm, lv, stream)) return PN_ECUDA;
+      }
       continue;
     }
     if (launch_power_a(cm, lv, stream)) return PN_ECUDA;

@@ -5,11 +5,13 @@
 // One CTA per SM (cooperative launch, so every CTA is resident), 10 warps.
 // For each slot of the level schedule (largest p first):
 //   1. operand blocks -- warps 2-9 build the powered images of the blocks
-//      this level needs: at the top level every A row block and B column
-//      block of every problem, reading the block once for its row / column
-//      maxima (domain test, power-of-two scales) and once more, from L2, for
-//      the images; below it only the blocks of pushed tiles.  Each block is
-//      published with a release store of its ready flag (slot + 1).
+//      this level needs: below the top level only the blocks of pushed
+//      tiles.  The top level's images (every block of every problem) are
+//      either written before the launch by the high-occupancy image kernels
+//      (top_built), or built here, reading each block once for its row /
+//      column maxima (domain test, power-of-two scales) and once more, from
+//      L2, for the images.  Each block is published with a release store of
+//      its ready flag (slot + 1).
 //   2. tiles -- the tensor-core roles of the level kernel (copy producer,
 //      MMA issuer, two epilogue groups) over the slot's tiles; the producer
 //      waits, bounded, for a tile's two ready flags before copying its
@@ -62,7 +64,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       if (count == 0 || *cx.abort_flag) break;  // uniform
     }
     // ---------------------------------------------------- operand blocks ---
-    if (warp >= 2) {
+    const bool built = t == 0 && gr.top_built;
+    if (warp >= 2 && !built) {
       const int ti = threadIdx.x - 64;
       float* stile = reinterpret_cast<float*>(cx.smem);  // the ring is idle between slots
       uint32_t* red = reinterpret_cast<uint32_t*>(cx.smem + mode_bk(MODE) * 129 * 4);
@@ -97,7 +100,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     __syncthreads();
     // ------------------------------------------------------------- tiles ---
-    const Ready rd{gr.ready, t + 1, gr.n_a};
+    const Ready rd{built ? nullptr : gr.ready, t + 1, gr.n_a};
     if (warp == 0) {
       if (lane == 0) run_producer<MODE, BN>(cm, lv, cx, count, ps, rd);
       __syncwarp();

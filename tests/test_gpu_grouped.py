@@ -165,7 +165,8 @@ def _multilevel_problems(seed, count=12):
                           ("tf32", 256, 0, 0), ("f16", 128, 0, 0), ("e4m3", 256, 0, 0),
                           ("bf16", 256, 1, 0), ("f32", 128, 0, 1)])
 def test_grouped_persistent_equals_level_launches(pn, mode, tile_n, estimator, correction):
-    """The single persistent launch and the per-level launch sequence run the
+    """The single persistent launch (top-level images written before it, or
+    by its own block builders) and the per-level launch sequence run the
     same arithmetic: bit-identical results, here with entries resolving at
     several levels (work lists carried between levels inside the launch), the
     r = 1 projection and the K^(1/p*) correction."""
@@ -175,11 +176,14 @@ def test_grouped_persistent_equals_level_launches(pn, mode, tile_n, estimator, c
     kw = dict(compute=mode, tile_n=tile_n, estimator=estimator, correction=correction)
     tau = 1.0 if mode == "f16" else None  # FP16 operands: a tau the data clears at low p
     persist = pn.GroupedProduct(As, Bs, tau=tau, **kw)
+    inside = pn.GroupedProduct(As, Bs, tau=tau, debug_flags=8, **kw)
     levels = pn.GroupedProduct(As, Bs, tau=tau, debug_flags=4, **kw)
     C1 = persist.run(check=True)
     C2 = levels.run(check=True)
-    for a, c1, c2 in zip(As, C1, C2):
+    C3 = inside.run(check=True)
+    for a, c1, c2, c3 in zip(As, C1, C2, C3):
         assert torch.equal(c1, c2), (tuple(a.shape), mode)
+        assert torch.equal(c3, c2), (tuple(a.shape), mode)
     # several levels took part
     C, psel, _ = pn.maxprod_pnorm(As[0], Bs[0], compute=mode, tile_n=tile_n, tau=tau)
     assert len(torch.unique(psel & 0x7F)) >= 2
@@ -202,22 +206,24 @@ def test_grouped_persistent_multilevel_matches_oracle(pn, orc):
     assert len(levels) >= 2  # tiles carried to a lower level inside the launch
 
 
-def test_grouped_persistent_domain_error(pn):
-    """A negative value in one problem of the group raises PN_EDOMAIN from the
-    block builders of the persistent launch, and the context stays usable."""
+@pytest.mark.parametrize("flags", [0, 8])
+def test_grouped_persistent_domain_error(pn, flags):
+    """A negative value in one problem of the group raises PN_EDOMAIN (from
+    the maxima kernel, or with flag 8 from the block builders of the
+    persistent launch), and the context stays usable."""
     probs = _problems(850, count=10)
     As = [_dev(a) for a, _ in probs]
     Bs = [_dev(b) for _, b in probs]
     As[3][2, 1] = -1.0
-    plan = pn.GroupedProduct(As, Bs, compute="bf16")
+    plan = pn.GroupedProduct(As, Bs, compute="bf16", debug_flags=flags)
     with pytest.raises(pn.PnError) as ei:
         plan.run(check=True)
     assert ei.value.status == 4
     As[3][2, 1] = 0.5
     Bs[5][0, 0] = float("nan")
-    plan = pn.GroupedProduct(As, Bs, compute="bf16")
+    plan = pn.GroupedProduct(As, Bs, compute="bf16", debug_flags=flags)
     with pytest.raises(pn.PnError) as ei:
         plan.run(check=True)
     assert ei.value.status == 4
     Bs[5][0, 0] = 0.5
-    pn.GroupedProduct(As, Bs, compute="bf16").run(check=True)
+    pn.GroupedProduct(As, Bs, compute="bf16", debug_flags=flags).run(check=True)
