@@ -286,34 +286,26 @@ __device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
 }
-// Arrive on an mbarrier of another CTA of the cluster (release at cluster scope).
-__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
-               : "memory");
+// Arrive on an mbarrier of the other CTA of a pair (the default release
+// semantics at CTA scope).  The pair's arrivals only report that this CTA's
+// tcgen05 loads of an accumulator have completed (tcgen05.wait::ld, then the
+// thread-sync fence), so no data is published through them and no fence at
+// cluster scope is needed (issued per operand stage, such fences measured at
+// half the pair's MMA rate).
+__device__ __forceinline__ void mbar_arrive_peer(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
-__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
+// 2-D tensor copy global -> this CTA's shared memory for a CTA pair
+// (cta_group::2): the completion is counted on `bar_cluster`, an mbarrier of
+// either CTA of the pair (the pair's operand stages all complete on rank 0's
+// barrier, which the MMA issuer waits on).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst_smem, const void* map, int x, int y,
+                                                 uint32_t bar_cluster, uint64_t policy) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      ".L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst_smem),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster), "l"(policy)
       : "memory");
-  return ok != 0;
-}
-// mbar_wait for barriers that receive arrivals from the other CTA of a pair.
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity,
-                                                  uint64_t timeout_ns, volatile int32_t* abort) {
-  if (mbar_try_wait_cluster(bar, parity)) return true;
-  const uint64_t t0 = globaltimer_ns();
-  while (true) {
-#pragma unroll 1
-    for (int i = 0; i < 32; ++i)
-      if (mbar_try_wait_cluster(bar, parity)) return true;
-    if (*abort) return false;
-    if (globaltimer_ns() - t0 > timeout_ns) return false;
-  }
 }
 // Every thread of both CTAs: release / acquire at cluster scope.
 __device__ __forceinline__ void cluster_sync_all() {

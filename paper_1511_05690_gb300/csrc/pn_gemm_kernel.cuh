@@ -2,6 +2,7 @@
 // operand format in pn_gemm_*.cu).  See pn_gemm.cu for the design notes.
 #pragma once
 #include <cfloat>
+#include <type_traits>
 
 #include "pn_device.cuh"
 
@@ -284,7 +285,6 @@ struct Ctx {
   uint8_t* smem;
   uint64_t* full;
   uint64_t* empty;
-  uint64_t* pfull;            // CTA pair, rank 0: the other CTA's stage is full (relayed)
   uint64_t* acc_full;
   uint64_t* acc_empty;
   uint64_t* drain;
@@ -335,8 +335,7 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   cx.smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
   cx.full = reinterpret_cast<uint64_t*>(cx.smem + STAGES * STAGE_BYTES);
   cx.empty = cx.full + STAGES;
-  cx.pfull = cx.empty + STAGES;
-  cx.acc_full = cx.pfull + STAGES;
+  cx.acc_full = cx.empty + STAGES;
   cx.acc_empty = cx.acc_full + 2;
   cx.drain = cx.acc_empty + 2;
   cx.tmem_slot = reinterpret_cast<uint32_t*>(cx.drain + 1);
@@ -355,9 +354,9 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   const int warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
+      // a pair: rank 0's full barrier counts both CTAs' copies (rank 1's stay unused)
       mbar_init(&cx.full[s], 1);
       mbar_init(&cx.empty[s], 1);
-      mbar_init(&cx.pfull[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&cx.acc_full[b], 1);
@@ -414,7 +413,8 @@ __device__ __forceinline__ void ctx_teardown(const Ctx& cx) {
 // tiles blockIdx.x, blockIdx.x + gridDim.x, ... < count into the ring.
 template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, const Ctx& cx,
-                                             int count, ProdState& ps, const Ready& rd) {
+                                             int count, ProdState& ps, const Ready& rd,
+                                             const ImgMaps* maps = nullptr) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
   constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
@@ -474,7 +474,31 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
           }
           pend[stage] = -1;
           const bool drop = (cm.debug_flags & 1) && first && kb == 0;
-          if (!drop) {
+          if constexpr (CG == 2) {
+            // a pair: both CTAs copy their own halves into their own ring,
+            // completing on rank 0's full barrier, which rank 0 arms with the
+            // bytes of both (rank 1's copies may land before it is armed: the
+            // transaction count goes below zero until then).  Rank 1 may
+            // only refill a stage after rank 0's MMAs freed it, so its copies
+            // always count toward the phase rank 0 waits for next.
+            if (!drop) {
+              const uint32_t fb = cx.rank == 0 ? smem_u32(&full[stage])
+                                               : mapa_shared(smem_u32(&full[stage]), 0);
+              if (cx.rank == 0) mbar_arrive_expect_tx(&full[stage], 2 * STAGE_BYTES);
+              const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+#pragma unroll
+              for (int pl = 0; pl < PLANES; ++pl) {
+                const uint32_t base = sa + pl * (A_BYTES + B_BYTES);
+                const int64_t ya = (pl * P.a_plane + ((int64_t)tm * P.KB + kb) * IMG_BYTES) >> 7;
+                const int64_t yb =
+                    (pl * P.b_plane + ((int64_t)(2 * tn + static_cast<int>(cx.rank)) * P.KB + kb) *
+                                          IMG_BYTES) >> 7;
+                tma_load_2d_pair(base, &maps->a, 0, static_cast<int>(ya), fb, pol);
+                tma_load_2d_pair(base + A_BYTES, &maps->b, 0, static_cast<int>(yb), fb, pol);
+              }
+              pend[stage] = static_cast<int8_t>(phase);
+            }
+          } else if (!drop) {
             mbar_arrive_expect_tx(&full[stage], STAGE_BYTES);
             const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
 #pragma unroll
@@ -505,8 +529,19 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
         *abort_flag = 1;
         set_status(cm.status, PN_ETIMEOUT);
         // let every copy still in flight land before the CTA exits
-        for (int s = 0; s < STAGES; ++s)
-          if (pend[s] >= 0) mbar_wait_drain(&full[s], static_cast<uint32_t>(pend[s]), tmo);
+        if (CG == 2 && cx.rank == 1) {
+          // its copies complete on rank 0's barriers: a bounded grace period
+          // (a 16 KB copy lands within microseconds)
+          bool any = false;
+          for (int s = 0; s < STAGES; ++s) any |= pend[s] >= 0;
+          if (any) {
+            const uint64_t t0 = globaltimer_ns();
+            while (globaltimer_ns() - t0 < 200000ull) __nanosleep(1000);
+          }
+        } else {
+          for (int s = 0; s < STAGES; ++s)
+            if (pend[s] >= 0) mbar_wait_drain(&full[s], static_cast<uint32_t>(pend[s]), tmo);
+        }
       }
 }
 
@@ -541,36 +576,7 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
   (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
   if (ms.aborted) return;
   if constexpr (CG == 2) {
-    if (cx.rank == 1) {
-      // rank 1 issues no MMA: it relays each of its stages, once its copies
-      // have landed, to rank 0's pfull barrier of the same stage
-      int stage = ms.stage;
-      uint32_t phase = ms.phase;
-      bool aborted = false;
-      for (int idx = cx.wid; idx < count && !aborted; idx += cx.wstride) {
-        const int t = lv.is_top ? idx : lv.work[idx];
-        const Prob& P = prob_at(cm, find_prob(cm, t, 0));
-        for (int kb = 0; kb < P.KB; ++kb) {
-          if (!mbar_wait(&full[stage], phase, tmo, abort_flag)) {
-            aborted = true;
-            break;
-          }
-          mbar_arrive_remote(mapa_shared(smem_u32(&cx.pfull[stage]), 0));
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
-        }
-      }
-      ms.stage = stage;
-      ms.phase = phase;
-      if (aborted) {
-        ms.aborted = true;
-        *abort_flag = 1;
-        set_status(cm.status, PN_ETIMEOUT);
-      }
-      return;
-    }
+    if (cx.rank == 1) return;  // rank 0 issues the pair's MMAs
   }
     int stage = ms.stage;
       uint32_t phase = ms.phase;
@@ -581,18 +587,15 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
         const int buf = it & 1;
         // a pair: the epilogues of both CTAs release the accumulator
-        const bool acc_ok = CG == 2
-            ? mbar_wait_cluster(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)
-            : mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag);
-        if (!acc_ok) {
+        if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)) {
           aborted = true;
           break;
         }
         tc_fence_after();
         const uint32_t d = tmem_base + buf * BN;
         for (int kb = 0; kb < P.KB; ++kb) {
-          if (!mbar_wait(&full[stage], phase, tmo, abort_flag) ||
-              (CG == 2 && !mbar_wait_cluster(&cx.pfull[stage], phase, tmo, abort_flag))) {
+          // a pair: rank 0's barrier completes once both CTAs' copies landed
+          if (!mbar_wait(&full[stage], phase, tmo, abort_flag)) {
             aborted = true;
             break;
           }
@@ -778,7 +781,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
               if (cx.rank == 0)
                 mbar_arrive(&acc_empty[buf]);
               else
-                mbar_arrive_remote(mapa_shared(smem_u32(&acc_empty[buf]), 0));
+                mbar_arrive_peer(mapa_shared(smem_u32(&acc_empty[buf]), 0));
             }
           } else {
             mbar_arrive(&acc_empty[buf]);
@@ -1054,9 +1057,13 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
 
 // One p level: every CTA processes tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ... of the level's tile list (the whole problem at the top level).
+template <int CG>
+using MapsArg = typename std::conditional<CG == 2, ImgMaps, NoMaps>::type;
+
 template <int MODE, int BN, int EPI, int CG = 1>
 __global__ void __launch_bounds__(GEMM_THREADS, 1)
-    k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+    k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
+                 const __grid_constant__ MapsArg<CG> maps) {
   static_assert(num_stages(MODE, BN, CG) >= 2, "operand ring too small");
   static_assert(CG == 1 || (BN == 256 && EPI == 0), "CTA pairs: 256 x 256 p-norm tiles");
   if constexpr (EPI == 1) {
@@ -1078,7 +1085,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
       ProdState ps{};
       for (int s = 0; s < 8; ++s) ps.pend[s] = -1;
       ps.first = true;
-      run_producer<MODE, BN, CG>(cm, lv, cx, count, ps, none);
+      if constexpr (CG == 2)
+        run_producer<MODE, BN, CG>(cm, lv, cx, count, ps, none, &maps);
+      else
+        run_producer<MODE, BN, CG>(cm, lv, cx, count, ps, none);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -1111,7 +1121,7 @@ inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream
   int grid = cm.total_tiles < num_sms ? cm.total_tiles : num_sms;
   if (grid < 1) return 0;
   k_gemm_level<MODE, BN, EPI><<<grid, GEMM_THREADS, smem_total(MODE, BN),
-                           static_cast<cudaStream_t>(stream)>>>(cm, lv);
+                           static_cast<cudaStream_t>(stream)>>>(cm, lv, NoMaps{});
   return cudaGetLastError();
 }
 
@@ -1156,7 +1166,16 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
   const int clusters = cm.total_tiles < pairs ? cm.total_tiles : pairs;
   if (clusters < 1) return 0;
   cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
-  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, 256, 0, 2>, cm, lv);
+  // the operand-image regions as tensors of 128-byte rows (the pair's copies
+  // complete on rank 0's barriers, which only tensor copies can address)
+  ImgMaps maps;
+  const Prob& P = cm.single;
+  constexpr int PL = mode_planes(MODE);
+  if (cm.nprob != 1 ||
+      !encode_img_rows(maps.a, lv.a_level + P.a_img, P.a_plane * PL) ||
+      !encode_img_rows(maps.b, lv.b_level + P.b_img, P.b_plane * PL))
+    return cudaErrorNotSupported;
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, 256, 0, 2>, cm, lv, maps);
   return le != cudaSuccess ? le : cudaGetLastError();
 }
 

@@ -260,9 +260,23 @@ struct OperandMaps {
   TensorMapBytes a, b;
   int32_t has_a, has_b;
 };
+// Tensor maps over the A and B operand-image regions of a CTA-pair launch:
+// each region as rows of 128 bytes (one image block = 128 rows), copied
+// unswizzled (the blocks are stored in their shared-memory layout).
+struct ImgMaps {
+  TensorMapBytes a, b;
+};
+struct NoMaps {};
+// Encodes a region of `bytes` bytes (a multiple of 128, base 16-byte aligned)
+// as a 2-D tensor of 128-byte rows with 128 x 128-byte boxes; false if the
+// driver's encoder is unavailable or the region is out of range.
+bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes);
 void make_operand_maps(const Common& cm, OperandMaps& maps);
 
 int launch_maxes(const Common& cm, void* stream);
+// Grouped top level (scaling 0 or 2): maxima, domain test, scales and images
+// of every operand block in one launch (CTA per block).
+int launch_blocks_fused(const Common& cm, const Level& lv, void* stream);
 int launch_power_a(const Common& cm, const Level& lv, void* stream,
                    const OperandMaps* maps = nullptr);
 int launch_power_b(const Common& cm, const Level& lv, void* stream,

@@ -656,13 +656,83 @@ int grid_for(int64_t total, int threads) {
   return static_cast<int>(b > 0 ? b : 1);
 }
 
+// Grouped products, top level: one CTA per operand block (A row block, or B
+// tile column of BN / 128 column blocks), each reading its block once for the
+// maxima (domain test, no atomics: the block owns its rows / columns) and
+// again, from L2, for the powered images; several CTAs per SM keep the loads
+// of many blocks in flight.
+template <int MODE>
+__global__ void __launch_bounds__(PRO_THREADS)
+    k_blocks_fused(const __grid_constant__ Common cm, const __grid_constant__ Level lv, int n_a) {
+  extern __shared__ __align__(16) float stile_fused[];
+  const int item = static_cast<int>(blockIdx.x);
+  bool bad = false;
+  if (item < n_a) {
+    const int g = find_prob(cm, item, 3);
+    const Prob& P = prob_at(cm, g);
+    bad = a_block_fused<MODE>(cm, lv, g, P, item - P.tm_base, true, threadIdx.x, 0);
+  } else {
+    const int id = item - n_a;
+    const int g = find_prob(cm, id, 4);
+    const Prob& P = prob_at(cm, g);
+    uint32_t* red = reinterpret_cast<uint32_t*>(stile_fused + mode_bk(MODE) * 129);
+    for (int h = 0; h < cm.BN / TILE_M; ++h)
+      bad |= b_block_fused<MODE>(cm, lv, g, P, (id - P.tn_base) * (cm.BN / TILE_M) + h, true,
+                                 stile_fused, red, threadIdx.x, 0);
+  }
+  if (bad) set_status(cm.status, PN_EDOMAIN);
+}
+
+template <int MODE>
+int launch_blocks_fused_t(const Common& cm, const Level& lv, void* stream) {
+  const int smem = mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(k_blocks_fused<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int grid = cm.total_tm + cm.total_tn;
+  k_blocks_fused<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(
+      cm, lv, cm.total_tm);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+int launch_blocks_fused(const Common& cm, const Level& lv, void* stream) {
+  if (cm.total_tm + cm.total_tn <= 0) return 0;
+  switch (cm.mode) {
+    case MODE_3XTF32: return launch_blocks_fused_t<MODE_3XTF32>(cm, lv, stream);
+    case MODE_TF32: return launch_blocks_fused_t<MODE_TF32>(cm, lv, stream);
+    case MODE_BF16: return launch_blocks_fused_t<MODE_BF16>(cm, lv, stream);
+    case MODE_F16: return launch_blocks_fused_t<MODE_F16>(cm, lv, stream);
+    case MODE_E4M3: return launch_blocks_fused_t<MODE_E4M3>(cm, lv, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 int launch_maxes(const Common& cm, void* stream) {
   const int blocks = cm.total_ma + cm.total_mb;
   if (blocks <= 0) return 0;
   k_maxes<<<blocks, PRO_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(cm);
   return cudaGetLastError();
+}
+
+bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base || bytes < 128 * 128 || (bytes & 127) != 0) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bytes >> 7) > (int64_t(1) << 31))
+    return false;
+  const cuuint64_t dims[2] = {128, static_cast<cuuint64_t>(bytes >> 7)};
+  const cuuint64_t strides[1] = {128};
+  const cuuint32_t box[2] = {128, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(reinterpret_cast<CUtensorMap*>(&out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 void make_operand_maps(const Common& cm, OperandMaps& maps) {
