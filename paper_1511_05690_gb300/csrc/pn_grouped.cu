@@ -359,15 +359,16 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   gr.n_b = L.total_tn;
   gr.ready = reinterpret_cast<int32_t*>(ws + L.off_ready);
   gr.level_done = reinterpret_cast<int32_t*>(ws + L.off_ldone);
-  // The image kernels run at several CTAs per SM and keep far more loads in
-  // flight than the persistent kernel's eight builder warps per SM, so the
-  // maxima and the top level's images (every block) are written before the
-  // persistent launch; it builds only the pushed blocks of the lower levels.
-  // debug_flags bit 3 builds the top level inside the persistent kernel too.
+  // A kernel of one CTA per operand block, several per SM, keeps far more
+  // loads in flight than the persistent kernel's eight builder warps per SM,
+  // so it writes the maxima and the top level's images (every block) before
+  // the persistent launch, which builds only the pushed blocks of the lower
+  // levels.  debug_flags bit 3 builds the top level inside the persistent
+  // kernel too.
   const bool top_inside = persist && (o->debug_flags & 8);
   gr.maxima = top_inside ? 1 : 0;
   gr.top_built = top_inside ? 0 : 1;
-  if (!top_inside && launch_maxes(cm, stream)) return PN_ECUDA;
+  if (!persist && launch_maxes(cm, stream)) return PN_ECUDA;
   for (int q = o->n_p - 1; q >= 0; --q) {
     const int qn = q > 0 ? q - 1 : 0;
     Level lv;
@@ -389,10 +390,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     set_projection(lv, o, q);
     if (persist) {
       gr.lv[o->n_p - 1 - q] = lv;
-      if (lv.is_top && !top_inside) {
-        if (launch_power_a(cm, lv, stream)) return PN_ECUDA;
-        if (launch_power_b(cm, lv, stream)) return PN_ECUDA;
-      }
+      if (lv.is_top && !top_inside && launch_blocks_fused(cm, lv, stream)) return PN_ECUDA;
       continue;
     }
     if (launch_power_a(cm, lv, stream)) return PN_ECUDA;
