@@ -66,38 +66,16 @@ __device__ __forceinline__ void warp_store_f32(float* stg, const float (&v)[32],
       const float4 t = *reinterpret_cast<const float4*>(stg + r * 32 + ((g ^ (r & 7)) << 2));
       *reinterpret_cast<float4*>(base + r * ld + 4 * g) = t;
     }
-  } else if (__all_sync(0xffffffffu, mask == 0u || mask == 0xffffffffu)) {
-    // whole rows, rows not 16-byte aligned: a row starting o floats past a
-    // 16-byte boundary is written as 7 aligned float4 (columns 4 - o + 4 q,
-    // q < 7) and its head (columns < 4 - o) and tail (columns >= 32 - o) as
-    // single floats; 8 lanes per row, four rows per instruction
-    const int q = lane & 7;
-    const uint32_t e0 = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(base) >> 2) & 3u;
-    const uint32_t l4 = static_cast<uint32_t>(ld) & 3u;
-#pragma unroll 1
-    for (int r0 = 0; r0 < 32; r0 += 4) {
-      const int r = r0 + (lane >> 3);
-      if (__shfl_sync(0xffffffffu, mask, r) == 0u) continue;
-      const int o = static_cast<int>((e0 + static_cast<uint32_t>(r) * l4) & 3u);
-      float* rowp = base + r * ld;
-      const float* srow = stg + r * 32;
-      const int sw = r & 7;
-      if (o == 0) {
-        *reinterpret_cast<float4*>(rowp + 4 * q) =
-            *reinterpret_cast<const float4*>(srow + ((q ^ sw) << 2));
-      } else if (q < 7) {
-        const int c0 = 4 - o + 4 * q;
-        float4 t;
-        t.x = srow[((((c0 + 0) >> 2) ^ sw) << 2) + ((c0 + 0) & 3)];
-        t.y = srow[((((c0 + 1) >> 2) ^ sw) << 2) + ((c0 + 1) & 3)];
-        t.z = srow[((((c0 + 2) >> 2) ^ sw) << 2) + ((c0 + 2) & 3)];
-        t.w = srow[((((c0 + 3) >> 2) ^ sw) << 2) + ((c0 + 3) & 3)];
-        *reinterpret_cast<float4*>(rowp + c0) = t;
-      } else {
-        for (int c = 0; c < 4 - o; ++c) rowp[c] = srow[((c >> 2) ^ sw) * 4 + (c & 3)];
-        for (int c = 32 - o; c < 32; ++c) rowp[c] = srow[((c >> 2) ^ sw) * 4 + (c & 3)];
-      }
-    }
+  } else if (__all_sync(0xffffffffu, mask == 0xffffffffu)) {
+    // a whole block, rows not 16-byte aligned: one row per instruction (a
+    // contiguous 128-byte run), every row unrolled so that the shared-memory
+    // loads and global stores of several rows overlap.  (Aligned float4 runs
+    // plus head and tail floats per row measured slower: four-way divergence
+    // and address arithmetic per row.)
+    float* p = base + lane;
+    const int c4 = lane >> 2, c1 = lane & 3;
+#pragma unroll 8
+    for (int r = 0; r < 32; ++r) p[r * ld] = stg[r * 32 + ((c4 ^ (r & 7)) << 2) + c1];
   } else {
 #pragma unroll 4
     for (int r = 0; r < 32; ++r) {
@@ -992,8 +970,10 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
                   x[e] *= rs * cv.x; x[e + 1] *= rs * cv.y; x[e + 2] *= rs * cv.z; x[e + 3] *= rs * cv.w;
                 }
               } else {
+                // one load per lane, broadcast by shuffles (the same products)
+                const float cl = lane < jn ? __ldg(cs + lane) : 0.0f;
 #pragma unroll
-                for (int e = 0; e < 32; ++e) x[e] *= rs * (e < jn ? __ldg(cs + e) : 0.0f);
+                for (int e = 0; e < 32; ++e) x[e] *= rs * __shfl_sync(0xffffffffu, cl, e);
               }
               if (cm.post) {
                 // APSP squaring: distances are >= 0 (x <= 1) and d_ii = 0 (x_ii = 1)
