@@ -390,7 +390,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
     set_projection(lv, o, q);
     if (persist) {
       gr.lv[o->n_p - 1 - q] = lv;
-      if (lv.is_top && !top_inside && launch_blocks_fused(cm, lv, stream)) return PN_ECUDA;
+      if (lv.is_top && !top_inside && launch_strips(cm, lv, stream)) return PN_ECUDA;
       continue;
     }
     if (launch_power_a(cm, lv, stream)) return PN_ECUDA;

@@ -275,8 +275,8 @@ void make_operand_maps(const Common& cm, OperandMaps& maps);
 
 int launch_maxes(const Common& cm, void* stream);
 // Grouped top level (scaling 0 or 2): maxima, domain test, scales and images
-// of every operand block in one launch (CTA per block).
-int launch_blocks_fused(const Common& cm, const Level& lv, void* stream);
+// of every operand block in one launch (a CTA per 32-row / 32-column strip).
+int launch_strips(const Common& cm, const Level& lv, void* stream);
 int launch_power_a(const Common& cm, const Level& lv, void* stream,
                    const OperandMaps* maps = nullptr);
 int launch_power_b(const Common& cm, const Level& lv, void* stream,

@@ -656,59 +656,269 @@ int grid_for(int64_t total, int threads) {
   return static_cast<int>(b > 0 ? b : 1);
 }
 
-// Grouped products, top level: one CTA per operand block (A row block, or B
-// tile column of BN / 128 column blocks), each reading its block once for the
-// maxima (domain test, no atomics: the block owns its rows / columns) and
-// again, from L2, for the powered images; several CTAs per SM keep the loads
-// of many blocks in flight.
+// Grouped products, top level: the maxima (domain test), scales and powered
+// images of every operand block, in strips of 32 rows of A or 32 columns of
+// B, one strip per CTA.  A strip is read once from memory for its maxima and
+// once more for its images, from L2 (at most 32 K floats per CTA, so the
+// strips in flight fit in it); every load instruction of a warp reads one
+// contiguous row segment, and shared memory regroups the values into the
+// image layout.  The arithmetic per value is that of power_a_store /
+// power_b_tile (same scales, same operation order), so the images are
+// bit-identical to theirs.
+constexpr int STRIP_ROWS = 32;
+
+// A rows 128 rb + 32 s .. + 31 of problem P.  Warp w owns rows 4w .. 4w + 3
+// of the strip: their maxima stay in registers, and its shared area `sm`
+// (4 rows of BK floats, 4 floats of padding after every 32) stages them.
+template <int MODE>
+__device__ __forceinline__ bool a_strip(const Common& cm, const Level& lv, const Prob& P, int rb,
+                                        int s, float* sm) {
+  using PK = Packer<MODE>;
+  constexpr int EPC = PK::EPC;
+  constexpr int BK = mode_bk(MODE);
+  constexpr int LDS = BK + BK / 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rloc = s * STRIP_ROWS + warp * 4;  // first row of the warp within the block
+  const int row0 = rb * TILE_M + rloc;
+  bool bad = false;
+  uint32_t u[4] = {0u, 0u, 0u, 0u};
+  // the warp's rows (a row past M reads row M - 1 and is never committed)
+  const float* src[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) src[r] = P.A + (int64_t)min(row0 + r, P.M - 1) * P.lda;
+  if (row0 < P.M) {  // warp-uniform
+    int kk0 = lane;
+    for (; kk0 + 96 < P.K; kk0 += 128) {  // whole 128-column steps: no clamps
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[r] = max(u[r], __float_as_uint(__ldg(src[r] + kk0 + 32 * q)));
+    }
+    if (kk0 < P.K) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          u[r] = max(u[r], __float_as_uint(__ldg(src[r] + min(kk0 + 32 * q, P.K - 1))));
+    }
+  }
+  float rs[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int row = row0 + r;
+    rs[r] = 1.0f;
+    if (row < P.M) {  // warp-uniform
+      if (u[r] > DOMAIN_MAX_BITS) {
+        const int cnt = lane < P.K ? (P.K - 1 - lane) / 32 + 1 : 0;
+        u[r] = take_exact(exact_max_bits(P.A + (int64_t)row * P.lda + lane, 32, cnt), bad);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) u[r] = max(u[r], __shfl_xor_sync(0xffffffffu, u[r], o));
+      rs[r] = scale_from_bits(cm, u[r]);
+      if (lane == 0) {
+        cm.rmax[P.rc_r + row] = u[r];
+        if (lv.is_top) cm.r[P.rc_r + row] = rs[r];
+      }
+    }
+  }
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  float* wsm = sm + warp * 4 * LDS;
+  const int jr = lane >> 3, cc = lane & 7;
+  const float rsj[1] = {jr == 0 ? rs[0] : jr == 1 ? rs[1] : jr == 2 ? rs[2] : rs[3]};
+  const float* rp = wsm + jr * LDS + cc * EPC + ((cc * EPC) >> 5) * 4;
+  const bool rows_in = row0 + 3 < P.M;  // warp-uniform: all four rows exist
+  for (int kb = 0; kb < P.KB; ++kb) {
+    float t[4][BK / 32];
+    if (rows_in && (kb + 1) * BK <= P.K) {  // warp-uniform: no clamps, no zeros
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int h = 0; h < BK / 32; ++h) t[r][h] = __ldg(src[r] + kb * BK + 32 * h + lane);
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const bool rok = row0 + r < P.M;
+#pragma unroll
+        for (int h = 0; h < BK / 32; ++h) {
+          const int k = kb * BK + 32 * h + lane;
+          const float x = __ldg(src[r] + min(k, P.K - 1));
+          t[r][h] = (rok && k < P.K) ? x : 0.0f;
+        }
+      }
+    }
+    __syncwarp();  // the previous k-block's reads of wsm are done
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int h = 0; h < BK / 32; ++h) wsm[r * LDS + 36 * h + lane] = t[r][h];
+    __syncwarp();
+    float v[1][EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; e += 4) {
+      const float4 f = *reinterpret_cast<const float4*>(rp + e);
+      v[0][e] = f.x; v[0][e + 1] = f.y; v[0][e + 2] = f.z; v[0][e + 3] = f.w;
+    }
+    div_scales(v, rsj);
+    power_all(v, lv.plog, lv.half, opscale);
+    uint4 hi, lo;
+    PK::pack(v[0], hi, lo);
+    uint8_t* dst = lv.a_level + P.a_img + ((int64_t)(rb * P.KB + kb) << 14);
+    const uint32_t off = sw128_offset(static_cast<uint32_t>(rloc + jr), cc * 16);
+    *reinterpret_cast<uint4*>(dst + off) = hi;
+    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.a_plane + off) = lo;
+  }
+  return bad;
+}
+
+// B columns 128 cb + 32 s .. + 31 of problem P (rows of the B^T image).
+// Lane l owns column l of the strip for the maxima and the staging; warp w
+// writes image rows 4w .. 4w + 3.  `sm` holds two staged k-blocks (BK x 33
+// floats each), `red` 288 words.
+template <int MODE>
+__device__ __forceinline__ bool b_strip(const Common& cm, const Level& lv, const Prob& P, int cb,
+                                        int s, float* sm, uint32_t* red) {
+  using PK = Packer<MODE>;
+  constexpr int EPC = PK::EPC;
+  constexpr int BK = mode_bk(MODE);
+  constexpr int TS = 33;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int col0 = cb * TILE_M + s * STRIP_ROWS;
+  const int col = col0 + lane;
+  const int colc = min(col, P.N - 1);
+  bool bad = false;
+  uint32_t u = 0u;
+  const int64_t ld8 = 8 * P.ldb;
+  if (col0 < P.N) {  // block-uniform
+    int k0 = warp;
+    const float* p = P.B + (int64_t)warp * P.ldb + colc;
+    for (; k0 + 8 * 15 < P.K; k0 += 128, p += 16 * ld8) {  // 16 whole rows: no clamps
+#pragma unroll
+      for (int q = 0; q < 16; ++q) u = max(u, __float_as_uint(__ldg(p + q * ld8)));
+    }
+    if (k0 < P.K) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        u = max(u, __float_as_uint(__ldg(P.B + (int64_t)min(k0 + 8 * q, P.K - 1) * P.ldb + colc)));
+    }
+    if (col >= P.N) u = 0u;
+    if (u > DOMAIN_MAX_BITS) {
+      const int cnt = warp < P.K ? (P.K - 1 - warp) / 8 + 1 : 0;
+      u = take_exact(exact_max_bits(P.B + (int64_t)warp * P.ldb + col, 8 * P.ldb, cnt), bad);
+    }
+  }
+  red[warp * 32 + lane] = u;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t m = red[lane];
+#pragma unroll
+    for (int w = 1; w < PRO_THREADS / 32; ++w) m = max(m, red[w * 32 + lane]);
+    const float cs = col < P.N ? scale_from_bits(cm, m) : 1.0f;
+    if (col < P.N) {
+      cm.cmax[P.rc_c + col] = m;
+      if (lv.is_top) cm.c[P.rc_c + col] = cs;
+    }
+    red[256 + lane] = __float_as_uint(cs);
+  }
+  __syncthreads();
+  const float cs_l = __uint_as_float(red[256 + lane]);
+  const float inv = 1.0f / cs_l;
+  const bool inv_ok = recip_exact(cs_l);
+  const float opscale = ldexpf(1.0f, cm.s_op);
+  const int jr = lane >> 3, cc = lane & 7;
+  const int irow = s * STRIP_ROWS + warp * 4 + jr;  // image row within the block
+  for (int kb = 0; kb < P.KB; ++kb) {
+    float* st = sm + (kb & 1) * (BK * TS);
+    float t[BK / 8];
+    if ((kb + 1) * BK <= P.K) {  // block-uniform: whole rows, no clamps
+      const float* p = P.B + (int64_t)(kb * BK + warp) * P.ldb + colc;
+#pragma unroll
+      for (int i = 0; i < BK / 8; ++i) t[i] = __ldg(p + i * ld8);
+#pragma unroll
+      for (int i = 0; i < BK / 8; ++i) t[i] = col < P.N ? t[i] : 0.0f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < BK / 8; ++i) {
+        const int k = kb * BK + warp + 8 * i;
+        const float x = __ldg(P.B + (int64_t)min(k, P.K - 1) * P.ldb + colc);
+        t[i] = (k < P.K && col < P.N) ? x : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < BK / 8; ++i)
+      st[(warp + 8 * i) * TS + lane] = div_pow2(t[i], cs_l, inv, inv_ok);
+    __syncthreads();  // (two buffers: the reads of k-block kb - 1 ended before)
+    float v[1][EPC];
+#pragma unroll
+    for (int e = 0; e < EPC; ++e) v[0][e] = st[(cc * EPC + e) * TS + warp * 4 + jr];
+    power_all(v, lv.plog, lv.half, opscale);
+    uint4 hi, lo;
+    PK::pack(v[0], hi, lo);
+    uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(cb * P.KB + kb) << 14);
+    const uint32_t off = sw128_offset(static_cast<uint32_t>(irow), cc * 16);
+    *reinterpret_cast<uint4*>(dst + off) = hi;
+    if constexpr (MODE == MODE_3XTF32) *reinterpret_cast<uint4*>(dst + P.b_plane + off) = lo;
+  }
+  return bad;
+}
+
+template <int MODE>
+__host__ __device__ constexpr int strip_smem() {
+  constexpr int a = 8 * 4 * (mode_bk(MODE) + mode_bk(MODE) / 8) * 4;
+  constexpr int b = 2 * mode_bk(MODE) * 33 * 4;
+  return (a > b ? a : b) + 288 * 4;
+}
+
+// One CTA per strip: A strips (4 per row block) first, then B strips (4 per
+// 128-column block, BN / 128 blocks per tile column).
 template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS)
-    k_blocks_fused(const __grid_constant__ Common cm, const __grid_constant__ Level lv, int n_a) {
-  extern __shared__ __align__(16) float stile_fused[];
-  const int item = static_cast<int>(blockIdx.x);
-  bool bad = false;
-  if (item < n_a) {
-    const int g = find_prob(cm, item, 3);
+    k_strips(const __grid_constant__ Common cm, const __grid_constant__ Level lv, int n_a) {
+  extern __shared__ __align__(16) float sm_strip[];
+  const int unit = static_cast<int>(blockIdx.x);
+  constexpr int SM_FLOATS = strip_smem<MODE>() / 4 - 288;
+  uint32_t* red = reinterpret_cast<uint32_t*>(sm_strip + SM_FLOATS);
+  bool bad;
+  if (unit < n_a) {
+    const int g = find_prob(cm, unit >> 2, 3);
     const Prob& P = prob_at(cm, g);
-    bad = a_block_fused<MODE>(cm, lv, g, P, item - P.tm_base, true, threadIdx.x, 0);
+    bad = a_strip<MODE>(cm, lv, P, (unit >> 2) - P.tm_base, unit & 3, sm_strip);
   } else {
-    const int id = item - n_a;
-    const int g = find_prob(cm, id, 4);
+    const int bpt = cm.BN / TILE_M;
+    const int cbg = (unit - n_a) >> 2;
+    const int g = find_prob(cm, cbg / bpt, 4);
     const Prob& P = prob_at(cm, g);
-    uint32_t* red = reinterpret_cast<uint32_t*>(stile_fused + mode_bk(MODE) * 129);
-    for (int h = 0; h < cm.BN / TILE_M; ++h)
-      bad |= b_block_fused<MODE>(cm, lv, g, P, (id - P.tn_base) * (cm.BN / TILE_M) + h, true,
-                                 stile_fused, red, threadIdx.x, 0);
+    bad = b_strip<MODE>(cm, lv, P, cbg - P.tn_base * bpt, (unit - n_a) & 3, sm_strip, red);
   }
   if (bad) set_status(cm.status, PN_EDOMAIN);
 }
 
 template <int MODE>
-int launch_blocks_fused_t(const Common& cm, const Level& lv, void* stream) {
-  const int smem = mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4;
+int launch_strips_t(const Common& cm, const Level& lv, void* stream) {
+  constexpr int smem = strip_smem<MODE>();
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(k_blocks_fused<MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_strips<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
-  const int grid = cm.total_tm + cm.total_tn;
-  k_blocks_fused<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(
-      cm, lv, cm.total_tm);
+  const int n_a = 4 * cm.total_tm;
+  const int grid = n_a + 4 * cm.total_tn * (cm.BN / TILE_M);
+  k_strips<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(cm, lv, n_a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int launch_blocks_fused(const Common& cm, const Level& lv, void* stream) {
+int launch_strips(const Common& cm, const Level& lv, void* stream) {
   if (cm.total_tm + cm.total_tn <= 0) return 0;
+  if (cm.scaling == 1 || !lv.is_top) return cudaErrorInvalidValue;  // per-row / column scales only
   switch (cm.mode) {
-    case MODE_3XTF32: return launch_blocks_fused_t<MODE_3XTF32>(cm, lv, stream);
-    case MODE_TF32: return launch_blocks_fused_t<MODE_TF32>(cm, lv, stream);
-    case MODE_BF16: return launch_blocks_fused_t<MODE_BF16>(cm, lv, stream);
-    case MODE_F16: return launch_blocks_fused_t<MODE_F16>(cm, lv, stream);
-    case MODE_E4M3: return launch_blocks_fused_t<MODE_E4M3>(cm, lv, stream);
+    case MODE_3XTF32: return launch_strips_t<MODE_3XTF32>(cm, lv, stream);
+    case MODE_TF32: return launch_strips_t<MODE_TF32>(cm, lv, stream);
+    case MODE_BF16: return launch_strips_t<MODE_BF16>(cm, lv, stream);
+    case MODE_F16: return launch_strips_t<MODE_F16>(cm, lv, stream);
+    case MODE_E4M3: return launch_strips_t<MODE_E4M3>(cm, lv, stream);
     default: return cudaErrorInvalidValue;
   }
 }
