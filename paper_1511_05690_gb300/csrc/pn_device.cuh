@@ -421,6 +421,29 @@ __device__ __forceinline__ float pow_pm1(float x, int k) {
 // exponent is applied once at the end (ldexpf: one rounding, into the
 // subnormal range if the result lies there).  x = 0 gives 0 for k >= 1.
 __device__ __forceinline__ float grad_factor(float acc, float x, float s, int k) {
+  // Fast path: the plain FP32 chain, taken when s = 2^E has a normal
+  // reciprocal and x'^(2^k - 1), acc times it and the result are normal.
+  // Every factor and partial product of the chain then lies between that
+  // power and 1, so each product rounds exactly as its renormalised
+  // counterpart below and the two paths agree bit for bit.  It is tried only
+  // where the exponent of x' = x / s alone shows the power to stay above
+  // 2^-125, so entries bound for the slow path skip it.
+  const uint32_t sb = __float_as_uint(s);
+  const int ex_xp = static_cast<int>((__float_as_uint(x) >> 23) & 0xFFu) - static_cast<int>(sb >> 23);
+  if (sb >= 0x00800000u && sb < 0x7F000000u && (sb & 0x007FFFFFu) == 0u &&
+      ex_xp * ((1 << k) - 1) >= -125) {
+    const float inv = __uint_as_float(0x7F000000u - sb);  // 2^-E
+    float y = __fmul_rn(x, inv);
+    float r = 1.0f;
+    for (int t = 0; t < k; ++t) {
+      r = __fmul_rn(r, y);
+      y = __fmul_rn(y, y);
+    }
+    const float ar = __fmul_rn(acc, r);
+    const float g = __fmul_rn(ar, inv);
+    const float fmin = 1.17549435e-38f;
+    if (r >= fmin && fabsf(ar) >= fmin && fabsf(g) >= fmin && fabsf(g) <= 3.40282347e38f) return g;
+  }
   int ls, ex, d;
   frexpf(s, &ls);
   ls -= 1;                        // s = 2^ls

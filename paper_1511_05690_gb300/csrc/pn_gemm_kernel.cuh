@@ -24,6 +24,11 @@ __host__ __device__ constexpr int num_stages(int mode, int BN, int CG = 1) {
   return SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG) > 8 ? 8
                                                           : SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG);
 }
+// TMEM accumulator buffers: all 512 columns, so 128-wide tiles get four.
+// With the epilogue slower than the MMAs (short contractions), the MMA issuer
+// then fills the next buffers while both epilogue groups are still busy,
+// instead of waiting for a buffer to be released before each tile.
+__host__ __device__ constexpr int acc_bufs(int BN) { return 512 / BN; }
 constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
 __host__ __device__ constexpr int smem_total(int mode, int BN, int CG = 1) {
   return num_stages(mode, BN, CG) * stage_bytes(mode, BN, CG) + 1024 /*align*/ + 256 /*barriers*/ +
@@ -306,7 +311,7 @@ template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
   constexpr int STAGES = num_stages(MODE, BN, CG);
-  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr uint32_t TMEM_COLS = acc_bufs(BN) * BN;
   extern __shared__ uint8_t smem_raw[];
   Ctx cx{};
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -314,8 +319,8 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   cx.full = reinterpret_cast<uint64_t*>(cx.smem + STAGES * STAGE_BYTES);
   cx.empty = cx.full + STAGES;
   cx.acc_full = cx.empty + STAGES;
-  cx.acc_empty = cx.acc_full + 2;
-  cx.drain = cx.acc_empty + 2;
+  cx.acc_empty = cx.acc_full + 4;
+  cx.drain = cx.acc_empty + 4;
   cx.tmem_slot = reinterpret_cast<uint32_t*>(cx.drain + 1);
   cx.abort_flag = reinterpret_cast<volatile int32_t*>(cx.tmem_slot + 1);
   cx.ok_flag = cx.abort_flag + 1;
@@ -336,7 +341,7 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
       mbar_init(&cx.full[s], 1);
       mbar_init(&cx.empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < acc_bufs(BN); ++b) {
       mbar_init(&cx.acc_full[b], 1);
       // single CTA: every epilogue thread of the group arrives; a pair: one
       // lane per epilogue warp of both CTAs, on rank 0's barrier
@@ -381,9 +386,9 @@ __device__ __forceinline__ void ctx_teardown(const Ctx& cx) {
   if ((threadIdx.x >> 5) == 1) {
     tc_fence_after();
     if constexpr (CG == 2)
-      tmem_dealloc_pair(cx.tmem_base, 2 * BN);
+      tmem_dealloc_pair(cx.tmem_base, acc_bufs(BN) * BN);
     else
-      tmem_dealloc(cx.tmem_base, 2 * BN);
+      tmem_dealloc(cx.tmem_base, acc_bufs(BN) * BN);
   }
 }
 
@@ -524,8 +529,8 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
 }
 
 // MMA issuer (one thread): the tensor-core K loop of each tile into the
-// accumulator buffer it & 1, it = it0, it0 + 1, ... counting this CTA's
-// tiles over the whole launch.
+// accumulator buffer it mod acc_bufs(BN), it = it0, it0 + 1, ... counting
+// this CTA's tiles over the whole launch.
 template <int MODE, int BN, int CG = 1>
 __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const Ctx& cx,
                                         int count, int it0, MmaState& ms) {
@@ -563,9 +568,10 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
       for (int idx = cx.wid; idx < count && !aborted; idx += cx.wstride, ++it) {
         const int t = lv.is_top ? idx : lv.work[idx];
         const Prob& P = prob_at(cm, find_prob(cm, t, 0));
-        const int buf = it & 1;
+        constexpr int NB = acc_bufs(BN);
+        const int buf = it & (NB - 1);
         // a pair: the epilogues of both CTAs release the accumulator
-        if (!mbar_wait(&acc_empty[buf], ((it >> 1) & 1) ^ 1u, tmo, abort_flag)) {
+        if (!mbar_wait(&acc_empty[buf], ((it / NB) & 1) ^ 1u, tmo, abort_flag)) {
           aborted = true;
           break;
         }
@@ -670,9 +676,9 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
   (void)abort_flag; (void)ok_flag; (void)tmem_base; (void)tmo; (void)warp; (void)lane;
     // Warp w may only read TMEM lanes 32*(w%4)..+31 (one output row each).
     // With several tiles per CTA (by_tile) the epilogue warps form two groups
-    // of four, one warp per lane quarter each; group g finishes the tiles
-    // that use accumulator buffer g (every other tile), so two tiles'
-    // epilogues overlap their latencies.  With few tiles all eight warps
+    // of four, one warp per lane quarter each; group g finishes every other
+    // tile (it = g mod 2; accumulator buffers g, g + 2, ... of the
+    // acc_bufs(BN)), so two tiles' epilogues overlap their latencies.  With few tiles all eight warps
     // finish every tile, the two warps of a lane quarter taking one half of
     // the columns each, which shortens the last tile's epilogue.
     const int ew = warp - 2;
@@ -704,10 +710,11 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       const int64_t Prc_c = P.rc_c;
       int tm, tn;
       tile_coords<CG>(P, t, cx.rank, tm, tn);
-      const int buf = it & 1;
+      constexpr int NB = acc_bufs(BN);
+      const int buf = it & (NB - 1);
       const int okslot = 2 * grp + ((it >> 1) & 1);
       if (et == 0) {
-        const bool ok = mbar_wait(&acc_full[buf], (it >> 1) & 1, tmo, abort_flag);
+        const bool ok = mbar_wait(&acc_full[buf], (it / NB) & 1, tmo, abort_flag);
         if (!ok) {
           *abort_flag = 1;
           set_status(cm.status, PN_ETIMEOUT);

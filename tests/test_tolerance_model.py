@@ -287,3 +287,42 @@ def test_adjoint_tolerance_holds_the_emulated_gradient(orc, shape, plog):
                               & (g >= 2.0 ** -126)))
     if plog == 6:
         assert rescued > 0
+
+
+def _grad_factor_fast(acc, x, s, k):
+    """The gradient epilogue's fast path: the plain FP32 chain with x' = x 2^-E
+    (s = 2^E), used where s has a normal reciprocal and x'^(2^k - 1), acc times
+    it and the result are normal; NaN marks entries that take the exponent-
+    carrying path."""
+    f32 = np.float32
+    inv = (1.0 / s.astype(np.float64)).astype(np.float32)
+    y = (x * inv).astype(f32)
+    r = np.ones_like(y)
+    for _ in range(k):
+        r = (r * y).astype(f32)
+        y = (y * y).astype(f32)
+    ar = (acc * r).astype(f32)
+    g = (ar * inv).astype(f32)
+    fmin = f32(2.0 ** -126)
+    ok = (r >= fmin) & (np.abs(ar) >= fmin) & (np.abs(g) >= fmin) & np.isfinite(g)
+    return np.where(ok, g, np.nan).astype(f32)
+
+
+@pytest.mark.parametrize("k", [0, 1, 3, 6])
+def test_grad_factor_fast_path_matches_exponent_path(k):
+    """Where the fast path applies it gives the same bits as the mantissa chain
+    with separate exponents: over x' spread across enough binades that
+    x'^(2^k - 1) leaves the FP32 range for part of them (so that both paths
+    occur), random accumulators and power-of-two scales."""
+    g = workloads.rng(None, 77 + k)
+    n = 200000
+    s = np.ldexp(np.ones(n, dtype=np.float32), g.integers(-60, 60, n)).astype(np.float32)
+    xp = np.ldexp(g.random(n), -g.integers(0, max(2, 300 // 2 ** k), n))
+    x = (xp * s).astype(np.float32)
+    acc = (g.random(n) * np.ldexp(1.0, g.integers(-20, 20, n))).astype(np.float32)
+    fast = _grad_factor_fast(acc, x, s, k)
+    slow = _grad_factor(acc, x, s, k)
+    used = ~np.isnan(fast)
+    assert used.mean() > 0.2
+    assert used.all() if k == 0 else (~used).sum() > 100
+    assert np.array_equal(fast[used].view(np.uint32), slow[used].view(np.uint32))
