@@ -449,13 +449,25 @@ __device__ __forceinline__ float grad_factor(float acc, float x, float s, int k)
   ls -= 1;                        // s = 2^ls
   float xm = frexpf(x, &ex);      // x = xm 2^ex, so x' = xm 2^(ex - ls)
   ex -= ls;
+  (void)d;
   float rm = 1.0f;
   int re = 0;
+  // A product of two values in [0.5, 1] lies in [0.25, 1) (it cannot round
+  // up to 1), so renormalising it into [0.5, 1) is at most one doubling:
+  // the same mantissa and exponent as frexpf of the product.
   for (int t = 0; t < k; ++t) {
-    rm = frexpf(rm * xm, &d);     // product of two values in [0.5, 1]: normal
-    re += ex + d;
-    xm = frexpf(xm * xm, &d);
-    ex = 2 * ex + d;
+    rm *= xm;
+    re += ex;
+    if (rm < 0.5f) {
+      rm *= 2.0f;
+      re -= 1;
+    }
+    xm *= xm;
+    ex *= 2;
+    if (xm < 0.5f) {
+      xm *= 2.0f;
+      ex -= 1;
+    }
   }
   return ldexpf(acc * rm, re - ls);
 }

@@ -9,10 +9,14 @@
 namespace pn {
 namespace gemm {
 
-constexpr int EPI_WARPS = 8;                       // two groups, one warp per TMEM lane quarter each
+// Epilogue warps: NG groups of four, one warp per TMEM lane quarter each.
+// The level kernel runs two groups; the persistent grouped kernel three at
+// 128-wide tiles (its epilogue, not the MMA, bounds the small problems).
+constexpr int EPI_WARPS = 8;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int GEMM_THREADS = 64 + EPI_THREADS;     // producer, MMA, epilogue
-constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
+constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring (two epilogue groups)
+constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
 
 // Bytes of one ring stage: the A image tile and this CTA's B image tiles of
 // 128 rows each (CG = 2: a CTA pair, each CTA holding half of the BN rows of
@@ -20,19 +24,21 @@ constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring
 __host__ __device__ constexpr inline int stage_bytes(int mode, int BN, int CG = 1) {
   return mode_planes(mode) * (IMG_BYTES + IMG_BYTES * (BN / TILE_M) / CG);
 }
-__host__ __device__ constexpr int num_stages(int mode, int BN, int CG = 1) {
-  return SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG) > 8 ? 8
-                                                          : SMEM_STAGE_BUDGET / stage_bytes(mode, BN, CG);
+// Ring stages: each epilogue group beyond two takes its staging buffers
+// from the ring's budget.
+__host__ __device__ constexpr int num_stages(int mode, int BN, int CG = 1, int NG = 2) {
+  return (SMEM_STAGE_BUDGET - (NG - 2) * 4 * STG_BYTES) / stage_bytes(mode, BN, CG) > 8
+             ? 8
+             : (SMEM_STAGE_BUDGET - (NG - 2) * 4 * STG_BYTES) / stage_bytes(mode, BN, CG);
 }
 // TMEM accumulator buffers: all 512 columns, so 128-wide tiles get four.
 // With the epilogue slower than the MMAs (short contractions), the MMA issuer
 // then fills the next buffers while both epilogue groups are still busy,
 // instead of waiting for a buffer to be released before each tile.
 __host__ __device__ constexpr int acc_bufs(int BN) { return 512 / BN; }
-constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
-__host__ __device__ constexpr int smem_total(int mode, int BN, int CG = 1) {
-  return num_stages(mode, BN, CG) * stage_bytes(mode, BN, CG) + 1024 /*align*/ + 256 /*barriers*/ +
-         EPI_WARPS * STG_BYTES;
+__host__ __device__ constexpr int smem_total(int mode, int BN, int CG = 1, int NG = 2) {
+  return num_stages(mode, BN, CG, NG) * stage_bytes(mode, BN, CG) + 1024 /*align*/ +
+         256 /*barriers*/ + 4 * NG * STG_BYTES;
 }
 __host__ __device__ constexpr int mma_kind(int mode) {
   return (mode == MODE_BF16 || mode == MODE_F16) ? KIND_F16 : mode == MODE_E4M3 ? KIND_F8 : KIND_TF32;
@@ -273,7 +279,7 @@ struct Ctx {
   uint64_t* drain;
   uint32_t* tmem_slot;
   volatile int32_t* abort_flag;
-  volatile int32_t* ok_flag;  // [4], epilogue item hand-off (2 per group)
+  volatile int32_t* ok_flag;  // [2 NG], epilogue item hand-off (2 per group)
   uint32_t tmem_base;
   uint64_t tmo;
   uint32_t rank;              // CTA pair: rank in the cluster (0 issues the MMAs); else 0
@@ -307,10 +313,10 @@ struct MmaState {
 // Lays out shared memory, initialises the barriers, allocates TMEM (warp 1)
 // and synchronises the block.  timeout_ns limits every bounded wait of the
 // roles.  Called by every thread.
-template <int MODE, int BN, int CG = 1>
+template <int MODE, int BN, int CG = 1, int NG = 2>
 __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
-  constexpr int STAGES = num_stages(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG, NG);
   constexpr uint32_t TMEM_COLS = acc_bufs(BN) * BN;
   extern __shared__ uint8_t smem_raw[];
   Ctx cx{};
@@ -345,12 +351,12 @@ __device__ __forceinline__ Ctx ctx_setup(bool by_tile, uint64_t timeout_ns) {
       mbar_init(&cx.acc_full[b], 1);
       // single CTA: every epilogue thread of the group arrives; a pair: one
       // lane per epilogue warp of both CTAs, on rank 0's barrier
-      mbar_init(&cx.acc_empty[b], CG == 2 ? 2 * (by_tile ? EPI_WARPS / 2 : EPI_WARPS)
-                                          : (by_tile ? EPI_THREADS / 2 : EPI_THREADS));
+      mbar_init(&cx.acc_empty[b], CG == 2 ? 2 * (by_tile ? 4 : 4 * NG)
+                                          : (by_tile ? 128 : 128 * NG));
     }
     mbar_init(cx.drain, 1);
     *cx.abort_flag = 0;
-    cx.ok_flag[0] = cx.ok_flag[1] = cx.ok_flag[2] = cx.ok_flag[3] = 0;
+    for (int i = 0; i < 2 * NG; ++i) cx.ok_flag[i] = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -394,7 +400,7 @@ __device__ __forceinline__ void ctx_teardown(const Ctx& cx) {
 
 // Producer (one thread): bulk copies of the operand images of this CTA's
 // tiles blockIdx.x, blockIdx.x + gridDim.x, ... < count into the ring.
-template <int MODE, int BN, int CG = 1>
+template <int MODE, int BN, int CG = 1, int NG = 2>
 __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, const Ctx& cx,
                                              int count, ProdState& ps, const Ready& rd,
                                              const ImgMaps* maps = nullptr) {
@@ -402,7 +408,7 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
   constexpr int A_BYTES = IMG_BYTES;
   constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
-  constexpr int STAGES = num_stages(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG, NG);
   constexpr int KIND = mma_kind(MODE);
   constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
@@ -531,14 +537,14 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
 // MMA issuer (one thread): the tensor-core K loop of each tile into the
 // accumulator buffer it mod acc_bufs(BN), it = it0, it0 + 1, ... counting
 // this CTA's tiles over the whole launch.
-template <int MODE, int BN, int CG = 1>
+template <int MODE, int BN, int CG = 1, int NG = 2>
 __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const Ctx& cx,
                                         int count, int it0, MmaState& ms) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
   constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
-  constexpr int STAGES = num_stages(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG, NG);
   constexpr int KIND = mma_kind(MODE);
   constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
@@ -648,14 +654,14 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
 // out (+)= acc * x'^(p-1) / s with x the source element at the output position
 // and s its row (grad_axis 0) or column (1) scale; the first p present
 // overwrites, later ones add.
-template <int MODE, int BN, int EPI, int CG = 1>
+template <int MODE, int BN, int EPI, int CG = 1, int NG = 2>
 __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, const Ctx& cx,
                                              int count, bool by_tile, int it0, const Ready& rd) {
   constexpr int PLANES = mode_planes(MODE);
   constexpr int A_BYTES = IMG_BYTES;
   constexpr int B_BYTES = IMG_BYTES * (BN / TILE_M) / CG;
   constexpr int STAGE_BYTES = stage_bytes(MODE, BN, CG);
-  constexpr int STAGES = num_stages(MODE, BN, CG);
+  constexpr int STAGES = num_stages(MODE, BN, CG, NG);
   constexpr int KIND = mma_kind(MODE);
   constexpr uint32_t IDESC = idesc_make(ab_format(MODE), TILE_M * CG, BN);
   constexpr int CHUNKS = BN / 32;
@@ -684,13 +690,14 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int grp = by_tile ? ew >> 2 : 0;
-    const int nch = by_tile ? CHUNKS : CHUNKS / 2;  // 32-column chunks per warp
+    // (more than two groups only with by_tile)
+    const int nch = by_tile ? CHUNKS : CHUNKS / NG;  // 32-column chunks per warp
     const int ch0 = by_tile ? 0 : (ew >> 2) * nch;
-    const int gthreads = by_tile ? EPI_THREADS / 2 : EPI_THREADS;
+    const int gthreads = by_tile ? 128 : 128 * NG;
     const int et = (threadIdx.x - 64) & (gthreads - 1);  // thread of the group
     float* stg = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256 + ew * STG_BYTES);
-    const int step = by_tile ? 2 : 1;
-    for (int j = by_tile ? ((grp - it0) & 1) : 0;; j += step) {
+    const int step = by_tile ? NG : 1;
+    for (int j = by_tile ? ((grp - it0) % NG + NG) % NG : 0;; j += step) {
       const int idx = cx.wid + j * cx.wstride;
       if (idx >= count) break;
       const int it = it0 + j;
@@ -712,7 +719,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       tile_coords<CG>(P, t, cx.rank, tm, tn);
       constexpr int NB = acc_bufs(BN);
       const int buf = it & (NB - 1);
-      const int okslot = 2 * grp + ((it >> 1) & 1);
+      const int okslot = 2 * grp + ((it / NG) & 1);
       if (et == 0) {
         const bool ok = mbar_wait(&acc_full[buf], (it / NB) & 1, tmo, abort_flag);
         if (!ok) {
@@ -1003,7 +1010,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
         res_all[hc] = res;
       }
       if (EPI == 0 && !lv.is_bottom) {
-        const bool tile_left = bar_red_or(any_left, 3 + grp, gthreads);
+        const bool tile_left = bar_red_or(any_left, 1 + NG + grp, gthreads);
         // a pair's tile goes down if either half has entries left, so each
         // half's state is written whenever it could be needed
         if (tile_left || CG == 2) {
@@ -1024,7 +1031,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
             }
           }
           // r = 2: a tile that starts no chain here skips the half level
-          const bool skip = lv.skip_work && !bar_red_or(new_chain, 3 + grp, gthreads);
+          const bool skip = lv.skip_work && !bar_red_or(new_chain, 1 + NG + grp, gthreads);
           // a pair's tile is pushed once, by whichever half claims it first
           bool push = et == 0 && tile_left;
           if constexpr (CG == 2)

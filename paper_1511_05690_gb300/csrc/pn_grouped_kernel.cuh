@@ -2,7 +2,10 @@
 // independent products in ONE launch (the p rings and the problems
 // parallelise coarsely, Sec. 4; Alg. 5 per problem).
 //
-// One CTA per SM (cooperative launch, so every CTA is resident), 10 warps.
+// One CTA per SM (cooperative launch, so every CTA is resident): the copy
+// producer, the MMA issuer and grouped_ng(BN) epilogue groups of four warps
+// (three at 128-wide tiles: the epilogues of small problems, not the MMAs,
+// bound the launch, and TMEM holds four 128-column accumulators).
 // For each slot of the level schedule (largest p first):
 //   1. operand blocks -- warps 2-9 build the powered images of the blocks
 //      this level needs: below the top level only the blocks of pushed
@@ -28,17 +31,22 @@
 namespace pn {
 namespace gemm {
 
-constexpr int IMG_BAR = 5;  // named barrier of the block builders (warps 2-9)
+constexpr int IMG_BAR = 15;  // named barrier of the block builders (warps 2-9)
+
+__host__ __device__ constexpr int grouped_ng(int BN) { return BN == 128 ? 3 : 2; }
+__host__ __device__ constexpr int grouped_threads(int BN) { return 64 + 128 * grouped_ng(BN); }
 
 template <int MODE, int BN>
-__global__ void __launch_bounds__(GEMM_THREADS, 1)
+__global__ void __launch_bounds__(grouped_threads(BN), 1)
     k_grouped_persist(const __grid_constant__ Common cm, const __grid_constant__ GroupedRun gr) {
-  static_assert(num_stages(MODE, BN) >= 2, "operand ring too small");
-  static_assert(mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4 <= num_stages(MODE, BN) * stage_bytes(MODE, BN),
+  constexpr int NG = grouped_ng(BN);
+  static_assert(num_stages(MODE, BN, 1, NG) >= 2, "operand ring too small");
+  static_assert(mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4 <=
+                    num_stages(MODE, BN, 1, NG) * stage_bytes(MODE, BN),
                 "block builders' staging does not fit the ring");
   __shared__ int32_t s_count;
-  // tiles alternate between the two epilogue groups
-  const Ctx cx = ctx_setup<MODE, BN>(true, cm.timeout_ns);
+  // tiles rotate over the epilogue groups
+  const Ctx cx = ctx_setup<MODE, BN, 1, NG>(true, cm.timeout_ns);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ProdState ps{};
   for (int s = 0; s < 8; ++s) ps.pend[s] = -1;
@@ -65,7 +73,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     }
     // ---------------------------------------------------- operand blocks ---
     const bool built = t == 0 && gr.top_built;
-    if (warp >= 2 && !built) {
+    if (warp >= 2 && warp < 10 && !built) {  // PRO_THREADS builder threads
       const int ti = threadIdx.x - 64;
       float* stile = reinterpret_cast<float*>(cx.smem);  // the ring is idle between slots
       uint32_t* red = reinterpret_cast<uint32_t*>(cx.smem + mode_bk(MODE) * 129 * 4);
@@ -102,13 +110,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     // ------------------------------------------------------------- tiles ---
     const Ready rd{built ? nullptr : gr.ready, t + 1, gr.n_a};
     if (warp == 0) {
-      if (lane == 0) run_producer<MODE, BN>(cm, lv, cx, count, ps, rd);
+      if (lane == 0) run_producer<MODE, BN, 1, NG>(cm, lv, cx, count, ps, rd);
       __syncwarp();
     } else if (warp == 1) {
-      if (lane == 0) run_mma<MODE, BN>(cm, lv, cx, count, it0, ms);
+      if (lane == 0) run_mma<MODE, BN, 1, NG>(cm, lv, cx, count, it0, ms);
       __syncwarp();
     } else {
-      run_epilogue<MODE, BN, 0>(cm, lv, cx, count, true, it0, rd);
+      run_epilogue<MODE, BN, 0, 1, NG>(cm, lv, cx, count, true, it0, rd);
     }
     if (count > static_cast<int>(blockIdx.x)) it0 += (count - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1;
     __syncthreads();
@@ -128,14 +136,14 @@ inline int launch_grouped_persist_t(const Common& cm, const GroupedRun& gr, int 
   if (!attr_done) {
     const cudaError_t e = cudaFuncSetAttribute(k_grouped_persist<MODE, BN>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               smem_total(MODE, BN));
+                                               smem_total(MODE, BN, 1, grouped_ng(BN)));
     if (e != cudaSuccess) return e;
     attr_done = 1;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(num_sms));
-  cfg.blockDim = dim3(GEMM_THREADS);
-  cfg.dynamicSmemBytes = smem_total(MODE, BN);
+  cfg.blockDim = dim3(grouped_threads(BN));
+  cfg.dynamicSmemBytes = smem_total(MODE, BN, 1, grouped_ng(BN));
   cfg.stream = static_cast<cudaStream_t>(stream);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the flags and the

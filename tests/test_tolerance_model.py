@@ -326,3 +326,31 @@ def test_grad_factor_fast_path_matches_exponent_path(k):
     assert used.mean() > 0.2
     assert used.all() if k == 0 else (~used).sum() > 100
     assert np.array_equal(fast[used].view(np.uint32), slow[used].view(np.uint32))
+
+
+def test_grad_factor_renormalisation_equals_frexp():
+    """The gradient epilogue's exponent-carrying chain renormalises each
+    product of two mantissas in [0.5, 1] by at most one doubling instead of
+    calling frexp: the same mantissas and exponents, step by step."""
+    g = workloads.rng(None, 91)
+    f32 = np.float32
+    xm = (0.5 + 0.5 * g.random(100000)).astype(f32)
+    xm[:3] = [0.5, np.nextafter(f32(1), f32(0)), 0.75]
+    rm_a = np.ones_like(xm)
+    rm_b = np.ones_like(xm)
+    ea = np.zeros(xm.shape, dtype=np.int64)
+    eb = np.zeros(xm.shape, dtype=np.int64)
+    xa, xb = xm.copy(), xm.copy()
+    for _ in range(6):
+        rm_a, d = np.frexp((rm_a * xa).astype(f32))
+        ea += d
+        xa = np.frexp((xa * xa).astype(f32))[0]
+        p = (rm_b * xb).astype(f32)
+        low = p < 0.5
+        rm_b = np.where(low, p * 2, p).astype(f32)
+        eb -= low
+        xb = (xb * xb).astype(f32)
+        xb = np.where(xb < 0.5, xb * 2, xb).astype(f32)
+        assert np.array_equal(rm_a.view(np.uint32), rm_b.view(np.uint32))
+        assert np.array_equal(xa.view(np.uint32), xb.view(np.uint32))
+        assert np.array_equal(ea, eb)
