@@ -228,23 +228,44 @@ __device__ __forceinline__ void r1_finish_block(float* stg, const float (&x)[32]
     *reinterpret_cast<float4*>(stg + lane * 32 + ((g ^ (lane & 7)) << 2)) =
         make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
   __syncwarp();
-#pragma unroll 4
-  for (int r = 0; r < 32; ++r) {
-    const uint32_t m = __shfl_sync(0xffffffffu, pend, r);
-    const float rsr = __shfl_sync(0xffffffffu, rs, r);
-    if (m == 0u) continue;
-    if ((m >> lane) & 1u) {
-      const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
-      float* c = crow + r * ldc + lane;
-      const float s2 = *c;
-      float y = s2 / fmaxf(s1, s2);
-      if constexpr (SQRT_ROOT) {
-        for (int t = 0; t < plog; ++t) y = sqrtf(y);
-      } else if (plog > 0) {
-        y = ex2_approx(lg2_approx(y) * inv_p);
+  auto finish = [&](float s1, float s2, float rsr) {
+    float y = s2 / fmaxf(s1, s2);
+    if constexpr (SQRT_ROOT) {
+      for (int t = 0; t < plog; ++t) y = sqrtf(y);
+    } else if (plog > 0) {
+      y = ex2_approx(lg2_approx(y) * inv_p);
+    }
+    if (affine) y = fmaf(pa, y, pb);
+    return y * (rsr * cs_lane);
+  };
+  if (__all_sync(0xffffffffu, pend == 0xffffffffu)) {
+    // a whole block: the stored sums of eight rows are loaded before any is
+    // used, so their latencies overlap
+    float* c0 = crow + lane;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 8) {
+      float s2[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s2[i] = c0[(r0 + i) * ldc];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = r0 + i;
+        const float rsr = __shfl_sync(0xffffffffu, rs, r);
+        const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+        c0[r * ldc] = finish(s1, s2[i], rsr);
       }
-      if (affine) y = fmaf(pa, y, pb);
-      *c = y * (rsr * cs_lane);
+    }
+  } else {
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t m = __shfl_sync(0xffffffffu, pend, r);
+      const float rsr = __shfl_sync(0xffffffffu, rs, r);
+      if (m == 0u) continue;
+      if ((m >> lane) & 1u) {
+        const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+        float* c = crow + r * ldc + lane;
+        *c = finish(s1, *c, rsr);
+      }
     }
   }
   __syncwarp();
