@@ -189,23 +189,48 @@ __device__ __forceinline__ void r2_finish_block(float* stg, const float (&x)[32]
     *reinterpret_cast<float4*>(stg + lane * 32 + ((g ^ (lane & 7)) << 2)) =
         make_float4(x[4 * g], x[4 * g + 1], x[4 * g + 2], x[4 * g + 3]);
   __syncwarp();
-#pragma unroll 4
-  for (int r = 0; r < 32; ++r) {
-    const uint32_t m = __shfl_sync(0xffffffffu, w3, r);
-    const float rsr = __shfl_sync(0xffffffffu, rs, r);
-    if (m == 0u) continue;
-    if ((m >> lane) & 1u) {
-      const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
-      const float s2 = __ldg(s2row + r * ldp + lane);  // parked at earlier levels
-      const float s3 = __ldg(s3row + r * ldp + lane);
-      float* c = crow + r * ldc + lane;
-      float a = r2_project(s1, s2, s3, *c, eta);
-      if constexpr (SQRT_ROOT) {
-        for (int t = 0; t < plog; ++t) a = sqrtf(a);
-      } else if (plog > 0) {
-        a = ex2_approx(lg2_approx(a) * inv_p);
+  auto finish = [&](float s1, float s2, float s3, float s0, float rsr) {
+    float a = r2_project(s1, s2, s3, s0, eta);
+    if constexpr (SQRT_ROOT) {
+      for (int t = 0; t < plog; ++t) a = sqrtf(a);
+    } else if (plog > 0) {
+      a = ex2_approx(lg2_approx(a) * inv_p);
+    }
+    return a * rsr * cs_lane;
+  };
+  if (__all_sync(0xffffffffu, w3 == 0xffffffffu)) {
+    // a whole block: the sums of four rows (two parked, C) are loaded
+    // before any is used, so their latencies overlap
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+      float s2[4], s3[4], s0[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        s2[i] = __ldg(s2row + (r0 + i) * ldp + lane);  // parked at earlier levels
+        s3[i] = __ldg(s3row + (r0 + i) * ldp + lane);
+        s0[i] = crow[(r0 + i) * ldc + lane];
       }
-      *c = a * rsr * cs_lane;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = r0 + i;
+        const float rsr = __shfl_sync(0xffffffffu, rs, r);
+        const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+        crow[r * ldc + lane] = finish(s1, s2[i], s3[i], s0[i], rsr);
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t m = __shfl_sync(0xffffffffu, w3, r);
+      const float rsr = __shfl_sync(0xffffffffu, rs, r);
+      if (m == 0u) continue;
+      if ((m >> lane) & 1u) {
+        const float s1 = stg[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+        const float s2 = __ldg(s2row + r * ldp + lane);  // parked at earlier levels
+        const float s3 = __ldg(s3row + r * ldp + lane);
+        float* c = crow + r * ldc + lane;
+        *c = finish(s1, s2, s3, *c, rsr);
+      }
     }
   }
   __syncwarp();
