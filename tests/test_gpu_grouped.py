@@ -88,6 +88,24 @@ def test_grouped_equals_single_products(pn):
             assert torch.equal(C, C1)
 
 
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_grouped_scaling_modes_equal_single_products(pn, scaling):
+    """Scaling 0 (no scales; the strip kernel and the persistent launch) and
+    scaling 1 (one global scale per problem; the per-level launches) give the
+    single products' results bit for bit, over ragged and empty problems."""
+    probs = _problems(815, count=24)
+    As = [_dev(a) for a, _ in probs]
+    Bs = [_dev(b) for _, b in probs]
+    for tile_n in (128, 256):
+        plan = pn.GroupedProduct(As, Bs, compute="bf16", tile_n=tile_n, scaling=scaling)
+        Cs = plan.run(check=True)
+        for A, B, C in zip(As, Bs, Cs):
+            if A.shape[0] == 0:
+                continue
+            C1, _, _ = pn.maxprod_pnorm(A, B, compute="bf16", tile_n=tile_n, scaling=scaling)
+            assert torch.equal(C, C1), (tuple(A.shape), tuple(B.shape), tile_n)
+
+
 def test_grouped_cuda_graph_replay(pn):
     """The run step is captured once and replayed on new input values."""
     probs = _problems(812, count=24)
