@@ -10,13 +10,13 @@
 //   1. operand blocks -- warps 2-9 build the powered images of the blocks
 //      this level needs: below the top level only the blocks of pushed
 //      tiles.  The top level's images (every block of every problem) are
-//      either written before the launch by the high-occupancy image kernels
-//      (top_built), or built here, reading each block once for its row /
+//      either written before the launch by the strip kernel (top_built), or
+//      built here (a test mode), reading each block once for its row /
 //      column maxima (domain test, power-of-two scales) and once more, from
 //      L2, for the images.  Each block is published with a release store of
 //      its ready flag (slot + 1).
 //   2. tiles -- the tensor-core roles of the level kernel (copy producer,
-//      MMA issuer, two epilogue groups) over the slot's tiles; the producer
+//      MMA issuer, the epilogue groups) over the slot's tiles; the producer
 //      waits, bounded, for a tile's two ready flags before copying its
 //      images, and the epilogue acquires them before reading the scales.
 //   3. a bounded grid-wide barrier (a counter per slot): once every CTA has
