@@ -276,8 +276,11 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
 }
 
 // ------------------------------------------------ TMA top-level images ---
-// The top level of a single product builds every operand tile once.  One
-// persistent CTA per SM walks the tile ids blockIdx.x, blockIdx.x + gridDim.x,
+// The top level of a single product builds every operand tile once.
+// Persistent CTAs (two per SM, 256 threads each, where a source tile is at
+// most 32 KB: while one waits at its block barrier the other computes; one
+// per SM with 512 threads for E4M3's 64 KB tiles) walk the tile ids
+// blockIdx.x, blockIdx.x + gridDim.x,
 // ... and keeps the FP32 source tiles of its next NST tiles in flight in a
 // shared-memory ring: one thread issues a 2-D tensor copy per tile (an A tile
 // is 128 rows x BK values, a B tile BK rows x 128 values; the copy fills
@@ -285,8 +288,8 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
 // while all warps power and pack the current tile.  A images leave with
 // coalesced 16-byte stores; B^T images are transposed into a double-buffered
 // shared 16 KB image and written with one bulk copy per tile.
-constexpr int TMA_THREADS = 512;
-constexpr int TMA_MAX_OWNED = 4096;  // tiles per CTA the tensor-copy kernel takes
+constexpr int TMA_CTAS_32K = 2;  // resident CTAs per SM where a source tile is at most 32 KB
+constexpr int TMA_MAX_OWNED = 4096;  // tiles per SM the tensor-copy kernel takes
 
 template <int MODE, bool IS_B>
 struct TmaCfg {
@@ -296,7 +299,10 @@ struct TmaCfg {
   static constexpr int STAGE_BYTES = ROWS * COLS * 4;
   static constexpr int PLANES = MODE == MODE_3XTF32 ? 2 : 1;
   static constexpr int OUT_BYTES = IS_B ? 2 * PLANES * IMG_BYTES : 0;
-  static constexpr int RING_BUDGET = 200 * 1024 - OUT_BYTES;
+  static constexpr int CTAS = STAGE_BYTES <= 32768 ? TMA_CTAS_32K : 1;
+  static constexpr int THREADS = 512 / CTAS;
+  static constexpr int MAX_OWNED = TMA_MAX_OWNED / CTAS;
+  static constexpr int RING_BUDGET = 200 * 1024 / CTAS - OUT_BYTES;
   static constexpr int NST = RING_BUDGET / STAGE_BYTES > 8 ? 8 : RING_BUDGET / STAGE_BYTES;
   static constexpr int SMEM = 1024 + NST * STAGE_BYTES + OUT_BYTES + 8 * NST + 16;
   static_assert(NST >= 2, "ring too small");
@@ -330,13 +336,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst_smem, const CUtensorMap
 }
 
 template <int MODE, bool IS_B>
-__global__ void __launch_bounds__(TMA_THREADS, 1)
+__global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B>::CTAS)
     k_image_tma(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
                 const __grid_constant__ CUtensorMap map) {
   using CF = TmaCfg<MODE, IS_B>;
   using PK = Packer<MODE>;
   constexpr int EPC = PK::EPC;
   constexpr int BK = CF::BK, NST = CF::NST;
+  constexpr int TMA_THREADS = CF::THREADS;
   constexpr int U = 1024 / TMA_THREADS;  // 16-byte image chunks per thread and tile
   extern __shared__ uint8_t smem_dyn[];
   const uint32_t raw = smem_u32(smem_dyn);
@@ -353,8 +360,8 @@ __global__ void __launch_bounds__(TMA_THREADS, 1)
   if (!lv.is_top && *lv.work_count == 0) return;  // no tile pushed to this level (uniform)
   // This CTA's tiles: ids blockIdx.x + k * gridDim.x, k < owned; below the top
   // level only those whose row block (A) or tile column (B) is flagged,
-  // compacted into tile_k[] (the launcher bounds owned by TMA_MAX_OWNED).
-  __shared__ int32_t tile_k[TMA_MAX_OWNED];
+  // compacted into tile_k[] (the launcher bounds owned by CF::MAX_OWNED).
+  __shared__ int32_t tile_k[CF::MAX_OWNED];
   __shared__ int32_t n_tiles;
   if (tid == 0) {
     for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
@@ -575,13 +582,13 @@ int launch_tma_t(const Common& cm, const Level& lv, void* stream, const TensorMa
     attr_done = true;
   }
   const int total = IS_B ? cm.total_xb : cm.total_xa;
-  const int grid = total < sm_count() ? total : sm_count();
-  k_image_tma<MODE, IS_B><<<grid, TMA_THREADS, CF::SMEM, static_cast<cudaStream_t>(stream)>>>(
+  const int grid = total < CF::CTAS * sm_count() ? total : CF::CTAS * sm_count();
+  k_image_tma<MODE, IS_B><<<grid, CF::THREADS, CF::SMEM, static_cast<cudaStream_t>(stream)>>>(
       cm, lv, *reinterpret_cast<const CUtensorMap*>(&map));
   return cudaGetLastError();
 }
 
-// The tensor-copy kernel takes at most TMA_MAX_OWNED tiles per CTA.
+// The tensor-copy kernel takes at most TMA_MAX_OWNED tiles per SM.
 bool tma_fits(int total) { return total <= TMA_MAX_OWNED * sm_count(); }
 
 template <bool IS_B>
