@@ -291,11 +291,22 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
 constexpr int TMA_CTAS_32K = 2;  // resident CTAs per SM where a source tile is at most 32 KB
 constexpr int TMA_MAX_OWNED = 4096;  // tiles per SM the tensor-copy kernel takes
 
+// Source values of K per stage: an image tile whose FP32 source exceeds 32 KB
+// (E4M3: 128 x 128 values) arrives as two halves of K, so that every format
+// keeps 32 KB stages and two CTAs per SM.
+__host__ __device__ constexpr int tma_halves(int mode) {
+  return mode_bk(mode) * TILE_M * 4 > 32768 ? 2 : 1;
+}
+__host__ __device__ constexpr int tma_src_bk(int mode) { return mode_bk(mode) / tma_halves(mode); }
+
 template <int MODE, bool IS_B>
 struct TmaCfg {
   static constexpr int BK = mode_bk(MODE);
-  static constexpr int ROWS = IS_B ? BK : TILE_M;  // source rows per tile
-  static constexpr int COLS = IS_B ? TILE_M : BK;  // source values per row
+  static constexpr int HALVES = tma_halves(MODE);
+  static constexpr int SBK = tma_src_bk(MODE);   // K values per stage
+  static constexpr int CPR = 8 / HALVES;         // 16-byte image chunks per image row and stage
+  static constexpr int ROWS = IS_B ? SBK : TILE_M;  // source rows per stage
+  static constexpr int COLS = IS_B ? TILE_M : SBK;  // source values per row
   static constexpr int STAGE_BYTES = ROWS * COLS * 4;
   static constexpr int PLANES = MODE == MODE_3XTF32 ? 2 : 1;
   static constexpr int OUT_BYTES = IS_B ? 2 * PLANES * IMG_BYTES : 0;
@@ -342,9 +353,9 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
   using CF = TmaCfg<MODE, IS_B>;
   using PK = Packer<MODE>;
   constexpr int EPC = PK::EPC;
-  constexpr int BK = CF::BK, NST = CF::NST;
+  constexpr int BK = CF::BK, NST = CF::NST, H = CF::HALVES, SBK = CF::SBK, CPR = CF::CPR;
   constexpr int TMA_THREADS = CF::THREADS;
-  constexpr int U = 1024 / TMA_THREADS;  // 16-byte image chunks per thread and tile
+  constexpr int U = TILE_M * CPR / TMA_THREADS;  // 16-byte image chunks per thread and stage
   extern __shared__ uint8_t smem_dyn[];
   const uint32_t raw = smem_u32(smem_dyn);
   uint8_t* smem = smem_dyn + (((raw + 1023u) & ~1023u) - raw);
@@ -394,10 +405,12 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
   const int mine = n_tiles;
   if (mine == 0) return;  // uniform
 
-  // thread 0: the tensor copy of this CTA's j-th tile into stage j % NST
+  // thread 0: the tensor copy of this CTA's j-th stage (tile j / H, half
+  // j % H of its K values) into ring slot j % NST
   auto issue = [&](int j) {
-    const int id = (int)blockIdx.x + tile_k[j] * (int)gridDim.x;
+    const int id = (int)blockIdx.x + tile_k[j / H] * (int)gridDim.x;
     const int rb = id / P.KB, kb = id - rb * P.KB;
+    const int k0 = kb * BK + (j % H) * SBK;
     uint64_t* bar = &full[j % NST];
     mbar_arrive_expect_tx(bar, CF::STAGE_BYTES);
     // test hook (debug_flags bit 1): the first tile's bytes are announced but
@@ -405,18 +418,25 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
     if ((cm.debug_flags & 2) && j == 0) return;
     const uint32_t dst = smem_u32(ring) + (j % NST) * CF::STAGE_BYTES;
     if constexpr (!IS_B)
-      tma_load_2d(dst, &map, kb * BK, rb * TILE_M, bar);
+      tma_load_2d(dst, &map, k0, rb * TILE_M, bar);
     else
-      tma_load_2d(dst, &map, rb * TILE_M, kb * BK, bar);
+      tma_load_2d(dst, &map, rb * TILE_M, k0, bar);
   };
 
-  // A: thread = image chunks (row (tid >> 3) + (128 / U) u, slot tid & 7).
-  // B: warp w = slot w & 7 of image rows nr = lane + 32 (U (w >> 3) + u),
-  // i.e. contraction indices (w & 7) EPC + e of column rb 128 + nr.
-  const int cc = IS_B ? (warp & 7) : (tid & 7);
+  // A: thread = image chunks (row tid / CPR + (128 / U) u, slot tid % CPR of
+  // the stage's CPR).  B: warp w = slot w % CPR of image rows nr = lane + 32
+  // (U (w / CPR) + u), i.e. contraction indices (w % CPR) EPC + e of column
+  // rb 128 + nr.  The slot's chunk of the image row is ccl + CPR h for the
+  // stage's half h.
+  const int ccl = IS_B ? (warp % CPR) : (tid % CPR);
   auto line = [&](int u) {  // this thread's image row of chunk u
-    return IS_B ? lane + 32 * (U * (warp >> 3) + u) : (tid >> 3) + (TILE_M / U) * u;
+    return IS_B ? lane + 32 * (U * (warp / CPR) + u) : tid / CPR + (TILE_M / U) * u;
   };
+  // shared-memory reads of a staged A row: the 8 threads of a quarter warp
+  // (8 / CPR rows, CPR slots) rotate their float4 order so that they hit
+  // distinct banks
+  const int rot = (ccl * (EPC / 4) / 8 + (tid / CPR) % (8 / CPR) * (EPC / 4) * CPR / 8) &
+                  (EPC / 4 - 1);
   // the maxima behind this thread's U row (A) or column (B) scales of tile
   // j, loaded one tile ahead of their use
   uint32_t pre[U];
@@ -433,40 +453,45 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
   };
 
   const uint64_t tmo = cm.timeout_ns;
+  const int nj = mine * H;  // stages of this CTA
   if (tid == 0)
-    for (int j = 0; j < NST && j < mine; ++j) issue(j);
+    for (int j = 0; j < NST && j < nj; ++j) issue(j);
   prefetch(0);
   const float opscale = ldexpf(1.0f, cm.s_op);
+  float sc[U];
   int j = 0;
-  for (; j < mine; ++j) {
+  for (; j < nj; ++j) {
     const int s = j % NST;
     if (tid == 0 && !mbar_wait(&full[s], (j / NST) & 1, tmo, abort_flag)) {
       *abort_flag = 1;
       set_status(cm.status, PN_ETIMEOUT);
     }
-    __syncthreads();  // also: the shared B image (j & 1) is free again
+    __syncthreads();  // also: the shared B image ((j / H) & 1) is free again
     if (*abort_flag) break;
-    const int id = (int)blockIdx.x + tile_k[j] * (int)gridDim.x;
+    const int tj = j / H, h = j % H;
+    const int id = (int)blockIdx.x + tile_k[tj] * (int)gridDim.x;
     const int rb = id / P.KB, kb = id - rb * P.KB;
+    const int cc = ccl + CPR * h;  // this thread's chunk of the image row
     const float* st = ring + s * (CF::STAGE_BYTES / 4);
-    float sc[U];
+    if (h == 0) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) sc[u] = scale_from_bits(cm, pre[u]);
-    if (j + 1 < mine) prefetch(j + 1);
+      for (int u = 0; u < U; ++u) sc[u] = scale_from_bits(cm, pre[u]);
+      if (tj + 1 < mine) prefetch(tj + 1);
+    }
     float v[U][EPC];  // the copy filled zeros past M, N and K
     if constexpr (!IS_B) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        lds_rotated<EPC / 4>(st + line(u) * BK + cc * EPC, (cc * (EPC / 4) / 8) & (EPC / 4 - 1),
-                             v[u]);
-      power_a_store<MODE, U>(cm, lv, P, rb, kb, v, sc, threadIdx.x);
+      for (int u = 0; u < U; ++u) lds_rotated<EPC / 4>(st + line(u) * SBK + ccl * EPC, rot, v[u]);
+      // power_a_store's mapping (row t / 8 + (128 / U) u, chunk t % 8) for
+      // this thread's rows and chunk
+      power_a_store<MODE, U>(cm, lv, P, rb, kb, v, sc, (tid / CPR) * 8 + cc);
     } else {
-      uint8_t* ob = outimg + (j & 1) * CF::PLANES * IMG_BYTES;
+      uint8_t* ob = outimg + (tj & 1) * CF::PLANES * IMG_BYTES;
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int nr = line(u);
 #pragma unroll
-        for (int e = 0; e < EPC; ++e) v[u][e] = st[(cc * EPC + e) * TILE_M + nr];
+        for (int e = 0; e < EPC; ++e) v[u][e] = st[(ccl * EPC + e) * TILE_M + nr];
         if (lv.is_top && kb == 0 && cc == 0 && rb * TILE_M + nr < P.N)
           cm.c[P.rc_c + rb * TILE_M + nr] = sc[u];
       }
@@ -486,20 +511,22 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
     __syncthreads();  // stage s is consumed; the shared B image is complete
     if (tid == 0) {
       if constexpr (IS_B) {
-        uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
-        const uint32_t src = smem_u32(outimg + (j & 1) * CF::PLANES * IMG_BYTES);
-        bulk_s2g(dst, src, IMG_BYTES);
-        if constexpr (CF::PLANES == 2) bulk_s2g(dst + P.b_plane, src + IMG_BYTES, IMG_BYTES);
-        bulk_commit();
-        bulk_wait_read<1>();  // the image of tile j - 1 has been read out
+        if (h == H - 1) {
+          uint8_t* dst = lv.b_level + P.b_img + ((int64_t)(rb * P.KB + kb) << 14);
+          const uint32_t src = smem_u32(outimg + (tj & 1) * CF::PLANES * IMG_BYTES);
+          bulk_s2g(dst, src, IMG_BYTES);
+          if constexpr (CF::PLANES == 2) bulk_s2g(dst + P.b_plane, src + IMG_BYTES, IMG_BYTES);
+          bulk_commit();
+          bulk_wait_read<1>();  // the image of tile tj - 1 has been read out
+        }
       }
-      if (j + NST < mine) issue(j + NST);
+      if (j + NST < nj) issue(j + NST);
     }
   }
   if (tid == 0) {
-    if (j < mine) {  // gave up: let the copies in flight land before exiting
+    if (j < nj) {  // gave up: let the copies in flight land before exiting
       int32_t never = 0;
-      const int last = mine < j + NST ? mine : j + NST;
+      const int last = nj < j + NST ? nj : j + NST;
       for (int t = j; t < last; ++t) mbar_wait(&full[t % NST], (t / NST) & 1, tmo, &never);
     }
     if constexpr (IS_B) bulk_wait_all();
@@ -956,7 +983,7 @@ void make_operand_maps(const Common& cm, OperandMaps& maps) {
   std::memset(&maps, 0, sizeof(maps));
   if (cm.nprob != 1) return;
   const Prob& P = cm.single;
-  const int bk = mode_bk(cm.mode);
+  const int bk = tma_src_bk(cm.mode);  // K values per stage of the tensor-copy kernel
   maps.has_a = encode_fp32_2d(maps.a, P.A, P.M, P.K, P.lda, TILE_M, bk) ? 1 : 0;
   maps.has_b = encode_fp32_2d(maps.b, P.B, P.K, P.N, P.ldb, bk, TILE_M) ? 1 : 0;
 }
