@@ -277,18 +277,18 @@ __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
 
 // ------------------------------------------------ TMA top-level images ---
 // The top level of a single product builds every operand tile once.
-// Persistent CTAs (two per SM, 256 threads each, where a source tile is at
-// most 32 KB: while one waits at its block barrier the other computes; one
-// per SM with 512 threads for E4M3's 64 KB tiles) walk the tile ids
-// blockIdx.x, blockIdx.x + gridDim.x,
-// ... and keeps the FP32 source tiles of its next NST tiles in flight in a
-// shared-memory ring: one thread issues a 2-D tensor copy per tile (an A tile
+// Persistent CTAs (two per SM, 256 threads each: while one waits at its
+// block barrier the other computes) walk the tile ids blockIdx.x,
+// blockIdx.x + gridDim.x, ... and keep the FP32 sources of their next NST
+// stages in flight in a shared-memory ring (a stage is a tile, or half of
+// the K values of a tile whose source exceeds 32 KB: E4M3); one thread
+// issues a 2-D tensor copy per stage (an A tile
 // is 128 rows x BK values, a B tile BK rows x 128 values; the copy fills
 // zeros past M, N and K), completion counted in bytes on the stage's mbarrier,
 // while all warps power and pack the current tile.  A images leave with
 // coalesced 16-byte stores; B^T images are transposed into a double-buffered
 // shared 16 KB image and written with one bulk copy per tile.
-constexpr int TMA_CTAS_32K = 2;  // resident CTAs per SM where a source tile is at most 32 KB
+constexpr int TMA_CTAS_32K = 2;  // resident CTAs per SM with stages of at most 32 KB (every format)
 constexpr int TMA_MAX_OWNED = 4096;  // tiles per SM the tensor-copy kernel takes
 
 // Source values of K per stage: an image tile whose FP32 source exceeds 32 KB
