@@ -152,6 +152,18 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the kernel before it in the stream still
+// runs; pdl_wait() returns once that kernel (and, transitively, everything
+// before it) has completed and its memory is visible (a no-op for a normal
+// launch).  Every kernel of the product path calls it before touching global
+// memory, then pdl_trigger() lets the next kernel's CTAs be scheduled, so
+// their launch overlaps this kernel's run instead of following its end.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));

@@ -1106,6 +1106,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                  const __grid_constant__ MapsArg<CG> maps) {
   static_assert(num_stages(MODE, BN, CG) >= 2, "operand ring too small");
   static_assert(CG == 1 || (BN == 256 && EPI == 0), "CTA pairs: 256 x 256 p-norm tiles");
+  pdl_wait();
+  pdl_trigger();
   if constexpr (EPI == 1) {
     if (!((*lv.pmask >> lv.q) & 1u)) return;  // no entry selected this p
   }
@@ -1160,9 +1162,9 @@ inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream
   if (e) return e;
   int grid = cm.total_tiles < num_sms ? cm.total_tiles : num_sms;
   if (grid < 1) return 0;
-  k_gemm_level<MODE, BN, EPI><<<grid, GEMM_THREADS, smem_total(MODE, BN),
-                           static_cast<cudaStream_t>(stream)>>>(cm, lv, NoMaps{});
-  return cudaGetLastError();
+  const cudaError_t le = launch_pdl(k_gemm_level<MODE, BN, EPI>, dim3(grid), dim3(GEMM_THREADS),
+                                    smem_total(MODE, BN), stream, cm, lv, NoMaps{});
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 // A CTA pair per 256 x 256 output tile (cta_group::2): clusters of two CTAs,
@@ -1175,13 +1177,15 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
   cfg.blockDim = dim3(GEMM_THREADS);
   cfg.dynamicSmemBytes = smem_total(MODE, 256, 2);
   cfg.stream = static_cast<cudaStream_t>(stream);
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see launch_pdl
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 1;  // the occupancy query below sees the cluster shape only
   // A pair needs two SMs of one GPC; with an odd number of SMs in a GPC fewer
   // than num_sms / 2 pairs fit at once.  The tile walk is persistent (each
   // pair strides over the tiles), so a pair that is not resident would start
@@ -1206,6 +1210,7 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
   const int clusters = cm.total_tiles < pairs ? cm.total_tiles : pairs;
   if (clusters < 1) return 0;
   cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
+  cfg.numAttrs = 2;
   // the operand-image regions as tensors of 128-byte rows (the pair's copies
   // complete on rank 0's barriers, which only tensor copies can address)
   ImgMaps maps;

@@ -247,6 +247,25 @@ double host_default_tau(int64_t K, int compute);
 float host_tau_up(double t);                // smallest float >= t
 int host_tuned_bn(int mode, int64_t M, int64_t N, int64_t K);  // autotune cache, 0 if none
 
+// Launch with programmatic stream serialisation (the kernel must call
+// pdl_wait() before it touches global memory): its CTAs may be scheduled as
+// soon as every CTA of the previous kernel has called pdl_trigger().
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              void* stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------ launchers ---
 // All return a cudaError_t value as int (0 = success).
 // Tensor maps (CUtensorMap, 128 opaque bytes) of the FP32 operands of a

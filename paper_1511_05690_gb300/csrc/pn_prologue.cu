@@ -22,6 +22,8 @@ namespace pn {
 namespace {
 
 __global__ void __launch_bounds__(PRO_THREADS) k_maxes(const __grid_constant__ Common cm) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ uint32_t red[8][128];
   __shared__ float blk_max[PRO_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -350,6 +352,8 @@ template <int MODE, bool IS_B>
 __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B>::CTAS)
     k_image_tma(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
                 const __grid_constant__ CUtensorMap map) {
+  pdl_wait();
+  pdl_trigger();
   using CF = TmaCfg<MODE, IS_B>;
   using PK = Packer<MODE>;
   constexpr int EPC = PK::EPC;
@@ -610,9 +614,9 @@ int launch_tma_t(const Common& cm, const Level& lv, void* stream, const TensorMa
   }
   const int total = IS_B ? cm.total_xb : cm.total_xa;
   const int grid = total < CF::CTAS * sm_count() ? total : CF::CTAS * sm_count();
-  k_image_tma<MODE, IS_B><<<grid, CF::THREADS, CF::SMEM, static_cast<cudaStream_t>(stream)>>>(
-      cm, lv, *reinterpret_cast<const CUtensorMap*>(&map));
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_image_tma<MODE, IS_B>, dim3(grid), dim3(CF::THREADS), CF::SMEM,
+                                   stream, cm, lv, *reinterpret_cast<const CUtensorMap*>(&map));
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // The tensor-copy kernel takes at most TMA_MAX_OWNED tiles per SM.
@@ -960,8 +964,8 @@ int launch_strips(const Common& cm, const Level& lv, void* stream) {
 int launch_maxes(const Common& cm, void* stream) {
   const int blocks = cm.total_ma + cm.total_mb;
   if (blocks <= 0) return 0;
-  k_maxes<<<blocks, PRO_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(cm);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_maxes, dim3(blocks), dim3(PRO_THREADS), 0, stream, cm);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes) {
