@@ -27,6 +27,8 @@ struct PList {
 
 __global__ void k_bw_mask(const uint8_t* __restrict__ psel, int64_t count, PList pl,
                           uint32_t* mask) {
+  pdl_wait();
+  pdl_trigger();
   uint32_t bits = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -40,6 +42,8 @@ __global__ void k_bw_mask(const uint8_t* __restrict__ psel, int64_t count, PList
 
 // Row and column scales from the maxima (same rule as the forward).
 __global__ void k_scales(const __grid_constant__ Common cm) {
+  pdl_wait();
+  pdl_trigger();
   const Prob& P = cm.single;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)P.M + P.N;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -71,6 +75,8 @@ __device__ __forceinline__ float bw_value(const BwImage& im, int64_t srow, int64
 // One 16 KB tile image (128 image rows x 128 bytes of contraction) per block.
 template <int MODE, int TRANS, int KIND>
 __global__ void __launch_bounds__(BW_THREADS) k_bw_image(const __grid_constant__ BwImage im) {
+  pdl_wait();
+  pdl_trigger();
   using PK = Packer<MODE>;
   constexpr int EPC = PK::EPC;
   constexpr int BK = mode_bk(MODE);
@@ -123,9 +129,9 @@ int launch_img_t(const BwImage& im, void* stream) {
   }
   const int blocks = im.RB * im.KB;
   if (blocks <= 0) return 0;
-  k_bw_image<MODE, TRANS, KIND>
-      <<<blocks, BW_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(im);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_bw_image<MODE, TRANS, KIND>, dim3(blocks), dim3(BW_THREADS),
+                                   smem, stream, im);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int MODE>
@@ -145,9 +151,9 @@ int launch_bw_mask(const uint8_t* psel, int64_t count, const int32_t* plog_list,
   for (int q = 0; q < n_p; ++q) pl.plog[q] = plog_list[q];
   int64_t blocks = (count + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_bw_mask<<<static_cast<int>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(psel, count,
-                                                                                    pl, mask);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_bw_mask, dim3(static_cast<unsigned>(blocks)), dim3(256), 0,
+                                   stream, psel, count, pl, mask);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int launch_scales(const Common& cm, void* stream) {
@@ -155,8 +161,9 @@ int launch_scales(const Common& cm, void* stream) {
   if (total <= 0) return 0;
   int64_t blocks = (total + 255) / 256;
   if (blocks > 1024) blocks = 1024;
-  k_scales<<<static_cast<int>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(cm);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_scales, dim3(static_cast<unsigned>(blocks)), dim3(256), 0,
+                                   stream, cm);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int launch_bw_image(int mode, const BwImage& im, void* stream) {

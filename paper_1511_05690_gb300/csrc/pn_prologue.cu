@@ -219,6 +219,8 @@ constexpr int img_min_blocks() {
 template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_a(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
+  pdl_wait();
+  pdl_trigger();
   if (lv.is_top) {
     const int id = blockIdx.x;
     const int g = find_prob(cm, id, 1);
@@ -251,6 +253,8 @@ template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS, img_min_blocks<MODE>())
     k_power_b(const __grid_constant__ Common cm, const __grid_constant__ Level lv) {
   extern __shared__ float stile[];  // [BK][129]
+  pdl_wait();
+  pdl_trigger();
   if (lv.is_top) {
     const int id = blockIdx.x;
     const int g = find_prob(cm, id, 2);
@@ -541,6 +545,8 @@ __global__ void __launch_bounds__(TmaCfg<MODE, IS_B>::THREADS, TmaCfg<MODE, IS_B
 // Empty contraction: every S^(p) is 0, so p* is the smallest p (unstable)
 // and the estimate is the exact empty max, 0.
 __global__ void k_fill_empty(const __grid_constant__ Common cm, int plog0) {
+  pdl_wait();
+  pdl_trigger();
   const Prob& P = cm.single;
   const int64_t total = (int64_t)P.M * P.N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -556,6 +562,8 @@ __global__ void k_fill_empty(const __grid_constant__ Common cm, int plog0) {
 // x = exp(-w) (Sec. 2.2), +inf -> 0; weights must be >= 0 or +inf.
 __global__ void k_apsp_init(int64_t n, const float* __restrict__ W, int64_t ldw,
                             float* __restrict__ X, int diag, int32_t* status) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = n * n;
   bool bad = false;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -572,6 +580,8 @@ __global__ void k_apsp_init(int64_t n, const float* __restrict__ W, int64_t ldw,
 
 // d = -log x; x = 0 (no path) -> +inf.
 __global__ void k_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t total = n * n;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -684,8 +694,8 @@ int launch_power_b_t(const Common& cm, const Level& lv, void* stream) {
     attr_done = true;
   }
   const int grid = lv.is_top ? cm.total_xb : lower_grid(cm.total_xb, img_min_blocks<MODE>());
-  k_power_b<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(cm, lv);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_power_b<MODE>, dim3(grid), dim3(PRO_THREADS), smem, stream, cm, lv);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int grid_for(int64_t total, int threads) {
@@ -912,6 +922,8 @@ template <int MODE>
 __global__ void __launch_bounds__(PRO_THREADS)
     k_strips(const __grid_constant__ Common cm, const __grid_constant__ Level lv, int n_a) {
   extern __shared__ __align__(16) float sm_strip[];
+  pdl_wait();
+  pdl_trigger();
   const int unit = static_cast<int>(blockIdx.x);
   constexpr int SM_FLOATS = strip_smem<MODE>() / 4 - 288;
   uint32_t* red = reinterpret_cast<uint32_t*>(sm_strip + SM_FLOATS);
@@ -942,8 +954,9 @@ int launch_strips_t(const Common& cm, const Level& lv, void* stream) {
   }
   const int n_a = 4 * cm.total_tm;
   const int grid = n_a + 4 * cm.total_tn * (cm.BN / TILE_M);
-  k_strips<MODE><<<grid, PRO_THREADS, smem, static_cast<cudaStream_t>(stream)>>>(cm, lv, n_a);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_strips<MODE>, dim3(grid), dim3(PRO_THREADS), smem, stream, cm,
+                                   lv, n_a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace
@@ -995,27 +1008,32 @@ void make_operand_maps(const Common& cm, OperandMaps& maps) {
 int launch_power_a(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
   if (cm.total_xa <= 0) return 0;
   if (maps && maps->has_a && tma_fits(cm.total_xa)) return launch_tma<false>(cm, lv, stream, maps->a);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   auto grid = [&](int per_sm) { return lv.is_top ? cm.total_xa : lower_grid(cm.total_xa, per_sm); };
+  cudaError_t e = cudaSuccess;
   switch (cm.mode) {
     case MODE_3XTF32:
-      k_power_a<MODE_3XTF32><<<grid(img_min_blocks<MODE_3XTF32>()), PRO_THREADS, 0, s>>>(cm, lv);
+      e = launch_pdl(k_power_a<MODE_3XTF32>, dim3(grid(img_min_blocks<MODE_3XTF32>())), dim3(PRO_THREADS), 0,
+                     stream, cm, lv);
       break;
     case MODE_TF32:
-      k_power_a<MODE_TF32><<<grid(img_min_blocks<MODE_TF32>()), PRO_THREADS, 0, s>>>(cm, lv);
+      e = launch_pdl(k_power_a<MODE_TF32>, dim3(grid(img_min_blocks<MODE_TF32>())), dim3(PRO_THREADS), 0,
+                     stream, cm, lv);
       break;
     case MODE_BF16:
-      k_power_a<MODE_BF16><<<grid(img_min_blocks<MODE_BF16>()), PRO_THREADS, 0, s>>>(cm, lv);
+      e = launch_pdl(k_power_a<MODE_BF16>, dim3(grid(img_min_blocks<MODE_BF16>())), dim3(PRO_THREADS), 0,
+                     stream, cm, lv);
       break;
     case MODE_F16:
-      k_power_a<MODE_F16><<<grid(img_min_blocks<MODE_F16>()), PRO_THREADS, 0, s>>>(cm, lv);
+      e = launch_pdl(k_power_a<MODE_F16>, dim3(grid(img_min_blocks<MODE_F16>())), dim3(PRO_THREADS), 0,
+                     stream, cm, lv);
       break;
     case MODE_E4M3:
-      k_power_a<MODE_E4M3><<<grid(img_min_blocks<MODE_E4M3>()), PRO_THREADS, 0, s>>>(cm, lv);
+      e = launch_pdl(k_power_a<MODE_E4M3>, dim3(grid(img_min_blocks<MODE_E4M3>())), dim3(PRO_THREADS), 0,
+                     stream, cm, lv);
       break;
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int launch_power_b(const Common& cm, const Level& lv, void* stream, const OperandMaps* maps) {
@@ -1034,24 +1052,25 @@ int launch_power_b(const Common& cm, const Level& lv, void* stream, const Operan
 int launch_fill_empty(const Common& cm, int plog0, void* stream) {
   const int64_t total = (int64_t)cm.single.M * cm.single.N;
   if (total <= 0) return 0;
-  k_fill_empty<<<grid_for(total, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(cm, plog0);
-  return cudaGetLastError();
+  const cudaError_t e =
+      launch_pdl(k_fill_empty, dim3(grid_for(total, 256)), dim3(256), 0, stream, cm, plog0);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int launch_apsp_init(int64_t n, const float* W, int64_t ldw, float* X, int diag, int32_t* status,
                      void* stream) {
   if (n <= 0) return 0;
-  k_apsp_init<<<grid_for(n * n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, W, ldw, X,
-                                                                                 diag, status);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_apsp_init, dim3(grid_for(n * n, 256)), dim3(256), 0, stream, n,
+                                   W, ldw, X, diag, status);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 int launch_apsp_final(int64_t n, const float* X, int64_t ldx, float* D, int64_t ldd,
                       void* stream) {
   if (n <= 0) return 0;
-  k_apsp_final<<<grid_for(n * n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, X, ldx, D,
-                                                                                  ldd);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(k_apsp_final, dim3(grid_for(n * n, 256)), dim3(256), 0, stream,
+                                   n, X, ldx, D, ldd);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace pn
