@@ -174,9 +174,8 @@ typedef struct pn_opts {
    * 128-row half of A and of B and the pair's MMA reads both, so each SM
    * moves a third less operand data per result); 0 = automatic (pairs for
    * M and N >= 256, or the autotuner's choice).  Pairs serve maxprod_pnorm,
-   * maxprod_pnorm_static and apsp_pnorm with estimator 0 or 1 and tile_n 0
-   * or 256; otherwise, and for the grouped call and the adjoint, tiles are
-   * 128 rows high. */
+   * maxprod_pnorm_static and apsp_pnorm with tile_n 0 or 256; otherwise,
+   * and for the grouped call and the adjoint, tiles are 128 rows high. */
   int32_t tile_m;
 } pn_opts;
 

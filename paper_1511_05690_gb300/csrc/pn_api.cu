@@ -68,7 +68,7 @@ bool opts_valid(const pn_opts* o) {
 // A CTA pair (cta_group::2) per 256 x 256 tile, or one CTA per tile.  The
 // autotune cache records a pair as 512.
 int choose_cg(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
-  if (o->tile_m == 128 || o->estimator == 2 || o->tile_n == 128) return 1;
+  if (o->tile_m == 128 || o->tile_n == 128) return 1;
   if (o->tile_m == 256) return 2;
   const int tuned = host_tuned_bn(o->compute, M, N, K);
   if (tuned) return tuned == 512 ? 2 : 1;

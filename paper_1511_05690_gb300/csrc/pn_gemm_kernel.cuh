@@ -1077,11 +1077,27 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
             }
           }
           // r = 2: a tile that starts no chain here skips the half level
-          const bool skip = lv.skip_work && !bar_red_or(new_chain, 1 + NG + grp, gthreads);
-          // a pair's tile is pushed once, by whichever half claims it first
+          const bool chain = lv.skip_work && bar_red_or(new_chain, 1 + NG + grp, gthreads);
+          bool skip = lv.skip_work && !chain;
           bool push = et == 0 && tile_left;
-          if constexpr (CG == 2)
-            if (push) push = atomicCAS(lv.pair_pushed + t, 0u, 1u) == 0u;
+          if constexpr (CG == 2) {
+            // a pair's tile is pushed once, with both halves' decisions: each
+            // half adds its bits (entries left, a chain started) in its own
+            // field and one arrival; the second to arrive pushes if either
+            // half has entries left, to the half level if either started a
+            // chain
+            push = false;
+            if (et == 0) {
+              const uint32_t mine = (tile_left ? 1u : 0u) | (chain ? 2u : 0u);
+              const uint32_t old =
+                  atomicAdd(lv.pair_pushed + t, (1u << 8) | (mine << (2 * cx.rank)));
+              if ((old >> 8) != 0u) {
+                const uint32_t both = mine | ((old >> (2 * (cx.rank ^ 1u))) & 3u);
+                push = (both & 1u) != 0u;
+                skip = lv.skip_work && (both & 2u) == 0u;
+              }
+            }
+          }
           if (push) {
             int32_t* cnt = skip ? lv.skip_count : lv.next_count;
             const int slot = atomicAdd(cnt, 1);

@@ -77,6 +77,21 @@ def test_pairs_projection_r1(pn, orc):
     assert np.all(err <= tol), float(err.max())
 
 
+@pytest.mark.parametrize("mode", ["f32", "bf16"])
+def test_pairs_projection_r2_equals_single(pn, mode):
+    """The r = 2 projection with pairs: the two halves of a pair tile decide
+    together whether it visits the half level (either half started a chain),
+    and the results equal the single-CTA run bit for bit over several levels
+    (a half without chains at a half level parks nothing)."""
+    A, B = _multilevel_inputs(384, 520, 200, seed=4300)
+    dA, dB = _dev(A), _dev(B)
+    r2 = pn.maxprod_pnorm(dA, dB, compute=mode, estimator=2, tile_m=256)
+    r1 = pn.maxprod_pnorm(dA, dB, compute=mode, estimator=2, tile_m=128)
+    for x2, x1 in zip(r2, r1):
+        assert torch.equal(x2, x1)
+    assert len(torch.unique(r2[1] & 0x7F)) >= 2
+
+
 def test_pairs_apsp_matches_single(pn, orc):
     """APSP squarings (diagonal reset and clamp in the epilogue) with pairs:
     the same distances as with single CTAs within the per-squaring bar."""
