@@ -12,12 +12,15 @@
 // mask of its resolved entries, and only those tiles are recomputed at the
 // next p.  The smallest p resolves whatever is left (flagged unstable).
 //
-// Kernel structure (one persistent CTA per SM, 10 warps):
-//   warp 0      one thread issues 1-D bulk copies of pre-swizzled 16 KB
-//               operand tile images into a STAGES-deep shared-memory ring
-//               (192 KB);
-//   warp 1      allocates TMEM (two accumulators of 128 x BN FP32) and one
-//               thread issues tcgen05.mma (M=128, N=BN, 32 bytes of K each);
+// Kernel structure (one persistent CTA per SM, 10 warps; or a CTA pair per
+// 256 x 256 tile, cta_group::2):
+//   warp 0      one thread issues copies of pre-swizzled 16 KB operand tile
+//               images into a STAGES-deep shared-memory ring (192 KB): 1-D
+//               bulk copies, or for a pair 2-D tensor copies completing on
+//               rank 0's barrier;
+//   warp 1      allocates TMEM (all 512 columns: 512 / BN accumulators of
+//               128 x BN FP32) and one thread issues tcgen05.mma (M = 128,
+//               or 256 over a pair; N = BN; 32 bytes of K each);
 //   warps 2-9   epilogue: tcgen05.ld of the accumulator (lane = output row),
 //               tau test, root, un-scaling, and stores staged through a 4 KB
 //               shared buffer per warp so that global writes are whole
@@ -28,8 +31,8 @@
 //               each.  The projection estimators (Sec. 2.1) park sums in C
 //               and the workspace and finish them at a lower level, walking
 //               each warp's 32 x 32 block row by row.
-// The accumulator is double-buffered so the epilogue of one tile overlaps the
-// MMAs of the next.  Every wait is bounded (PN_ETIMEOUT on expiry).
+// The accumulators rotate so the epilogue of one tile overlaps the MMAs of
+// the next ones.  Every wait is bounded (PN_ETIMEOUT on expiry).
 #include "pn_gemm_kernel.cuh"
 
 namespace pn {

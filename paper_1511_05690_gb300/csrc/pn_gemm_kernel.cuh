@@ -15,7 +15,7 @@ namespace gemm {
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_THREADS = EPI_WARPS * 32;
 constexpr int GEMM_THREADS = 64 + EPI_THREADS;     // producer, MMA, epilogue
-constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring (two epilogue groups)
+constexpr int SMEM_STAGE_BUDGET = 196608;  // bytes of the operand ring with two epilogue groups
 constexpr int STG_BYTES = 4096;  // per epilogue warp: a 32 x 32 FP32 block for the transposed stores
 
 // Bytes of one ring stage: the A image tile and this CTA's B image tiles of
