@@ -700,7 +700,9 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
 // out (+)= acc * x'^(p-1) / s with x the source element at the output position
 // and s its row (grad_axis 0) or column (1) scale; the first p present
 // overwrites, later ones add.
-template <int MODE, int BN, int EPI, int CG = 1, int NG = 2>
+// PLAIN: the plain estimator only (no projection state, no parked sums, no
+// affine line), compiled without those paths for launches that never take them.
+template <int MODE, int BN, int EPI, int CG = 1, int NG = 2, bool PLAIN = false>
 __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, const Ctx& cx,
                                              int count, bool by_tile, int it0, const Ready& rd) {
   constexpr int PLANES = mode_planes(MODE);
@@ -797,7 +799,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       // or the affine line of this level's class
       float corr_a = 1.0f, corr_b = 0.0f;
       if (EPI == 0 && cm.corr == 1) corr_a = exp2f(-log2f(static_cast<float>(P.K)) * inv_p);
-      if (EPI == 0 && cm.corr == 2) {
+      if (EPI == 0 && !PLAIN && cm.corr == 2) {
         corr_a = cm.coef[2 * lv.q];
         corr_b = cm.coef[2 * lv.q + 1];
       }
@@ -916,8 +918,8 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
           // r = 1 projection (Sec. 2.1): entries resolved at 2p hold S^(2p) in C;
           // with S^(p) from this level the estimate is (S^(2p) / S^(p))^(1/p).
           // The ratio is clamped to <= 1 (S is non-increasing in p).
-          const uint32_t pend = lv.proj_here && row_ok ? cm.pend[st_idx + hc] : 0u;
-          if (lv.proj_here && __any_sync(0xffffffffu, pend != 0u)) {
+          const uint32_t pend = !PLAIN && lv.proj_here && row_ok ? cm.pend[st_idx + hc] : 0u;
+          if (!PLAIN && lv.proj_here && __any_sync(0xffffffffu, pend != 0u)) {
             const float cs_lane = lane < PN - j0 ? __ldg(cm.c + Prc_c + j0 + lane) : 0.0f;
             // the affine line of p*'s class (the level above)
             const bool affine = cm.corr == 2;
@@ -927,14 +929,14 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
                 stg, x, pend, rs, PC + ((int64_t)tm * TILE_M + quarter * 32) * Pldc + j0, Pldc,
                 cs_lane, lv.plog, inv_p, affine, pa, pb, lane);
           }
-          if (lv.proj_next) {
+          if (!PLAIN && lv.proj_next) {
             any_left |= cand != 0u;  // their S^(p/2) comes from the next level
             pend_all[hc] = cand;
           }
           // r = 2 projection (Sec. 2.1): entries resolved at p* wait, in stages
           // 1..3, for S^(3p*/4) (half level), S^(p*/2) and S^(p*/4); C keeps
           // S^(p*), the two middle sums are parked in the workspace
-          if (lv.r2_state || lv.r2_new) {
+          if (!PLAIN && (lv.r2_state || lv.r2_new)) {
             uint32_t b0 = 0, b1 = 0;
             if (lv.r2_state && row_ok) {
               b0 = cm.pend[st_idx + hc];
@@ -991,7 +993,7 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
               warp_store_f32(stg, x, cand, PSsel + ibase * Pldaux + j0, Pldaux, Pvec, lane);
             // a projection still to come (r = 1: level p/2 below; r = 2: the
             // chain down to p/4): C keeps S^(p) until then
-            if (!lv.proj_next && !lv.r2_new) {
+            if (PLAIN || (!lv.proj_next && !lv.r2_new)) {
               if constexpr (MODE == MODE_3XTF32) {
                 // FP32-accurate mode: (S^(p))^(1/p) for p = 2^plog as plog correctly
                 // rounded square roots (about one ulp in total); repeated APSP
@@ -1065,19 +1067,19 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
 #pragma unroll
             for (int hc = 0; hc < CHUNKS; ++hc)
               if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) st_w[hc] = res_all[hc];
-            if (cm.pend) {
+            if (!PLAIN && cm.pend) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
                 if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend[st_idx + hc] = pend_all[hc];
             }
-            if (cm.pend2) {
+            if (!PLAIN && cm.pend2) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
                 if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend2[st_idx + hc] = pend2_all[hc];
             }
           }
           // r = 2: a tile that starts no chain here skips the half level
-          const bool chain = lv.skip_work && bar_red_or(new_chain, 1 + NG + grp, gthreads);
+          const bool chain = !PLAIN && lv.skip_work && bar_red_or(new_chain, 1 + NG + grp, gthreads);
           bool skip = lv.skip_work && !chain;
           bool push = et == 0 && tile_left;
           if constexpr (CG == 2) {

@@ -367,6 +367,7 @@ static pn_status run_group(const GroupHeader* H, const void* dev_table, int l, c
   // kernel too.
   const bool top_inside = persist && (o->debug_flags & 8);
   gr.maxima = top_inside ? 1 : 0;
+  gr.plain = (H->estimator == 0 && o->correction != 2) ? 1 : 0;
   gr.top_built = top_inside ? 0 : 1;
   if (!persist && launch_maxes(cm, stream)) return PN_ECUDA;
   for (int q = o->n_p - 1; q >= 0; --q) {

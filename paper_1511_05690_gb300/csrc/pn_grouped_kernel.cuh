@@ -36,7 +36,7 @@ constexpr int IMG_BAR = 15;  // named barrier of the block builders (warps 2-9)
 __host__ __device__ constexpr int grouped_ng(int BN) { return BN == 128 ? 3 : 2; }
 __host__ __device__ constexpr int grouped_threads(int BN) { return 64 + 128 * grouped_ng(BN); }
 
-template <int MODE, int BN>
+template <int MODE, int BN, bool PLAIN>
 __global__ void __launch_bounds__(grouped_threads(BN), 1)
     k_grouped_persist(const __grid_constant__ Common cm, const __grid_constant__ GroupedRun gr) {
   constexpr int NG = grouped_ng(BN);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(grouped_threads(BN), 1)
       if (lane == 0) run_mma<MODE, BN, 1, NG>(cm, lv, cx, count, it0, ms);
       __syncwarp();
     } else {
-      run_epilogue<MODE, BN, 0, 1, NG>(cm, lv, cx, count, true, it0, rd);
+      run_epilogue<MODE, BN, 0, 1, NG, PLAIN>(cm, lv, cx, count, true, it0, rd);
     }
     if (count > static_cast<int>(blockIdx.x)) it0 += (count - 1 - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x) + 1;
     __syncthreads();
@@ -129,12 +129,12 @@ __global__ void __launch_bounds__(grouped_threads(BN), 1)
   ctx_teardown<BN>(cx);
 }
 
-template <int MODE, int BN>
-inline int launch_grouped_persist_t(const Common& cm, const GroupedRun& gr, int num_sms,
+template <int MODE, int BN, bool PLAIN>
+inline int launch_grouped_persist_k(const Common& cm, const GroupedRun& gr, int num_sms,
                                     void* stream) {
   static int attr_done = 0;
   if (!attr_done) {
-    const cudaError_t e = cudaFuncSetAttribute(k_grouped_persist<MODE, BN>,
+    const cudaError_t e = cudaFuncSetAttribute(k_grouped_persist<MODE, BN, PLAIN>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                smem_total(MODE, BN, 1, grouped_ng(BN)));
     if (e != cudaSuccess) return e;
@@ -150,8 +150,16 @@ inline int launch_grouped_persist_t(const Common& cm, const GroupedRun& gr, int 
   attr[0].val.cooperative = 1;                  // level barrier wait on other CTAs
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_grouped_persist<MODE, BN>, cm, gr);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, k_grouped_persist<MODE, BN, PLAIN>, cm, gr);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The plain flavour for the plain estimator (no projection state).
+template <int MODE, int BN>
+inline int launch_grouped_persist_t(const Common& cm, const GroupedRun& gr, int num_sms,
+                                    void* stream, bool plain) {
+  return plain ? launch_grouped_persist_k<MODE, BN, true>(cm, gr, num_sms, stream)
+               : launch_grouped_persist_k<MODE, BN, false>(cm, gr, num_sms, stream);
 }
 
 }  // namespace gemm

@@ -155,6 +155,7 @@ struct GroupedRun {
   int32_t n_a, n_b;
   int32_t maxima;        // top level: maxima and domain test in the block builders
   int32_t top_built;     // the top level's images were written before the launch
+  int32_t plain;         // plain estimator, no affine line: the epilogue without those paths
   int32_t* ready;        // [n_a + n_b]: slot + 1 once the block's images of that slot are written
   int32_t* level_done;   // [n_slots]: CTAs that finished the slot
 };
