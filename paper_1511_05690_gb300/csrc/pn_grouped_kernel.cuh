@@ -33,13 +33,18 @@ namespace gemm {
 
 constexpr int IMG_BAR = 15;  // named barrier of the block builders (warps 2-9)
 
-__host__ __device__ constexpr int grouped_ng(int BN) { return BN == 128 ? 3 : 2; }
-__host__ __device__ constexpr int grouped_threads(int BN) { return 64 + 128 * grouped_ng(BN); }
+constexpr int GROUPED_NG_PLAIN_128 = 3;  // epilogue groups of the plain flavour at 128-wide tiles
+__host__ __device__ constexpr int grouped_ng(int BN, bool plain) {
+  return BN == 128 ? (plain ? GROUPED_NG_PLAIN_128 : 3) : 2;
+}
+__host__ __device__ constexpr int grouped_threads(int BN, bool plain) {
+  return 64 + 128 * grouped_ng(BN, plain);
+}
 
 template <int MODE, int BN, bool PLAIN>
-__global__ void __launch_bounds__(grouped_threads(BN), 1)
+__global__ void __launch_bounds__(grouped_threads(BN, PLAIN), 1)
     k_grouped_persist(const __grid_constant__ Common cm, const __grid_constant__ GroupedRun gr) {
-  constexpr int NG = grouped_ng(BN);
+  constexpr int NG = grouped_ng(BN, PLAIN);
   static_assert(num_stages(MODE, BN, 1, NG) >= 2, "operand ring too small");
   static_assert(mode_bk(MODE) * 129 * 4 + 8 * TILE_M * 4 <=
                     num_stages(MODE, BN, 1, NG) * stage_bytes(MODE, BN),
@@ -136,14 +141,14 @@ inline int launch_grouped_persist_k(const Common& cm, const GroupedRun& gr, int 
   if (!attr_done) {
     const cudaError_t e = cudaFuncSetAttribute(k_grouped_persist<MODE, BN, PLAIN>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               smem_total(MODE, BN, 1, grouped_ng(BN)));
+                                               smem_total(MODE, BN, 1, grouped_ng(BN, PLAIN)));
     if (e != cudaSuccess) return e;
     attr_done = 1;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(num_sms));
-  cfg.blockDim = dim3(grouped_threads(BN));
-  cfg.dynamicSmemBytes = smem_total(MODE, BN, 1, grouped_ng(BN));
+  cfg.blockDim = dim3(grouped_threads(BN, PLAIN));
+  cfg.dynamicSmemBytes = smem_total(MODE, BN, 1, grouped_ng(BN, PLAIN));
   cfg.stream = static_cast<cudaStream_t>(stream);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the flags and the
