@@ -935,13 +935,14 @@ def run_other(args):
         n, T = 4096, 12
         W = torch.from_numpy(workloads.apsp_weights(n, density=0.1, index=1)).cuda()
         D = torch.empty_like(W)
-        pn.apsp_pnorm(W, out=D)
+        shape = dict(tile_n=args.tile_n, tile_m=args.tile_m)
+        pn.apsp_pnorm(W, out=D, **shape)
         graph = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
         s.wait_stream(stream)
         with torch.cuda.stream(s):
             with torch.cuda.graph(graph, stream=s):
-                pn.apsp_pnorm(W, out=D, check=False, stream=s)
+                pn.apsp_pnorm(W, out=D, check=False, stream=s, **shape)
         stream.wait_stream(s)
         ms = _timed(torch, graph.replay, K, args.warmup, stream)
         E = torch.empty_like(W)

@@ -91,9 +91,9 @@ typedef struct pn_opts {
    * overestimated entries above 1 form cycles whose value grows with every
    * squaring. */
   int32_t diag_policy;
-  /* Output tile width of the tensor-core kernel: 0 = autotuned, else 128 or
-   * 256 (PN_F32_EXACT on one CTA always uses 128; a CTA pair tile, see
-   * tile_m, is 256 wide). */
+  /* Output tile width of the tensor-core kernel: 0 = automatic (the
+   * autotuner's choice, else a size rule), else 128 or 256 (PN_F32_EXACT on
+   * one CTA always uses 128; see tile_m for CTA pairs). */
   int32_t tile_n;
   /* Optional device int32 receiving device-side errors (see above). */
   int32_t* dev_status;
@@ -170,12 +170,18 @@ typedef struct pn_opts {
   float* fit_coef;
   /* Output tile height of the tensor-core kernel (no counterpart in the
    * paper): 128 = one CTA (one SM) per 128 x tile_n tile; 256 = a CTA pair
-   * per 256 x 256 tile (cta_group::2: the two SMs of a cluster each load one
-   * 128-row half of A and of B and the pair's MMA reads both, so each SM
-   * moves a third less operand data per result); 0 = automatic (pairs for
-   * M and N >= 256, or the autotuner's choice).  Pairs serve maxprod_pnorm,
-   * maxprod_pnorm_static and apsp_pnorm with tile_n 0 or 256; otherwise,
-   * and for the grouped call and the adjoint, tiles are 128 rows high. */
+   * per 256 x tile_n tile (cta_group::2: the two SMs of a cluster each load
+   * one 128-row half of A and one half of the B^T column tile, and the
+   * pair's MMA reads both, so each SM moves less operand data per result:
+   * a third less than one CTA per 128 x 256 tile at width 256, a quarter
+   * less than one per 128 x 128 tile at width 128); 0 = automatic (pairs for
+   * M and N >= 256 unless tile_n = 128, or the autotuner's choice).  A
+   * pair's width with tile_n = 0 is 256 unless 128-wide tiles need no more
+   * waves of clusters (small outputs): with every cluster busy a 256 x 128
+   * tile takes 0.94 of the time of a 256 x 256 one, its operand traffic per
+   * SM being more than L2 serves.  Pairs serve maxprod_pnorm, maxprod_pnorm_static
+   * and apsp_pnorm; the grouped call and the adjoint use tiles 128 rows
+   * high. */
   int32_t tile_m;
 } pn_opts;
 
@@ -417,13 +423,14 @@ PN_API pn_status maxprod_pnorm_grouped(const void* host_table, const void* dev_t
 /* Autotuner of the output tile shape (no counterpart in the paper).  Times
  * every candidate the options leave open -- for a product one CTA per
  * 128 x 128 or 128 x 256 tile (3xTF32: 128 x 128 only) and a CTA pair per
- * 256 x 256 tile; for a group the widths 128 and 256 -- on the caller's
+ * 256 x 256 or 256 x 128 tile; for a group the widths 128 and 256 -- on the caller's
  * buffers with CUDA events (three timed runs each after a warm-up) and
  * remembers the fastest for this device and shape class (ceil(log2) of M, N,
  * K for a product; the table's sizes for a group).  Later calls with
  * tile_n = 0 and tile_m = 0 use it.  Synchronises the stream; not for use
  * inside a stream capture.  The choice is returned in *chosen_tile_n
- * (nullable): the width, or 512 for a CTA pair.  The buffers are overwritten
+ * (nullable): the width, or 256 + the width for a CTA pair (512 or 384).
+ * The buffers are overwritten
  * exactly as by the product itself. */
 PN_API pn_status pn_autotune(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda,
                              const float* B, int64_t ldb, float* C, int64_t ldc,

@@ -113,7 +113,8 @@ def maxprod_pnorm(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), c
                   debug_flags=0, estimator=0, correction=0, fit_i=None, fit_j=None,
                   fit_coef=None, tile_m=0):
     """p-norm estimate of C = A (x,max) B.  Returns (C, p_sel or None, S_sel or None).
-    tile_m: 0 automatic, 128 one CTA per tile, 256 a CTA pair per 256 x 256 tile.
+    tile_m: 0 automatic, 128 one CTA per tile, 256 a CTA pair per 256 x tile_n tile
+    (tile_n 0: a size rule picks the pair's width).
     estimator 0: plain (S^(p*))^(1/p*); 1: r = 1 projection (S^(p*)/S^(p*/2))^(2/p*);
     2: r = 2 projection from the sums at p*/4, p*/2, 3p*/4 and p* (Sec. 2.1).
     correction 1: divide by K^(1/p*); 2: affine model per p* class fitted to the
@@ -158,7 +159,8 @@ def autotune(A: torch.Tensor, B: torch.Tensor, *, p_log2=tuple(range(7)), comput
              tau=None, scaling=2, stream=None) -> int:
     """Times the tile shapes for this shape class and remembers the fastest
     (later calls with tile_n=0, tile_m=0 use it).  Synchronises; returns the
-    width of one CTA's tile (128 or 256), or 512 for a CTA pair."""
+    width of one CTA's tile (128 or 256), or 256 + the width for a CTA pair
+    (512 or 384)."""
     A, B = _mat(A, "A"), _mat(B, "B")
     M, K = A.shape
     N = B.shape[1]

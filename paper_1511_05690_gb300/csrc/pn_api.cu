@@ -65,20 +65,48 @@ bool opts_valid(const pn_opts* o) {
   return true;
 }
 
-// A CTA pair (cta_group::2) per 256 x 256 tile, or one CTA per tile.  The
-// autotune cache records a pair as 512.
+// A CTA pair (cta_group::2) per 256 x BN tile, or one CTA per 128 x BN tile.
+// The autotune cache records a pair as 256 + BN (512 or 384).
 int choose_cg(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
-  if (o->tile_m == 128 || o->tile_n == 128) return 1;
-  if (o->tile_m == 256) return 2;
+  if (o->tile_m) return o->tile_m == 256 ? 2 : 1;
+  if (o->tile_n == 128) return 1;
   const int tuned = host_tuned_bn(o->compute, M, N, K);
-  if (tuned) return tuned == 512 ? 2 : 1;
+  if (tuned) return tuned > 256 ? 2 : 1;
   return (M >= 256 && N >= 256) ? 2 : 1;
 }
 
-// Tile width of one CTA: 3xTF32 carries two operand planes, so only 128 fits
-// its ring; a CTA pair's tile is 256 wide.
+// Time of a 256 x 128 pair tile relative to a 256 x 256 one with every
+// cluster busy (measured, BF16, n = 8192 and 16384: 0.93 and 0.945).  The
+// narrow tile does half the MMAs, but each SM then loads 24 KB of operand
+// images per 256 tensor cycles instead of 32 KB per 512, more than L2 serves
+// to all SMs at once.
+constexpr double PAIR_NARROW_COST = 0.94;
+
+// Width of a pair tile when the options leave it open: tiles run in waves of
+// one per cluster (two SMs); the narrow tile wins only where it needs no more
+// waves than the wide one (small outputs, where it spreads the work over
+// twice the SMs).  A 4096 x 4096 output: 4 waves of 256 wide tiles on 76
+// clusters against 7 of 128 wide ones (7 x 0.94 > 4).
+int pair_width(int64_t M, int64_t N) {
+  const int sms = device_sms();
+  const int64_t clusters = sms > 1 ? sms / 2 : 76;
+  const int64_t rows = ceil_div(M, 2 * TILE_M);
+  const int64_t w256 = ceil_div(rows * ceil_div(N, 256), clusters);
+  const int64_t w128 = ceil_div(rows * ceil_div(N, 128), clusters);
+  return static_cast<double>(w128) * PAIR_NARROW_COST < static_cast<double>(w256) ? 128 : 256;
+}
+
+// Tile width: 3xTF32 carries two operand planes, so only 128 fits one CTA's
+// ring; a CTA pair's tile is 256 or 128 wide.
 int choose_bn(const pn_opts* o, int64_t M, int64_t N, int64_t K) {
-  if (choose_cg(o, M, N, K) == 2) return 256;
+  if (choose_cg(o, M, N, K) == 2) {
+    if (o->tile_n) return o->tile_n;
+    if (o->tile_m == 0) {
+      const int tuned = host_tuned_bn(o->compute, M, N, K);
+      if (tuned == 512 || tuned == 384) return tuned - 256;
+    }
+    return pair_width(M, N);
+  }
   if (o->compute == PN_F32_EXACT) return 128;
   if (o->tile_n) return o->tile_n;
   const int tuned = host_tuned_bn(o->compute, M, N, K);  // autotune cache

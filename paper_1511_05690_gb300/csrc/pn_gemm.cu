@@ -13,7 +13,7 @@
 // next p.  The smallest p resolves whatever is left (flagged unstable).
 //
 // Kernel structure (one persistent CTA per SM, 10 warps; or a CTA pair per
-// 256 x 256 tile, cta_group::2):
+// 256 x BN tile, cta_group::2):
 //   warp 0      one thread issues copies of pre-swizzled 16 KB operand tile
 //               images into a STAGES-deep shared-memory ring (192 KB): 1-D
 //               bulk copies, or for a pair 2-D tensor copies completing on
@@ -48,7 +48,6 @@ int gemm_stages(int mode, int BN) { return gemm::num_stages(mode, BN); }
 
 int launch_gemm_level(const Common& cm, const Level& lv, int num_sms, void* stream) {
   if (cm.BN != 128 && cm.BN != 256) return cudaErrorInvalidValue;
-  if (cm.cg == 2 && cm.BN != 256) return cudaErrorInvalidValue;
   switch (cm.mode) {
     case MODE_BF16:
     case MODE_F16: return gemm_launch_f16(cm.mode, cm.BN, cm, lv, num_sms, stream);

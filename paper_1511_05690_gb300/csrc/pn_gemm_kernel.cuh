@@ -497,11 +497,10 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
           fence_proxy_async_global();
         }
         const uint8_t* a_src = lv.a_level + P.a_img + (int64_t)tm * P.KB * IMG_BYTES;
-        // this CTA's B^T blocks: all BN / 128 of the column tile, or for a
-        // pair its own half (block 2 tn + rank)
+        // a single CTA's B^T blocks: all BN / 128 of the column tile (a pair
+        // addresses its half through the tensor map)
         const uint8_t* b_src =
-            lv.b_level + P.b_img +
-            (int64_t)(tn * (BN / TILE_M) + (CG == 2 ? static_cast<int>(cx.rank) : 0)) * P.KB * IMG_BYTES;
+            lv.b_level + P.b_img + (int64_t)tn * (BN / TILE_M) * P.KB * IMG_BYTES;
         for (int kb = 0; kb < P.KB; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, tmo, abort_flag)) {
             aborted = true;
@@ -525,9 +524,12 @@ __device__ __forceinline__ void run_producer(const Common& cm, const Level& lv, 
               for (int pl = 0; pl < PLANES; ++pl) {
                 const uint32_t base = sa + pl * (A_BYTES + B_BYTES);
                 const int64_t ya = (pl * P.a_plane + ((int64_t)tm * P.KB + kb) * IMG_BYTES) >> 7;
+                // this CTA's half of the B^T column tile: BN / 2 rows from
+                // row tn BN + rank BN / 2 (a whole 128-row block, or half of one)
+                const int brow = tn * BN + static_cast<int>(cx.rank) * (BN / 2);
                 const int64_t yb =
-                    (pl * P.b_plane + ((int64_t)(2 * tn + static_cast<int>(cx.rank)) * P.KB + kb) *
-                                          IMG_BYTES) >> 7;
+                    ((pl * P.b_plane + ((int64_t)(brow >> 7) * P.KB + kb) * IMG_BYTES) >> 7) +
+                    (brow & 127);
                 tma_load_2d_pair(base, &maps->a, 0, static_cast<int>(ya), fb, pol);
                 tma_load_2d_pair(base + A_BYTES, &maps->b, 0, static_cast<int>(yb), fb, pol);
               }
@@ -644,7 +646,7 @@ __device__ __forceinline__ void run_mma(const Common& cm, const Level& lv, const
             const uint64_t bd = sdesc_sw128(sb + kk * 32);
             const uint32_t acc = (kb | kk) != 0;
             if constexpr (CG == 2) {
-              // M = 256 over both CTAs' A halves, N = 256 over both B halves
+              // M = 256 over both CTAs' A halves, N = BN over both B halves
               if constexpr (PLANES == 1) {
                 mma_pair<KIND>(d, ad, bd, IDESC, acc);
               } else {
@@ -1123,7 +1125,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
                  const __grid_constant__ MapsArg<CG> maps) {
   static_assert(num_stages(MODE, BN, CG) >= 2, "operand ring too small");
-  static_assert(CG == 1 || (BN == 256 && EPI == 0), "CTA pairs: 256 x 256 p-norm tiles");
+  static_assert(CG == 1 || EPI == 0, "CTA pairs: p-norm tiles of 256 x BN");
   pdl_wait();
   pdl_trigger();
   if constexpr (EPI == 1) {
@@ -1185,15 +1187,15 @@ inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream
   return le != cudaSuccess ? le : cudaGetLastError();
 }
 
-// A CTA pair per 256 x 256 output tile (cta_group::2): clusters of two CTAs,
+// A CTA pair per 256 x BN output tile (cta_group::2): clusters of two CTAs,
 // one cluster per pair of SMs (cm.total_tiles counts pair tiles).
-template <int MODE>
+template <int MODE, int BN>
 inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
-  const int e = set_attr_t<MODE, 256, 0, 2>();
+  const int e = set_attr_t<MODE, BN, 0, 2>();
   if (e) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(GEMM_THREADS);
-  cfg.dynamicSmemBytes = smem_total(MODE, 256, 2);
+  cfg.dynamicSmemBytes = smem_total(MODE, BN, 2);
   cfg.stream = static_cast<cudaStream_t>(stream);
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1216,7 +1218,7 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
     if (resident[dev] == 0) {
       cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs));
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_gemm_level<MODE, 256, 0, 2>, &cfg) != cudaSuccess ||
+      if (cudaOccupancyMaxActiveClusters(&n, k_gemm_level<MODE, BN, 0, 2>, &cfg) != cudaSuccess ||
           n < 1) {
         cudaGetLastError();
         n = pairs;
@@ -1236,9 +1238,9 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
   constexpr int PL = mode_planes(MODE);
   if (cm.nprob != 1 ||
       !encode_img_rows(maps.a, lv.a_level + P.a_img, P.a_plane * PL) ||
-      !encode_img_rows(maps.b, lv.b_level + P.b_img, P.b_plane * PL))
+      !encode_img_rows(maps.b, lv.b_level + P.b_img, P.b_plane * PL, BN / 2))
     return cudaErrorNotSupported;
-  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, 256, 0, 2>, cm, lv, maps);
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, BN, 0, 2>, cm, lv, maps);
   return le != cudaSuccess ? le : cudaGetLastError();
 }
 

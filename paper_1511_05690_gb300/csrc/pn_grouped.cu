@@ -492,15 +492,15 @@ pn_status pn_autotune(int64_t M, int64_t N, int64_t K, const float* A, int64_t l
   pn_opts o = *opts;
   o.ev_gemm_begin = o.ev_gemm_end = nullptr;
   // candidates: one CTA per 128 x 128 and per 128 x 256 tile, and a CTA pair
-  // per 256 x 256 tile (recorded as 512); the options may fix some of these
+  // per 256 x 256 and per 256 x 128 tile (recorded as 512 and 384); the
+  // options may fix some of these
   int best = 0;
   float best_ms = 0.0f;
-  for (int c = 0; c < 3; ++c) {
-    const int tile_m = c == 2 ? 256 : 128, tile_n = c == 0 ? 128 : 256;
+  for (int c = 0; c < 4; ++c) {
+    const int tile_m = c >= 2 ? 256 : 128, tile_n = (c == 0 || c == 3) ? 128 : 256;
     if (opts->tile_m && opts->tile_m != tile_m) continue;
     if (opts->tile_n && opts->tile_n != tile_n) continue;
     if (c == 1 && opts->compute == PN_F32_EXACT) continue;  // one CTA: 128 wide only
-    if (c == 2 && opts->estimator == 2) continue;            // pairs: estimators 0, 1
     o.tile_m = tile_m;
     o.tile_n = tile_n;
     pn_status st = PN_OK;
@@ -509,7 +509,7 @@ pn_status pn_autotune(int64_t M, int64_t N, int64_t K, const float* A, int64_t l
     }, s, 3, &st);
     if (st != PN_OK) return st;
     if (best == 0 || ms < best_ms) {
-      best = c == 2 ? 512 : tile_n;
+      best = c >= 2 ? 256 + tile_n : tile_n;
       best_ms = ms;
     }
   }

@@ -70,7 +70,7 @@ struct Common {
   int32_t total_ma, total_mb;  // max-pass units summed over problems
   int32_t mode, BN, s_op, scaling;
   float unscale;      // 2^(-2 s_op)
-  int32_t cg;         // 2: a CTA pair (cta_group::2) per 256 x 256 tile, total_tiles counts pairs
+  int32_t cg;         // 2: a CTA pair (cta_group::2) per 256 x BN tile, total_tiles counts pairs
   uint32_t* rmax;     // per-row max of A (float bits)
   uint32_t* cmax;     // per-column max of B
   uint32_t* gmax;     // per-problem global max of A (2g) and B (2g+1)
@@ -288,9 +288,9 @@ struct ImgMaps {
 };
 struct NoMaps {};
 // Encodes a region of `bytes` bytes (a multiple of 128, base 16-byte aligned)
-// as a 2-D tensor of 128-byte rows with 128 x 128-byte boxes; false if the
-// driver's encoder is unavailable or the region is out of range.
-bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes);
+// as a 2-D tensor of 128-byte rows with boxes of box_rows x 128 bytes; false
+// if the driver's encoder is unavailable or the region is out of range.
+bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes, int box_rows = 128);
 void make_operand_maps(const Common& cm, OperandMaps& maps);
 
 int launch_maxes(const Common& cm, void* stream);

@@ -981,14 +981,15 @@ int launch_maxes(const Common& cm, void* stream) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes) {
+bool encode_img_rows(TensorMapBytes& out, const void* base, int64_t bytes, int box_rows) {
   const EncodeTiledFn fn = encode_tiled();
   if (!fn || !base || bytes < 128 * 128 || (bytes & 127) != 0) return false;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (bytes >> 7) > (int64_t(1) << 31))
     return false;
   const cuuint64_t dims[2] = {128, static_cast<cuuint64_t>(bytes >> 7)};
   const cuuint64_t strides[1] = {128};
-  const cuuint32_t box[2] = {128, 128};
+  if (box_rows < 8 || box_rows > 256) return false;
+  const cuuint32_t box[2] = {128, static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
   return fn(reinterpret_cast<CUtensorMap*>(&out), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

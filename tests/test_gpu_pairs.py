@@ -1,6 +1,7 @@
 """GPU parity of the CTA-pair tensor-core path (tile_m = 256: two SMs of a
-cluster share one 256 x 256 tile through cta_group::2 MMAs, each loading one
-128-row half of A and of B).  The arithmetic per entry is that of the
+cluster share one 256 x 256 or 256 x 128 tile through cta_group::2 MMAs, each
+loading one 128-row half of A and one half of the B^T column tile: a whole
+128-row image block, or 64 rows of one).  The arithmetic per entry is that of the
 single-CTA path, so the oracle tolerances of the product tests apply, and the
 pair and single-CTA results are held to each other within them.  Shapes with
 an odd number of 128-row tiles use the padded zero block of A; several-level
@@ -29,17 +30,19 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
 
 
+@pytest.mark.parametrize("width", [256, 128])
 @pytest.mark.parametrize("mode", ["f32", "bf16", "tf32", "f16", "e4m3"])
 @pytest.mark.parametrize("shape", [(256, 256, 300), (300, 520, 257), (640, 384, 1000),
                                    (100, 300, 64)])
-def test_pairs_match_oracle(pn, orc, mode, shape):
-    """Every format, ragged shapes, an odd count of 128-row tiles (300, 640
-    rows: 3 and 5 tile rows) and a product smaller than one pair tile."""
+def test_pairs_match_oracle(pn, orc, mode, shape, width):
+    """Every format and both pair widths, ragged shapes, an odd count of
+    128-row tiles (300, 640 rows: 3 and 5 tile rows) and a product smaller
+    than one pair tile."""
     M, N, K = shape
     A, B = workloads.wide_range_pair(M, N, K, seed=4000 + M + K)
     tau = orc.default_tau(K, 3) if mode == "f16" else None
     C, psel, ssel, err = _compare(pn, orc, A, B, mode, list(range(7)), tau=tau,
-                                  tile_n=256, tile_m=256)
+                                  tile_n=width, tile_m=256)
     Cs, ps, ss = pn.maxprod_pnorm(_dev(A), _dev(B), compute=mode, tau=tau, tile_n=256,
                                   tile_m=128)
     Cs, ps = Cs.cpu().numpy(), ps.cpu().numpy()
@@ -49,12 +52,13 @@ def test_pairs_match_oracle(pn, orc, mode, shape):
     assert np.all(rel[agree] <= 2 * tol[agree])
 
 
+@pytest.mark.parametrize("width", [256, 128])
 @pytest.mark.parametrize("mode", ["f32", "bf16"])
-def test_pairs_lower_levels(pn, orc, mode):
+def test_pairs_lower_levels(pn, orc, mode, width):
     """Entries resolving at several levels: a pair tile goes down when either
     half has entries left, each half keeps its own resolved bits."""
     A, B = _multilevel_inputs(520, 700, 256, seed=4100)
-    C, psel, _, _ = _compare(pn, orc, A, B, mode, list(range(7)), tile_n=256, tile_m=256)
+    C, psel, _, _ = _compare(pn, orc, A, B, mode, list(range(7)), tile_n=width, tile_m=256)
     assert len(set(np.unique(psel & 0x7F).tolist())) >= 2
 
 
@@ -77,29 +81,31 @@ def test_pairs_projection_r1(pn, orc):
     assert np.all(err <= tol), float(err.max())
 
 
+@pytest.mark.parametrize("width", [256, 128])
 @pytest.mark.parametrize("mode", ["f32", "bf16"])
-def test_pairs_projection_r2_equals_single(pn, mode):
+def test_pairs_projection_r2_equals_single(pn, mode, width):
     """The r = 2 projection with pairs: the two halves of a pair tile decide
     together whether it visits the half level (either half started a chain),
     and the results equal the single-CTA run bit for bit over several levels
     (a half without chains at a half level parks nothing)."""
     A, B = _multilevel_inputs(384, 520, 200, seed=4300)
     dA, dB = _dev(A), _dev(B)
-    r2 = pn.maxprod_pnorm(dA, dB, compute=mode, estimator=2, tile_m=256)
+    r2 = pn.maxprod_pnorm(dA, dB, compute=mode, estimator=2, tile_m=256, tile_n=width)
     r1 = pn.maxprod_pnorm(dA, dB, compute=mode, estimator=2, tile_m=128)
     for x2, x1 in zip(r2, r1):
         assert torch.equal(x2, x1)
     assert len(torch.unique(r2[1] & 0x7F)) >= 2
 
 
-def test_pairs_apsp_matches_single(pn, orc):
+@pytest.mark.parametrize("width", [256, 128])
+def test_pairs_apsp_matches_single(pn, orc, width):
     """APSP squarings (diagonal reset and clamp in the epilogue) with pairs:
     the same distances as with single CTAs within the per-squaring bar."""
     n = 700
     W = workloads.apsp_weights(n, density=0.1, seed=4300)
     tau = orc.default_tau(n, orc.F32_EXACT)
     dW = torch.from_numpy(W).cuda()
-    D2 = pn.apsp_pnorm(dW, compute="f32", tau=tau, tile_m=256).cpu().numpy()
+    D2 = pn.apsp_pnorm(dW, compute="f32", tau=tau, tile_m=256, tile_n=width).cpu().numpy()
     D1 = pn.apsp_pnorm(dW, compute="f32", tau=tau, tile_m=128).cpu().numpy()
     fin = np.isfinite(D1)
     assert np.array_equal(np.isfinite(D2), fin)
