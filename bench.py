@@ -1000,7 +1000,8 @@ def run_other(args):
         ops = float(np.sum(sizes.astype(np.float64) ** 3))
         line.update(value=ops / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="bf16",
                     config={"workload": f"{args.count} square products, n = round(16 * 64^U), "
-                            "BF16, P={1..64}, one launch per p level, CUDA graph replay",
+                            "BF16, P={1..64}, an image-strip launch then one persistent launch "
+                            "over every p level, CUDA graph replay",
                             "sum_n3": ops, "tile_n": chosen})
     print(json.dumps(line), flush=True)
 

@@ -808,27 +808,37 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
       uint32_t res_all[CHUNKS], pend_all[CHUNKS], pend2_all[CHUNKS];
       bool any_left = false;
       bool new_chain = false;  // r = 2: an entry of the tile resolved here
+      // the warp's chunks that hold outputs: none when its 32 rows all lie
+      // past M (a padded tile of a small problem), else those starting
+      // before N; the others are neither read from TMEM nor processed
+      const int jw = PN - (tn * BN + ch0 * 32);
+      const int nv = (tm * TILE_M + quarter * 32 >= P.M || jw <= 0) ? 0
+                     : ((jw + 31) >> 5) < nch                        ? ((jw + 31) >> 5)
+                                                                     : nch;
+      // hands the accumulator back once this warp's last TMEM load completed
+      auto release = [&]() {
+        tc_fence_before();
+        if constexpr (CG == 2) {
+          // one lane per warp, on rank 0's barrier (the MMA issuer's)
+          __syncwarp();
+          if (lane == 0) {
+            if (cx.rank == 0)
+              mbar_arrive(&acc_empty[buf]);
+            else
+              mbar_arrive_peer(mapa_shared(smem_u32(&acc_empty[buf]), 0));
+          }
+        } else {
+          mbar_arrive(&acc_empty[buf]);
+        }
+      };
+      if (nv == 0) release();
 #pragma unroll 1
-      for (int hc = 0; hc < nch; ++hc) {
+      for (int hc = 0; hc < nv; ++hc) {
         const int ch = ch0 + hc;
         uint32_t v[32];
         tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * BN + ch * 32, v);
         tmem_ld_wait();
-        if (hc == nch - 1) {
-          tc_fence_before();
-          if constexpr (CG == 2) {
-            // one lane per warp, on rank 0's barrier (the MMA issuer's)
-            __syncwarp();
-            if (lane == 0) {
-              if (cx.rank == 0)
-                mbar_arrive(&acc_empty[buf]);
-              else
-                mbar_arrive_peer(mapa_shared(smem_u32(&acc_empty[buf]), 0));
-            }
-          } else {
-            mbar_arrive(&acc_empty[buf]);
-          }
-        }
+        if (hc == nv - 1) release();
         const int j0 = tn * BN + ch * 32;
         uint32_t res = 0;
         pend_all[hc] = 0;
@@ -1068,16 +1078,16 @@ __device__ __forceinline__ void run_epilogue(const Common& cm, const Level& lv, 
             uint32_t* st_w = cm.state + st_idx;
 #pragma unroll
             for (int hc = 0; hc < CHUNKS; ++hc)
-              if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) st_w[hc] = res_all[hc];
+              if (hc < nv) st_w[hc] = res_all[hc];
             if (!PLAIN && cm.pend) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
-                if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend[st_idx + hc] = pend_all[hc];
+                if (hc < nv) cm.pend[st_idx + hc] = pend_all[hc];
             }
             if (!PLAIN && cm.pend2) {
 #pragma unroll
               for (int hc = 0; hc < CHUNKS; ++hc)
-                if (hc < nch && tn * BN + (ch0 + hc) * 32 < PN) cm.pend2[st_idx + hc] = pend2_all[hc];
+                if (hc < nv) cm.pend2[st_idx + hc] = pend2_all[hc];
             }
           }
           // r = 2: a tile that starts no chain here skips the half level
