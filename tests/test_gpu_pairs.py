@@ -97,6 +97,21 @@ def test_pairs_projection_r2_equals_single(pn, mode, width):
     assert len(torch.unique(r2[1] & 0x7F)) >= 2
 
 
+@pytest.mark.parametrize("width,n", [(256, 5120), (128, 3584)])
+def test_pairs_tile_per_epilogue_group(pn, width, n):
+    """Short contractions over many tiles (K = 256, at least four pair tiles
+    per cluster): each epilogue group of a pair's CTAs finishes whole tiles
+    in turn instead of all groups sharing every tile.  Entries spread over
+    several levels; C, p_sel and S_sel equal the single-CTA run bit for bit."""
+    A, B = _multilevel_inputs(n, n, 256, seed=4500 + width)
+    dA, dB = _dev(A), _dev(B)
+    r2 = pn.maxprod_pnorm(dA, dB, compute="bf16", tile_m=256, tile_n=width)
+    r1 = pn.maxprod_pnorm(dA, dB, compute="bf16", tile_m=128, tile_n=width)
+    for x2, x1 in zip(r2, r1):
+        assert torch.equal(x2, x1)
+    assert len(torch.unique(r2[1] & 0x7F)) >= 2
+
+
 @pytest.mark.parametrize("width", [256, 128])
 def test_pairs_apsp_matches_single(pn, orc, width):
     """APSP squarings (diagonal reset and clamp in the epilogue) with pairs:
