@@ -180,8 +180,10 @@ typedef struct pn_opts {
    * waves of clusters (small outputs): with every cluster busy a 256 x 128
    * tile takes 0.94 of the time of a 256 x 256 one, its operand traffic per
    * SM being more than L2 serves.  Pairs serve maxprod_pnorm, maxprod_pnorm_static
-   * and apsp_pnorm; the grouped call and the adjoint use tiles 128 rows
-   * high. */
+   * and apsp_pnorm, and the adjoint's two GEMMs (256 x 256 tiles, chosen
+   * automatically when each GEMM gives every pair of SMs at least two tiles,
+   * e.g. n >= 4096 on 152 SMs; tile_n = 128 or tile_m = 128 keeps one CTA per
+   * tile there); the grouped call uses tiles 128 rows high. */
   int32_t tile_m;
 } pn_opts;
 
@@ -382,7 +384,8 @@ PN_API size_t pn_backward_workspace_size(int64_t M, int64_t N, int64_t K, const 
  * (recomputed, not stored).  A: M x K, B: K x N, C, S_sel, p_sel, dC: M x N,
  * dA: M x K, dB: K x N, all contiguous row-major (leading dimension = number
  * of columns); C, S_sel and p_sel are the outputs of maxprod_pnorm with the
- * same options.  dA and dB are overwritten. */
+ * same options.  dA and dB are overwritten.  opts->tile_m / tile_n select the
+ * gradient GEMMs' tiles as described at tile_m. */
 PN_API pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A,
                                  const float* B, const float* C, const float* S_sel,
                                  const uint8_t* p_sel, const float* dC, float* dA, float* dB,

@@ -383,8 +383,12 @@ def apsp_pnorm(W: torch.Tensor, *, n_squarings=0, p_log2=tuple(range(7)), comput
 
 
 def maxprod_pnorm_backward(A, B, C, S_sel, p_sel, dC, *, p_log2=tuple(range(7)),
-                           compute="f32", tau=None, scaling=2, check=True, stream=None):
-    """Adjoint of maxprod_pnorm at fixed p* per entry; returns (dA, dB)."""
+                           compute="f32", tau=None, scaling=2, check=True, stream=None,
+                           tile_m=0, tile_n=0):
+    """Adjoint of maxprod_pnorm at fixed p* per entry; returns (dA, dB).
+    tile_m / tile_n: the gradient GEMMs' tiles (0 automatic: CTA pairs on
+    256 x 256 tiles when each GEMM has at least two pair tiles per pair of
+    SMs)."""
     A, B = _mat(A, "A").contiguous(), _mat(B, "B").contiguous()
     C, S_sel, dC = C.contiguous(), S_sel.contiguous(), dC.contiguous()
     p_sel = p_sel.contiguous()
@@ -394,7 +398,7 @@ def maxprod_pnorm_backward(A, B, C, S_sel, p_sel, dC, *, p_log2=tuple(range(7)),
     dA = torch.empty((M, K), dtype=torch.float32, device=dev)
     dB = torch.empty((K, N), dtype=torch.float32, device=dev)
     st = status_word(dev)
-    o = make_opts(p_log2, compute, tau, scaling, 1, 0, st.data_ptr())
+    o = make_opts(p_log2, compute, tau, scaling, 1, tile_n, st.data_ptr(), tile_m=tile_m)
     L = lib()
     need = L.pn_backward_workspace_size(M, N, K, ctypes.byref(o))
     ws = workspace(max(need, 256), dev)

@@ -394,7 +394,7 @@ bool bw_mode_ok(int compute) {
 // Workspace of the adjoint: control words, scales and the four operand images
 // of one p (reused for every p, stream order).
 struct BwLayout {
-  int BN = 0, KB1 = 0, KB2 = 0, RB1a = 0, RB1b = 0, RB2a = 0, RB2b = 0;
+  int BN = 0, cg = 1, KB1 = 0, KB2 = 0, RB1a = 0, RB1b = 0, RB2a = 0, RB2b = 0;
   size_t off_rmax = 0, off_cmax = 0, off_gmax = 0, off_mask = 0, ctrl_bytes = 0;
   size_t off_r = 0, off_c = 0, off_w1 = 0, off_b1 = 0, off_a2 = 0, off_w2 = 0;
   size_t plane_w1 = 0, plane_b1 = 0, plane_a2 = 0, plane_w2 = 0, total = 0;
@@ -404,13 +404,27 @@ BwLayout make_bw_layout(int64_t M, int64_t N, int64_t K, const pn_opts* o) {
   BwLayout L;
   const int mode = o->compute;
   const int bk = mode_bk(mode), planes = mode_planes(mode);
-  L.BN = mode == PN_F32_EXACT ? 128 : (o->tile_n ? o->tile_n : 256);
+  // CTA pairs on 256 x 256 tiles for both gradient GEMMs (outputs M x K and
+  // K x N) when each gives every cluster at least two pair tiles, so that a
+  // pair's gradient epilogue overlaps its next tile's MMAs (measured, 3xTF32,
+  // P = {16}: n = 2048 0.43 ms with pairs against 0.40 with one CTA per tile,
+  // 4096 1.40 against 1.56, 8192 7.42 against 9.54); unless the options ask
+  // for one CTA per tile or for 128-wide tiles
+  const int sms = device_sms();
+  const int64_t clusters = sms > 1 ? sms / 2 : 76;
+  const int64_t t1 = ceil_div(M, 256) * ceil_div(K, 256), t2 = ceil_div(K, 256) * ceil_div(N, 256);
+  const bool many = t1 >= 2 * clusters && t2 >= 2 * clusters;
+  L.cg = (o->tile_m == 256 || (o->tile_m == 0 && many)) && o->tile_n != 128 ? 2 : 1;
+  L.BN = L.cg == 2 ? 256 : mode == PN_F32_EXACT ? 128 : (o->tile_n ? o->tile_n : 256);
   const int per = L.BN / TILE_M;
+  auto even = [&](int rb) { return L.cg == 2 ? (rb + 1) / 2 * 2 : rb; };
   L.KB1 = static_cast<int>(ceil_div(N, bk));
   L.KB2 = static_cast<int>(ceil_div(M, bk));
-  L.RB1a = static_cast<int>(ceil_div(M, TILE_M));
+  // a pair's second CTA reads A row block 2 TM + 1: an odd count is padded
+  // with a block of zeros (the image kernel zero-fills rows past the source)
+  L.RB1a = even(static_cast<int>(ceil_div(M, TILE_M)));
   L.RB1b = static_cast<int>(ceil_div(K, L.BN)) * per;
-  L.RB2a = static_cast<int>(ceil_div(K, TILE_M));
+  L.RB2a = even(static_cast<int>(ceil_div(K, TILE_M)));
   L.RB2b = static_cast<int>(ceil_div(N, L.BN)) * per;
   size_t off = 0;
   L.off_rmax = off; off += sizeof(uint32_t) * M;
@@ -644,7 +658,7 @@ pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A
     P.b_plane = static_cast<int64_t>(L.plane_b1);
     P.vec_c = (K % 4 == 0) && (reinterpret_cast<uintptr_t>(dA) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(A) % 16 == 0);
-    g1.total_tiles = P.tiles_m * P.tiles_n;
+    g1.total_tiles = (L.cg == 2 ? (P.tiles_m + 1) / 2 : P.tiles_m) * P.tiles_n;
   }
   // G2: dB (K x N) = A'^p^T (K x M) . W^(p), contraction over M
   Common g2;
@@ -660,10 +674,11 @@ pn_status maxprod_pnorm_backward(int64_t M, int64_t N, int64_t K, const float* A
     P.b_plane = static_cast<int64_t>(L.plane_w2);
     P.vec_c = (N % 4 == 0) && (reinterpret_cast<uintptr_t>(dB) % 16 == 0) &&
               (reinterpret_cast<uintptr_t>(B) % 16 == 0);
-    g2.total_tiles = P.tiles_m * P.tiles_n;
+    g2.total_tiles = (L.cg == 2 ? (P.tiles_m + 1) / 2 : P.tiles_m) * P.tiles_n;
   }
   for (Common* g : {&g1, &g2}) {
     g->nprob = 1;
+    g->cg = L.cg;
     g->mode = opts->compute;
     g->BN = L.BN;
     g->r = fw.r;

@@ -1135,7 +1135,6 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
     k_gemm_level(const __grid_constant__ Common cm, const __grid_constant__ Level lv,
                  const __grid_constant__ MapsArg<CG> maps) {
   static_assert(num_stages(MODE, BN, CG) >= 2, "operand ring too small");
-  static_assert(CG == 1 || EPI == 0, "CTA pairs: p-norm tiles of 256 x BN");
   pdl_wait();
   pdl_trigger();
   if constexpr (EPI == 1) {
@@ -1198,10 +1197,11 @@ inline int launch_t(const Common& cm, const Level& lv, int num_sms, void* stream
 }
 
 // A CTA pair per 256 x BN output tile (cta_group::2): clusters of two CTAs,
-// one cluster per pair of SMs (cm.total_tiles counts pair tiles).
-template <int MODE, int BN>
+// one cluster per pair of SMs (cm.total_tiles counts pair tiles).  EPI as for
+// k_gemm_level.
+template <int MODE, int BN, int EPI = 0>
 inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* stream) {
-  const int e = set_attr_t<MODE, BN, 0, 2>();
+  const int e = set_attr_t<MODE, BN, EPI, 2>();
   if (e) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(GEMM_THREADS);
@@ -1228,7 +1228,7 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
     if (resident[dev] == 0) {
       cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs));
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_gemm_level<MODE, BN, 0, 2>, &cfg) != cudaSuccess ||
+      if (cudaOccupancyMaxActiveClusters(&n, k_gemm_level<MODE, BN, EPI, 2>, &cfg) != cudaSuccess ||
           n < 1) {
         cudaGetLastError();
         n = pairs;
@@ -1250,7 +1250,7 @@ inline int launch_pair_t(const Common& cm, const Level& lv, int num_sms, void* s
       !encode_img_rows(maps.a, lv.a_level + P.a_img, P.a_plane * PL) ||
       !encode_img_rows(maps.b, lv.b_level + P.b_img, P.b_plane * PL, BN / 2))
     return cudaErrorNotSupported;
-  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, BN, 0, 2>, cm, lv, maps);
+  const cudaError_t le = cudaLaunchKernelEx(&cfg, k_gemm_level<MODE, BN, EPI, 2>, cm, lv, maps);
   return le != cudaSuccess ? le : cudaGetLastError();
 }
 

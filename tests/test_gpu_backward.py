@@ -157,6 +157,39 @@ def test_backward_n2048_sampled(pn, orc, pl):
     assert np.all(np.abs(gB[kb, jb] - fdB) <= fd_rel * np.abs(fdB) + resB)
 
 
+@pytest.mark.parametrize("mode", ["f32", "tf32", "bf16"])
+@pytest.mark.parametrize("shape", [(300, 520, 384), (256, 300, 700)])
+def test_backward_pairs_equal_single(pn, orc, mode, shape):
+    """The gradient GEMMs on CTA pairs (256 x 256 tiles; automatic for larger
+    products) give dA and dB bit-identical to one CTA per tile -- with odd
+    counts of 128-row blocks on either GEMM's output rows (300 rows of dA,
+    384 and 700 rows of dB, padded with a zero block), and entries selected
+    at several p.  The 3xTF32 case is also held to the oracle's gradient."""
+    M, N, K = shape
+    A, B = _multilevel_inputs(M, N, K, seed=720 + K)
+    pl = list(range(7))
+    tau = orc.default_tau(K, {"f32": orc.F32_EXACT, "tf32": orc.TF32, "bf16": orc.BF16}[mode])
+    dA_, dB_ = _dev(A), _dev(B)
+    C, psel, ssel = pn.maxprod_pnorm(dA_, dB_, p_log2=pl, compute=mode, tau=tau)
+    assert len(torch.unique(psel & 0x7F)) >= 2
+    G = 1.0 / C
+    got = pn.maxprod_pnorm_backward(dA_, dB_, C, ssel, psel, G, p_log2=pl, compute=mode, tau=tau)
+    one = pn.maxprod_pnorm_backward(dA_, dB_, C, ssel, psel, G, p_log2=pl, compute=mode, tau=tau,
+                                    tile_m=128)
+    pair = pn.maxprod_pnorm_backward(dA_, dB_, C, ssel, psel, G, p_log2=pl, compute=mode,
+                                     tau=tau, tile_m=256)
+    for x, y, z in zip(got, one, pair):
+        assert torch.equal(x, z) and torch.equal(y, z)
+    if mode == "f32":
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        ref = orc.pnorm(A64, B64, pl, tau)
+        assert np.array_equal(psel.cpu().numpy(), ref["p_sel"])
+        rA, rB = orc.pnorm_grad(A64, B64, ref["p_sel"], 1.0 / ref["C"])
+        pmax = int(np.max(ref["p_sel"] & 0x7F))
+        assert grad_ok(pair[0].cpu().numpy(), rA, grad_tol(pmax, N))
+        assert grad_ok(pair[1].cpu().numpy(), rB, grad_tol(pmax, M))
+
+
 def test_backward_bf16_mode(pn, orc):
     """BF16 operands: error stated against the oracle (BF16 u = 2^-8 per operand)."""
     M, N, K = 200, 190, 300
