@@ -582,13 +582,20 @@ def run_ours(args):
                         **corr)
     KE = max(1, args.e2e_steps)
     pipe.run([(Ah, Bh, Ch)] * 2)  # warm-up
-    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    stages = []
-    pipe.run([(Ah, Bh, Ch)] * KE, ev_start=x0, ev_end=x1, stages=stages)
-    e2e_ms = max_over_ranks(x0.elapsed_time(x1) / KE, world, device="cuda")
+    # three timed runs of KE steps each, the median reported: the host link is
+    # shared with the other GPU of the same CPU, whose transfers can halve it
+    # for a while (every run's time is in the line)
+    runs = []
+    for _ in range(3):
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        stages = []
+        pipe.run([(Ah, Bh, Ch)] * KE, ev_start=x0, ev_end=x1, stages=stages)
+        runs.append((max_over_ranks(x0.elapsed_time(x1) / KE, world, device="cuda"), stages))
+    e2e_runs_ms = [r[0] for r in runs]
+    e2e_ms, stages = sorted(runs, key=lambda r: r[0])[1]
     e2e_value = job_value(world, ops, 1, e2e_ms)
     pn.check_device_status(A.device, "e2e")
     from paper_1511_05690_gb300.pipeline import stage_summary
@@ -617,8 +624,10 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": e2e_value, "unit": "Gop/s", "h2d_bytes_per_step": 2 * 4 * n * Kc,
                 "d2h_bytes_per_step": 4 * n * n, "steps": KE, "ms_per_step": e2e_ms,
+                "runs_ms_per_step": e2e_runs_ms,
                 "how": "pinned host A, B in / C out every step; steps overlap copy-in, "
-                       "compute and copy-out on three streams (one per copy direction)",
+                       "compute and copy-out on three streams (one per copy direction); "
+                       "median of three timed runs of `steps` steps",
                 "stages": e2e_stages, "link": e2e_link},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(args.compute),
