@@ -957,11 +957,26 @@ def run_other(args):
         E = torch.empty_like(W)
         ems = _timed(torch, lambda: [pn.maxprod_exact(W, W, semiring=1, out=E) for _ in range(1)],
                      1, 1, stream)
+        # the exact closure by as many exact (+,min) squarings: the estimate's
+        # error at this configuration (it never exceeds the exact distance)
+        X = W.clone()
+        for _ in range(T):
+            X = pn.maxprod_exact(X, X, semiring=1)
+        fin = torch.isfinite(X)
+        dd, xx = D[fin].double(), X[fin].double()
+        apsp_err = {"max_abs_vs_exact": float((dd - xx).abs().max()),
+                    "median_abs_vs_exact": float((dd - xx).abs().median()),
+                    "exact_median_distance": float(xx.median()),
+                    "exact_max_distance": float(xx.max()),
+                    "zero_estimate_fraction": float((dd == 0).double().mean()),
+                    "never_above_exact": bool((dd <= xx + 1e-5 + 1e-5 * xx).all())}
+        del X, E
         line.update(value=T * n ** 3 / (ms / 1e3) / 1e9, ms_per_step=ms, dtype="f32 (3xTF32)",
                     config={"workload": "apsp_pnorm n=4096 density 0.1 U[0,1] weights, 12 "
                             "squarings, P={1..64}, diag reset + clamp, CUDA graph", "n": n},
                     exact_kernel={"one_minplus_squaring_ms": ems,
                                   "gops": n ** 3 / (ems / 1e3) / 1e9},
+                    err=apsp_err,
                     gpu_launches=K * (1 + T * 22 + 1))
     elif args.workload == "backward":
         n = 2048
