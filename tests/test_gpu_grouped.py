@@ -246,3 +246,45 @@ def test_grouped_persistent_domain_error(pn, flags):
     assert ei.value.status == 4
     Bs[5][0, 0] = 0.5
     pn.GroupedProduct(As, Bs, compute="bf16", debug_flags=flags).run(check=True)
+
+
+def test_grouped_bench_configuration_sampled(pn, orc):
+    """The grouped configuration the bench times, at full size: 4096 square
+    problems of n = round(16 * 64^U) with entries 1 - U[0,1), BF16 operands,
+    P = {1..64}, the tile width the autotuner picks and the launches the bench
+    replays (the strip kernel, then the persistent launch).  In 48 problems
+    (the largest, the smallest and 46 drawn at random) 32 sampled entries each
+    against the FP64 oracle at the oracle's own p*, entries within the error
+    band of tau excepted."""
+    sizes = workloads.grouped_sizes(4096)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(workloads.SEED_BASE + 3)
+    As = [1 - torch.rand((int(m), int(m)), generator=g, device="cuda") for m in sizes]
+    Bs = [1 - torch.rand((int(m), int(m)), generator=g, device="cuda") for m in sizes]
+    plan = pn.GroupedProduct(As, Bs, compute="bf16")
+    assert plan.autotune() in (128, 256)
+    Cs = plan.run(check=True)
+    h = workloads.rng(None, 140)
+    pick = set(h.choice(len(sizes), 46, replace=False).tolist())
+    pick |= {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    pl = list(range(7))
+    checked = 0
+    for gi in sorted(pick):
+        A = As[gi].double().cpu().numpy()
+        B = Bs[gi].double().cpu().numpy()
+        n = A.shape[0]
+        ii, jj = h.integers(0, n, 32), h.integers(0, n, 32)
+        r, c = orc.row_scales(A), orc.col_scales(B)
+        _, S = orc.entries(A, B, ii, jj, pl, r, c)
+        tau = orc.default_tau(n, orc.BF16)
+        stable = S >= tau
+        q = np.where(stable.any(axis=1), len(pl) - 1 - np.argmax(stable[:, ::-1], axis=1), 0)
+        lp = np.array(pl)[q]
+        expect = r[ii] * c[jj] * np.power(S[np.arange(len(ii)), q], 1.0 / 2.0 ** lp)
+        got = Cs[gi][torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()].double().cpu().numpy()
+        tol = np.array([_tol("bf16", n, int(x)) for x in lp])
+        near = (np.abs(S / tau - 1) < 4 * 1.5 * _tol("bf16", n, 0)).any(axis=1)
+        err = np.abs(got - expect) / expect
+        assert np.all((err <= tol) | near), (n, float(err.max()))
+        checked += int((~near).sum())
+    assert checked >= 48 * 32 // 2
