@@ -209,6 +209,19 @@ def test_maxconv_long_matches_oracle(pn, orc, nx, ny):
     _check_long(pn, orc, x[0], y[0], list(range(7)), m)
 
 
+def test_maxconv_long_bench_size(pn, orc):
+    """The long path at the size the bench times: n = 2^21 per vector (2^22 - 1
+    outputs through the four-step transform of length 2^22), entries U^(1/4)
+    as in the bench; the 40 outputs at each end and 160 interior ones (about
+    2^21 terms each) against the oracle."""
+    n = 1 << 21
+    g = workloads.rng(None, 6)
+    x = ((1.0 - g.random(n)) ** 0.25).astype(np.float32)
+    y = ((1.0 - g.random(n)) ** 0.25).astype(np.float32)
+    m = _sample_outputs(2 * n - 1, 160, 2330)
+    _check_long(pn, orc, x, y, list(range(7)), m)
+
+
 def test_maxconv_long_several_levels(pn, orc):
     """Small floor and a few spikes: most indices resolve at small p, so the
     open terms stay many and the FFT levels run down the family."""
