@@ -130,6 +130,22 @@ def test_maxconv_pnorm_matches_oracle(pn, orc, shape):
     _check_pnorm(pn, orc, x, y, list(range(7)))
 
 
+def test_maxconv_pnorm_bench_batch(pn, orc):
+    """The batch the bench times: 1024 problems of n = 4096 (8191 outputs,
+    one CTA each), entries U^(1/4) as in the bench.  Six rows (the first, the
+    last and four drawn at random) against the oracle, and the same rows of
+    the full batch's launch bit-identical to them."""
+    batch, n = 1024, 4096
+    g = workloads.rng(None, 5)
+    x = ((1.0 - g.random((batch, n))) ** 0.25).astype(np.float32)
+    y = ((1.0 - g.random((batch, n))) ** 0.25).astype(np.float32)
+    zf, pf = pn.maxconv_pnorm(_dev(x), _dev(y))
+    rows = np.unique(np.concatenate([[0, batch - 1], workloads.rng(2140).integers(0, batch, 4)]))
+    z, psel, _ = _check_pnorm(pn, orc, x[rows], y[rows], list(range(7)))
+    assert np.array_equal(zf.cpu().numpy()[rows], z)
+    assert np.array_equal(pf.cpu().numpy()[rows], psel)
+
+
 def test_maxconv_pnorm_several_levels(pn, orc):
     """Vectors with a few large entries and a small floor: indices far from the
     large ones resolve at small p (S^(p) falls below tau), so p* varies."""
