@@ -64,6 +64,35 @@ def test_topk_matches_oracle(pn, orc, n, k):
         assert np.all(np.abs(prod - vals[b][rep]) <= 1e-2 * vals[b][rep])
 
 
+def test_topk_bench_batch(pn, orc):
+    """The batch the bench times: 256 pairs of n = 4096, k = 1024, x, y
+    U[0,1), P = {1..4096}.  Four rows (the first, the last and two drawn at
+    random) held to the oracle as above, and bit-identical to the same rows
+    launched alone."""
+    batch, n, k = 256, 4096, 1024
+    g = workloads.rng(None, 7)
+    x = g.random((batch, n)).astype(np.float32)
+    y = g.random((batch, n)).astype(np.float32)
+    vals, ii, jj = pn.topk_xy(_dev(x), _dev(y), k, p_log2=P13)
+    rows = np.unique(np.concatenate([[0, batch - 1], workloads.rng(2530).integers(0, batch, 2)]))
+    for b in rows:
+        v1, i1, j1 = pn.topk_xy(_dev(x[b]), _dev(y[b]), k, p_log2=P13)
+        assert torch.equal(vals[b], v1[0]) and torch.equal(ii[b], i1[0]) and torch.equal(jj[b], j1[0])
+        vb, ib, jb = vals[b].cpu().numpy(), ii[b].cpu().numpy(), jj[b].cpu().numpy()
+        x64, y64 = x[b].astype(np.float64), y[b].astype(np.float64)
+        v, d = orc.topk_xy(x64, y64, k, P13)
+        ok = d >= 0
+        np.testing.assert_allclose(vb[:8], v[:8], rtol=1e-6)
+        exact = np.sort(np.outer(x64, y64).ravel())[::-1][:int(ok.sum())]
+        eg = np.abs(np.sort(vb[ok])[::-1] - exact) / exact
+        eo = np.abs(np.sort(v[ok])[::-1] - exact) / exact
+        assert eg.max() <= max(3 * eo.max(), 5e-3), (eg.max(), eo.max())
+        assert np.median(eg) <= max(5 * np.median(eo), 1e-6), (np.median(eg), np.median(eo))
+        rep = ib >= 0
+        prod = x[b][ib[rep]].astype(np.float64) * y[b][jb[rep]]
+        assert np.all(np.abs(prod - vb[rep]) <= 1e-2 * vb[rep])
+
+
 def test_topk_close_to_exact_and_indices(pn, orc):
     n, k = 2000, 400
     x, y = _pair(1, n, 2510)
