@@ -162,6 +162,36 @@ def test_projection_n2048_sampled(pn, orc):
     assert e1 < e0
 
 
+def test_projection_n16384_sampled(pn, orc):
+    """The bench's r = 1 configuration at full size: n = 16384, entries
+    exp(-Exp(4)), BF16, the default tau, CTA pairs; 512 sampled entries against
+    the oracle's projection from its own p-sums at those entries."""
+    n = 16384
+    A, B = workloads.wide_range_pair(n, n, n)
+    pl = list(range(7))
+    C, psel, _ = pn.maxprod_pnorm(_dev(A), _dev(B), p_log2=pl, compute="bf16", estimator=1)
+    g = workloads.rng(None, 1742)
+    ii, jj = g.integers(0, n, 512), g.integers(0, n, 512)
+    ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
+    Cs, ps_gpu = C[ti, tj].cpu().numpy(), psel[ti, tj].cpu().numpy()
+    del C, psel
+    tau = orc.default_tau(n, _CODE["bf16"])
+    rows = np.unique(ii)
+    rr = np.zeros(n)
+    rr[rows] = orc.row_scales(A[rows].astype(np.float64))
+    c = orc.col_scales(B.astype(np.float64))
+    exact, S = orc.entries(A, B, ii, jj, pl, rr, c)
+    Chat, ps, _ = orc.estimate(S.T[:, None, :], pl, np.ones(1), rr[ii] * c[jj], tau, estimator=1)
+    Chat, ps = Chat[0], ps[0]
+    assert np.array_equal(ps_gpu, ps)
+    tol = np.vectorize(lambda lp: proj_tol("bf16", n, lp))(ps & 0x7F)
+    err = np.abs(Cs - Chat) / Chat
+    assert np.all(err <= tol), float(err.max())
+    pstar = 2.0 ** (ps & 0x7F)
+    assert np.all(Cs <= exact * (1 + tol))
+    assert np.all(Cs >= exact * (2 / (math.sqrt(n) + 1)) ** (2 / pstar) * (1 - tol))
+
+
 def test_projection_grouped(pn, orc):
     sizes = np.minimum(workloads.grouped_sizes(12, seed=1750), 300)
     probs = workloads.grouped_problems(sizes, seed=1750)

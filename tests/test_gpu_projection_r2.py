@@ -247,6 +247,40 @@ def test_r2_n2048_sampled(pn, orc):
     assert e2 < e1 < e0
 
 
+def test_r2_n16384_sampled(pn, orc):
+    """The bench's r = 2 configuration at full size: n = 16384, entries
+    exp(-Exp(4)), BF16, the default tau, CTA pairs; 512 sampled entries within
+    the bounds the oracle's own sums at those entries give."""
+    n = 16384
+    A, B = workloads.wide_range_pair(n, n, n)
+    pl = list(range(7))
+    C, psel, _ = pn.maxprod_pnorm(_dev(A), _dev(B), p_log2=pl, compute="bf16", estimator=2)
+    g = workloads.rng(None, 1942)
+    ii, jj = g.integers(0, n, 512), g.integers(0, n, 512)
+    ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
+    Cs, ps_gpu = C[ti, tj].cpu().numpy(), psel[ti, tj].cpu().numpy()
+    del C, psel
+    tau = orc.default_tau(n, _CODE["bf16"])
+    rows = np.unique(ii)
+    rr = np.zeros(n)
+    rr[rows] = orc.row_scales(A[rows].astype(np.float64))
+    c = orc.col_scales(B.astype(np.float64))
+    exact, S = orc.entries(A, B, ii, jj, pl, rr, c)
+    S34 = orc.entries_real(A, B, ii, jj, [0.75 * 2.0 ** lp for lp in pl], rr, c)
+    _, ps, _ = orc.estimate(S.T[:, None, :], pl, np.ones(1), rr[ii] * c[jj], tau, estimator=2,
+                            S34=S34.T[:, None, :])
+    ps = ps[0]
+    assert np.array_equal(ps_gpu, ps)
+    assert np.all(ps == 6)  # every sampled entry stable at p = 64: one chain
+    q = 6
+    s = np.stack([S[:, q - 2], S[:, q - 1], S34[:, q], S[:, q]])
+    lo, hi, strong = r2_bounds(orc, s, 64.0, "bf16", n, tau)
+    assert strong.mean() > 0.9
+    gv = Cs / (rr[ii] * c[jj])
+    assert np.all(gv >= lo * (1 - EPS)) and np.all(gv <= hi * (1 + EPS))
+    assert np.all(Cs <= exact * (1 + EPS))
+
+
 def test_r2_rejected_where_unsupported(pn):
     """APSP, the adjoint and the grouped call take no r = 2; it excludes the
     affine correction."""
