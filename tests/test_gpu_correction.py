@@ -171,6 +171,57 @@ def test_affine_reduces_error_n2048(pn, orc):
     assert e2 < e0 / 5, (e0, e2)
 
 
+def test_affine_n16384_sampled(pn, orc):
+    """The bench's affine-correction configuration at full size: n = 16384,
+    entries exp(-Exp(4)), BF16, the default tau, CTA pairs, 1024 fit samples
+    drawn as the bench draws them.  The library's fitted lines against the
+    oracle's fit of its own estimates and exact maxima at those samples (by
+    their predictions there), and 512 other corrected entries against the
+    oracle's line applied to the oracle's estimate."""
+    n = 16384
+    A, B = workloads.wide_range_pair(n, n, n)
+    pl = list(range(7))
+    gfit = workloads.rng(None, 150)
+    fi, fj = gfit.integers(0, n, 1024), gfit.integers(0, n, 1024)
+    coef = torch.zeros(2 * len(pl), dtype=torch.float32, device="cuda")
+    dA, dB = _dev(A), _dev(B)
+    C2, psel, _ = pn.maxprod_pnorm(dA, dB, p_log2=pl, compute="bf16", correction=2,
+                                   fit_i=torch.from_numpy(fi.astype(np.int32)).cuda(),
+                                   fit_j=torch.from_numpy(fj.astype(np.int32)).cuda(),
+                                   fit_coef=coef)
+    g = workloads.rng(None, 151)
+    ii, jj = g.integers(0, n, 512), g.integers(0, n, 512)
+    ti, tj = torch.from_numpy(ii).cuda(), torch.from_numpy(jj).cuda()
+    C2s, ps_gpu = C2[ti, tj].cpu().numpy().astype(np.float64), psel[ti, tj].cpu().numpy()
+    del C2, psel, dA, dB
+    coef = coef.cpu().numpy().reshape(-1, 2).astype(np.float64)
+    tau = orc.default_tau(n, _CODE["bf16"])
+    rows = np.unique(np.concatenate([fi, ii]))
+    r = np.zeros(n)
+    r[rows] = orc.row_scales(A[rows].astype(np.float64))
+    c = orc.col_scales(B.astype(np.float64))
+    idx = {lp: q for q, lp in enumerate(pl)}
+
+    def scaled(ei, ej):
+        exact, S = orc.entries(A, B, ei, ej, pl, r, c)
+        est, ps, _ = orc.estimate(S.T[:, None, :], pl, np.ones(1), np.ones(len(ei)), tau, 0)
+        cls = np.array([idx[int(b) & 0x7F] for b in ps[0]])
+        return est[0], exact / (r[ei] * c[ej]), cls, ps[0]
+    x, y, cls, _ = scaled(fi, fj)
+    co = orc.affine_fit(x, y, cls, len(pl))
+    pg = coef[cls, 0] * x + coef[cls, 1]
+    po = co[cls, 0] * x + co[cls, 1]
+    assert np.all(np.abs(pg - po) <= FIT_TOL * np.abs(po)), float(np.max(np.abs(pg - po) / po))
+    x2, _, cls2, ps2 = scaled(ii, jj)
+    assert np.array_equal(ps_gpu, ps2)
+    rc = r[ii] * c[jj]
+    want = rc * (co[cls2, 0] * x2 + co[cls2, 1])
+    t = np.array([plain_tol("bf16", n, int(b) & 0x7F) for b in ps2])
+    tol = t * np.abs(co[cls2, 0]) * x2 * rc / np.abs(want) + 2 * FIT_TOL
+    err = np.abs(C2s - want) / np.abs(want)
+    assert np.all(err <= tol), float(err.max())
+
+
 def test_correction_grouped_divide(pn, orc):
     sizes = np.minimum(workloads.grouped_sizes(10, seed=1950), 260)
     probs = workloads.grouped_problems(sizes, seed=1950)
